@@ -1,0 +1,630 @@
+// Oracle for the tetrahedron splatting rasterizer.  TEST INFRASTRUCTURE ONLY:
+// only the test suite, the smoke check and the benchmark's CPU-baseline leg may
+// load this library.  It shares no code with the CUDA path.
+//
+// A plain, slow CPU restatement of the method, in FP64 except for the binning
+// key path, which is an exact FP32 op sequence (the GPU sorts FP32 keys and the
+// key lists are compared bit for bit).
+//
+//   prefilter      Sec. 3.2 "Pre-filtering" + Eq. 1: alpha_max from the max and
+//                  min vertex SDF, keep iff alpha_max >= T_f.
+//   bin            Sec. 3.3: cull against the near plane and the image, pixel
+//                  bbox -> tile rect, one key (tile, mean vertex depth) per
+//                  overlapped tile, stable sort (ties: survivor order).
+//   render         Sec. 3.2 + App. A.1/A.2: per pixel, every listed tet whose
+//                  bbox holds the pixel is intersected through its four
+//                  projected triangles (2D barycentrics, App. A.1), each hit is
+//                  perspective corrected (App. A.2) to (z_p, f_p); the nearest
+//                  and farthest hits give f_prev, f_next; Eq. 1 gives alpha;
+//                  Eq. 2 composites front to back with the 3DGS conventions
+//                  (cap 0.99, skip below 1/255, stop before T drops under 1e-4).
+//   adjoint        exact derivatives: the compositing adjoint written out, and
+//                  per-fragment d alpha / d(vertex xyz, vertex f) from
+//                  forward-mode dual numbers through the same FP64 code.
+//
+// Parity status: pinned (closed forms, three-route chord agreement,
+// telescoping identity, invariants, dual numbers, finite differences) except
+// the decision-band alternative branch, which is a test aid.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+extern "C" {
+
+struct OrcCam {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy, znear;
+  int32_t width, height;
+};
+
+struct OrcParams {
+  double s;                 // Eq. 1 steepness
+  double prefilter_thresh;  // T_f
+  double alpha_skip;        // 3DGS skip threshold
+  double alpha_cap;         // 3DGS cap
+  double t_eps;             // 3DGS termination threshold
+  double band;              // relative half-width of the decision bands
+  int32_t tile;             // tile edge in pixels
+  int32_t flags;            // bit 0: PURE (no cap, skip, termination, pre-filter)
+};
+
+}  // extern "C"
+
+static const int ORC_PURE = 1;
+
+// ---------------------------------------------------------------------------
+// forward-mode dual numbers with a fixed number of tangents
+// ---------------------------------------------------------------------------
+template <int NT>
+struct Dual {
+  double v;
+  double d[NT];
+  Dual() : v(0) { for (int i = 0; i < NT; ++i) d[i] = 0; }
+  Dual(double x) : v(x) { for (int i = 0; i < NT; ++i) d[i] = 0; }
+};
+template <int NT> Dual<NT> operator+(const Dual<NT>& a, const Dual<NT>& b) { Dual<NT> r(a.v + b.v); for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int NT> Dual<NT> operator-(const Dual<NT>& a, const Dual<NT>& b) { Dual<NT> r(a.v - b.v); for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int NT> Dual<NT> operator-(const Dual<NT>& a) { Dual<NT> r(-a.v); for (int i = 0; i < NT; ++i) r.d[i] = -a.d[i]; return r; }
+template <int NT> Dual<NT> operator*(const Dual<NT>& a, const Dual<NT>& b) { Dual<NT> r(a.v * b.v); for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int NT> Dual<NT> operator/(const Dual<NT>& a, const Dual<NT>& b) { Dual<NT> r(a.v / b.v); for (int i = 0; i < NT; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v; return r; }
+template <int NT> Dual<NT> operator+(const Dual<NT>& a, double b) { Dual<NT> r = a; r.v += b; return r; }
+template <int NT> Dual<NT> operator+(double b, const Dual<NT>& a) { return a + b; }
+template <int NT> Dual<NT> operator-(const Dual<NT>& a, double b) { Dual<NT> r = a; r.v -= b; return r; }
+template <int NT> Dual<NT> operator-(double b, const Dual<NT>& a) { return -(a - b); }
+template <int NT> Dual<NT> operator*(const Dual<NT>& a, double b) { Dual<NT> r(a.v * b); for (int i = 0; i < NT; ++i) r.d[i] = a.d[i] * b; return r; }
+template <int NT> Dual<NT> operator*(double b, const Dual<NT>& a) { return a * b; }
+template <int NT> Dual<NT> operator/(const Dual<NT>& a, double b) { return a * (1.0 / b); }
+template <int NT> Dual<NT> operator/(double a, const Dual<NT>& b) { return Dual<NT>(a) / b; }
+template <int NT> Dual<NT> dexp(const Dual<NT>& a) { double e = std::exp(a.v); Dual<NT> r(e); for (int i = 0; i < NT; ++i) r.d[i] = e * a.d[i]; return r; }
+template <int NT> Dual<NT> dexpm1(const Dual<NT>& a) { double e = std::exp(a.v); Dual<NT> r(std::expm1(a.v)); for (int i = 0; i < NT; ++i) r.d[i] = e * a.d[i]; return r; }
+inline double dexp(double a) { return std::exp(a); }
+inline double dexpm1(double a) { return std::expm1(a); }
+template <int NT> double val(const Dual<NT>& a) { return a.v; }
+inline double val(double a) { return a; }
+
+// ---------------------------------------------------------------------------
+// Eq. 1 in the exact rewrite that cannot form 0/0:
+//   (Phi(fp) - Phi(fn)) / Phi(fp) = -expm1(-s (fp - fn)) * sigmoid(-s fn)
+// and 0 when fp <= fn (the max(., 0) of Eq. 1).
+// ---------------------------------------------------------------------------
+template <class S>
+static S opacity_eq1(const S& fp, const S& fn, double s) {
+  if (!(val(fp) > val(fn))) return S(0.0);
+  S a = -dexpm1(-(s * (fp - fn)));
+  S b = 1.0 / (1.0 + dexp(s * fn));
+  return a * b;
+}
+
+// ---------------------------------------------------------------------------
+// one fragment: ray through pixel centre (px, py) against tet with camera-space
+// vertices X[4][3] and vertex SDF F[4].  App. A.1 (2D barycentrics of the four
+// projected triangles, closed inside test) and App. A.2 (perspective
+// correction).  Returns false when the ray meets the tet in fewer than two
+// distinct points.
+// ---------------------------------------------------------------------------
+template <class S>
+struct FragOut {
+  S f_prev, f_next, z_in, z_out;
+};
+
+template <class S>
+static bool eval_fragment(const S X[4][3], const S F[4], double px, double py,
+                          double fx, double fy, double cx, double cy,
+                          FragOut<S>* out) {
+  S u[4], v[4];
+  for (int j = 0; j < 4; ++j) {
+    u[j] = fx * (X[j][0] / X[j][2]) + cx;
+    v[j] = fy * (X[j][1] / X[j][2]) + cy;
+  }
+  static const int faces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+  int nhit = 0;
+  S hz[4], hf[4];
+  for (int k = 0; k < 4; ++k) {
+    const int a = faces[k][0], b = faces[k][1], c = faces[k][2];
+    // [v_a' v_b' v_c'; 1 1 1] [1-u'-v', u', v']^T = [p; 1]  (App. A.1), Cramer
+    S ub = u[b] - u[a], vb = v[b] - v[a], uc = u[c] - u[a], vc = v[c] - v[a];
+    S det = ub * vc - uc * vb;
+    double scale = std::fabs(val(ub) * val(vc)) + std::fabs(val(uc) * val(vb));
+    if (!(std::fabs(val(det)) > 1e-14 * scale) || scale == 0.0) continue;  // edge-on face
+    S qx = px - u[a], qy = py - v[a];
+    S bu = (qx * vc - uc * qy) / det;   // u'
+    S bv = (ub * qy - qx * vb) / det;   // v'
+    S b0 = 1.0 - bu - bv;               // 1 - u' - v'
+    const double tol = -1e-12;
+    if (val(b0) < tol || val(bu) < tol || val(bv) < tol) continue;
+    // App. A.2: perspective-correct barycentrics and the interpolated SDF/depth
+    S sig = b0 / X[a][2] + bu / X[b][2] + bv / X[c][2];
+    S uu = (bu / X[b][2]) / sig;
+    S vv = (bv / X[c][2]) / sig;
+    S fp = (1.0 - uu - vv) * F[a] + uu * F[b] + vv * F[c];
+    S zp = 1.0 / sig;
+    hz[nhit] = zp;
+    hf[nhit] = fp;
+    ++nhit;
+  }
+  if (nhit < 2) return false;
+  int imin = 0, imax = 0;
+  for (int h = 1; h < nhit; ++h) {
+    if (val(hz[h]) < val(hz[imin])) imin = h;
+    if (val(hz[h]) > val(hz[imax])) imax = h;
+  }
+  if (!(val(hz[imax]) - val(hz[imin]) > 1e-12 * val(hz[imax]))) return false;
+  out->f_prev = hf[imin];
+  out->f_next = hf[imax];
+  out->z_in = hz[imin];
+  out->z_out = hz[imax];
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// camera transform in FP64 (from the FP32 inputs)
+// ---------------------------------------------------------------------------
+static inline void cam_xform(const OrcCam& c, const double* v, double out[3]) {
+  for (int r = 0; r < 3; ++r)
+    out[r] = (double)c.R[3 * r] * v[0] + (double)c.R[3 * r + 1] * v[1] +
+             (double)c.R[3 * r + 2] * v[2] + (double)c.t[r];
+}
+
+// FP64 view of the vertex data: the FP32 inputs widened, or caller-supplied
+// FP64 overrides (finite-difference tests perturb those; the binning lists stay
+// those of the FP32 inputs).
+struct Fields {
+  std::vector<double> V, f, rgb;
+  Fields(int64_t N, const float* V32, const float* f32, const float* rgb32, const double* V64,
+         const double* f64, const double* rgb64)
+      : V(3 * N), f(N), rgb(3 * N) {
+    for (int64_t i = 0; i < 3 * N; ++i) {
+      V[i] = V64 ? V64[i] : (double)V32[i];
+      rgb[i] = rgb64 ? rgb64[i] : (double)rgb32[i];
+    }
+    for (int64_t i = 0; i < N; ++i) f[i] = f64 ? f64[i] : (double)f32[i];
+  }
+};
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// Pre-filter (Sec. 3.2): alpha_max = Eq. 1 at (f_max, f_min).  keep[k] = 1 iff
+// alpha_max >= T_f (PURE: every tet kept).  amb[k] = 1 iff alpha_max lies within
+// band*T_f of T_f.  Returns the number kept, or -1 on an index outside [0, N).
+// ---------------------------------------------------------------------------
+int64_t orc_prefilter(int64_t K, const int32_t* T, int64_t N, const float* f,
+                      const OrcParams* p, int8_t* keep, int8_t* amb, double* amax_out) {
+  int64_t n = 0;
+  for (int64_t k = 0; k < K; ++k) {
+    double fmax = -INFINITY, fmin = INFINITY;
+    for (int j = 0; j < 4; ++j) {
+      int32_t id = T[4 * k + j];
+      if (id < 0 || id >= N) return -1;
+      fmax = std::max(fmax, (double)f[id]);
+      fmin = std::min(fmin, (double)f[id]);
+    }
+    double am = opacity_eq1<double>(fmax, fmin, p->s);
+    if (amax_out) amax_out[k] = am;
+    bool kp = (p->flags & ORC_PURE) ? true : (am >= p->prefilter_thresh);
+    keep[k] = kp ? 1 : 0;
+    amb[k] = (!(p->flags & ORC_PURE) &&
+              std::fabs(am - p->prefilter_thresh) <= p->band * p->prefilter_thresh) ? 1 : 0;
+    n += kp;
+  }
+  return n;
+}
+
+// ---------------------------------------------------------------------------
+// Binning key path, an exact FP32 op sequence (compile without contraction):
+//   x = fma(R0, vx, fma(R1, vy, fma(R2, vz, t0)))       (same for y, z)
+//   cull if any z < znear
+//   zbar = ((za + zb) + (zc + zd)) * 0.25
+//   u = fma(fx, x / z, cx), v = fma(fy, y / z, cy)       (correctly rounded /)
+//   i0 = max(ceil(umin - 0.5), 0), i1 = min(floor(umax - 0.5), W - 1)   (same j)
+//   empty (culled) if i0 > i1 or j0 > j1
+//   tile rect = [i0 / B, i1 / B] x [j0 / B, j1 / B]
+// rect[4s] = (i0, i1, j0, j1) or (-1,-1,-1,-1) when culled; zbits[s] = bits of
+// zbar; ntl[s] = tiles overlapped.  Returns the total number of keys.
+// ---------------------------------------------------------------------------
+int64_t orc_bin_prepare(int64_t ns, const int32_t* surv, const int32_t* T, const float* V,
+                        const OrcCam* cam, int32_t tile, int32_t* rect, uint32_t* zbits,
+                        int32_t* ntl) {
+  const OrcCam& c = *cam;
+  int64_t total = 0;
+  const float W1 = (float)(c.width - 1), H1 = (float)(c.height - 1);
+  for (int64_t s = 0; s < ns; ++s) {
+    const int32_t* t = T + 4 * (int64_t)surv[s];
+    float x[4], y[4], z[4];
+    bool cull = false;
+    for (int j = 0; j < 4; ++j) {
+      const float* v = V + 3 * (int64_t)t[j];
+      x[j] = std::fma(c.R[0], v[0], std::fma(c.R[1], v[1], std::fma(c.R[2], v[2], c.t[0])));
+      y[j] = std::fma(c.R[3], v[0], std::fma(c.R[4], v[1], std::fma(c.R[5], v[2], c.t[1])));
+      z[j] = std::fma(c.R[6], v[0], std::fma(c.R[7], v[1], std::fma(c.R[8], v[2], c.t[2])));
+      if (!(z[j] >= c.znear)) cull = true;
+    }
+    float zb = ((z[0] + z[1]) + (z[2] + z[3])) * 0.25f;
+    uint32_t zbit;
+    std::memcpy(&zbit, &zb, 4);
+    zbits[s] = zbit;
+    rect[4 * s + 0] = rect[4 * s + 1] = rect[4 * s + 2] = rect[4 * s + 3] = -1;
+    ntl[s] = 0;
+    if (cull) continue;
+    float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    for (int j = 0; j < 4; ++j) {
+      float u = std::fma(c.fx, x[j] / z[j], c.cx);
+      float v = std::fma(c.fy, y[j] / z[j], c.cy);
+      umin = std::fmin(umin, u); umax = std::fmax(umax, u);
+      vmin = std::fmin(vmin, v); vmax = std::fmax(vmax, v);
+    }
+    float i0 = std::fmax(std::ceil(umin - 0.5f), 0.0f);
+    float i1 = std::fmin(std::floor(umax - 0.5f), W1);
+    float j0 = std::fmax(std::ceil(vmin - 0.5f), 0.0f);
+    float j1 = std::fmin(std::floor(vmax - 0.5f), H1);
+    if (!(i0 <= i1) || !(j0 <= j1)) continue;
+    int ii0 = (int)i0, ii1 = (int)i1, jj0 = (int)j0, jj1 = (int)j1;
+    rect[4 * s + 0] = ii0; rect[4 * s + 1] = ii1; rect[4 * s + 2] = jj0; rect[4 * s + 3] = jj1;
+    int nt = (ii1 / tile - ii0 / tile + 1) * (jj1 / tile - jj0 / tile + 1);
+    ntl[s] = nt;
+    total += nt;
+  }
+  return total;
+}
+
+// Duplicate and sort: one entry (tile, zbits, survivor index) per overlapped
+// tile, sorted by (tile, zbits) with std::stable_sort (ties keep survivor
+// order).  ranges[2*tile] = [start, end).
+int64_t orc_bin_sort(int64_t ns, const int32_t* rect, const uint32_t* zbits, const OrcCam* cam,
+                     int32_t tile, int32_t* out_tile, uint32_t* out_z, int32_t* out_val,
+                     int32_t* ranges) {
+  const int tx = (cam->width + tile - 1) / tile, ty = (cam->height + tile - 1) / tile;
+  struct E { int32_t tile; uint32_t z; int32_t val; };
+  std::vector<E> ent;
+  for (int64_t s = 0; s < ns; ++s) {
+    if (rect[4 * s] < 0) continue;
+    for (int b = rect[4 * s + 2] / tile; b <= rect[4 * s + 3] / tile; ++b)
+      for (int a = rect[4 * s] / tile; a <= rect[4 * s + 1] / tile; ++a)
+        ent.push_back({b * tx + a, zbits[s], (int32_t)s});
+  }
+  std::stable_sort(ent.begin(), ent.end(), [](const E& p, const E& q) {
+    if (p.tile != q.tile) return p.tile < q.tile;
+    return p.z < q.z;
+  });
+  for (int i = 0; i < tx * ty; ++i) ranges[2 * i] = ranges[2 * i + 1] = 0;
+  for (size_t i = 0; i < ent.size(); ++i) {
+    out_tile[i] = ent[i].tile;
+    out_z[i] = ent[i].z;
+    out_val[i] = ent[i].val;
+    if (i == 0 || ent[i - 1].tile != ent[i].tile) ranges[2 * ent[i].tile] = (int32_t)i;
+    ranges[2 * ent[i].tile + 1] = (int32_t)(i + 1);
+  }
+  return (int64_t)ent.size();
+}
+
+// single-fragment probe (tests): camera-space vertices X (12), F (4)
+int orc_fragment(const double* X, const double* F, double px, double py, double fx, double fy,
+                 double cx, double cy, double s, double* out /* f_prev f_next z_in z_out alpha */) {
+  double Xa[4][3], Fa[4];
+  for (int j = 0; j < 4; ++j) { for (int r = 0; r < 3; ++r) Xa[j][r] = X[3 * j + r]; Fa[j] = F[j]; }
+  FragOut<double> o;
+  if (!eval_fragment<double>(Xa, Fa, px, py, fx, fy, cx, cy, &o)) return 0;
+  out[0] = o.f_prev; out[1] = o.f_next; out[2] = o.z_in; out[3] = o.z_out;
+  out[4] = opacity_eq1<double>(o.f_prev, o.f_next, s);
+  return 1;
+}
+
+// gradient of the single-fragment alpha wrt X (12) and F (4), by dual numbers
+int orc_fragment_grad(const double* X, const double* F, double px, double py, double fx, double fy,
+                      double cx, double cy, double s, double* alpha, double* grad16) {
+  typedef Dual<16> D;
+  D Xa[4][3], Fa[4];
+  for (int j = 0; j < 4; ++j) {
+    for (int r = 0; r < 3; ++r) { Xa[j][r] = D(X[3 * j + r]); Xa[j][r].d[3 * j + r] = 1.0; }
+    Fa[j] = D(F[j]); Fa[j].d[12 + j] = 1.0;
+  }
+  FragOut<D> o;
+  if (!eval_fragment<D>(Xa, Fa, px, py, fx, fy, cx, cy, &o)) return 0;
+  D a = opacity_eq1<D>(o.f_prev, o.f_next, s);
+  *alpha = a.v;
+  for (int i = 0; i < 16; ++i) grad16[i] = a.d[i];
+  return 1;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// per-pixel compositing (Eq. 2 with the 3DGS conventions)
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Frag {
+  int32_t s;       // survivor index
+  double alpha;    // Eq. 1
+  double zbar;     // mean vertex depth (Eq. 2 depth term)
+  double c[3];     // tet colour: mean of the vertex colours
+};
+
+struct Blended {
+  int32_t s;
+  double a, T, zbar, c[3];
+  bool clamped;
+};
+
+struct PixelResult {
+  double C[3], D, O;
+  int amb;            // ambiguous decisions met on the primary branch
+  int first_amb;      // decision index of the first one (-1 none)
+  std::vector<Blended> blended;
+};
+
+// Walk the fragment list.  Decision indices count every threshold test in
+// evaluation order; flip = index of the decision to invert (-1: none).
+static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip, bool record,
+                      PixelResult* r) {
+  const bool pure = (p.flags & ORC_PURE) != 0;
+  double T = 1.0, C[3] = {0, 0, 0}, D = 0;
+  int dec = 0;
+  r->amb = 0;
+  r->first_amb = -1;
+  r->blended.clear();
+  auto decide = [&](bool outcome, double x, double thr) {
+    int id = dec++;
+    if (std::fabs(x - thr) <= p.band * thr) {
+      if (r->first_amb < 0) r->first_amb = id;
+      r->amb++;
+    }
+    return (id == flip) ? !outcome : outcome;
+  };
+  for (const Frag& f : fr) {
+    double a = f.alpha;
+    bool clamped = false;
+    if (!pure) {
+      if (decide(a > p.alpha_cap, a, p.alpha_cap)) { a = p.alpha_cap; clamped = true; }
+      if (decide(a < p.alpha_skip, a, p.alpha_skip)) continue;
+    }
+    double Tn = T * (1.0 - a);
+    if (!pure) {
+      if (decide(Tn < p.t_eps, Tn, p.t_eps)) break;
+    }
+    for (int q = 0; q < 3; ++q) C[q] += T * a * f.c[q];
+    D += T * a * f.zbar;
+    if (record) r->blended.push_back({f.s, a, T, f.zbar, {f.c[0], f.c[1], f.c[2]}, clamped});
+    T = Tn;
+  }
+  for (int q = 0; q < 3; ++q) r->C[q] = C[q];
+  r->D = D;
+  r->O = 1.0 - T;
+}
+
+}  // namespace
+
+extern "C" {
+
+// ---------------------------------------------------------------------------
+// Render one view.  Inputs: the survivor list (original tet ids), the binning
+// result of orc_bin_prepare/orc_bin_sort.  Outputs (planar, H x W):
+//   img (3HW), alpha (HW), depth (HW): primary branch
+//   amb (HW): ambiguous decisions on the primary branch
+//   alt_img/alt_alpha/alt_depth: first ambiguous decision inverted (== primary
+//   when amb == 0)
+//   nfrag (HW): fragments (hits) met by the walk before it stopped
+// When dimg != nullptr, also accumulates the gradient of
+//   L = sum(dimg * img) + sum(dalpha * alpha) + sum(ddepth * depth)
+// into dV (3N), df (N), drgb (3N) (FP64, added to what is there).
+// ---------------------------------------------------------------------------
+int orc_render(int64_t N, const float* V, const float* f, const float* rgb, const int32_t* T,
+               int64_t ns, const int32_t* surv, const int32_t* rect, const OrcCam* cam,
+               const OrcParams* p, const int32_t* key_val, const int32_t* ranges,
+               double* img, double* alpha, double* depth, int32_t* amb,
+               double* alt_img, double* alt_alpha, double* alt_depth, int32_t* nfrag,
+               const float* dimg, const float* dalpha, const float* ddepth,
+               double* dV, double* df, double* drgb, int nthreads,
+               const double* V64, const double* f64, const double* rgb64) {
+  const OrcCam& c = *cam;
+  const Fields fld(N, V, f, rgb, V64, f64, rgb64);
+  const int W = c.width, H = c.height, B = p->tile;
+  const int tx = (W + B - 1) / B;
+  const bool want_grad = dimg != nullptr;
+  const int64_t HW = (int64_t)H * W;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+  const int nth = (nthreads > 0) ? nthreads : omp_get_max_threads();
+#else
+  const int nth = 1;
+  (void)nthreads;
+#endif
+  std::vector<std::vector<double>> gbuf;
+  if (want_grad) gbuf.assign(nth, std::vector<double>(7 * (size_t)N, 0.0));
+
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int j = 0; j < H; ++j) {
+#ifdef _OPENMP
+    const int tid = omp_get_thread_num();
+#else
+    const int tid = 0;
+#endif
+    std::vector<Frag> fr;
+    PixelResult pr, alt;
+    for (int i = 0; i < W; ++i) {
+      const int tile = (j / B) * tx + (i / B);
+      const double px = i + 0.5, py = j + 0.5;
+      fr.clear();
+      // walk this tile's list in key order; the pixel-local fragments
+      struct FragG { double g[16]; };
+      std::vector<FragG> fgrad;
+      int hits = 0;
+      for (int e = ranges[2 * tile]; e < ranges[2 * tile + 1]; ++e) {
+        const int32_t s = key_val[e];
+        const int32_t* r4 = rect + 4 * (int64_t)s;
+        if (i < r4[0] || i > r4[1] || j < r4[2] || j > r4[3]) continue;
+        const int32_t* t = T + 4 * (int64_t)surv[s];
+        double X[4][3], F[4];
+        for (int q = 0; q < 4; ++q) { cam_xform(c, &fld.V[3 * (int64_t)t[q]], X[q]); F[q] = fld.f[t[q]]; }
+        Frag fg;
+        fg.s = s;
+        FragOut<double> o;
+        if (!eval_fragment<double>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, &o)) continue;
+        ++hits;
+        fg.alpha = opacity_eq1<double>(o.f_prev, o.f_next, p->s);
+        fg.zbar = 0.25 * (X[0][2] + X[1][2] + X[2][2] + X[3][2]);
+        for (int q = 0; q < 3; ++q)
+          fg.c[q] = 0.25 * (((fld.rgb[3 * t[0] + q] + fld.rgb[3 * t[1] + q]) + fld.rgb[3 * t[2] + q]) + fld.rgb[3 * t[3] + q]);
+        fr.push_back(fg);
+      }
+      composite(fr, *p, -1, want_grad, &pr);
+      const int64_t pix = (int64_t)j * W + i;
+      for (int q = 0; q < 3; ++q) img[q * HW + pix] = pr.C[q];
+      alpha[pix] = pr.O;
+      depth[pix] = pr.D;
+      amb[pix] = pr.amb;
+      nfrag[pix] = hits;
+      if (pr.first_amb >= 0) {
+        composite(fr, *p, pr.first_amb, false, &alt);
+        for (int q = 0; q < 3; ++q) alt_img[q * HW + pix] = alt.C[q];
+        alt_alpha[pix] = alt.O;
+        alt_depth[pix] = alt.D;
+      } else {
+        for (int q = 0; q < 3; ++q) alt_img[q * HW + pix] = pr.C[q];
+        alt_alpha[pix] = pr.O;
+        alt_depth[pix] = pr.D;
+      }
+      if (!want_grad || pr.blended.empty()) continue;
+      // ---- adjoint of the composite (primary branch) ----
+      const double gC[3] = {dimg[pix], dimg[HW + pix], dimg[2 * HW + pix]};
+      const double gO = dalpha[pix], gD = ddepth[pix];
+      const double Tfin = 1.0 - pr.O;
+      double Ssuf = 0.0;
+      double* G = gbuf[tid].data();
+      for (int b = (int)pr.blended.size() - 1; b >= 0; --b) {
+        const Blended& bl = pr.blended[b];
+        const double w = gC[0] * bl.c[0] + gC[1] * bl.c[1] + gC[2] * bl.c[2] + gD * bl.zbar;
+        const double dLda = bl.T * w - (Ssuf - gO * Tfin) / (1.0 - bl.a);
+        Ssuf += bl.T * bl.a * w;
+        const int32_t* t = T + 4 * (int64_t)surv[bl.s];
+        // colour: c = mean of the 4 vertex colours
+        for (int q = 0; q < 4; ++q)
+          for (int ch = 0; ch < 3; ++ch) G[4 * (size_t)N + 3 * (size_t)t[q] + ch] += 0.25 * bl.T * bl.a * gC[ch];
+        // depth term: zbar = mean camera z -> world via R^T (third row)
+        double dX[4][3] = {{0}};
+        const double dz = 0.25 * bl.T * bl.a * gD;
+        for (int q = 0; q < 4; ++q) dX[q][2] += dz;
+        double dF[4] = {0, 0, 0, 0};
+        if (!bl.clamped && dLda != 0.0) {
+          typedef Dual<16> D16;
+          D16 X[4][3], F[4];
+          for (int q = 0; q < 4; ++q) {
+            double xd[3];
+            cam_xform(c, &fld.V[3 * (int64_t)t[q]], xd);
+            for (int r = 0; r < 3; ++r) { X[q][r] = D16(xd[r]); X[q][r].d[3 * q + r] = 1.0; }
+            F[q] = D16(fld.f[t[q]]);
+            F[q].d[12 + q] = 1.0;
+          }
+          FragOut<D16> o;
+          if (eval_fragment<D16>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, &o)) {
+            D16 a = opacity_eq1<D16>(o.f_prev, o.f_next, p->s);
+            for (int q = 0; q < 4; ++q) {
+              for (int r = 0; r < 3; ++r) dX[q][r] += dLda * a.d[3 * q + r];
+              dF[q] += dLda * a.d[12 + q];
+            }
+          }
+        }
+        for (int q = 0; q < 4; ++q) {
+          // world gradient: x_c = R v + t  ->  dv = R^T dx_c
+          for (int r = 0; r < 3; ++r) {
+            double g = c.R[r] * dX[q][0] + c.R[3 + r] * dX[q][1] + c.R[6 + r] * dX[q][2];
+            G[3 * (size_t)t[q] + r] += g;
+          }
+          G[3 * (size_t)N + t[q]] += dF[q];
+        }
+      }
+    }
+  }
+  if (want_grad) {
+    for (int th = 0; th < nth; ++th) {
+      const double* G = gbuf[th].data();
+      for (int64_t v = 0; v < N; ++v) {
+        for (int r = 0; r < 3; ++r) dV[3 * v + r] += G[3 * v + r];
+        df[v] += G[3 * N + v];
+        for (int r = 0; r < 3; ++r) drgb[3 * v + r] += G[4 * N + 3 * v + r];
+      }
+    }
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Directional derivative of L along (tV, tf, trgb) by a single-tangent dual
+// pass through the whole render (tests: pins the adjoint).  Uses the same
+// binning lists; returns L in out[0] and dL in out[1].
+// ---------------------------------------------------------------------------
+int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* rgb,
+                        const int32_t* T, int64_t ns, const int32_t* surv, const int32_t* rect,
+                        const OrcCam* cam, const OrcParams* p, const int32_t* key_val,
+                        const int32_t* ranges, const float* dimg, const float* dalpha,
+                        const float* ddepth, const double* tV, const double* tf,
+                        const double* trgb, double* out, const double* V64, const double* f64,
+                        const double* rgb64) {
+  typedef Dual<1> D1;
+  const OrcCam& c = *cam;
+  const Fields fld(N, V, f, rgb, V64, f64, rgb64);
+  const int W = c.width, H = c.height, B = p->tile;
+  const int tx = (W + B - 1) / B;
+  const bool pure = (p->flags & ORC_PURE) != 0;
+  const int64_t HW = (int64_t)H * W;
+  D1 L(0.0);
+  (void)ns;
+  for (int j = 0; j < H; ++j)
+    for (int i = 0; i < W; ++i) {
+      const int tile = (j / B) * tx + (i / B);
+      const double px = i + 0.5, py = j + 0.5;
+      D1 Tr(1.0), C[3] = {D1(0.0), D1(0.0), D1(0.0)}, Dp(0.0);
+      for (int e = ranges[2 * tile]; e < ranges[2 * tile + 1]; ++e) {
+        const int32_t s = key_val[e];
+        const int32_t* r4 = rect + 4 * (int64_t)s;
+        if (i < r4[0] || i > r4[1] || j < r4[2] || j > r4[3]) continue;
+        const int32_t* t = T + 4 * (int64_t)surv[s];
+        D1 X[4][3], F[4];
+        for (int q = 0; q < 4; ++q) {
+          const double* v = &fld.V[3 * (int64_t)t[q]];
+          for (int r = 0; r < 3; ++r) {
+            double xv = (double)c.R[3 * r] * v[0] + (double)c.R[3 * r + 1] * v[1] +
+                        (double)c.R[3 * r + 2] * v[2] + (double)c.t[r];
+            double xt = (double)c.R[3 * r] * tV[3 * t[q]] + (double)c.R[3 * r + 1] * tV[3 * t[q] + 1] +
+                        (double)c.R[3 * r + 2] * tV[3 * t[q] + 2];
+            X[q][r] = D1(xv);
+            X[q][r].d[0] = xt;
+          }
+          F[q] = D1(fld.f[t[q]]);
+          F[q].d[0] = tf[t[q]];
+        }
+        FragOut<D1> o;
+        if (!eval_fragment<D1>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, &o)) continue;
+        D1 a = opacity_eq1<D1>(o.f_prev, o.f_next, p->s);
+        if (!pure) {
+          if (a.v > p->alpha_cap) a = D1(p->alpha_cap);
+          if (a.v < p->alpha_skip) continue;
+        }
+        D1 Tn = Tr * (1.0 - a);
+        if (!pure && Tn.v < p->t_eps) break;
+        D1 zb = 0.25 * (((X[0][2] + X[1][2]) + X[2][2]) + X[3][2]);
+        for (int q = 0; q < 3; ++q) {
+          D1 cc = 0.25 * (((D1(fld.rgb[3 * t[0] + q]) + D1(fld.rgb[3 * t[1] + q])) + D1(fld.rgb[3 * t[2] + q])) + D1(fld.rgb[3 * t[3] + q]));
+          cc.d[0] = 0.25 * (trgb[3 * t[0] + q] + trgb[3 * t[1] + q] + trgb[3 * t[2] + q] + trgb[3 * t[3] + q]);
+          C[q] = C[q] + Tr * a * cc;
+        }
+        Dp = Dp + Tr * a * zb;
+        Tr = Tn;
+      }
+      const int64_t pix = (int64_t)j * W + i;
+      L = L + (double)dimg[pix] * C[0] + (double)dimg[HW + pix] * C[1] + (double)dimg[2 * HW + pix] * C[2] +
+          (double)dalpha[pix] * (1.0 - Tr) + (double)ddepth[pix] * Dp;
+    }
+  out[0] = L.v;
+  out[1] = L.d[0];
+  return 0;
+}
+
+}  // extern "C"
