@@ -1,0 +1,433 @@
+"""Benchmark of the tetrahedron splatting rasterizer: forward + backward
+throughput in Mpixel/s.
+
+Workload (default): the 128^3 structured grid (12,582,912 tets, 2,146,689
+vertices) with the three-sphere SDF, 4 views at 512x512, s = 175, 16x16 tiles.
+One step = pre-filter (view independent) + forward of all views + backward of
+all views, the inputs resident in HBM.  The seeded synthetic inputs come from
+``synth``; the upstream gradient is seeded N(0, 1).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the same workload instead (one view per step, bounded sample).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("fwd+bwd Mpixel/s (128³ grid, 4×512² views) vs plain path; "
+          "serve p50/p99 latency")
+UNIT = "Mpixel/s"
+
+# FP32 work per fragment of the forward blend (chord test 18, opacity and
+# compositing 30: see the design notes), and the FP32 peak of 148 SMs x 128
+# lanes x 2 flops (FMA) at the maximum SM clock.
+FWD_FLOP_PER_FRAG = 48
+BWD_FLOP_PER_FRAG = 150
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--s", type=float, default=175.0)
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--res", type=int, default=512)
+    ap.add_argument("--views", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"spheres128: 128^3 grid x6 tets (12,582,912 tets, 2,146,689 vertices), "
+            f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}")
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv",
+                 "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
+            # wait for the first sample so that the timed region is covered
+            t0 = time.time()
+            while time.time() - t0 < 10:
+                self.fh.flush()
+                if len(open(self.path).read().splitlines()) >= 2:
+                    break
+                time.sleep(0.02)
+        except Exception:
+            self.proc = None
+        self.window = [None, None]
+
+    def mark(self, i):
+        self.window[i] = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        import datetime
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        rows = []
+        for line in open(self.path).read().splitlines()[1:]:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1].split()[0]), float(parts[2].split()[0]), parts))
+            except ValueError:
+                continue
+        lo, hi = self.window
+        inside = [r for r in rows if lo is not None and lo - 0.03 <= r[0] <= hi + 0.03]
+        if not inside and rows:   # timed region shorter than the sampling period
+            inside = [min(rows, key=lambda r: abs(r[0] - lo))] if lo is not None else rows[-1:]
+        for ts, c, cm, parts in inside:
+            sm.append(c)
+            smax.append(cm)
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(a, rank, world):
+    import torch
+
+    import synth
+    from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors, _lib
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    sc = synth.scene_spheres128(res=a.res, n_views=a.views)
+    if rank > 0:  # weak scaling: each rank renders its own views of the scene
+        rng = np.random.default_rng(1000 + rank)
+        sc.cams = [synth.random_camera(rng, a.res, a.res) for _ in range(a.views)]
+    st = SceneTensors(*(torch.from_numpy(x).to(dev) for x in (sc.V, sc.T, sc.f, sc.rgb)))
+    params = Params(s=a.s, tile=a.tile)
+    r = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
+    r.forward()
+    r.shrink_to_fit(1.15)
+    r.forward()
+    ups = synth.upstream_grads(2 + rank, sc.cams)
+    gi = torch.from_numpy(np.concatenate([u[0].ravel() for u in ups])).to(dev)
+    ga = torch.from_numpy(np.concatenate([u[1].ravel() for u in ups])).to(dev)
+    gd = torch.from_numpy(np.concatenate([u[2].ravel() for u in ups])).to(dev)
+    img, alpha, depth = r._outputs()
+    grads = [(torch.empty_like(st.V), torch.empty_like(st.f), torch.empty_like(st.rgb))]
+    L = r.lib
+    import ctypes
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    dV = (ctypes.c_void_p * 1)(grads[0][0].data_ptr())
+    df = (ctypes.c_void_p * 1)(grads[0][1].data_ptr())
+    dc = (ctypes.c_void_p * 1)(grads[0][2].data_ptr())
+    b = r.batch()
+    bp = ctypes.byref(b)
+    stages = ["prefilter", "bin", "blend_fwd", "blend_bwd", "scatter_bwd"]
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        _lib.check(L.tts_prepare_scene(bp, sp))
+        if ev is not None:
+            ev[1].record(stream)
+        _lib.check(L.tts_bin_views(bp, sp))
+        if ev is not None:
+            ev[2].record(stream)
+        _lib.check(L.tts_blend_fwd(bp, img.data_ptr(), alpha.data_ptr(), depth.data_ptr(), sp))
+        if ev is not None:
+            ev[3].record(stream)
+        _lib.check(L.tts_blend_bwd(bp, gi.data_ptr(), ga.data_ptr(), gd.data_ptr(), sp))
+        if ev is not None:
+            ev[4].record(stream)
+        _lib.check(L.tts_scatter_bwd(bp, dV, df, dc, sp))
+        if ev is not None:
+            ev[5].record(stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(a.warmup, 3)):
+        step()
+    info = r.info()
+    assert info.status == 0, f"status {info.status}"
+    barrier()
+    clk = ClockSampler(dev.index)
+    clk.start()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(a.steps)]
+    n0 = L.tts_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clk.mark(0)
+    t_start.record(stream)
+    for k in range(a.steps):
+        step(evs[k])
+    t_end.record(stream)
+    barrier()
+    clk.mark(1)
+    time.sleep(0.05)
+    clocks = clk.stop()
+    launches = L.tts_launch_count() - n0
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    stage_ms = {s: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(a.steps))
+                for i, s in enumerate(stages)}
+    info = r.info()
+    assert info.status == 0, f"status {info.status}"
+    if dist is not None:
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    pixels_per_step = sum(c.width * c.height for c in sc.cams)
+    value = world * pixels_per_step * a.steps / elapsed / 1e6
+    # fragments met by the forward (per-pixel counters of the last step)
+    Tp, Lp, Np = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+    _lib.check(L.tts_debug_pixels(bp, ctypes.byref(Tp), ctypes.byref(Lp), ctypes.byref(Np), sp))
+    nfrag = int(r._ws_slice(Np.value, 4 * r.total_pixels, torch.int32).sum().item())
+    lasts = int(r._ws_slice(Lp.value, 4 * r.total_pixels, torch.int32).sum().item())
+    res = {
+        "elapsed": elapsed, "value": value, "stage_ms": stage_ms, "launches": launches,
+        "clocks": clocks, "nfrag": nfrag, "entries_walked": lasts, "n_keys": int(info.n_keys),
+        "n_surv": int(info.n_surv[0]), "sort_passes": int(info.sort_passes),
+        "pixels_per_step": pixels_per_step,
+    }
+
+    # plain single-view path: one view per call, everything per call
+    if not a.no_plain and rank == 0:
+        plains = [Rasterizer([st], [(c, 0)], params, device=dev) for c in sc.cams]
+        for p_ in plains:
+            p_.forward()
+            p_.shrink_to_fit(1.15)
+        for p_, (ui, ua, ud) in zip(plains, ups):
+            p_._gi = torch.from_numpy(ui.ravel()).to(dev)
+            p_._ga = torch.from_numpy(ua.ravel()).to(dev)
+            p_._gd = torch.from_numpy(ud.ravel()).to(dev)
+
+        def plain_step():
+            for p_ in plains:
+                p_.forward(prepare=True, check_status=False)
+                p_.backward(p_._gi, p_._ga, p_._gd, grads=grads)
+
+        for _ in range(3):
+            plain_step()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ns = max(3, a.steps // 2)
+        e0.record(stream)
+        for _ in range(ns):
+            plain_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tp = e0.elapsed_time(e1) / 1e3
+        res["plain"] = pixels_per_step * ns / tp / 1e6
+        del plains
+
+    # end to end through the public API with host buffers
+    if not a.no_e2e:
+        hV = torch.from_numpy(sc.V).pin_memory()
+        hf = torch.from_numpy(sc.f).pin_memory()
+        hc = torch.from_numpy(sc.rgb).pin_memory()
+        hgi, hga, hgd = gi.cpu().pin_memory(), ga.cpu().pin_memory(), gd.cpu().pin_memory()
+        odV = torch.empty(grads[0][0].shape, dtype=torch.float32).pin_memory()
+        odf = torch.empty(grads[0][1].shape, dtype=torch.float32).pin_memory()
+        odc = torch.empty(grads[0][2].shape, dtype=torch.float32).pin_memory()
+        bi = sum(x.numel() * 4 for x in (hV, hf, hc, hgi, hga, hgd))
+        bo = sum(x.numel() * 4 for x in (odV, odf, odc))
+
+        def e2e_step():
+            st.V.copy_(hV, non_blocking=True)
+            st.f.copy_(hf, non_blocking=True)
+            st.rgb.copy_(hc, non_blocking=True)
+            gi.copy_(hgi, non_blocking=True)
+            ga.copy_(hga, non_blocking=True)
+            gd.copy_(hgd, non_blocking=True)
+            step()
+            odV.copy_(grads[0][0], non_blocking=True)
+            odf.copy_(grads[0][1], non_blocking=True)
+            odc.copy_(grads[0][2], non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        if dist is not None:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        res["e2e"] = {"value": world * pixels_per_step * a.steps / te / 1e6, "unit": UNIT,
+                      "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    res["sc"] = sc
+    if dist is not None:
+        dist.barrier()
+    return res
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU) on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_step(sc, view_ids, a, upstream):
+    import oracle
+    op = oracle.make_params(s=float(np.float32(a.s)), tile=a.tile,
+                            prefilter_thresh=float(np.float32(1 / 255)),
+                            alpha_skip=float(np.float32(1 / 255)),
+                            alpha_cap=float(np.float32(0.99)), t_eps=float(np.float32(1e-4)))
+    surv, _, _ = oracle.prefilter(sc.T, sc.f, op)
+    px = 0
+    for v in view_ids:
+        cam = sc.cams[v]
+        bins = oracle.bin_view(surv, sc.T, sc.V, cam, a.tile)
+        oracle.render(sc.V, sc.T, sc.f, sc.rgb, cam, op, surv=surv, bins=bins, upstream=upstream[v])
+        px += cam.width * cam.height
+    return px
+
+
+def cpu_baseline(a, sc=None, n_views=2):
+    import synth
+    if sc is None:
+        sc = synth.scene_spheres128(res=a.res, n_views=a.views)
+    ups = synth.upstream_grads(2, sc.cams)
+    views = list(range(min(n_views, len(sc.cams))))
+    t = time.perf_counter()
+    px = oracle_step(sc, views, a, ups)
+    dt = time.perf_counter() - t
+    return {"value": px / dt / 1e6, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"pre-filter of the full grid + {len(views)} of the {len(sc.cams)} views "
+                      f"(bin, FP64 render, adjoint) of the same workload; {dt:.1f} s"}
+
+
+def run_reference(a):
+    import synth
+    sc = synth.scene_spheres128(res=a.res, n_views=a.views)
+    ups = synth.upstream_grads(2, sc.cams)
+    for k in range(a.warmup):
+        oracle_step(sc, [k % len(sc.cams)], a, ups)
+    t = time.perf_counter()
+    px = 0
+    for k in range(a.steps):
+        px += oracle_step(sc, [k % len(sc.cams)], a, ups)
+    dt = time.perf_counter() - t
+    v = px / dt / 1e6
+    sample = ("each step: pre-filter of the full grid + one of the 4 views (bin, FP64 render, "
+              "adjoint), views in turn")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": workload_name(a)},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if a.impl == "reference":
+        if rank == 0:
+            run_reference(a)
+        return
+    res = run_ours(a, rank, world)
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s FP32
+    st = res["stage_ms"]
+    dom = max(st, key=st.get)
+    launch_s = {"blend_fwd": st["blend_fwd"], "blend_bwd": st["blend_bwd"]}
+    flops = {"blend_fwd": res["nfrag"] * FWD_FLOP_PER_FRAG,
+             "blend_bwd": res["nfrag"] * BWD_FLOP_PER_FRAG}
+    rk = dom if dom in flops else "blend_bwd"
+    achieved = flops[rk] / (launch_s[rk] / 1e3) / 1e12
+    roofline = {"kernel": rk, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
+    out = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": res["elapsed"] / a.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(a), "global_views": a.views * world,
+                   "l2": "inputs larger than L2 (tet indices 201 MB, per-step records "
+                         f"{res['n_surv'] * a.views * 96 / 1e6:.0f} MB)",
+                   "parallelism": f"dp{world} (independent views per GPU)"},
+        "roofline": roofline,
+        "stage_ms": st, "dominant_stage": dom,
+        "plain_path_mpix_s": res.get("plain"),
+        "gpu_launches": res["launches"],
+        "fragments_per_step": res["nfrag"], "keys_per_step": res["n_keys"],
+        "survivors": res["n_surv"], "sort_passes": res["sort_passes"],
+        "mtet_per_s": 12582912 * a.steps / res["elapsed"] / 1e6,
+        "clocks": res["clocks"],
+    }
+    if "e2e" in res:
+        out["e2e"] = res["e2e"]
+    if not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, res["sc"])
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

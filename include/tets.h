@@ -1,0 +1,224 @@
+/*
+ * tets.h — C ABI of the tetrahedron splatting rasterizer (libtets.so).
+ *
+ * Renders structured or unstructured tetrahedral grids whose vertices carry a
+ * signed distance value f and a colour, following "Tetrahedron Splatting for
+ * 3D Generation" (TeT-Splatting), Sec. 3.2-3.3 and App. A:
+ *
+ *   tts_prepare_scene   pre-filter (Sec. 3.2 "Pre-filtering"): per tet
+ *                       alpha_max = Eq. 1 at (max f, min f); keep the tets with
+ *                       alpha_max >= T_f, in their original order.
+ *   tts_render_fwd      per view: project and cull the survivors, build one
+ *                       (tile id, mean vertex depth) key per overlapped tile,
+ *                       radix sort the keys (Sec. 3.3), then per pixel blend the
+ *                       tile's tets front to back with the Eq. 1 opacity of the
+ *                       ray's chord through the tet and Eq. 2 compositing
+ *                       (3DGS conventions), writing image, alpha and depth.
+ *   tts_render_bwd      gradients of a scalar loss through the forward, given
+ *                       dL/dimage, dL/dalpha, dL/ddepth: written to the vertex
+ *                       positions, vertex SDF values and vertex colours.
+ *
+ * Everything runs on one CUDA device, asynchronously on the caller's stream.
+ * No entry point allocates device memory: the caller provides one workspace
+ * buffer sized by tts_workspace_size and keeps it (unchanged) from a forward
+ * to the backward that follows it.
+ *
+ * Conventions
+ *   camera     world->camera x_c = R v + t, R row-major, OpenCV axes (x right,
+ *              y down, z forward); pixel (i, j) has its centre at
+ *              (i + 0.5, j + 0.5) and sees the ray direction
+ *              ((i + 0.5 - cx) / fx, (j + 0.5 - cy) / fy, 1).
+ *   layouts    V: N x 3 fp32, T: K x 4 int32 (vertex indices), f: N fp32,
+ *              rgb: N x 3 fp32, all contiguous.  Outputs are view-major and
+ *              planar: view v occupies image[3 * P_v ...] as 3 planes of
+ *              H_v x W_v, alpha[P_v ...] and depth[P_v ...] as H_v x W_v,
+ *              where P_v = sum of H_u W_u over the views u < v.
+ *   depth      Eq. 2 depth term: the blend of each tet's mean camera-space
+ *              vertex depth z (not Euclidean distance).
+ *   colour     each tet's colour is the mean of its four vertex colours.
+ *   blending   alpha' = min(alpha, alpha_cap); fragments with alpha' <
+ *              alpha_skip are skipped; a pixel stops before the fragment that
+ *              would take its transmittance below t_eps; background is 0.
+ *              With TTS_FLAG_PURE: no cap, no skip, no stop, no pre-filter.
+ *
+ * Errors: every call returns TTS_OK or a TTS_ERR_* code.  Argument errors are
+ * found on the host before anything is enqueued.  Conditions found on the
+ * device (an index outside [0, N), more keys than key_capacity, more
+ * survivors than surv_capacity) set bits of a status word in the workspace;
+ * tts_get_info reads it (and synchronises the stream).  When the status is not
+ * zero the outputs of that forward/backward are undefined; enlarge the
+ * capacities and call again.  Kernels never trap.
+ */
+#ifndef TETS_H_
+#define TETS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tts_stream; /* a cudaStream_t (NULL: legacy default stream) */
+
+enum {
+  TTS_OK = 0,
+  TTS_ERR_ARG = 1,        /* bad argument (host check) */
+  TTS_ERR_WORKSPACE = 2,  /* workspace missing, misaligned or too small */
+  TTS_ERR_OVERFLOW = 3,   /* status: key or survivor capacity exceeded */
+  TTS_ERR_CUDA = 4,       /* a CUDA launch/runtime call failed */
+  TTS_ERR_TIMEOUT = 5,    /* status: a bounded device wait gave up */
+  TTS_ERR_BAD_INDEX = 6   /* status: a tet index outside [0, N) (tet dropped) */
+};
+
+/* status word bits (tts_info.status) */
+enum {
+  TTS_STATUS_BAD_INDEX = 1,
+  TTS_STATUS_SURV_OVERFLOW = 2,
+  TTS_STATUS_KEY_OVERFLOW = 4,
+  TTS_STATUS_TIMEOUT = 8
+};
+
+enum {
+  TTS_FLAG_PURE = 1,        /* no cap / skip / early stop / pre-filter */
+  TTS_FLAG_ACCUM_GRAD = 2   /* backward adds into dV/df/drgb instead of overwriting */
+};
+
+#define TTS_MAX_SCENES 64
+#define TTS_MAX_VIEWS 128
+
+typedef struct {
+  float R[9];     /* world -> camera rotation, row-major */
+  float t[3];     /* world -> camera translation */
+  float fx, fy, cx, cy;
+  float znear;    /* a tet with any vertex at z < znear is culled */
+  int32_t width, height;
+} tts_camera;
+
+typedef struct {
+  float s;                /* Eq. 1 steepness */
+  float prefilter_thresh; /* T_f, Sec. 3.2 (paper: 1/255) */
+  float alpha_skip;       /* 1/255 */
+  float alpha_cap;        /* 0.99 */
+  float t_eps;            /* 1e-4 */
+  int32_t tile;           /* tile edge in pixels: 8, 16 or 32 */
+  int32_t flags;          /* TTS_FLAG_* */
+  int32_t reserved;       /* 0 */
+} tts_params;
+
+/* One scene: caller-owned device arrays (must outlive every call using them). */
+typedef struct {
+  const float* V;     /* N x 3 vertex positions */
+  const int32_t* T;   /* K x 4 vertex indices */
+  const float* f;     /* N vertex SDF values */
+  const float* rgb;   /* N x 3 vertex colours */
+  int64_t N, K;
+  int64_t surv_capacity; /* record slots per view of this scene; 0 means K */
+} tts_scene;
+
+/* One view of one scene. */
+typedef struct {
+  tts_camera cam;
+  int32_t scene;      /* index into the scene array */
+  int32_t reserved;
+} tts_view;
+
+/* A batch: any number of scenes and views (up to the maxima above).  The
+ * workspace layout is a pure function of (scenes' N, K, surv_capacity; views'
+ * sizes and scenes; tile; key_capacity). */
+typedef struct {
+  const tts_scene* scenes; /* host array */
+  int32_t n_scenes;
+  const tts_view* views;   /* host array */
+  int32_t n_views;
+  tts_params params;
+  int64_t key_capacity;    /* (tile, tet) keys over all views */
+  void* workspace;         /* device, 256-byte aligned */
+  size_t workspace_bytes;
+} tts_batch;
+
+typedef struct {
+  uint32_t status;          /* TTS_STATUS_* bits */
+  int32_t n_scenes;
+  int64_t n_keys;           /* keys produced by the last forward (needed capacity) */
+  int64_t n_surv[TTS_MAX_SCENES]; /* survivors per scene of the last prepare */
+  int32_t sort_bits;        /* key bits sorted by the last forward */
+  int32_t sort_passes;
+} tts_info;
+
+/* Bytes of workspace the batch needs (host only; nothing is enqueued). */
+int tts_workspace_size(const tts_batch* b, size_t* bytes);
+
+/* Clears the workspace's persistent state (status word, gradient
+ * accumulators).  Call once after allocating or resizing the workspace. */
+int tts_workspace_init(const tts_batch* b, tts_stream stream);
+
+/* Pre-filter every scene of the batch (Sec. 3.2, view independent, hoisted
+ * once per iteration as App. B.1 describes).  Writes the survivor lists into
+ * the workspace. */
+int tts_prepare_scene(const tts_batch* b, tts_stream stream);
+
+/* Forward for every view of the batch (needs tts_prepare_scene first).
+ * image: 3 * sum(H W) floats, alpha and depth: sum(H W) floats (device). */
+int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
+                   tts_stream stream);
+
+/* Backward of the last forward on this workspace.  dimage/dalpha/ddepth have
+ * the layouts of the forward outputs; ddepth or dalpha may be NULL (zero).
+ * dV, df, drgb: host arrays of n_scenes device pointers (N_s x 3, N_s,
+ * N_s x 3 fp32), overwritten unless TTS_FLAG_ACCUM_GRAD. */
+int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha,
+                   const float* ddepth, float* const* dV, float* const* df,
+                   float* const* drgb, tts_stream stream);
+
+/* The forward and backward as their stages, for callers that interleave
+ * their own work or time the stages: tts_render_fwd == tts_bin_views then
+ * tts_blend_fwd; tts_render_bwd == tts_blend_bwd then tts_scatter_bwd (both
+ * stages of a pair take the same batch).  tts_blend_bwd clears nothing:
+ * tts_scatter_bwd overwrites (or, with TTS_FLAG_ACCUM_GRAD, adds into) the
+ * vertex gradients. */
+int tts_bin_views(const tts_batch* b, tts_stream stream);       /* cull, keys, sort, ranges */
+int tts_blend_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
+                  tts_stream stream);                            /* per-tile blend */
+int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha,
+                  const float* ddepth, tts_stream stream);       /* per-tile adjoint */
+int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df,
+                    float* const* drgb, tts_stream stream);      /* record -> vertex */
+
+/* Number of kernels this library has launched in this process so far
+ * (host-side counter, all threads). */
+int64_t tts_launch_count(void);
+
+/* Device pointers to the per-pixel forward state (view-major, like alpha):
+ * final transmittance (fp32), number of list entries walked up to the last
+ * blended one (int32) and number of fragments met (int32: list entries whose
+ * chord was non-empty, up to where the pixel stopped). */
+int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last,
+                     const void** n_frag, tts_stream stream);
+
+/* Synchronises the stream and copies the status word and counters. */
+int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream);
+
+/* Device pointers into the workspace (for inspection and tests): the sorted
+ * keys (uint64: (global tile << depth_bits) | (zbits - zmin_bits)), values
+ * (uint32 record slot), per-tile ranges (int32 pairs [start, end) per global
+ * tile), survivor list of scene 0.., and the key encoding (zmin_bits,
+ * depth_bits).  Synchronises the stream. */
+int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
+                    const void** ranges, const void** surv, uint32_t* zmin_bits,
+                    int32_t* depth_bits, tts_stream stream);
+
+/* Device pointer to the per-slot records (6 float4 each, see the design
+ * notes) and to the per-slot survivor-relative tet index order. */
+int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
+
+const char* tts_error_string(int code);
+
+/* Library version and the GPU architecture it was built for. */
+const char* tts_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TETS_H_ */

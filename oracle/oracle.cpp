@@ -436,16 +436,10 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
   const int nth = 1;
   (void)nthreads;
 #endif
-  std::vector<std::vector<double>> gbuf;
-  if (want_grad) gbuf.assign(nth, std::vector<double>(7 * (size_t)N, 0.0));
+  (void)nth;
 
 #pragma omp parallel for schedule(dynamic, 1)
   for (int j = 0; j < H; ++j) {
-#ifdef _OPENMP
-    const int tid = omp_get_thread_num();
-#else
-    const int tid = 0;
-#endif
     std::vector<Frag> fr;
     PixelResult pr, alt;
     for (int i = 0; i < W; ++i) {
@@ -497,7 +491,6 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
       const double gO = dalpha[pix], gD = ddepth[pix];
       const double Tfin = 1.0 - pr.O;
       double Ssuf = 0.0;
-      double* G = gbuf[tid].data();
       for (int b = (int)pr.blended.size() - 1; b >= 0; --b) {
         const Blended& bl = pr.blended[b];
         const double w = gC[0] * bl.c[0] + gC[1] * bl.c[1] + gC[2] * bl.c[2] + gD * bl.zbar;
@@ -506,7 +499,10 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
         const int32_t* t = T + 4 * (int64_t)surv[bl.s];
         // colour: c = mean of the 4 vertex colours
         for (int q = 0; q < 4; ++q)
-          for (int ch = 0; ch < 3; ++ch) G[4 * (size_t)N + 3 * (size_t)t[q] + ch] += 0.25 * bl.T * bl.a * gC[ch];
+          for (int ch = 0; ch < 3; ++ch) {
+#pragma omp atomic
+            drgb[3 * (size_t)t[q] + ch] += 0.25 * bl.T * bl.a * gC[ch];
+          }
         // depth term: zbar = mean camera z -> world via R^T (third row)
         double dX[4][3] = {{0}};
         const double dz = 0.25 * bl.T * bl.a * gD;
@@ -535,20 +531,12 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
           // world gradient: x_c = R v + t  ->  dv = R^T dx_c
           for (int r = 0; r < 3; ++r) {
             double g = c.R[r] * dX[q][0] + c.R[3 + r] * dX[q][1] + c.R[6 + r] * dX[q][2];
-            G[3 * (size_t)t[q] + r] += g;
+#pragma omp atomic
+            dV[3 * (size_t)t[q] + r] += g;
           }
-          G[3 * (size_t)N + t[q]] += dF[q];
+#pragma omp atomic
+          df[t[q]] += dF[q];
         }
-      }
-    }
-  }
-  if (want_grad) {
-    for (int th = 0; th < nth; ++th) {
-      const double* G = gbuf[th].data();
-      for (int64_t v = 0; v < N; ++v) {
-        for (int r = 0; r < 3; ++r) dV[3 * v + r] += G[3 * v + r];
-        df[v] += G[3 * N + v];
-        for (int r = 0; r < 3; ++r) drgb[3 * v + r] += G[4 * N + 3 * v + r];
       }
     }
   }

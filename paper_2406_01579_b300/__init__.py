@@ -1,0 +1,10 @@
+"""B300-native tetrahedron splatting rasterizer (TeT-Splatting, Sec. 3.2-3.3,
+App. A): CUDA kernels for sm_103a behind the C ABI of include/tets.h, with a
+thin PyTorch binding.  There is no CPU fallback: importing the rasterizer
+requires the built libtets.so."""
+
+from ._lib import TetsError, load  # noqa: F401
+from .rasterizer import Params, Rasterizer, SceneTensors, TetRender, make_camera, render  # noqa: F401
+
+__all__ = ["Params", "Rasterizer", "SceneTensors", "TetRender", "render", "make_camera", "load",
+           "TetsError"]

@@ -1,0 +1,436 @@
+// C ABI of libtets: argument checks, workspace layout, launch sequences.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "launch.h"
+
+namespace tts {
+
+static_assert(SORT_THREADS == RADIX, "scatter maps one thread per digit");
+static_assert(sizeof(Batch) < 30000, "descriptor must fit in kernel parameters");
+
+// Copies the by-value descriptor into the workspace (kernel parameters are
+// captured by value in CUDA graphs, so this stays valid under capture).
+__global__ void k_upload(const Batch b, Batch* dst) {
+  const unsigned* src = reinterpret_cast<const unsigned*>(&b);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  constexpr int n = (int)(sizeof(Batch) / 4);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = src[i];
+}
+
+int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st) {
+  k_upload<<<1, 256, 0, st>>>(hb, dB);
+  return 1;
+}
+
+static std::atomic<long long> g_launches{0};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int bit_length(long long x) {
+  int b = 0;
+  while (x > 0) { ++b; x >>= 1; }
+  return b;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+struct Plan {
+  Batch hb;      // descriptor with device pointers filled in
+  HostPlan hp;
+  size_t bytes;
+  size_t off_desc;
+  size_t off_ctr, off_rec_grad, bytes_rec_grad;
+};
+
+// Validates the batch and computes the workspace layout.  When base is null
+// only sizes are computed.
+int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
+  if (!b || !b->scenes || !b->views) return TTS_ERR_ARG;
+  if (b->n_scenes < 1 || b->n_scenes > TTS_MAX_SCENES) return TTS_ERR_ARG;
+  if (b->n_views < 1 || b->n_views > TTS_MAX_VIEWS) return TTS_ERR_ARG;
+  const tts_params& pr = b->params;
+  if (!(pr.tile == 8 || pr.tile == 16 || pr.tile == 32)) return TTS_ERR_ARG;
+  if (!(std::isfinite(pr.s) && pr.s > 0.f)) return TTS_ERR_ARG;
+  if (!(pr.alpha_cap > 0.f && pr.alpha_cap <= 1.f && pr.t_eps >= 0.f && pr.alpha_skip >= 0.f &&
+        pr.prefilter_thresh >= 0.f))
+    return TTS_ERR_ARG;
+  if (b->key_capacity < 1 || b->key_capacity > 0x7fffffffLL) return TTS_ERR_ARG;
+  std::memset(&P->hb, 0, sizeof(Batch));
+  Batch& B = P->hb;
+  B.n_scenes = b->n_scenes;
+  B.n_views = b->n_views;
+  B.s = pr.s;
+  B.prefilter_thresh = pr.prefilter_thresh;
+  B.alpha_skip = pr.alpha_skip;
+  B.alpha_cap = pr.alpha_cap;
+  B.t_eps = pr.t_eps;
+  B.tile = pr.tile;
+  B.flags = pr.flags;
+  B.key_cap = b->key_capacity;
+  // scenes
+  long long surv_total = 0, flag_total = 0;
+  int pf_chunks = 0, max_pf = 1;
+  std::vector<int> views_of(b->n_scenes, 0);
+  for (int v = 0; v < b->n_views; ++v) {
+    const int s = b->views[v].scene;
+    if (s < 0 || s >= b->n_scenes) return TTS_ERR_ARG;
+    views_of[s]++;
+  }
+  int voff = 0;
+  for (int s = 0; s < b->n_scenes; ++s) {
+    const tts_scene& sc = b->scenes[s];
+    if (!sc.V || !sc.T || !sc.f || !sc.rgb) return TTS_ERR_ARG;
+    if (sc.N < 1 || sc.K < 1 || sc.K > 0x7fffffffLL || sc.N > 0x7fffffffLL) return TTS_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(sc.T) % 16 != 0) return TTS_ERR_ARG;  // int4 loads
+    SceneD& S = B.sc[s];
+    S.V = sc.V;
+    S.T = reinterpret_cast<const int4*>(sc.T);
+    S.f = sc.f;
+    S.rgb = sc.rgb;
+    S.N = sc.N;
+    S.K = sc.K;
+    S.surv_cap = (sc.surv_capacity > 0) ? std::min<long long>(sc.surv_capacity, sc.K) : sc.K;
+    S.surv_off = surv_total;
+    surv_total += S.surv_cap;
+    S.flag_off = flag_total;
+    flag_total += align_up(sc.K, 16);
+    S.pf_chunks = (int)((sc.K + PF_CHUNK - 1) / PF_CHUNK);
+    S.pf_chunk_base = pf_chunks;
+    pf_chunks += S.pf_chunks;
+    max_pf = std::max(max_pf, S.pf_chunks);
+    S.view_off = voff;
+    S.view_cnt = 0;
+    voff += views_of[s];
+  }
+  // views
+  long long slots = 0, pix = 0;
+  int tiles = 0, pp_chunks = 0, max_pp = 1;
+  for (int v = 0; v < b->n_views; ++v) {
+    const tts_view& tv = b->views[v];
+    const tts_camera& c = tv.cam;
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384) return TTS_ERR_ARG;
+    if (!(c.fx > 0.f && c.fy > 0.f && std::isfinite(c.cx) && std::isfinite(c.cy) && c.znear > 0.f))
+      return TTS_ERR_ARG;
+    for (int i = 0; i < 9; ++i) if (!std::isfinite(c.R[i])) return TTS_ERR_ARG;
+    for (int i = 0; i < 3; ++i) if (!std::isfinite(c.t[i])) return TTS_ERR_ARG;
+    ViewD& V = B.vw[v];
+    std::memcpy(V.R, c.R, sizeof(V.R));
+    std::memcpy(V.t, c.t, sizeof(V.t));
+    V.fx = c.fx; V.fy = c.fy; V.cx = c.cx; V.cy = c.cy; V.znear = c.znear;
+    V.W = c.width; V.H = c.height;
+    V.tiles_x = (c.width + pr.tile - 1) / pr.tile;
+    V.tiles_y = (c.height + pr.tile - 1) / pr.tile;
+    V.scene = tv.scene;
+    V.tile_base = tiles;
+    tiles += V.tiles_x * V.tiles_y;
+    V.pix_base = pix;
+    pix += (long long)c.width * c.height;
+    V.rec_base = slots;
+    const long long cap = B.sc[tv.scene].surv_cap;
+    slots += cap;
+    V.pp_chunks = (int)((cap + PP_CHUNK - 1) / PP_CHUNK);
+    V.pp_chunk_base = pp_chunks;
+    pp_chunks += V.pp_chunks;
+    max_pp = std::max(max_pp, V.pp_chunks);
+    SceneD& S = B.sc[tv.scene];
+    B.scene_views[S.view_off + S.view_cnt++] = v;
+  }
+  if (slots > 0xffffffffLL) return TTS_ERR_ARG;  // 32-bit key values
+  B.total_tiles = tiles;
+  B.tile_bits = std::max(1, bit_length(tiles - 1));
+  B.pf_chunks_total = pf_chunks;
+  B.pp_chunks_total = pp_chunks;
+  B.max_pf_chunks = max_pf;
+  B.max_pp_chunks = max_pp;
+  B.total_pixels = pix;
+  B.total_slots = slots;
+  B.sort_blocks = 4 * sm_count();
+  // layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = align_up(off, 256);
+    const size_t r = off;
+    off += bytes;
+    return r;
+  };
+  const long long cap = b->key_capacity;
+  P->off_desc = take(sizeof(Batch));
+  P->off_ctr = take(sizeof(Counters));
+  const size_t o_pfb = take(sizeof(int) * pf_chunks);
+  const size_t o_pff = take((size_t)flag_total);
+  const size_t o_surv = take(sizeof(int) * surv_total);
+  const size_t o_rz = take(sizeof(unsigned) * slots);
+  const size_t o_rnt = take(sizeof(int) * slots);
+  const size_t o_rr = take(sizeof(int4) * slots);
+  const size_t o_rec = take(sizeof(float4) * REC_Q * slots);
+  P->off_rec_grad = take(sizeof(float4) * REC_Q * slots);
+  P->bytes_rec_grad = sizeof(float4) * REC_Q * slots;
+  const size_t o_ppb = take(sizeof(long long) * pp_chunks);
+  const size_t o_k0 = take(sizeof(unsigned long long) * cap);
+  const size_t o_k1 = take(sizeof(unsigned long long) * cap);
+  const size_t o_v0 = take(sizeof(unsigned) * cap);
+  const size_t o_v1 = take(sizeof(unsigned) * cap);
+  const size_t o_hist = take(sizeof(unsigned) * RADIX * (B.sort_blocks + 1));
+  const size_t o_rng = take(sizeof(int2) * tiles);
+  const size_t o_pT = take(sizeof(float) * pix);
+  const size_t o_pL = take(sizeof(int) * pix);
+  const size_t o_pN = take(sizeof(int) * pix);
+  P->bytes = align_up(off, 256);
+  if (need_ws) {
+    if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % 256) != 0)
+      return TTS_ERR_WORKSPACE;
+    if (b->workspace_bytes < P->bytes) return TTS_ERR_WORKSPACE;
+    char* base = static_cast<char*>(b->workspace);
+    B.ctr = reinterpret_cast<Counters*>(base + P->off_ctr);
+    B.pf_blocksum = reinterpret_cast<int*>(base + o_pfb);
+    B.pf_flags = reinterpret_cast<unsigned char*>(base + o_pff);
+    B.surv = reinterpret_cast<int*>(base + o_surv);
+    B.rec_z = reinterpret_cast<unsigned*>(base + o_rz);
+    B.rec_nt = reinterpret_cast<int*>(base + o_rnt);
+    B.rec_rect = reinterpret_cast<int4*>(base + o_rr);
+    B.rec = reinterpret_cast<float4*>(base + o_rec);
+    B.rec_grad = reinterpret_cast<float4*>(base + P->off_rec_grad);
+    B.pp_blocksum = reinterpret_cast<long long*>(base + o_ppb);
+    B.keys[0] = reinterpret_cast<unsigned long long*>(base + o_k0);
+    B.keys[1] = reinterpret_cast<unsigned long long*>(base + o_k1);
+    B.vals[0] = reinterpret_cast<unsigned*>(base + o_v0);
+    B.vals[1] = reinterpret_cast<unsigned*>(base + o_v1);
+    B.hist = reinterpret_cast<unsigned*>(base + o_hist);
+    B.ranges = reinterpret_cast<int2*>(base + o_rng);
+    B.pix_T = reinterpret_cast<float*>(base + o_pT);
+    B.pix_last = reinterpret_cast<int*>(base + o_pL);
+    B.pix_nfrag = reinterpret_cast<int*>(base + o_pN);
+  }
+  HostPlan& H = P->hp;
+  H.n_scenes = b->n_scenes;
+  H.n_views = b->n_views;
+  H.max_pf_chunks = max_pf;
+  H.max_pp_chunks = max_pp;
+  H.sort_blocks = B.sort_blocks;
+  H.max_passes = (32 + B.tile_bits + RADIX_BITS - 1) / RADIX_BITS;
+  H.range_blocks = 2 * sm_count();
+  H.total_tiles = tiles;
+  H.tile = pr.tile;
+  H.tet_bwd_blocks = 2 * sm_count();
+  H.total_pixels = pix;
+  return TTS_OK;
+}
+
+Batch* dev_desc(const tts_batch* b, const Plan& P) {
+  return reinterpret_cast<Batch*>(static_cast<char*>(b->workspace) + P.off_desc);
+}
+
+int check_launch() {
+  const cudaError_t e = cudaPeekAtLastError();
+  return (e == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace tts
+
+using namespace tts;
+
+extern "C" {
+
+int tts_workspace_size(const tts_batch* b, size_t* bytes) {
+  if (!bytes) return TTS_ERR_ARG;
+  Plan P;
+  const int rc = make_plan(b, &P, false);
+  if (rc != TTS_OK) return rc;
+  *bytes = P.bytes;
+  return TTS_OK;
+}
+
+int tts_workspace_init(const tts_batch* b, tts_stream stream) {
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(b->workspace);
+  if (cudaMemsetAsync(base + P.off_ctr, 0, sizeof(Counters), st) != cudaSuccess) return TTS_ERR_CUDA;
+  if (P.bytes_rec_grad &&
+      cudaMemsetAsync(base + P.off_rec_grad, 0, P.bytes_rec_grad, st) != cudaSuccess)
+    return TTS_ERR_CUDA;
+  return TTS_OK;
+}
+
+int tts_prepare_scene(const tts_batch* b, tts_stream stream) {
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Batch* dB = dev_desc(b, P);
+  long long n = launch_upload(P.hb, dB, st);
+  n += launch_prefilter(P.hp, dB, st);
+  g_launches += n;
+  return check_launch();
+}
+
+int tts_bin_views(const tts_batch* b, tts_stream stream) {
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Batch* dB = dev_desc(b, P);
+  long long n = launch_upload(P.hb, dB, st);
+  n += launch_binning(P.hp, dB, st);
+  g_launches += n;
+  return check_launch();
+}
+
+int tts_blend_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
+  if (!image || !alpha || !depth) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  g_launches += launch_blend_fwd(P.hp, dev_desc(b, P), image, alpha, depth, st);
+  return check_launch();
+}
+
+int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
+  if (!image || !alpha || !depth) return TTS_ERR_ARG;
+  int rc = tts_bin_views(b, stream);
+  if (rc != TTS_OK) return rc;
+  return tts_blend_fwd(b, image, alpha, depth, stream);
+}
+
+int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
+                  tts_stream stream) {
+  if (!dimage) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  g_launches += launch_blend_bwd(P.hp, dev_desc(b, P), dimage, dalpha, ddepth, st);
+  return check_launch();
+}
+
+int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
+                    tts_stream stream) {
+  if (!dV || !df || !drgb) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  GradOut go;
+  std::memset(&go, 0, sizeof(go));
+  for (int s = 0; s < b->n_scenes; ++s) {
+    if (!dV[s] || !df[s] || !drgb[s]) return TTS_ERR_ARG;
+    go.dV[s] = dV[s];
+    go.df[s] = df[s];
+    go.drgb[s] = drgb[s];
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!(b->params.flags & TTS_FLAG_ACCUM_GRAD)) {
+    for (int s = 0; s < b->n_scenes; ++s) {
+      const size_t N = (size_t)b->scenes[s].N;
+      if (cudaMemsetAsync(dV[s], 0, 12 * N, st) != cudaSuccess ||
+          cudaMemsetAsync(df[s], 0, 4 * N, st) != cudaSuccess ||
+          cudaMemsetAsync(drgb[s], 0, 12 * N, st) != cudaSuccess)
+        return TTS_ERR_CUDA;
+    }
+  }
+  g_launches += launch_tet_bwd(P.hp, dev_desc(b, P), go, st);
+  return check_launch();
+}
+
+int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
+                   float* const* dV, float* const* df, float* const* drgb, tts_stream stream) {
+  if (!dimage || !dV || !df || !drgb) return TTS_ERR_ARG;
+  int rc = tts_blend_bwd(b, dimage, dalpha, ddepth, stream);
+  if (rc != TTS_OK) return rc;
+  return tts_scatter_bwd(b, dV, df, drgb, stream);
+}
+
+int64_t tts_launch_count(void) { return g_launches.load(); }
+
+int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last,
+                     const void** n_frag, tts_stream stream) {
+  (void)stream;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  if (T_final) *T_final = P.hb.pix_T;
+  if (last) *last = P.hb.pix_last;
+  if (n_frag) *n_frag = P.hb.pix_nfrag;
+  return TTS_OK;
+}
+
+int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream) {
+  if (!info) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Counters c;
+  if (cudaMemcpyAsync(&c, P.hb.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TTS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TTS_ERR_CUDA;
+  std::memset(info, 0, sizeof(*info));
+  info->status = c.status;
+  info->n_scenes = b->n_scenes;
+  info->n_keys = c.n_keys;
+  for (int s = 0; s < b->n_scenes; ++s) info->n_surv[s] = c.n_surv[s];
+  info->sort_bits = c.total_bits;
+  info->sort_passes = c.n_passes;
+  return TTS_OK;
+}
+
+int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals, const void** ranges,
+                    const void** surv, uint32_t* zmin_bits, int32_t* depth_bits, tts_stream stream) {
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Counters c;
+  if (cudaMemcpyAsync(&c, P.hb.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TTS_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TTS_ERR_CUDA;
+  if (keys) *keys = P.hb.keys[c.n_passes & 1];
+  if (vals) *vals = P.hb.vals[c.n_passes & 1];
+  if (ranges) *ranges = P.hb.ranges;
+  if (surv) *surv = P.hb.surv;
+  if (zmin_bits) *zmin_bits = c.zmin_bits;
+  if (depth_bits) *depth_bits = c.depth_bits;
+  return TTS_OK;
+}
+
+int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream) {
+  (void)stream;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  if (records) *records = P.hb.rec;
+  return TTS_OK;
+}
+
+const char* tts_error_string(int code) {
+  switch (code) {
+    case TTS_OK: return "ok";
+    case TTS_ERR_ARG: return "invalid argument";
+    case TTS_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case TTS_ERR_OVERFLOW: return "key or survivor capacity exceeded";
+    case TTS_ERR_CUDA: return "CUDA error";
+    case TTS_ERR_TIMEOUT: return "device wait timed out";
+    case TTS_ERR_BAD_INDEX: return "tet index outside [0, N)";
+    default: return "unknown error";
+  }
+}
+
+const char* tts_version(void) { return "libtets 0.1 sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,474 @@
+// Pre-filter (Sec. 3.2), per-view preprocess and tile binning with a device
+// radix sort of (tile id, mean depth) keys (Sec. 3.3).
+#include "geometry.cuh"
+#include "launch.h"
+
+namespace tts {
+
+// ---------------------------------------------------------------------------
+// block-level helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Exclusive scan over the block; returns the block total in *total.
+template <typename T, int NT>
+__device__ __forceinline__ T block_excl_scan(T v, T* total) {
+  __shared__ T warp_sums[NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T inc = warp_incl_scan(v);
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    T s = (lane < NT / 32) ? warp_sums[lane] : T(0);
+    s = warp_incl_scan(s);
+    if (lane < NT / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const T base = (wid > 0) ? warp_sums[wid - 1] : T(0);
+  *total = warp_sums[NT / 32 - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// ---------------------------------------------------------------------------
+// per-call resets
+// ---------------------------------------------------------------------------
+__global__ void k_fwd_reset(const Batch* __restrict__ B) {
+  Counters* c = B->ctr;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->zmin_bits = 0xffffffffu;
+    c->zmax_bits = 0u;
+    c->depth_bits = 0;
+    c->total_bits = 0;
+    c->n_passes = 0;
+    c->n_keys = 0;
+    c->n_keys_used = 0;
+    c->status &= ~(unsigned)TTS_STATUS_KEY_OVERFLOW;
+  }
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
+    B->ranges[t] = make_int2(0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// K1: pre-filter.  alpha_max = Eq. 1 at (f_max, f_min) of the tet's vertices,
+// keep iff alpha_max >= T_f.  Flags, then a stable compaction.
+// grid (max_pf_chunks, n_scenes)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __restrict__ B) {
+  const int s = blockIdx.y;
+  const SceneD& S = B->sc[s];
+  const int chunk = blockIdx.x;
+  if (chunk >= S.pf_chunks) return;
+  const long long k0 = (long long)chunk * PF_CHUNK;
+  const long long k1 = min(k0 + PF_CHUNK, S.K);
+  const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
+  const float sv = B->s, thr = B->prefilter_thresh;
+  const unsigned N = (unsigned)S.N;
+  unsigned char* flags = B->pf_flags + S.flag_off;
+  int cnt = 0;
+  bool bad = false;
+  for (long long k = k0 + threadIdx.x; k < k1; k += PF_THREADS) {
+    const int4 t = __ldg(&S.T[k]);
+    unsigned char keep = 0;
+    if ((unsigned)t.x < N && (unsigned)t.y < N && (unsigned)t.z < N && (unsigned)t.w < N) {
+      if (pure) {
+        keep = 1;
+      } else {
+        const float fa = __ldg(S.f + t.x), fb = __ldg(S.f + t.y), fc = __ldg(S.f + t.z),
+                    fd = __ldg(S.f + t.w);
+        const float fmx = fmaxf(fmaxf(fa, fb), fmaxf(fc, fd));
+        const float fmn = fminf(fminf(fa, fb), fminf(fc, fd));
+        // Eq. 1 at (f_max, f_min): -expm1(-s (fmax - fmin)) * sigmoid(-s fmin)
+        const float amax = (fmx > fmn) ? -expm1f(-sv * (fmx - fmn)) / (1.f + expf(sv * fmn)) : 0.f;
+        keep = (amax >= thr) ? 1 : 0;
+      }
+    } else {
+      bad = true;
+    }
+    flags[k] = keep;
+    cnt += keep;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(B->ctr, TTS_STATUS_BAD_INDEX);
+  int total;
+  block_excl_scan<int, PF_THREADS>(cnt, &total);
+  if (threadIdx.x == 0) B->pf_blocksum[S.pf_chunk_base + chunk] = total;
+}
+
+// Single block: per-scene exclusive scans of the pre-filter block counts.
+__global__ void __launch_bounds__(SCAN_THREADS) k_prefilter_scan(const Batch* __restrict__ B) {
+  for (int s = 0; s < B->n_scenes; ++s) {
+    const SceneD& S = B->sc[s];
+    int* a = B->pf_blocksum + S.pf_chunk_base;
+    int carry = 0;
+    for (int base = 0; base < S.pf_chunks; base += SCAN_THREADS) {
+      const int i = base + threadIdx.x;
+      const int v = (i < S.pf_chunks) ? a[i] : 0;
+      int tot;
+      const int ex = block_excl_scan<int, SCAN_THREADS>(v, &tot);
+      if (i < S.pf_chunks) a[i] = carry + ex;
+      carry += tot;
+    }
+    if (threadIdx.x == 0) {
+      int n = carry;
+      if ((long long)n > S.surv_cap) {
+        set_status(B->ctr, TTS_STATUS_SURV_OVERFLOW);
+        n = (int)S.surv_cap;
+      }
+      B->ctr->n_surv[s] = n;
+    }
+    __syncthreads();
+  }
+}
+
+// Stable compaction: survivors in original tet order.
+__global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* __restrict__ B) {
+  const int s = blockIdx.y;
+  const SceneD& S = B->sc[s];
+  const int chunk = blockIdx.x;
+  if (chunk >= S.pf_chunks) return;
+  constexpr int PER = PF_CHUNK / PF_THREADS;  // 16 consecutive flags per thread
+  const long long k0 = (long long)chunk * PF_CHUNK + (long long)threadIdx.x * PER;
+  const unsigned char* flags = B->pf_flags + S.flag_off;
+  unsigned char fl[PER];
+  int cnt = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const long long k = k0 + q;
+    fl[q] = (k < S.K) ? flags[k] : 0;
+    cnt += fl[q];
+  }
+  int total;
+  int off = block_excl_scan<int, PF_THREADS>(cnt, &total) + B->pf_blocksum[S.pf_chunk_base + chunk];
+  int* out = B->surv + S.surv_off;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (fl[q]) {
+      if (off < S.surv_cap) out[off] = (int)(k0 + q);
+      ++off;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: per-view preprocess.  grid (max_pp_chunks, n_views)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PP_THREADS) k_preprocess(const Batch* __restrict__ B) {
+  const int v = blockIdx.y;
+  const ViewD& vw = B->vw[v];
+  const int chunk = blockIdx.x;
+  if (chunk >= vw.pp_chunks) return;
+  const SceneD& S = B->sc[vw.scene];
+  const int nsurv = B->ctr->n_surv[vw.scene];
+  const float s = B->s;
+  const int tile = B->tile;
+  long long nt_sum = 0;
+  unsigned zmn = 0xffffffffu, zmx = 0u;
+  for (int q = threadIdx.x; q < PP_CHUNK; q += PP_THREADS) {
+    const int k = chunk * PP_CHUNK + q;
+    if (k >= nsurv) break;
+    const long long slot = vw.rec_base + k;
+    const int tet = B->surv[S.surv_off + k];
+    TetIn in;
+    load_tet(S, tet, in);
+    Geo G;
+    tet_geometry(vw, s, in, G);
+    int nt = 0;
+    if (G.visible) {
+      const int tx0 = G.i0 / tile, tx1 = G.i1 / tile, ty0 = G.j0 / tile, ty1 = G.j1 / tile;
+      nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+      B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
+      write_record(vw, s, in, G, B->rec + slot * REC_Q);
+      zmn = min(zmn, G.zbits);
+      zmx = max(zmx, G.zbits);
+    }
+    B->rec_nt[slot] = nt;
+    B->rec_z[slot] = G.zbits;
+    nt_sum += nt;
+  }
+  long long tot;
+  block_excl_scan<long long, PP_THREADS>(nt_sum, &tot);
+  // block min/max of the depth bits
+  __shared__ unsigned smn, smx;
+  if (threadIdx.x == 0) { smn = 0xffffffffu; smx = 0u; }
+  __syncthreads();
+  if (zmn != 0xffffffffu) { atomicMin(&smn, zmn); atomicMax(&smx, zmx); }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    B->pp_blocksum[vw.pp_chunk_base + chunk] = tot;
+    if (smn != 0xffffffffu) {
+      atomicMin(&B->ctr->zmin_bits, smn);
+      atomicMax(&B->ctr->zmax_bits, smx);
+    }
+  }
+}
+
+// Single block: exclusive scan of all preprocess block sums (views in order)
+// -> key offsets; total -> n_keys; key encoding bit counts.
+__global__ void __launch_bounds__(SCAN_THREADS) k_preprocess_scan(const Batch* __restrict__ B) {
+  long long* a = B->pp_blocksum;
+  const int n = B->pp_chunks_total;
+  long long carry = 0;
+  for (int base = 0; base < n; base += SCAN_THREADS) {
+    const int i = base + threadIdx.x;
+    const long long v = (i < n) ? a[i] : 0;
+    long long tot;
+    const long long ex = block_excl_scan<long long, SCAN_THREADS>(v, &tot);
+    if (i < n) a[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    Counters* c = B->ctr;
+    c->n_keys = carry;
+    long long used = carry;
+    if (carry > B->key_cap) {
+      set_status(c, TTS_STATUS_KEY_OVERFLOW);
+      used = 0;
+    }
+    c->n_keys_used = used;
+    unsigned span = (c->zmax_bits >= c->zmin_bits) ? (c->zmax_bits - c->zmin_bits) : 0u;
+    if (c->zmin_bits == 0xffffffffu) span = 0;
+    const int db = (span == 0) ? 0 : (32 - __clz(span));
+    c->depth_bits = db;
+    c->total_bits = db + B->tile_bits;
+    c->n_passes = (used > 1) ? (c->total_bits + RADIX_BITS - 1) / RADIX_BITS : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3: duplicate.  One key per (slot, overlapped tile), in slot order and
+// row-major tile order within the slot's rect.  grid (max_pp_chunks, n_views)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PP_THREADS) k_duplicate(const Batch* __restrict__ B) {
+  const int v = blockIdx.y;
+  const ViewD& vw = B->vw[v];
+  const int chunk = blockIdx.x;
+  if (chunk >= vw.pp_chunks) return;
+  const Counters* c = B->ctr;
+  if (c->n_keys_used == 0) return;
+  const int nsurv = c->n_surv[vw.scene];
+  constexpr int PER = PP_CHUNK / PP_THREADS;
+  // thread handles PER consecutive slots so that key order follows slot order
+  const int k0 = chunk * PP_CHUNK + threadIdx.x * PER;
+  int nt[PER];
+  long long cnt = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int k = k0 + q;
+    nt[q] = (k < nsurv) ? B->rec_nt[vw.rec_base + k] : 0;
+    cnt += nt[q];
+  }
+  long long tot;
+  long long off = block_excl_scan<long long, PP_THREADS>(cnt, &tot) + B->pp_blocksum[vw.pp_chunk_base + chunk];
+  const unsigned zmin = c->zmin_bits;
+  const int db = c->depth_bits;
+  unsigned long long* keys = B->keys[0];
+  unsigned int* vals = B->vals[0];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    if (nt[q] == 0) continue;
+    const long long slot = vw.rec_base + k0 + q;
+    const int4 r = B->rec_rect[slot];
+    const unsigned long long zrel = (unsigned long long)(B->rec_z[slot] - zmin);
+    for (int ty = r.z; ty <= r.w; ++ty)
+      for (int tx = r.x; tx <= r.y; ++tx) {
+        const unsigned long long gt = (unsigned long long)(vw.tile_base + ty * vw.tiles_x + tx);
+        keys[off] = (gt << db) | zrel;
+        vals[off] = (unsigned)slot;
+        ++off;
+      }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K4: LSD radix sort, 8-bit digits, stable.  Per pass: histogram per block,
+// per-digit row scan, stable scatter (warp multisplit ranks).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sort_chunk(const Batch* B, long long n, long long* lo, long long* hi) {
+  const int nb = B->sort_blocks;
+  long long per = (n + nb - 1) / nb;
+  per = (per + SORT_TILE - 1) / SORT_TILE * SORT_TILE;
+  *lo = min(n, per * blockIdx.x);
+  *hi = min(n, *lo + per);
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const Batch* __restrict__ B, int pass) {
+  const Counters* c = B->ctr;
+  if (pass >= c->n_passes) return;
+  const long long n = c->n_keys_used;
+  long long lo, hi;
+  sort_chunk(B, n, &lo, &hi);
+  __shared__ unsigned h[SORT_THREADS / 32][RADIX];
+  for (int i = threadIdx.x; i < (SORT_THREADS / 32) * RADIX; i += SORT_THREADS) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned long long* src = B->keys[pass & 1];
+  const int sh = pass * RADIX_BITS;
+  const int wid = threadIdx.x >> 5;
+  for (long long i = lo + threadIdx.x; i < hi; i += SORT_THREADS) {
+    const unsigned d = (unsigned)(src[i] >> sh) & (RADIX - 1);
+    atomicAdd(&h[wid][d], 1u);
+  }
+  __syncthreads();
+  const int nb = B->sort_blocks;
+  for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) {
+    unsigned t = 0;
+#pragma unroll
+    for (int w = 0; w < SORT_THREADS / 32; ++w) t += h[w][d];
+    B->hist[(size_t)d * (nb + 1) + blockIdx.x] = t;
+  }
+}
+
+// grid RADIX blocks: exclusive scan of one digit's row over the blocks; the
+// row total goes to the extra last column.
+__global__ void __launch_bounds__(SCAN_THREADS) k_radix_rowscan(const Batch* __restrict__ B, int pass) {
+  if (pass >= B->ctr->n_passes) return;
+  const int nb = B->sort_blocks;
+  unsigned* row = B->hist + (size_t)blockIdx.x * (nb + 1);
+  unsigned carry = 0;
+  for (int base = 0; base < nb; base += SCAN_THREADS) {
+    const int i = base + threadIdx.x;
+    const unsigned v = (i < nb) ? row[i] : 0u;
+    unsigned tot;
+    const unsigned ex = block_excl_scan<unsigned, SCAN_THREADS>(v, &tot);
+    if (i < nb) row[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) row[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __restrict__ B, int pass) {
+  const Counters* c = B->ctr;
+  if (pass >= c->n_passes) return;
+  const long long n = c->n_keys_used;
+  long long lo, hi;
+  sort_chunk(B, n, &lo, &hi);
+  const int nb = B->sort_blocks;
+  constexpr int NW = SORT_THREADS / 32;
+  __shared__ unsigned base[RADIX];
+  __shared__ unsigned wcnt[NW][RADIX];
+  __shared__ unsigned tcnt[RADIX];
+  // digit base = (exclusive scan of digit totals) + this block's row prefix
+  {
+    const int d = threadIdx.x;  // SORT_THREADS == RADIX
+    const unsigned tot = B->hist[(size_t)d * (nb + 1) + nb];
+    unsigned t;
+    const unsigned ex = block_excl_scan<unsigned, SORT_THREADS>(tot, &t);
+    base[d] = ex + B->hist[(size_t)d * (nb + 1) + blockIdx.x];
+  }
+  for (int i = threadIdx.x; i < NW * RADIX; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned long long* ksrc = B->keys[pass & 1];
+  const unsigned* vsrc = B->vals[pass & 1];
+  unsigned long long* kdst = B->keys[(pass + 1) & 1];
+  unsigned* vdst = B->vals[(pass + 1) & 1];
+  const int sh = pass * RADIX_BITS;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (long long t0 = lo; t0 < hi; t0 += SORT_TILE) {
+    unsigned long long k[SORT_KPT];
+    unsigned val[SORT_KPT];
+    unsigned dg[SORT_KPT];
+    unsigned off[SORT_KPT];
+#pragma unroll
+    for (int j = 0; j < SORT_KPT; ++j) {
+      const long long i = t0 + (long long)wid * (32 * SORT_KPT) + j * 32 + lane;
+      if (i < hi) {
+        k[j] = ksrc[i];
+        val[j] = vsrc[i];
+        dg[j] = (unsigned)(k[j] >> sh) & (RADIX - 1);
+      } else {
+        dg[j] = RADIX;  // sentinel: not scattered
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SORT_KPT; ++j) {
+      const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
+      const unsigned rank = __popc(peers & lt_mask);
+      const unsigned d = dg[j] & (RADIX - 1);
+      const unsigned before = (dg[j] < RADIX) ? wcnt[wid][d] : 0u;
+      __syncwarp();
+      if (dg[j] < RADIX && rank == 0) wcnt[wid][d] = before + __popc(peers);
+      __syncwarp();
+      off[j] = before + rank;
+    }
+    __syncthreads();
+    {
+      const int d = threadIdx.x;
+      unsigned run = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        const unsigned x = wcnt[w][d];
+        wcnt[w][d] = run;
+        run += x;
+      }
+      tcnt[d] = run;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < SORT_KPT; ++j) {
+      if (dg[j] < RADIX) {
+        const unsigned pos = base[dg[j]] + wcnt[wid][dg[j]] + off[j];
+        kdst[pos] = k[j];
+        vdst[pos] = val[j];
+      }
+    }
+    __syncthreads();
+    {
+      const int d = threadIdx.x;
+      base[d] += tcnt[d];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) wcnt[w][d] = 0;
+    }
+    __syncthreads();
+  }
+}
+
+// K5: per-tile [start, end) from the sorted keys.
+__global__ void k_tile_ranges(const Batch* __restrict__ B) {
+  const Counters* c = B->ctr;
+  const long long n = c->n_keys_used;
+  const int db = c->depth_bits;
+  const unsigned long long* keys = B->keys[c->n_passes & 1];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(keys[i] >> db);
+    if (i == 0 || (int)(keys[i - 1] >> db) != t) B->ranges[t].x = (int)i;
+    if (i == n - 1 || (int)(keys[i + 1] >> db) != t) B->ranges[t].y = (int)(i + 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
+  dim3 g(P.max_pf_chunks, P.n_scenes);
+  k_prefilter_flags<<<g, PF_THREADS, 0, st>>>(dB);
+  k_prefilter_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
+  k_prefilter_compact<<<g, PF_THREADS, 0, st>>>(dB);
+  return 3;
+}
+
+int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
+  k_fwd_reset<<<64, 256, 0, st>>>(dB);
+  dim3 g(P.max_pp_chunks, P.n_views);
+  k_preprocess<<<g, PP_THREADS, 0, st>>>(dB);
+  k_preprocess_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
+  k_duplicate<<<g, PP_THREADS, 0, st>>>(dB);
+  for (int p = 0; p < P.max_passes; ++p) {
+    k_radix_hist<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB, p);
+    k_radix_rowscan<<<RADIX, SCAN_THREADS, 0, st>>>(dB, p);
+    k_radix_scatter<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB, p);
+  }
+  k_tile_ranges<<<P.range_blocks, 256, 0, st>>>(dB);
+  return 5 + 3 * P.max_passes;
+}
+
+}  // namespace tts

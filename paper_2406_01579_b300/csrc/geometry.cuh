@@ -1,0 +1,233 @@
+// Per-(view, tet) geometry shared by the preprocess kernel (which writes the
+// blend record) and the record->vertex backward kernel (which recomputes the
+// same intermediates and applies their adjoint).
+#pragma once
+
+#include "tets_internal.cuh"
+
+namespace tts {
+
+struct TetIn {
+  float3 v[4];   // world-space vertices
+  float f[4];    // vertex SDF
+  float3 c[4];   // vertex colours
+};
+
+struct Geo {
+  bool visible;
+  unsigned int zbits;      // FP32 mean camera depth (sort key)
+  float zbar;
+  int i0, i1, j0, j1;      // pixel bbox (inclusive)
+  // Pixel-scaled camera frame: xi = (fx x_c, fy y_c, z_c).  In it the ray of
+  // pixel (px, py) has the exact direction (px - cx, py - cy, 1).
+  float3 xm;               // centroid (high part of a double-float)
+  float3 y[4];             // vertex offsets from the centroid (from world differences)
+  float zr;                // reference depth
+  float3 dr;               // reference ray direction (u_r - cx, v_r - cy, 1), exact
+  float3 w;                // x_r - centroid, x_r = zr * dr (accurate: double-float centroid)
+  float3 n[4];             // outward face normals (face k opposite vertex k)
+  float e[4];              // plane offsets n . x_i (clamped away from 0)
+  float sgn[4];            // orientation sign applied to (y_j - y_i) x (y_l - y_i)
+  int slot_face[4];        // face index held by each record slot
+  int nf;                  // number of front faces
+  float3 g;                // SDF gradient in the pixel-scaled frame
+  float3 cof[3];           // cofactor columns of the edge matrix
+  float det;               // 6 * signed volume (pixel-scaled frame)
+  float fm, fr;            // SDF at the centroid and at x_r
+  float P[4], A[4], B[4];  // per slot
+};
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 rot(const float* R, float3 v) {
+  return f3(R[0] * v.x + R[1] * v.y + R[2] * v.z, R[3] * v.x + R[4] * v.y + R[5] * v.z,
+            R[6] * v.x + R[7] * v.y + R[8] * v.z);
+}
+__device__ __forceinline__ float3 rotT(const float* R, float3 v) {
+  return f3(R[0] * v.x + R[3] * v.y + R[6] * v.z, R[1] * v.x + R[4] * v.y + R[7] * v.z,
+            R[2] * v.x + R[5] * v.y + R[8] * v.z);
+}
+
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) for the
+// double-float centroid transform; explicit roundings keep them exact.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float z = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+  return {s, e};
+}
+__device__ __forceinline__ DF two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_norm(DF x) {
+  const float s = __fadd_rn(x.hi, x.lo);
+  return {s, __fsub_rn(x.lo, __fsub_rn(s, x.hi))};
+}
+// scale * (r0 a + r1 b + r2 c + t) with ~48-bit accuracy
+__device__ __forceinline__ DF df_affine(float r0, float r1, float r2, float t, float a, float b,
+                                        float c, float scale) {
+  DF acc = two_prod(r0, a);
+  DF p = two_prod(r1, b);
+  DF s = two_sum(acc.hi, p.hi);
+  acc = {s.hi, __fadd_rn(__fadd_rn(acc.lo, p.lo), s.lo)};
+  p = two_prod(r2, c);
+  s = two_sum(acc.hi, p.hi);
+  acc = {s.hi, __fadd_rn(__fadd_rn(acc.lo, p.lo), s.lo)};
+  s = two_sum(acc.hi, t);
+  acc = df_norm({s.hi, __fadd_rn(acc.lo, s.lo)});
+  p = two_prod(scale, acc.hi);
+  return df_norm({p.hi, __fmaf_rn(scale, acc.lo, p.lo)});
+}
+
+__constant__ static const int kFaceVerts[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+// The binning key path: an exact FP32 op sequence (the CPU checker replays
+// it bit for bit).  Returns false when the tet is culled (near plane or an
+// empty pixel bbox).
+__device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& G) {
+  float x[4], y[4], z[4];
+  bool cull = false;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float3 v = in.v[j];
+    x[j] = __fmaf_rn(vw.R[0], v.x, __fmaf_rn(vw.R[1], v.y, __fmaf_rn(vw.R[2], v.z, vw.t[0])));
+    y[j] = __fmaf_rn(vw.R[3], v.x, __fmaf_rn(vw.R[4], v.y, __fmaf_rn(vw.R[5], v.z, vw.t[1])));
+    z[j] = __fmaf_rn(vw.R[6], v.x, __fmaf_rn(vw.R[7], v.y, __fmaf_rn(vw.R[8], v.z, vw.t[2])));
+    cull |= !(z[j] >= vw.znear);
+  }
+  G.zbar = __fmul_rn(__fadd_rn(__fadd_rn(z[0], z[1]), __fadd_rn(z[2], z[3])), 0.25f);
+  G.zbits = __float_as_uint(G.zbar);
+  if (cull) return false;
+  float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float u = __fmaf_rn(vw.fx, __fdiv_rn(x[j], z[j]), vw.cx);
+    const float v = __fmaf_rn(vw.fy, __fdiv_rn(y[j], z[j]), vw.cy);
+    umin = fminf(umin, u); umax = fmaxf(umax, u);
+    vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+  }
+  const float i0 = fmaxf(ceilf(__fsub_rn(umin, 0.5f)), 0.f);
+  const float i1 = fminf(floorf(__fsub_rn(umax, 0.5f)), (float)(vw.W - 1));
+  const float j0 = fmaxf(ceilf(__fsub_rn(vmin, 0.5f)), 0.f);
+  const float j1 = fminf(floorf(__fsub_rn(vmax, 0.5f)), (float)(vw.H - 1));
+  if (!(i0 <= i1) || !(j0 <= j1)) return false;
+  G.i0 = (int)i0; G.i1 = (int)i1; G.j0 = (int)j0; G.j1 = (int)j1;
+  return true;
+}
+
+// Full per-(view, tet) geometry, in the pixel-scaled camera frame.  The chord
+// parametrisation is relative to the tet: vertex offsets come from world-space
+// differences and the centroid's camera position is a double-float, so the
+// offset between the tet and the reference pixel ray carries no rounding at
+// the scale of the camera distance (which the Eq. 1 steepness s would
+// amplify).
+__device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const TetIn& in, Geo& G) {
+  G.visible = key_path(vw, in, G);
+  if (!G.visible) return;
+  const float sx = vw.fx, sy = vw.fy;
+  const float3 m = 0.25f * ((in.v[0] + in.v[1]) + (in.v[2] + in.v[3]));
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float3 c = rot(vw.R, in.v[j] - m);
+    G.y[j] = f3(sx * c.x, sy * c.y, c.z);
+  }
+  const DF mx = df_affine(vw.R[0], vw.R[1], vw.R[2], vw.t[0], m.x, m.y, m.z, sx);
+  const DF my = df_affine(vw.R[3], vw.R[4], vw.R[5], vw.t[1], m.x, m.y, m.z, sy);
+  const DF mz = df_affine(vw.R[6], vw.R[7], vw.R[8], vw.t[2], m.x, m.y, m.z, 1.f);
+  G.xm = f3(mx.hi, my.hi, mz.hi);
+  // reference point: on the ray through the bbox corner pixel centre, at depth zr
+  G.zr = mz.hi;
+  G.dr = f3((float)G.i0 + 0.5f - vw.cx, (float)G.j0 + 0.5f - vw.cy, 1.f);
+  G.w = f3(__fsub_rn(__fmaf_rn(G.zr, G.dr.x, -mx.hi), mx.lo),
+           __fsub_rn(__fmaf_rn(G.zr, G.dr.y, -my.hi), my.lo), -mz.lo);
+  // edge matrix (rows y_j - y_0) and its cofactors
+  const float3 Y0 = G.y[1] - G.y[0], Y1 = G.y[2] - G.y[0], Y2 = G.y[3] - G.y[0];
+  G.cof[0] = cross3(Y1, Y2);
+  G.cof[1] = cross3(Y2, Y0);
+  G.cof[2] = cross3(Y0, Y1);
+  G.det = dot3(Y0, G.cof[0]);
+  const float l2 = fmaxf(fmaxf(dot3(Y0, Y0), dot3(Y1, Y1)), dot3(Y2, Y2));
+  if (!(fabsf(G.det) > 1e-9f * l2 * sqrtf(l2))) { G.visible = false; return; }   // flat tet
+  int nf = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int i = kFaceVerts[k][0], j = kFaceVerts[k][1], l = kFaceVerts[k][2];
+    float3 n = cross3(G.y[j] - G.y[i], G.y[l] - G.y[i]);
+    float sg = 1.f;
+    if (dot3(n, G.y[k] - G.y[i]) > 0.f) { n = -1.f * n; sg = -1.f; }
+    float e = dot3(n, G.xm) + dot3(n, G.y[i]);
+    const float emin = 1e-7f * (fabsf(n.x * G.xm.x) + fabsf(n.y * G.xm.y) + fabsf(n.z * G.xm.z));
+    if (fabsf(e) < emin) e = (e < 0.f) ? -emin : emin;
+    G.n[k] = n;
+    G.e[k] = e;
+    G.sgn[k] = sg;
+    nf += (e < 0.f);
+  }
+  G.nf = nf;
+  if (nf == 0 || nf == 4) { G.visible = false; return; }
+  int fs = 0, bs = nf;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if (G.e[k] < 0.f) G.slot_face[fs++] = k;
+    else G.slot_face[bs++] = k;
+  }
+#pragma unroll
+  for (int sl = 0; sl < 4; ++sl) {
+    const int k = G.slot_face[sl];
+    const int i = kFaceVerts[k][0];
+    const float3 n = G.n[k];
+    const float inv = 1.f / G.e[k];
+    G.P[sl] = dot3(n, G.w - G.y[i]) * inv;
+    G.A[sl] = G.zr * n.x * inv;
+    G.B[sl] = G.zr * n.y * inv;
+  }
+  // affine SDF: gradient g from the edge system, value at the reference point
+  const float d1 = in.f[1] - in.f[0], d2 = in.f[2] - in.f[0], d3 = in.f[3] - in.f[0];
+  const float idet = 1.f / G.det;
+  G.g = idet * (d1 * G.cof[0] + d2 * G.cof[1] + d3 * G.cof[2]);
+  G.fm = 0.25f * ((in.f[0] + in.f[1]) + (in.f[2] + in.f[3]));
+  G.fr = G.fm + dot3(G.g, G.w);
+  (void)s;
+}
+
+__device__ __forceinline__ void write_record(const ViewD& vw, float s, const TetIn& in, const Geo& G,
+                                             float4* __restrict__ out) {
+  (void)vw;
+  const float bx = (float)G.i0 + 0.5f, by = (float)G.j0 + 0.5f;
+  out[0] = make_float4((G.nf >= 2) ? -bx : bx, (G.nf >= 3) ? -by : by, (float)G.i1 + 0.5f,
+                       (float)G.j1 + 0.5f);
+  out[1] = make_float4(G.P[0], G.P[1], G.P[2], G.P[3]);
+  out[2] = make_float4(G.A[0], G.A[1], G.A[2], G.A[3]);
+  out[3] = make_float4(G.B[0], G.B[1], G.B[2], G.B[3]);
+  const float sz = s * G.zr;
+  const float F = s * G.fr;
+  const float K0 = sz * dot3(G.g, G.dr);
+  out[4] = make_float4(F, K0, sz * G.g.x, sz * G.g.y);
+  const float3 c = 0.25f * ((in.c[0] + in.c[1]) + (in.c[2] + in.c[3]));
+  out[5] = make_float4(G.zbar, c.x, c.y, c.z);
+}
+
+__device__ __forceinline__ void load_tet(const SceneD& S, int tet, TetIn& in) {
+  const int4 t = __ldg(&S.T[tet]);
+  const int id[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float* v = S.V + 3ll * id[j];
+    in.v[j] = f3(__ldg(v), __ldg(v + 1), __ldg(v + 2));
+    in.f[j] = __ldg(S.f + id[j]);
+    const float* c = S.rgb + 3ll * id[j];
+    in.c[j] = f3(__ldg(c), __ldg(c + 1), __ldg(c + 2));
+  }
+}
+
+}  // namespace tts

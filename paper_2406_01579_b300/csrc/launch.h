@@ -1,0 +1,37 @@
+// Host-side launch plan shared by the kernel translation units and the API.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "tets_internal.cuh"
+
+namespace tts {
+
+struct HostPlan {
+  int n_scenes, n_views;
+  int max_pf_chunks, max_pp_chunks;
+  int sort_blocks, max_passes;
+  int range_blocks;
+  int total_tiles;
+  int tile;
+  int tet_bwd_blocks;
+  long long total_pixels;
+};
+
+struct GradOut {
+  float* dV[TTS_MAX_SCENES];
+  float* df[TTS_MAX_SCENES];
+  float* drgb[TTS_MAX_SCENES];
+};
+
+// Each launcher returns the number of kernels it launched.
+int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st);
+int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st);
+int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
+                     cudaStream_t st);
+int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
+                     const float* ddepth, cudaStream_t st);
+int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
+int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);
+
+}  // namespace tts

@@ -1,0 +1,203 @@
+// Internal device-side definitions of libtets: the batch descriptor, the
+// workspace counters, the per-(view, tet) record and the chord/opacity
+// evaluation shared by the forward and backward blend kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tets.h"
+
+namespace tts {
+
+constexpr int PF_CHUNK = 4096;      // tets per pre-filter block
+constexpr int PF_THREADS = 256;
+constexpr int PP_CHUNK = 512;       // survivors per preprocess / duplicate block
+constexpr int PP_THREADS = 256;
+constexpr int RADIX_BITS = 8;
+constexpr int RADIX = 1 << RADIX_BITS;
+constexpr int MAX_PASSES = 8;       // 64-bit keys
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_KPT = 8;         // keys per thread per tile
+constexpr int SORT_TILE = SORT_THREADS * SORT_KPT;
+constexpr int SCAN_THREADS = 1024;
+
+// Counters at the start of the workspace (after the descriptor).
+struct Counters {
+  unsigned int status;
+  unsigned int zmin_bits;   // min over all views of the FP32 mean depth bits
+  unsigned int zmax_bits;
+  int depth_bits;           // bits of (zbits - zmin_bits)
+  int total_bits;           // depth_bits + tile_bits
+  int n_passes;             // radix passes actually needed
+  long long n_keys;         // keys produced (may exceed capacity: then overflow)
+  long long n_keys_used;    // keys the sort and blend see (0 on overflow)
+  int n_surv[TTS_MAX_SCENES];
+  int pad[16];
+};
+
+struct SceneD {
+  const float* V;
+  const int4* T;
+  const float* f;
+  const float* rgb;
+  long long N, K;
+  long long surv_off;       // into the survivor buffer
+  long long surv_cap;
+  long long flag_off;       // into the pre-filter flag buffer
+  int pf_chunk_base;        // first pre-filter block-sum slot
+  int pf_chunks;
+  int view_off, view_cnt;   // this scene's views in Batch::scene_views
+};
+
+struct ViewD {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy, znear;
+  int W, H, tiles_x, tiles_y;
+  int scene;
+  int tile_base;            // first global tile id
+  long long pix_base;       // first output pixel
+  long long rec_base;       // first record slot
+  int pp_chunk_base;        // first preprocess block-sum slot
+  int pp_chunks;
+};
+
+struct Batch {
+  int n_scenes, n_views;
+  int total_tiles, tile_bits;
+  int pf_chunks_total, pp_chunks_total;
+  int max_pf_chunks, max_pp_chunks;
+  float s, prefilter_thresh, alpha_skip, alpha_cap, t_eps;
+  int tile, flags;
+  int sort_blocks;
+  long long key_cap;
+  long long total_pixels;
+  long long total_slots;
+  // workspace regions
+  Counters* ctr;
+  int* pf_blocksum;         // [pf_chunks_total]
+  unsigned char* pf_flags;  // [sum K]
+  int* surv;                // [sum surv_cap]
+  unsigned int* rec_z;      // [slots] FP32 mean depth bits
+  int* rec_nt;              // [slots] tiles overlapped (0: culled)
+  int4* rec_rect;           // [slots] tile rect (tx0, tx1, ty0, ty1)
+  float4* rec;              // [slots * 6]
+  float4* rec_grad;         // [slots * 6]
+  long long* pp_blocksum;   // [pp_chunks_total]
+  unsigned long long* keys[2];
+  unsigned int* vals[2];
+  unsigned int* hist;       // [RADIX * sort_blocks]
+  int2* ranges;             // [total_tiles]
+  float* pix_T;             // [total_pixels]
+  int* pix_last;            // [total_pixels]
+  int* pix_nfrag;           // [total_pixels]
+  SceneD sc[TTS_MAX_SCENES];
+  ViewD vw[TTS_MAX_VIEWS];
+  int scene_views[TTS_MAX_VIEWS];
+};
+
+// ---------------------------------------------------------------------------
+// Record: 6 float4 per (view, survivor) slot.
+//   q0  bbox (+-(i0+.5), +-(j0+.5), i1+.5, j1+.5) in pixel-centre units; the
+//       sign of .x / .y says whether face slot 1 / 2 is a front face
+//       (negative: front).  Slot 0 is always front, slot 3 always back.
+//   q1  P_k, q2  A_k, q3  B_k  for face slots k = 0..3.  With the pixel offset
+//       (dx, dy) from the bbox corner pixel centre (i0+.5, j0+.5),
+//       rho_k = 1 + P_k + A_k dx + B_k dy = z_r / t_k where t_k is the depth at
+//       which the pixel ray meets face k's plane and z_r a per-tet reference
+//       depth.  Entry: min rho over front faces; exit: max rho over back faces.
+//   q4  (F, K0, Kx, Ky) = (s f(x_r), s g.x_r, s z_r g_x / fx, s z_r g_y / fy)
+//       for the tet's affine SDF f(x) with gradient g and the reference point
+//       x_r = z_r * ray(i0+.5, j0+.5).  Along the pixel ray, with
+//       lin = Kx dx + Ky dy:  s f(t) = (F + lin) + (K0 + lin) (t - z_r) / z_r.
+//   q5  (zbar, r, g, b): mean vertex depth (Eq. 2 depth) and mean colour.
+// The record gradient buffer has the same layout (q0 unused).
+// ---------------------------------------------------------------------------
+constexpr int REC_Q = 6;
+
+struct Chord {
+  bool hit;
+  int kin, kout;      // face slots binding the entry and the exit
+  float p_in, p_out;  // rho - 1 at entry and exit
+  float dx, dy;
+};
+
+// Everything below uses explicitly rounded intrinsics so that the forward
+// and the backward (which recomputes each fragment) agree bit for bit.
+__device__ __forceinline__ Chord chord_eval(const float4& q0, const float4& q1,
+                                            const float4& q2, const float4& q3,
+                                            float px, float py) {
+  Chord c;
+  c.dx = __fsub_rn(px, fabsf(q0.x));
+  c.dy = __fsub_rn(py, fabsf(q0.y));
+  const float p0 = __fmaf_rn(q2.x, c.dx, __fmaf_rn(q3.x, c.dy, q1.x));
+  const float p1 = __fmaf_rn(q2.y, c.dx, __fmaf_rn(q3.y, c.dy, q1.y));
+  const float p2 = __fmaf_rn(q2.z, c.dx, __fmaf_rn(q3.z, c.dy, q1.z));
+  const float p3 = __fmaf_rn(q2.w, c.dx, __fmaf_rn(q3.w, c.dy, q1.w));
+  float pin = p0, pout = p3;
+  int kin = 0, kout = 3;
+  if (q0.x < 0.f) {
+    if (p1 < pin) { pin = p1; kin = 1; }
+  } else {
+    if (p1 > pout) { pout = p1; kout = 1; }
+  }
+  if (q0.y < 0.f) {
+    if (p2 < pin) { pin = p2; kin = 2; }
+  } else {
+    if (p2 > pout) { pout = p2; kout = 2; }
+  }
+  const bool inside = (c.dx >= 0.f) & (c.dy >= 0.f) & (px <= q0.z) & (py <= q0.w);
+  c.hit = inside & (pin > pout) & (pout > -1.f);
+  c.p_in = pin;
+  c.p_out = pout;
+  c.kin = kin;
+  c.kout = kout;
+  return c;
+}
+
+struct Opacity {
+  float alpha;
+  float x, y;         // s (f_prev - f_next) and s f_next
+  float e1, B;        // exp(-x) and sigmoid(-y)
+  float r, rho_in, rho_out, sGz;
+};
+
+// Eq. 1 in the rewrite -expm1(-s (f_prev - f_next)) * sigmoid(-s f_next),
+// 0 unless f_prev > f_next.  The chord geometry (App. A.2's depths) enters
+// through rho_in, rho_out: t_in = z_r / rho_in, t_out = z_r / rho_out.
+__device__ __forceinline__ Opacity opacity_eval(const float4& q4, const Chord& c) {
+  Opacity o;
+  o.rho_in = __fadd_rn(1.f, c.p_in);
+  o.rho_out = __fadd_rn(1.f, c.p_out);
+  o.r = __frcp_rn(__fmul_rn(o.rho_in, o.rho_out));
+  const float lin = __fmaf_rn(q4.z, c.dx, __fmul_rn(q4.w, c.dy));
+  const float sF0 = __fadd_rn(q4.x, lin);
+  o.sGz = __fadd_rn(q4.y, lin);
+  // x = s (f_prev - f_next) = sGz (p_out - p_in) / (rho_in rho_out)
+  o.x = __fmul_rn(__fmul_rn(o.sGz, __fsub_rn(c.p_out, c.p_in)), o.r);
+  // y = s f_next = sF0 - sGz p_out / rho_out
+  o.y = __fmaf_rn(-__fmul_rn(o.sGz, c.p_out), __fmul_rn(o.rho_in, o.r), sF0);
+  if (o.x > 0.f) {
+    o.e1 = __expf(-fminf(o.x, 80.f));
+    const float e2 = __expf(fminf(o.y, 80.f));
+    o.B = __frcp_rn(__fadd_rn(1.f, e2));
+    o.alpha = __fmul_rn(__fsub_rn(1.f, o.e1), o.B);
+  } else {
+    o.e1 = 1.f;
+    o.B = 0.f;
+    o.alpha = 0.f;
+  }
+  return o;
+}
+
+__device__ __forceinline__ void set_status(Counters* c, unsigned int bit) {
+  atomicOr(&c->status, bit);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch wrappers (one per kernel group)
+// ---------------------------------------------------------------------------
+struct HostBatch;  // host mirror, defined in tets_api.cu
+
+}  // namespace tts

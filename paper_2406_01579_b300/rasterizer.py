@@ -1,0 +1,338 @@
+"""Python front end of libtets: device memory and streams come from PyTorch,
+every step of the rasterizer runs in the CUDA kernels behind the C ABI.
+
+``Rasterizer`` owns the workspace for one batch shape (scenes x views) and
+exposes prepare / forward / backward.  ``TetRender`` is the autograd
+Function over it, and ``render`` the one-call convenience for a single
+scene.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+from typing import Sequence
+
+import torch
+
+from . import _lib
+from ._lib import (TTS_FLAG_ACCUM_GRAD, TTS_FLAG_PURE, TTS_STATUS_BAD_INDEX,
+                   TTS_STATUS_KEY_OVERFLOW, TTS_STATUS_SURV_OVERFLOW, TetsError, check)
+
+
+@dataclasses.dataclass
+class Params:
+    """Rasterizer parameters.  ``s`` is the Eq. 1 steepness; the thresholds
+    are the 3DGS blending constants and the Sec. 3.2 pre-filter T_f."""
+    s: float = 175.0
+    tile: int = 16
+    pure: bool = False
+    prefilter_thresh: float = 1.0 / 255.0
+    alpha_skip: float = 1.0 / 255.0
+    alpha_cap: float = 0.99
+    t_eps: float = 1e-4
+    accum_grad: bool = False
+
+    def to_c(self) -> _lib.tts_params:
+        p = _lib.tts_params()
+        p.s = self.s
+        p.prefilter_thresh = self.prefilter_thresh
+        p.alpha_skip = self.alpha_skip
+        p.alpha_cap = self.alpha_cap
+        p.t_eps = self.t_eps
+        p.tile = self.tile
+        p.flags = (TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
+        p.reserved = 0
+        return p
+
+
+def make_camera(cam) -> _lib.tts_camera:
+    """From any object with R (3x3), t (3), fx, fy, cx, cy, znear, width, height."""
+    c = _lib.tts_camera()
+    R = [float(x) for x in _flat(cam.R)]
+    t = [float(x) for x in _flat(cam.t)]
+    for i in range(9):
+        c.R[i] = R[i]
+    for i in range(3):
+        c.t[i] = t[i]
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.znear = float(cam.znear)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def _flat(a):
+    if hasattr(a, "reshape"):
+        return a.reshape(-1).tolist()
+    out = []
+    for x in a:
+        out.extend(_flat(x) if hasattr(x, "__len__") else [x])
+    return out
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclasses.dataclass
+class SceneTensors:
+    V: torch.Tensor      # N x 3 float32
+    T: torch.Tensor      # K x 4 int32
+    f: torch.Tensor      # N float32
+    rgb: torch.Tensor    # N x 3 float32
+
+    def check(self):
+        for name, x, dt in (("V", self.V, torch.float32), ("T", self.T, torch.int32),
+                            ("f", self.f, torch.float32), ("rgb", self.rgb, torch.float32)):
+            if not x.is_cuda:
+                raise TetsError(f"{name} must be a CUDA tensor")
+            if x.dtype != dt or not x.is_contiguous():
+                raise TetsError(f"{name} must be contiguous {dt}")
+        N = self.V.shape[0]
+        if self.V.shape != (N, 3) or self.f.shape != (N,) or self.rgb.shape != (N, 3):
+            raise TetsError("V, f, rgb must be N x 3, N, N x 3")
+        if self.T.dim() != 2 or self.T.shape[1] != 4:
+            raise TetsError("T must be K x 4")
+
+
+class Rasterizer:
+    """Workspace + calls for one batch: ``scenes`` (SceneTensors) and
+    ``views`` as (camera, scene index) pairs."""
+
+    def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, params: Params,
+                 key_capacity: int | None = None, surv_capacity: Sequence[int] | None = None,
+                 device=None):
+        self.lib = _lib.load()
+        self.params = params
+        self.device = torch.device(device) if device is not None else scenes[0].V.device
+        self.views = [(c, int(s)) for c, s in views]
+        self.set_scenes(scenes)
+        K = [int(s.T.shape[0]) for s in self.scenes]
+        self.surv_capacity = list(surv_capacity) if surv_capacity is not None else K
+        if key_capacity is None:
+            key_capacity = sum(max(65536, K[s] // 3) for _, s in self.views)
+        self.key_capacity = int(key_capacity)
+        self.ws = None
+        self.ws_bytes = 0
+        self._c_views = (_lib.tts_view * len(self.views))()
+        for i, (cam, s) in enumerate(self.views):
+            self._c_views[i].cam = make_camera(cam)
+            self._c_views[i].scene = s
+            self._c_views[i].reserved = 0
+        self.pix_off = []
+        off = 0
+        for cam, _ in self.views:
+            self.pix_off.append(off)
+            off += int(cam.width) * int(cam.height)
+        self.total_pixels = off
+        self._alloc()
+
+    # -- batch / workspace -------------------------------------------------
+    def set_scenes(self, scenes: Sequence[SceneTensors]):
+        for s in scenes:
+            s.check()
+        self.scenes = list(scenes)
+        self._c_scenes = (_lib.tts_scene * len(self.scenes))()
+        caps = getattr(self, "surv_capacity", None)
+        for i, s in enumerate(self.scenes):
+            c = self._c_scenes[i]
+            c.V, c.T, c.f, c.rgb = (s.V.data_ptr(), s.T.data_ptr(), s.f.data_ptr(),
+                                    s.rgb.data_ptr())
+            c.N, c.K = s.V.shape[0], s.T.shape[0]
+            c.surv_capacity = caps[i] if caps is not None else 0
+
+    def batch(self) -> _lib.tts_batch:
+        b = _lib.tts_batch()
+        for i, cap in enumerate(self.surv_capacity):
+            self._c_scenes[i].surv_capacity = int(cap)
+        b.scenes = ctypes.cast(self._c_scenes, ctypes.POINTER(_lib.tts_scene))
+        b.n_scenes = len(self.scenes)
+        b.views = ctypes.cast(self._c_views, ctypes.POINTER(_lib.tts_view))
+        b.n_views = len(self.views)
+        b.params = self.params.to_c()
+        b.key_capacity = self.key_capacity
+        b.workspace = self.ws.data_ptr() if self.ws is not None else None
+        b.workspace_bytes = self.ws_bytes
+        return b
+
+    def workspace_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        b = self.batch()
+        check(self.lib.tts_workspace_size(ctypes.byref(b), ctypes.byref(n)), "tts_workspace_size")
+        return int(n.value)
+
+    def _alloc(self):
+        self.ws = None
+        nbytes = self.workspace_bytes()
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.ws_bytes = nbytes
+        b = self.batch()
+        check(self.lib.tts_workspace_init(ctypes.byref(b), _stream_ptr()), "tts_workspace_init")
+
+    # -- calls ------------------------------------------------------------
+    def prepare(self):
+        b = self.batch()
+        check(self.lib.tts_prepare_scene(ctypes.byref(b), _stream_ptr()), "tts_prepare_scene")
+
+    def _outputs(self):
+        dev = self.device
+        img = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=dev)
+        alpha = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
+        depth = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
+        return img, alpha, depth
+
+    def forward_raw(self, out=None):
+        """Enqueue the forward (no synchronisation, no capacity check)."""
+        img, alpha, depth = out if out is not None else self._outputs()
+        b = self.batch()
+        check(self.lib.tts_render_fwd(ctypes.byref(b), img.data_ptr(), alpha.data_ptr(),
+                                      depth.data_ptr(), _stream_ptr()), "tts_render_fwd")
+        return img, alpha, depth
+
+    def forward(self, prepare: bool = True, check_status: bool = True, out=None):
+        """prepare (optional) + forward; with ``check_status`` the status word
+        is read (one stream sync) and capacities grow and the call is re-run
+        when a capacity was exceeded."""
+        for _ in range(4):
+            if prepare:
+                self.prepare()
+            res = self.forward_raw(out)
+            if not check_status:
+                return res
+            info = self.info()
+            if info.status & TTS_STATUS_BAD_INDEX:
+                raise TetsError("a tet index is outside [0, N)")
+            grow = False
+            if info.status & TTS_STATUS_SURV_OVERFLOW:
+                self.surv_capacity = [int(s.T.shape[0]) for s in self.scenes]
+                grow = True
+            if info.status & TTS_STATUS_KEY_OVERFLOW:
+                self.key_capacity = int(math.ceil(info.n_keys * 1.25)) + 1024
+                grow = True
+            if not grow:
+                return res
+            self._alloc()
+            prepare = True
+        raise TetsError("capacity growth did not converge")
+
+    def shrink_to_fit(self, slack: float = 1.25):
+        """Resize survivor and key capacities to the last forward's counts
+        (times ``slack``).  Re-run prepare + forward afterwards."""
+        info = self.info()
+        self.surv_capacity = [min(int(s.T.shape[0]), int(math.ceil(info.n_surv[i] * slack)) + 1024)
+                              for i, s in enumerate(self.scenes)]
+        self.key_capacity = int(math.ceil(max(info.n_keys, 1) * slack)) + 4096
+        self._alloc()
+
+    def backward(self, dimage, dalpha=None, ddepth=None, grads=None):
+        """Gradients of the last forward; returns [(dV, df, drgb)] per scene."""
+        dev = self.device
+        if grads is None:
+            grads = [(torch.empty_like(s.V), torch.empty_like(s.f), torch.empty_like(s.rgb))
+                     for s in self.scenes]
+        n = len(self.scenes)
+        dV = (ctypes.c_void_p * n)(*[g[0].data_ptr() for g in grads])
+        df = (ctypes.c_void_p * n)(*[g[1].data_ptr() for g in grads])
+        dc = (ctypes.c_void_p * n)(*[g[2].data_ptr() for g in grads])
+        dimage = dimage.contiguous()
+        da = dalpha.contiguous() if dalpha is not None else None
+        dd = ddepth.contiguous() if ddepth is not None else None
+        b = self.batch()
+        check(self.lib.tts_render_bwd(ctypes.byref(b), dimage.data_ptr(),
+                                      da.data_ptr() if da is not None else None,
+                                      dd.data_ptr() if dd is not None else None,
+                                      dV, df, dc, _stream_ptr()), "tts_render_bwd")
+        del dev
+        return grads
+
+    def info(self) -> _lib.tts_info:
+        info = _lib.tts_info()
+        b = self.batch()
+        check(self.lib.tts_get_info(ctypes.byref(b), ctypes.byref(info), _stream_ptr()),
+              "tts_get_info")
+        return info
+
+    # -- inspection -------------------------------------------------------
+    def _ws_slice(self, ptr: int, nbytes: int, dtype) -> torch.Tensor:
+        off = ptr - self.ws.data_ptr()
+        assert 0 <= off and off + nbytes <= self.ws_bytes
+        return self.ws[off:off + nbytes].view(dtype)
+
+    def debug_lists(self):
+        """Sorted keys (int64 view of the uint64 keys), values (int32 slot),
+        ranges (total_tiles x 2), survivors (scene 0), zmin_bits, depth_bits."""
+        P = ctypes.c_void_p
+        k, v, r, s = P(), P(), P(), P()
+        zmin = ctypes.c_uint32()
+        db = ctypes.c_int32()
+        b = self.batch()
+        check(self.lib.tts_debug_lists(ctypes.byref(b), ctypes.byref(k), ctypes.byref(v),
+                                       ctypes.byref(r), ctypes.byref(s), ctypes.byref(zmin),
+                                       ctypes.byref(db), _stream_ptr()), "tts_debug_lists")
+        info = self.info()
+        n = int(info.n_keys)
+        tiles = sum(((int(c.width) + self.params.tile - 1) // self.params.tile) *
+                    ((int(c.height) + self.params.tile - 1) // self.params.tile)
+                    for c, _ in self.views)
+        keys = self._ws_slice(k.value, 8 * n, torch.int64) if n else torch.zeros(0, dtype=torch.int64)
+        vals = self._ws_slice(v.value, 4 * n, torch.int32) if n else torch.zeros(0, dtype=torch.int32)
+        ranges = self._ws_slice(r.value, 8 * tiles, torch.int32).view(tiles, 2)
+        surv = [self._ws_slice(s.value, 4 * int(self.surv_capacity[0]), torch.int32)[:int(info.n_surv[0])]]
+        return dict(keys=keys, vals=vals, ranges=ranges, surv=surv, zmin_bits=int(zmin.value),
+                    depth_bits=int(db.value), n_keys=n, info=info)
+
+    def view_outputs(self, img, alpha, depth):
+        """Split flat outputs into per-view (3,H,W), (H,W), (H,W) tensors."""
+        out = []
+        for (cam, _), off in zip(self.views, self.pix_off):
+            H, W = int(cam.height), int(cam.width)
+            out.append((img[3 * off:3 * off + 3 * H * W].view(3, H, W),
+                        alpha[off:off + H * W].view(H, W), depth[off:off + H * W].view(H, W)))
+        return out
+
+
+class TetRender(torch.autograd.Function):
+    """(V, f, rgb) -> (image, alpha, depth) for the views of a single-scene
+    ``Rasterizer``; outputs are flat view-major planar tensors."""
+
+    @staticmethod
+    def forward(ctx, V, f, rgb, raster: Rasterizer, check_status: bool = True):
+        sc = raster.scenes[0]
+        if V.data_ptr() != sc.V.data_ptr() or f.data_ptr() != sc.f.data_ptr() or \
+                rgb.data_ptr() != sc.rgb.data_ptr():
+            raster.set_scenes([SceneTensors(V.detach(), sc.T, f.detach(), rgb.detach())])
+        img, alpha, depth = raster.forward(prepare=True, check_status=check_status)
+        ctx.raster = raster
+        return img, alpha, depth
+
+    @staticmethod
+    def backward(ctx, gimg, galpha, gdepth):
+        raster = ctx.raster
+        gimg = gimg if gimg is not None else torch.zeros(3 * raster.total_pixels, device=raster.device)
+        (dV, df, drgb), = raster.backward(gimg, galpha, gdepth)
+        return dV, df, drgb, None, None
+
+
+_cache: dict = {}
+
+
+def render(V, T, f, rgb, cams, params: Params | None = None, check_status: bool = True):
+    """Renders the views ``cams`` of one scene and returns a list of
+    (image (3,H,W), alpha (H,W), depth (H,W)) per view; differentiable with
+    respect to V, f and rgb."""
+    params = params or Params()
+    key = (tuple(V.shape), tuple(T.shape), T.data_ptr(), len(cams),
+           tuple((int(c.width), int(c.height)) for c in cams), dataclasses.astuple(params))
+    raster = _cache.get(key)
+    if raster is None:
+        raster = Rasterizer([SceneTensors(V.detach(), T, f.detach(), rgb.detach())],
+                            [(c, 0) for c in cams], params)
+        _cache.clear()
+        _cache[key] = raster
+    else:
+        for i, c in enumerate(cams):
+            raster._c_views[i].cam = make_camera(c)
+    img, alpha, depth = TetRender.apply(V, f, rgb, raster, check_status)
+    return raster.view_outputs(img, alpha, depth)

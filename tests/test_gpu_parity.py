@@ -1,0 +1,253 @@
+"""Parity of the CUDA path (called through the C ABI) with the oracle.
+
+Sizes: the 16^3 sphere at 128^2 (several tiles, ragged tail views), the 64^3
+torus at 512^2 and the 128^3 three-sphere scene at 4 x 512^2 (the benchmark's
+workload, in the launch configuration the benchmark times).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors
+from parity import (GRAD_TOL, IMG_TOL, compare_images, compare_keys, gpu_run, grad_rel_err,
+                    masked_upstream, oracle_run, to_dev)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sphere16():
+    return synth.scene_sphere16()
+
+
+def _check_view(gpu, orc, name=""):
+    bad, namb, emax, multi = compare_images(gpu, orc)
+    npx = orc["alpha"].size
+    assert bad == 0, f"{name}: {bad} pixels off by > {IMG_TOL} (max unambiguous err {emax})"
+    assert multi <= max(2, 1e-4 * npx), f"{name}: {multi} multi-band pixels unmatched"
+    assert namb <= 0.1 * npx, f"{name}: {namb} band pixels"
+    return emax
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+@pytest.mark.parametrize("s", [20.0, 175.0, 620.0])
+def test_sphere16_keys_and_image(sphere16, tile, s):
+    p = Params(s=s, tile=tile)
+    cam = sphere16.cams[0]
+    gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
+    orc = oracle_run(sphere16, cam, p)
+    n = compare_keys(gpu, orc)
+    assert n > 1000
+    _check_view(gpu["views"][0], orc, f"tile{tile} s{s}")
+
+
+def test_sphere16_pure_mode(sphere16):
+    p = Params(s=20.0, tile=16, pure=True)
+    cam = sphere16.cams[0]
+    gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
+    orc = oracle_run(sphere16, cam, p)
+    compare_keys(gpu, orc)
+    assert orc["amb"].sum() == 0
+    _check_view(gpu["views"][0], orc, "pure")
+
+
+@pytest.mark.parametrize("s", [20.0, 175.0])
+def test_sphere16_gradients(sphere16, s):
+    p = Params(s=s, tile=16)
+    cam = sphere16.cams[0]
+    up0 = synth.upstream_grads(0, [cam])[0]
+    orc0 = oracle_run(sphere16, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(sphere16, cam, p, upstream=up)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
+    dV, df, drgb = gpu["grads"][0]
+    for name, g, o in (("dV", dV, orc["dV"]), ("df", df, orc["df"]), ("drgb", drgb, orc["drgb"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
+
+
+def test_gradients_pure_small_grids():
+    for n, s in ((2, 3.0), (4, 6.0)):
+        V = synth.grid_vertices(n)
+        T = synth.grid_tets(n)
+        f = (np.linalg.norm(V, axis=1) - 0.6 + 0.05 * V[:, 0]).astype(np.float32)
+        rgb = np.random.default_rng(n).uniform(size=(len(V), 3)).astype(np.float32)
+        cam = synth.orbit_camera(33.0, 21.0, 40, 40)
+        p = Params(s=s, tile=8, pure=True)
+        up = synth.upstream_grads(30 + n, [cam])[0]
+        orc = oracle_run((V, T, f, rgb), cam, p, upstream=up)
+        gpu = gpu_run([(V, T, f, rgb)], [(cam, 0)], p, upstream=[up])
+        _check_view(gpu["views"][0], orc, f"pure{n}")
+        for g, o in zip(gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
+            err = grad_rel_err(g, o)
+            assert err < GRAD_TOL, f"pure{n}: rel err {err:.3e}"
+
+
+def test_batch_of_views_and_scenes_matches_single_views(sphere16):
+    """Several scenes and views of uneven sizes (ragged tiles) in one call."""
+    rng = np.random.default_rng(5)
+    sc2 = synth.Scene(8, *synth.random_scene(rng, 8, "torus")[:4], [], "torus8")
+    cams = [synth.orbit_camera(30.0, 20.0, 128, 128), synth.random_camera(rng, 77, 53),
+            synth.random_camera(rng, 200, 96), synth.random_camera(rng, 33, 130)]
+    views = [(cams[0], 0), (cams[1], 1), (cams[2], 0), (cams[3], 1)]
+    p = Params(s=60.0, tile=16)
+    scenes = [sphere16, sc2]
+    ups = synth.upstream_grads(9, cams)
+    orcs = [oracle_run(scenes[si], c, p) for c, si in views]
+    ups = [masked_upstream(u, o["amb"]) for u, o in zip(ups, orcs)]
+    gpu = gpu_run(scenes, views, p, upstream=ups)
+    for i, ((c, si), o) in enumerate(zip(views, orcs)):
+        _check_view(gpu["views"][i], o, f"view{i}")
+    # gradients: sum over each scene's views
+    for si, sc in enumerate(scenes):
+        acc = [np.zeros((sc.N, 3)), np.zeros(sc.N), np.zeros((sc.N, 3))]
+        for (c, sj), u in zip(views, ups):
+            if sj != si:
+                continue
+            o = oracle_run(sc, c, p, upstream=u)
+            acc[0] += o["dV"]; acc[1] += o["df"]; acc[2] += o["drgb"]
+        for g, o in zip(gpu["grads"][si], acc):
+            err = grad_rel_err(g, o)
+            assert err < GRAD_TOL, f"scene{si}: rel err {err:.3e}"
+
+
+def test_empty_and_degenerate_inputs(sphere16):
+    p = Params(s=175.0, tile=16)
+    # all tets pre-filtered away: transparent image
+    f = np.full(sphere16.N, 2.0, np.float32)
+    sc = (sphere16.V, sphere16.T, f, sphere16.rgb)
+    gpu = gpu_run([sc], [(sphere16.cams[0], 0)], p, lists=True)
+    assert gpu["info"].n_surv[0] == 0 and gpu["info"].n_keys == 0
+    for x in gpu["views"][0]:
+        assert np.all(x == 0.0)
+    # camera looking away: everything culled
+    cam = synth.look_at_camera((0.0, 0.0, 2.5), 64, 64, target=(0.0, 0.0, 5.0))
+    gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
+    assert gpu["info"].n_keys == 0
+    assert np.all(gpu["views"][0][1] == 0.0)
+    # one-pixel image
+    cam = synth.orbit_camera(30.0, 20.0, 1, 1)
+    gpu = gpu_run([sphere16], [(cam, 0)], p)
+    orc = oracle_run(sphere16, cam, p)
+    _check_view(gpu["views"][0], orc, "1px")
+
+
+def test_bad_index_sets_status(sphere16):
+    T = sphere16.T.copy()
+    T[5, 2] = sphere16.N + 7
+    st = to_dev((sphere16.V, T, sphere16.f, sphere16.rgb))
+    r = Rasterizer([st], [(sphere16.cams[0], 0)], Params())
+    r.prepare()
+    r.forward_raw()
+    info = r.info()
+    assert info.status & 1
+
+
+def test_key_capacity_overflow_grows_and_matches(sphere16):
+    st = to_dev(sphere16)
+    p = Params(s=175.0, tile=8)
+    r = Rasterizer([st], [(sphere16.cams[0], 0)], p, key_capacity=16)
+    img, alpha, depth = r.forward()
+    assert r.key_capacity > 16
+    orc = oracle_run(sphere16, sphere16.cams[0], p)
+    gv = [x.cpu().numpy() for x in r.view_outputs(img, alpha, depth)[0]]
+    _check_view(gv, orc, "regrown")
+
+
+def test_repeat_calls_are_deterministic(sphere16):
+    st = to_dev(sphere16)
+    r = Rasterizer([st], [(sphere16.cams[0], 0)], Params())
+    a = [x.clone() for x in r.forward()]
+    b = r.forward()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.fixture(scope="module")
+def torus64():
+    return synth.scene_torus64()
+
+
+def test_torus64_full_size(torus64):
+    p = Params(s=175.0, tile=16)
+    cam = torus64.cams[0]
+    gpu = gpu_run([torus64], [(cam, 0)], p, lists=True)
+    orc = oracle_run(torus64, cam, p)
+    n = compare_keys(gpu, orc)
+    assert n > 100000
+    _check_view(gpu["views"][0], orc, "torus64")
+
+
+def test_torus64_gradients(torus64):
+    p = Params(s=175.0, tile=16)
+    cam = torus64.cams[0]
+    up0 = synth.upstream_grads(1, [cam])[0]
+    orc0 = oracle_run(torus64, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(torus64, cam, p, upstream=up)
+    gpu = gpu_run([torus64], [(cam, 0)], p, upstream=[up])
+    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
+
+
+@pytest.fixture(scope="module")
+def spheres128():
+    return synth.scene_spheres128()
+
+
+def test_spheres128_bench_workload(spheres128):
+    """The benchmark's configuration: 128^3 grid, 4 views at 512^2, s = 175,
+    one batched call.  Keys are compared bit for bit per view; images pixel
+    by pixel."""
+    p = Params(s=175.0, tile=16)
+    sc = spheres128
+    views = [(c, 0) for c in sc.cams]
+    gpu = gpu_run([sc], views, p, lists=True)
+    r = gpu["raster"]
+    lists = gpu["lists"]
+    keys = lists["keys"].view(np.uint64)
+    db = lists["depth_bits"]
+    gtile = (keys >> np.uint64(db)).astype(np.int64)
+    tiles_per_view = (512 // 16) ** 2
+    for vi, cam in enumerate(sc.cams):
+        orc = oracle_run(sc, cam, p)
+        sel = (gtile >= vi * tiles_per_view) & (gtile < (vi + 1) * tiles_per_view)
+        sub = dict(lists)
+        sub["keys"] = lists["keys"][sel]
+        sub["vals"] = lists["vals"][sel]
+        rec_base = vi * int(r.surv_capacity[0])
+        t_g = gtile[sel] - vi * tiles_per_view
+        z_g = ((keys[sel] & np.uint64((1 << db) - 1)).astype(np.int64) + lists["zmin_bits"]).astype(np.uint32)
+        id_g = gpu["surv"][lists["vals"][sel].astype(np.int64) - rec_base]
+        b = orc["bins"]
+        band = np.nonzero(orc["amb_tets"])[0]
+        kg = ~np.isin(id_g, band)
+        ko = ~np.isin(orc["surv"][b["key_val"]], band)
+        np.testing.assert_array_equal(t_g[kg], b["key_tile"][ko])
+        np.testing.assert_array_equal(z_g[kg], b["key_z"][ko])
+        np.testing.assert_array_equal(id_g[kg], orc["surv"][b["key_val"]][ko])
+        _check_view(gpu["views"][vi], orc, f"spheres128 view{vi}")
+
+
+def test_spheres128_subgrid_gradients(spheres128):
+    """Gradients on the 4^3 sub-grid (cubes [62,66)^3) against the oracle and
+    against central finite differences of the oracle."""
+    sub = synth.subgrid(spheres128, 62, 66)
+    p = Params(s=175.0, tile=16)
+    for cam in sub.cams:
+        up0 = synth.upstream_grads(2, [cam])[0]
+        orc0 = oracle_run(sub, cam, p)
+        if orc0["alpha"].max() == 0:
+            continue
+        up = masked_upstream(up0, orc0["amb"])
+        orc = oracle_run(sub, cam, p, upstream=up)
+        gpu = gpu_run([sub], [(cam, 0)], p, upstream=[up])
+        _check_view(gpu["views"][0], orc0, "sub")
+        for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0],
+                              (orc["dV"], orc["df"], orc["drgb"])):
+            err = grad_rel_err(g, o)
+            assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
