@@ -212,6 +212,24 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
  * notes) and to the per-slot survivor-relative tet index order. */
 int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
 
+/* Sorts n (key, value) pairs by the low key_bits bits of the key, stably
+ * (the LSD radix sort used for tile binning), without allocating anything.
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory themselves (code inside a host callback or an
+ * allocator hook, plugin hosts that own every device allocation, loops that
+ * cannot take cudaMalloc's implicit synchronisation).  keys_in/vals_in are
+ * read only; keys_out/vals_out (device, n each) receive the sorted pairs and
+ * must not alias the inputs.  Temporary storage is a fixed array of about
+ * 12.3 MiB compiled into the library, present on every device that loads it
+ * until the process exits, and shared by all calls: calls whose work overlaps
+ * on the GPU race.  The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make it before any stream capture.  Returns
+ * TTS_ERR_ARG for n > TTS_SORT_NOALLOC_MAX_KEYS, key_bits outside [1, 64] or
+ * aliasing outputs, before anything is enqueued. */
+#define TTS_SORT_NOALLOC_MAX_KEYS (1 << 20)
+int tts_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                           uint32_t* vals_out, int64_t n, int32_t key_bits, tts_stream stream);
+
 const char* tts_error_string(int code);
 
 /* Library version and the GPU architecture it was built for. */

@@ -27,6 +27,7 @@ TTS_FLAG_ACCUM_GRAD = 2
 
 TTS_MAX_SCENES = 64
 TTS_MAX_VIEWS = 128
+TTS_SORT_NOALLOC_MAX_KEYS = 1 << 20
 
 
 class tts_camera(ctypes.Structure):
@@ -68,7 +69,8 @@ class tts_info(ctypes.Structure):
 ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene", "tts_render_fwd",
                 "tts_render_bwd", "tts_bin_views", "tts_blend_fwd", "tts_blend_bwd",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
-                "tts_debug_lists", "tts_debug_records", "tts_error_string", "tts_version")
+                "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
+                "tts_error_string", "tts_version")
 
 _lib = None
 
@@ -105,6 +107,7 @@ def load():
                                   ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint32),
                                   ctypes.POINTER(ctypes.c_int32), P]
     L.tts_debug_records.argtypes = [B, ctypes.POINTER(P), P]
+    L.tts_sort_pairs_noalloc.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int32, P]
     L.tts_error_string.argtypes = [ctypes.c_int]
     L.tts_error_string.restype = ctypes.c_char_p
     L.tts_version.argtypes = []
