@@ -186,6 +186,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_v1 = take(sizeof(unsigned) * cap);
   const size_t o_hist = take(sizeof(unsigned) * RADIX * (B.sort_blocks + 1));
   const size_t o_rng = take(sizeof(int2) * tiles);
+  const size_t o_wl = take(sizeof(int) * tiles);
   const size_t o_pT = take(sizeof(float) * pix);
   const size_t o_pL = take(sizeof(int) * pix);
   const size_t o_pN = take(sizeof(int) * pix);
@@ -211,6 +212,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.vals[1] = reinterpret_cast<unsigned*>(base + o_v1);
     B.hist = reinterpret_cast<unsigned*>(base + o_hist);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
+    B.worklist = reinterpret_cast<int*>(base + o_wl);
     B.pix_T = reinterpret_cast<float*>(base + o_pT);
     B.pix_last = reinterpret_cast<int*>(base + o_pL);
     B.pix_nfrag = reinterpret_cast<int*>(base + o_pN);
@@ -226,6 +228,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.total_tiles = tiles;
   H.tile = pr.tile;
   H.tet_bwd_blocks = 2 * sm_count();
+  blend_grid(pr.tile, sm_count(), &H.blend_fwd_blocks, &H.blend_bwd_blocks);
   H.total_pixels = pix;
   return TTS_OK;
 }

@@ -53,6 +53,8 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->n_keys = 0;
     c->n_keys_used = 0;
     c->status &= ~(unsigned)TTS_STATUS_KEY_OVERFLOW;
+    c->work_fwd = c->work_bwd = 0u;
+    c->done_fwd = c->done_bwd = 0u;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
     B->ranges[t] = make_int2(0, 0);
@@ -445,6 +447,32 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
   }
 }
 
+// Work list for the persistent blend kernels: tiles in decreasing order of
+// list length (bucketed by bit length), so the longest lists start first.
+__global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __restrict__ B) {
+  __shared__ int cnt[33], off[33];
+  if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int nt = B->total_tiles;
+  for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
+    const int2 r = B->ranges[t];
+    const int len = r.y - r.x;
+    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int b = 32; b >= 0; --b) { off[b] = run; run += cnt[b]; }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
+    const int2 r = B->ranges[t];
+    const int len = r.y - r.x;
+    const int pos = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], 1);
+    B->worklist[pos] = t;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -468,7 +496,8 @@ int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
     k_radix_scatter<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB, p);
   }
   k_tile_ranges<<<P.range_blocks, 256, 0, st>>>(dB);
-  return 5 + 3 * P.max_passes;
+  k_build_worklist<<<1, SCAN_THREADS, 0, st>>>(dB);
+  return 6 + 3 * P.max_passes;
 }
 
 }  // namespace tts

@@ -5,7 +5,8 @@
 
 namespace tts {
 
-constexpr int BLEND_BATCH = 256;   // records staged in shared memory per round
+constexpr int WPB = 4;              // warps per block of the persistent blend kernels
+constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int find_view(const Batch* __restrict__ B, int gt) {
   int lo = 0, hi = B->n_views - 1;
@@ -16,254 +17,333 @@ __device__ __forceinline__ int find_view(const Batch* __restrict__ B, int gt) {
   return lo;
 }
 
-// Pixel of this thread inside the tile: warps cover 8x4 pixel blocks.
-template <int TILE>
-struct PixelMap {
-  int px, py;
-  float wx0, wx1, wy0, wy1;  // warp's pixel-centre rectangle
-  __device__ __forceinline__ PixelMap(int txi, int tyi) {
-    constexpr int WX = TILE / 8;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int wx = wid % WX, wy = wid / WX;
-    const int bx = txi * TILE + wx * 8, by = tyi * TILE + wy * 4;
-    px = bx + (lane & 7);
-    py = by + (lane >> 3);
-    wx0 = (float)bx + 0.5f;
-    wx1 = wx0 + 7.f;
-    wy0 = (float)by + 0.5f;
-    wy1 = wy0 + 3.f;
+// Next work item for this warp from a global queue.
+__device__ __forceinline__ int next_item(unsigned* counter) {
+  int it = 0;
+  if ((threadIdx.x & 31) == 0) it = (int)atomicAdd(counter, 1u);
+  return __shfl_sync(FULL, it, 0);
+}
+
+// The last warp to leave resets the queue so the next launch starts at 0.
+__device__ __forceinline__ void queue_done(unsigned* counter, unsigned* done) {
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence();
+    const unsigned total = gridDim.x * (blockDim.x >> 5);
+    if (atomicAdd(done, 1u) == total - 1u) {
+      *counter = 0u;
+      *done = 0u;
+      __threadfence();
+    }
   }
-  __device__ __forceinline__ bool warp_misses(const float4& q0) const {
+}
+
+// A warp's work item: one 8x4 pixel block of one tile, lanes row-major.
+struct WarpBlock {
+  int gt;
+  int px, py;
+  bool inimg;
+  float fpx, fpy;
+  float wx0, wx1, wy0, wy1;   // the block's pixel-centre rectangle
+  __device__ __forceinline__ bool misses(const float4& q0) const {
     return (fabsf(q0.x) > wx1) | (q0.z < wx0) | (fabsf(q0.y) > wy1) | (q0.w < wy0);
   }
 };
 
+template <int TILE>
+__device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
+                                                    WarpBlock& wb) {
+  constexpr int SBX = TILE / 8, SB = SBX * (TILE / 4);
+  wb.gt = B->worklist[item / SB];
+  const int sb = item - (item / SB) * SB;
+  const ViewD& vw = B->vw[find_view(B, wb.gt)];
+  const int lt = wb.gt - vw.tile_base;
+  const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
+  const int bx = txi * TILE + (sb % SBX) * 8, by = tyi * TILE + (sb / SBX) * 4;
+  const int lane = threadIdx.x & 31;
+  wb.px = bx + (lane & 7);
+  wb.py = by + (lane >> 3);
+  wb.inimg = (wb.px < vw.W) & (wb.py < vw.H);
+  wb.fpx = (float)wb.px + 0.5f;
+  wb.fpy = (float)wb.py + 0.5f;
+  wb.wx0 = (float)bx + 0.5f;
+  wb.wx1 = wb.wx0 + 7.f;
+  wb.wy0 = (float)by + 0.5f;
+  wb.wy1 = wb.wy0 + 3.f;
+  return vw;
+}
+
 // ---------------------------------------------------------------------------
-// K6: forward blend.  One CTA per (view, tile), one thread per pixel.
+// K6: forward blend.  Persistent warps; each takes 8x4 pixel blocks of tiles
+// from a queue (longest tile lists first), scans the tile's list 32 entries
+// at a time, keeps (ballot) the entries whose bbox meets the block, stages
+// their records in its own shared-memory slice and blends them front to back
+// (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions).
 // ---------------------------------------------------------------------------
 template <int TILE>
-__global__ void __launch_bounds__(TILE * TILE) k_blend_fwd(const Batch* __restrict__ B,
-                                                           float* __restrict__ image,
-                                                           float* __restrict__ alpha,
-                                                           float* __restrict__ depth) {
-  constexpr int NT = TILE * TILE;
-  __shared__ float4 sm[REC_Q][BLEND_BATCH];
-  const int gt = blockIdx.x;
-  const ViewD& vw = B->vw[find_view(B, gt)];
-  const int lt = gt - vw.tile_base;
-  const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
-  const PixelMap<TILE> pm(txi, tyi);
-  const bool inimg = (pm.px < vw.W) & (pm.py < vw.H);
-  const float fpx = (float)pm.px + 0.5f, fpy = (float)pm.py + 0.5f;
-  const Counters* c = B->ctr;
-  const int2 rg = B->ranges[gt];
+__global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict__ B,
+                                                       float* __restrict__ image,
+                                                       float* __restrict__ alpha,
+                                                       float* __restrict__ depth) {
+  constexpr int SB = (TILE / 8) * (TILE / 4);
+  __shared__ float4 st[WPB][REC_Q][32];
+  __shared__ int sidx[WPB][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
+  Counters* c = B->ctr;
   const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
   const float4* __restrict__ rec = B->rec;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
-  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
-  int last = 0, nfrag = 0;
-  bool done = !inimg;
-  for (int base = rg.x; base < rg.y; base += BLEND_BATCH) {
-    if (__syncthreads_count(!done) == 0) break;
-    const int n = min(BLEND_BATCH, rg.y - base);
-    for (int i = threadIdx.x; i < n; i += NT) {
-      const float4* r = rec + (size_t)vals[base + i] * REC_Q;
+  const int total = B->total_tiles * SB;
+  for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
+    WarpBlock wb;
+    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    if (!__any_sync(FULL, wb.inimg)) continue;
+    const int2 rg = B->ranges[wb.gt];
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    int last = 0, nfrag = 0;
+    bool done = !wb.inimg;
+    // one group of lookahead on (slot, bbox)
+    int idx = rg.x + lane;
+    unsigned slot = (idx < rg.y) ? vals[idx] : 0u;
+    float4 q0 = (idx < rg.y) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
+    unsigned slot_n = (idx + 32 < rg.y) ? vals[idx + 32] : 0u;
+    for (int g = rg.x; g < rg.y; g += 32) {
+      if (__all_sync(FULL, done)) break;
+      const int idn = g + 32 + lane;
+      const float4 q0_n = (idn < rg.y) ? __ldg(rec + (size_t)slot_n * REC_Q)
+                                       : make_float4(0.f, 0.f, -1.f, -1.f);
+      const unsigned slot_nn = (idn + 32 < rg.y) ? vals[idn + 32] : 0u;
+      const bool ov = (g + lane < rg.y) && !wb.misses(q0);
+      const unsigned m = __ballot_sync(FULL, ov);
+      if (m != 0u) {
+        if (ov) {
+          const int pos = __popc(m & ltm);
+          const float4* r = rec + (size_t)slot * REC_Q;
+          st[wid][0][pos] = q0;
 #pragma unroll
-      for (int q = 0; q < REC_Q; ++q) sm[q][i] = __ldg(r + q);
-    }
-    __syncthreads();
-    if (!done) {
-      for (int j = 0; j < n; ++j) {
-        const float4 q0 = sm[0][j];
-        if (pm.warp_misses(q0)) continue;
-        const Chord ch = chord_eval(q0, sm[1][j], sm[2][j], sm[3][j], fpx, fpy);
-        if (!ch.hit) continue;
-        ++nfrag;
-        const Opacity o = opacity_eval(sm[4][j], ch);
-        float a = o.alpha;
-        if (!pure) {
-          a = fminf(a, cap);
-          if (a < skip) continue;
-        } else if (!(a > 0.f)) {
-          continue;
+          for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+          sidx[wid][pos] = lane;
         }
-        const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
-        if (!pure && Tn < eps) { done = true; break; }
-        const float4 q5 = sm[5][j];
-        const float wgt = __fmul_rn(T, a);
-        C0 = __fmaf_rn(wgt, q5.y, C0);
-        C1 = __fmaf_rn(wgt, q5.z, C1);
-        C2 = __fmaf_rn(wgt, q5.w, C2);
-        D = __fmaf_rn(wgt, q5.x, D);
-        T = Tn;
-        last = base + j - rg.x + 1;
+        __syncwarp();
+        const int cnt = __popc(m);
+        for (int k = 0; k < cnt; ++k) {
+          if (!done) {
+            const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k],
+                                        st[wid][3][k], wb.fpx, wb.fpy);
+            if (ch.hit) {
+              ++nfrag;
+              const Opacity o = opacity_eval(st[wid][4][k], ch);
+              float a = o.alpha;
+              bool use = true;
+              if (!pure) {
+                a = fminf(a, cap);
+                use = a >= skip;
+              } else {
+                use = a > 0.f;
+              }
+              if (use) {
+                const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+                if (!pure && Tn < eps) {
+                  done = true;
+                } else {
+                  const float4 q5 = st[wid][5][k];
+                  const float wgt = __fmul_rn(T, a);
+                  C0 = __fmaf_rn(wgt, q5.y, C0);
+                  C1 = __fmaf_rn(wgt, q5.z, C1);
+                  C2 = __fmaf_rn(wgt, q5.w, C2);
+                  D = __fmaf_rn(wgt, q5.x, D);
+                  T = Tn;
+                  last = g - rg.x + sidx[wid][k] + 1;
+                }
+              }
+            }
+          }
+          if (__all_sync(FULL, done)) break;
+        }
+        __syncwarp();
       }
+      slot = slot_n;
+      q0 = q0_n;
+      slot_n = slot_nn;
+    }
+    if (wb.inimg) {
+      const long long HW = (long long)vw.W * vw.H;
+      const long long p = (long long)wb.py * vw.W + wb.px;
+      image[3 * vw.pix_base + p] = C0;
+      image[3 * vw.pix_base + HW + p] = C1;
+      image[3 * vw.pix_base + 2 * HW + p] = C2;
+      alpha[vw.pix_base + p] = 1.f - T;
+      depth[vw.pix_base + p] = D;
+      B->pix_T[vw.pix_base + p] = T;
+      B->pix_last[vw.pix_base + p] = last;
+      B->pix_nfrag[vw.pix_base + p] = nfrag;
     }
   }
-  if (inimg) {
-    const long long HW = (long long)vw.W * vw.H;
-    const long long p = (long long)pm.py * vw.W + pm.px;
-    image[3 * vw.pix_base + p] = C0;
-    image[3 * vw.pix_base + HW + p] = C1;
-    image[3 * vw.pix_base + 2 * HW + p] = C2;
-    alpha[vw.pix_base + p] = 1.f - T;
-    depth[vw.pix_base + p] = D;
-    B->pix_T[vw.pix_base + p] = T;
-    B->pix_last[vw.pix_base + p] = last;
-    B->pix_nfrag[vw.pix_base + p] = nfrag;
-  }
+  queue_done(&c->work_fwd, &c->done_fwd);
 }
 
 // ---------------------------------------------------------------------------
-// K7: backward blend.  Re-walks each tile's list back to front from the last
-// blended entry, recomputing every fragment bit for bit, and accumulates the
-// gradient of the record fields (warp-reduced, one vector atomic per field
-// group and warp) into the per-slot record gradient buffer.
+// K7: backward blend.  Same warp blocks; each warp re-walks its tile's list
+// back to front from the last entry any of its pixels blended, recomputes
+// every fragment bit for bit, and accumulates the record-field gradients
+// (warp-reduced; one vector atomic per field group) into the per-slot record
+// gradient buffer.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
   return v;
 }
 
 template <int TILE>
-__global__ void __launch_bounds__(TILE * TILE) k_blend_bwd(const Batch* __restrict__ B,
-                                                           const float* __restrict__ dimage,
-                                                           const float* __restrict__ dalpha,
-                                                           const float* __restrict__ ddepth) {
-  constexpr int NT = TILE * TILE;
-  __shared__ float4 sm[REC_Q][BLEND_BATCH];
-  __shared__ unsigned sslot[BLEND_BATCH];
-  __shared__ int smax;
-  const int gt = blockIdx.x;
-  const ViewD& vw = B->vw[find_view(B, gt)];
-  const int lt = gt - vw.tile_base;
-  const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
-  const PixelMap<TILE> pm(txi, tyi);
-  const bool inimg = (pm.px < vw.W) & (pm.py < vw.H);
-  const float fpx = (float)pm.px + 0.5f, fpy = (float)pm.py + 0.5f;
-  const Counters* c = B->ctr;
-  const int2 rg = B->ranges[gt];
+__global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict__ B,
+                                                       const float* __restrict__ dimage,
+                                                       const float* __restrict__ dalpha,
+                                                       const float* __restrict__ ddepth) {
+  constexpr int SB = (TILE / 8) * (TILE / 4);
+  __shared__ float4 st[WPB][REC_Q][32];
+  __shared__ int sidx[WPB][32];
+  __shared__ unsigned sslot[WPB][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
+  Counters* c = B->ctr;
   const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
   const float4* __restrict__ rec = B->rec;
   float4* __restrict__ rgrad = B->rec_grad;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip;
-  const long long HW = (long long)vw.W * vw.H;
-  const long long p = (long long)pm.py * vw.W + pm.px;
-  float Tfin = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gO = 0.f, gD = 0.f;
-  int last = 0;
-  if (inimg) {
-    Tfin = B->pix_T[vw.pix_base + p];
-    last = B->pix_last[vw.pix_base + p];
-    gC0 = dimage[3 * vw.pix_base + p];
-    gC1 = dimage[3 * vw.pix_base + HW + p];
-    gC2 = dimage[3 * vw.pix_base + 2 * HW + p];
-    if (dalpha) gO = dalpha[vw.pix_base + p];
-    if (ddepth) gD = ddepth[vw.pix_base + p];
-  }
-  if (threadIdx.x == 0) smax = 0;
-  __syncthreads();
-  if (last > 0) atomicMax(&smax, last);
-  __syncthreads();
-  const int maxlast = smax;
-  float T = Tfin, S = 0.f;
-  const float gOT = gO * Tfin;
-  const int lane = threadIdx.x & 31;
-  for (int top = rg.x + maxlast; top > rg.x; top -= BLEND_BATCH) {
-    const int base = max(rg.x, top - BLEND_BATCH);
-    const int n = top - base;
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += NT) {
-      const unsigned slot = vals[base + i];
-      sslot[i] = slot;
-      const float4* r = rec + (size_t)slot * REC_Q;
-#pragma unroll
-      for (int q = 0; q < REC_Q; ++q) sm[q][i] = __ldg(r + q);
+  const int total = B->total_tiles * SB;
+  for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
+    WarpBlock wb;
+    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    const int2 rg = B->ranges[wb.gt];
+    const long long HW = (long long)vw.W * vw.H;
+    const long long p = (long long)wb.py * vw.W + wb.px;
+    float Tfin = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gO = 0.f, gD = 0.f;
+    int last = 0;
+    if (wb.inimg) {
+      Tfin = B->pix_T[vw.pix_base + p];
+      last = B->pix_last[vw.pix_base + p];
+      gC0 = dimage[3 * vw.pix_base + p];
+      gC1 = dimage[3 * vw.pix_base + HW + p];
+      gC2 = dimage[3 * vw.pix_base + 2 * HW + p];
+      if (dalpha) gO = dalpha[vw.pix_base + p];
+      if (ddepth) gD = ddepth[vw.pix_base + p];
     }
-    __syncthreads();
-    for (int j = n - 1; j >= 0; --j) {
-      const bool active = (base + j - rg.x) < last;
-      const float4 q0 = sm[0][j];
-      if (pm.warp_misses(q0)) continue;
-      if (!__any_sync(0xffffffffu, active)) continue;
-      const Chord ch = chord_eval(q0, sm[1][j], sm[2][j], sm[3][j], fpx, fpy);
-      bool contrib = active & ch.hit;
-      Opacity o;
-      float a = 0.f;
-      if (contrib) {
-        o = opacity_eval(sm[4][j], ch);
-        a = pure ? o.alpha : fminf(o.alpha, cap);
-        contrib = pure ? (a > 0.f) : (a >= skip);
-      }
-      float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
-      float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
-      if (contrib) {
-        const float4 q5 = sm[5][j];
-        const float om = __fsub_rn(1.f, a);
-        const float Ti = __fdiv_rn(T, om);
-        const float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
-        const float dLda = Ti * wv - (S - gOT) / om;
-        S += Ti * a * wv;
-        T = Ti;
-        const float wgt = Ti * a;
-        gz = wgt * gD;
-        gc0 = wgt * gC0;
-        gc1 = wgt * gC1;
-        gc2 = wgt * gC2;
-        const bool clamped = !pure && (o.alpha > cap);
-        if (!clamped) {
-          // alpha = (1 - e1) B with x = s (f_prev - f_next), y = s f_next
-          const float dx = dLda * o.e1 * o.B;
-          const float dy = -dLda * o.alpha * (1.f - o.B);
-          const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
-          const float dpin = -dx * o.sGz * iin * iin;
-          const float dpout = (dx - dy) * o.sGz * iout * iout;
-          const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
+    int maxlast = last;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float dp = (k == ch.kin) ? dpin : ((k == ch.kout) ? dpout : 0.f);
-            gP[k] = dp;
-            gA[k] = dp * ch.dx;
-            gB[k] = dp * ch.dy;
-          }
-          gF = dy;
-          gK0 = dsGz;
-          gKx = (dy + dsGz) * ch.dx;
-          gKy = (dy + dsGz) * ch.dy;
-        }
+    for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(FULL, maxlast, o));
+    if (maxlast == 0) continue;
+    float T = Tfin, S = 0.f;
+    const float gOT = gO * Tfin;
+    const int top = rg.x + maxlast;
+    for (int ge = top; ge > rg.x; ge -= 32) {
+      const int g0 = max(rg.x, ge - 32);
+      const int idx = g0 + lane;
+      bool ov = false;
+      unsigned slot = 0u;
+      float4 q0;
+      if (idx < ge) {
+        slot = vals[idx];
+        q0 = __ldg(rec + (size_t)slot * REC_Q);
+        ov = !wb.misses(q0);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, contrib);
+      const unsigned m = __ballot_sync(FULL, ov);
       if (m == 0u) continue;
-      float4* dst = rgrad + (size_t)sslot[j] * REC_Q;
-      if (__popc(m) == 1) {
-        if (contrib) {
-          atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-          atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-          atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-          atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-          atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
-        }
-      } else {
+      if (ov) {
+        const int pos = __popc(m & ltm);
+        const float4* r = rec + (size_t)slot * REC_Q;
+        st[wid][0][pos] = q0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          gP[k] = warp_sum(gP[k]);
-          gA[k] = warp_sum(gA[k]);
-          gB[k] = warp_sum(gB[k]);
+        for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+        sidx[wid][pos] = lane;
+        sslot[wid][pos] = slot;
+      }
+      __syncwarp();
+      for (int k = __popc(m) - 1; k >= 0; --k) {
+        const bool active = (g0 + sidx[wid][k] - rg.x) < last;
+        if (!__any_sync(FULL, active)) continue;
+        const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k], st[wid][3][k],
+                                    wb.fpx, wb.fpy);
+        bool contrib = active & ch.hit;
+        Opacity o;
+        float a = 0.f;
+        if (contrib) {
+          o = opacity_eval(st[wid][4][k], ch);
+          a = pure ? o.alpha : fminf(o.alpha, cap);
+          contrib = pure ? (a > 0.f) : (a >= skip);
         }
-        gF = warp_sum(gF); gK0 = warp_sum(gK0); gKx = warp_sum(gKx); gKy = warp_sum(gKy);
-        gz = warp_sum(gz); gc0 = warp_sum(gc0); gc1 = warp_sum(gc1); gc2 = warp_sum(gc2);
-        if (lane == 0) {
-          atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-          atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-          atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-          atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-          atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+        const unsigned mc = __ballot_sync(FULL, contrib);
+        if (mc == 0u) continue;
+        float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
+        float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+        if (contrib) {
+          const float4 q5 = st[wid][5][k];
+          const float om = __fsub_rn(1.f, a);
+          const float Ti = __fdiv_rn(T, om);
+          const float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+          const float dLda = Ti * wv - (S - gOT) / om;
+          S += Ti * a * wv;
+          T = Ti;
+          const float wgt = Ti * a;
+          gz = wgt * gD;
+          gc0 = wgt * gC0;
+          gc1 = wgt * gC1;
+          gc2 = wgt * gC2;
+          const bool clamped = !pure && (o.alpha > cap);
+          if (!clamped) {
+            // alpha = (1 - e1) B with x = s (f_prev - f_next), y = s f_next
+            const float dx = dLda * o.e1 * o.B;
+            const float dy = -dLda * o.alpha * (1.f - o.B);
+            const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
+            const float dpin = -dx * o.sGz * iin * iin;
+            const float dpout = (dx - dy) * o.sGz * iout * iout;
+            const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
+              gP[q] = dp;
+              gA[q] = dp * ch.dx;
+              gB[q] = dp * ch.dy;
+            }
+            gF = dy;
+            gK0 = dsGz;
+            gKx = (dy + dsGz) * ch.dx;
+            gKy = (dy + dsGz) * ch.dy;
+          }
+        }
+        float4* dst = rgrad + (size_t)sslot[wid][k] * REC_Q;
+        if (__popc(mc) == 1) {
+          if (contrib) {
+            atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
+            atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
+            atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
+            atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
+            atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            gP[q] = warp_sum(gP[q]);
+            gA[q] = warp_sum(gA[q]);
+            gB[q] = warp_sum(gB[q]);
+          }
+          gF = warp_sum(gF); gK0 = warp_sum(gK0); gKx = warp_sum(gKx); gKy = warp_sum(gKy);
+          gz = warp_sum(gz); gc0 = warp_sum(gc0); gc1 = warp_sum(gc1); gc2 = warp_sum(gc2);
+          if (lane == 0) {
+            atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
+            atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
+            atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
+            atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
+            atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+          }
         }
       }
+      __syncwarp();
     }
   }
+  queue_done(&c->work_bwd, &c->done_bwd);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,22 +466,61 @@ __global__ void __launch_bounds__(256) k_tet_bwd(const Batch* __restrict__ B, Gr
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+template <typename K>
+static int occ_blocks(K kern, int sms) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, WPB * 32, 0) != cudaSuccess || per < 1)
+    per = 4;
+  return per * sms;
+}
+
+void blend_grid(int tile, int sms, int* fwd_blocks, int* bwd_blocks) {
+  static int cache[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  const int ti = (tile == 8) ? 0 : (tile == 16) ? 1 : 2;
+  if (cache[ti][0] > 0) {
+    *fwd_blocks = cache[ti][0];
+    *bwd_blocks = cache[ti][1];
+    return;
+  }
+  switch (tile) {
+    case 8:
+      *fwd_blocks = occ_blocks(k_blend_fwd<8>, sms);
+      *bwd_blocks = occ_blocks(k_blend_bwd<8>, sms);
+      break;
+    case 16:
+      *fwd_blocks = occ_blocks(k_blend_fwd<16>, sms);
+      *bwd_blocks = occ_blocks(k_blend_bwd<16>, sms);
+      break;
+    default:
+      *fwd_blocks = occ_blocks(k_blend_fwd<32>, sms);
+      *bwd_blocks = occ_blocks(k_blend_bwd<32>, sms);
+      break;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cache[ti][0] = *fwd_blocks;
+    cache[ti][1] = *bwd_blocks;
+  }
+}
+
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      cudaStream_t st) {
+  const int g = P.blend_fwd_blocks;
   switch (P.tile) {
-    case 8: k_blend_fwd<8><<<P.total_tiles, 64, 0, st>>>(dB, image, alpha, depth); break;
-    case 16: k_blend_fwd<16><<<P.total_tiles, 256, 0, st>>>(dB, image, alpha, depth); break;
-    default: k_blend_fwd<32><<<P.total_tiles, 1024, 0, st>>>(dB, image, alpha, depth); break;
+    case 8: k_blend_fwd<8><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+    case 16: k_blend_fwd<16><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+    default: k_blend_fwd<32><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
   }
   return 1;
 }
 
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                      const float* ddepth, cudaStream_t st) {
+  const int g = P.blend_bwd_blocks;
   switch (P.tile) {
-    case 8: k_blend_bwd<8><<<P.total_tiles, 64, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-    case 16: k_blend_bwd<16><<<P.total_tiles, 256, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-    default: k_blend_bwd<32><<<P.total_tiles, 1024, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+    case 8: k_blend_bwd<8><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+    case 16: k_blend_bwd<16><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+    default: k_blend_bwd<32><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
   }
   return 1;
 }

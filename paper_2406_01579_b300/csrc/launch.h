@@ -15,6 +15,7 @@ struct HostPlan {
   int total_tiles;
   int tile;
   int tet_bwd_blocks;
+  int blend_fwd_blocks, blend_bwd_blocks;
   long long total_pixels;
 };
 
@@ -33,5 +34,7 @@ int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, co
                      const float* ddepth, cudaStream_t st);
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);
+// persistent grid sizes of the blend kernels for a tile size (occupancy based)
+void blend_grid(int tile, int sms, int* fwd_blocks, int* bwd_blocks);
 
 }  // namespace tts

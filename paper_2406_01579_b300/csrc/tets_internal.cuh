@@ -33,7 +33,9 @@ struct Counters {
   long long n_keys;         // keys produced (may exceed capacity: then overflow)
   long long n_keys_used;    // keys the sort and blend see (0 on overflow)
   int n_surv[TTS_MAX_SCENES];
-  int pad[16];
+  unsigned int work_fwd, work_bwd;      // persistent blend work queues
+  unsigned int done_fwd, done_bwd;      // warps finished (last one resets)
+  int pad[12];
 };
 
 struct SceneD {
@@ -89,6 +91,7 @@ struct Batch {
   unsigned int* vals[2];
   unsigned int* hist;       // [RADIX * sort_blocks]
   int2* ranges;             // [total_tiles]
+  int* worklist;            // [total_tiles] tiles by decreasing list length
   float* pix_T;             // [total_pixels]
   int* pix_last;            // [total_pixels]
   int* pix_nfrag;           // [total_pixels]
