@@ -47,6 +47,22 @@ struct WarpBlock {
   __device__ __forceinline__ bool misses(const float4& q0) const {
     return (fabsf(q0.x) > wx1) | (q0.z < wx0) | (fabsf(q0.y) > wy1) | (q0.w < wy0);
   }
+  // Shrink the test rectangle to the pixels of the lanes in `live`: an entry
+  // whose bbox misses all of them cannot produce a fragment for any lane that
+  // still needs one.  Returns false when no lane is live.
+  __device__ __forceinline__ bool cull_to(bool live) {
+    const unsigned big = 0x7fffffffu;
+    const unsigned x0 = __reduce_min_sync(FULL, live ? (unsigned)px : big);
+    if (x0 == big) return false;
+    const unsigned x1 = __reduce_max_sync(FULL, live ? (unsigned)px : 0u);
+    const unsigned y0 = __reduce_min_sync(FULL, live ? (unsigned)py : big);
+    const unsigned y1 = __reduce_max_sync(FULL, live ? (unsigned)py : 0u);
+    wx0 = (float)x0 + 0.5f;
+    wx1 = (float)x1 + 0.5f;
+    wy0 = (float)y0 + 0.5f;
+    wy1 = (float)y1 + 0.5f;
+    return true;
+  }
 };
 
 template <int TILE>
@@ -109,7 +125,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
     float4 q0 = (idx < rg.y) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
     unsigned slot_n = (idx + 32 < rg.y) ? vals[idx + 32] : 0u;
     for (int g = rg.x; g < rg.y; g += 32) {
-      if (__all_sync(FULL, done)) break;
+      if (!wb.cull_to(!done)) break;
       const int idn = g + 32 + lane;
       const float4 q0_n = (idn < rg.y) ? __ldg(rec + (size_t)slot_n * REC_Q)
                                        : make_float4(0.f, 0.f, -1.f, -1.f);
@@ -240,6 +256,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
     const int top = rg.x + maxlast;
     for (int ge = top; ge > rg.x; ge -= 32) {
       const int g0 = max(rg.x, ge - 32);
+      if (!wb.cull_to(last > g0 - rg.x)) continue;
       const int idx = g0 + lane;
       bool ov = false;
       unsigned slot = 0u;
