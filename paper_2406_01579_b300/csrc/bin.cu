@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __r
   constexpr int NW = SORT_THREADS / 32;
   __shared__ unsigned base[RADIX];
   __shared__ unsigned wcnt[NW][RADIX];
-  __shared__ unsigned tcnt[RADIX];
+  __shared__ unsigned tstart[RADIX];
+  __shared__ unsigned long long sk[SORT_TILE];
+  __shared__ unsigned sv[SORT_TILE];
   // digit base = (exclusive scan of digit totals) + this block's row prefix
   {
     const int d = threadIdx.x;  // SORT_THREADS == RADIX
@@ -375,6 +377,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __r
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   for (long long t0 = lo; t0 < hi; t0 += SORT_TILE) {
+    const int tn = (int)min((long long)SORT_TILE, hi - t0);
     unsigned long long k[SORT_KPT];
     unsigned val[SORT_KPT];
     unsigned dg[SORT_KPT];
@@ -402,6 +405,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __r
       off[j] = before + rank;
     }
     __syncthreads();
+    unsigned tcnt;
     {
       const int d = threadIdx.x;
       unsigned run = 0;
@@ -411,21 +415,32 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __r
         wcnt[w][d] = run;
         run += x;
       }
-      tcnt[d] = run;
+      tcnt = run;
+      unsigned t;
+      tstart[d] = block_excl_scan<unsigned, SORT_THREADS>(run, &t);
     }
     __syncthreads();
+    // stage the tile in digit order, then write each digit's run contiguously
 #pragma unroll
     for (int j = 0; j < SORT_KPT; ++j) {
       if (dg[j] < RADIX) {
-        const unsigned pos = base[dg[j]] + wcnt[wid][dg[j]] + off[j];
-        kdst[pos] = k[j];
-        vdst[pos] = val[j];
+        const unsigned lp = tstart[dg[j]] + wcnt[wid][dg[j]] + off[j];
+        sk[lp] = k[j];
+        sv[lp] = val[j];
       }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < tn; q += SORT_THREADS) {
+      const unsigned long long key = sk[q];
+      const unsigned d = (unsigned)(key >> sh) & (RADIX - 1);
+      const unsigned pos = base[d] + (unsigned)q - tstart[d];
+      kdst[pos] = key;
+      vdst[pos] = sv[q];
     }
     __syncthreads();
     {
       const int d = threadIdx.x;
-      base[d] += tcnt[d];
+      base[d] += tcnt;
 #pragma unroll
       for (int w = 0; w < NW; ++w) wcnt[w][d] = 0;
     }

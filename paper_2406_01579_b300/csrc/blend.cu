@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
 // The reference point x_r (ray through the bbox corner pixel at the centroid
 // depth) is held constant: the fragment opacity does not depend on it.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
+__global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int nsurv = B->ctr->n_surv[s];
@@ -416,11 +416,13 @@ __global__ void __launch_bounds__(256) k_tet_bwd(const Batch* __restrict__ B, Gr
       // m = n / e, F = s f(x_r), K0 = s z_r g.d_r, Kx = s z_r g_x, Ky = s z_r g_y.
       const float3 xr = G.zr * G.dr;
 #pragma unroll
-      for (int sl = 0; sl < 4; ++sl) {
-        const int fk = G.slot_face[sl];
+      for (int fk = 0; fk < 4; ++fk) {
+        const int sl = G.slot_of[fk];
+        const float gP = (sl == 0) ? gPs[0] : (sl == 1) ? gPs[1] : (sl == 2) ? gPs[2] : gPs[3];
+        const float gA = (sl == 0) ? gAs[0] : (sl == 1) ? gAs[1] : (sl == 2) ? gAs[2] : gAs[3];
+        const float gB = (sl == 0) ? gBs[0] : (sl == 1) ? gBs[1] : (sl == 2) ? gBs[2] : gBs[3];
         const int i = kFaceVerts[fk][0], j = kFaceVerts[fk][1], l = kFaceVerts[fk][2];
-        const float3 dm = f3(gPs[sl] * xr.x + gAs[sl] * G.zr, gPs[sl] * xr.y + gBs[sl] * G.zr,
-                             gPs[sl] * xr.z);
+        const float3 dm = f3(gP * xr.x + gA * G.zr, gP * xr.y + gB * G.zr, gP * xr.z);
         const float e = G.e[fk];
         const float3 n = G.n[fk];
         const float lam = dot3(n, dm) / (e * e);

@@ -28,7 +28,7 @@ struct Geo {
   float3 n[4];             // outward face normals (face k opposite vertex k)
   float e[4];              // plane offsets n . x_i (clamped away from 0)
   float sgn[4];            // orientation sign applied to (y_j - y_i) x (y_l - y_i)
-  int slot_face[4];        // face index held by each record slot
+  int slot_of[4];          // record slot of face k (front faces first, in face order)
   int nf;                  // number of front faces
   float3 g;                // SDF gradient in the pixel-scaled frame
   float3 cof[3];           // cofactor columns of the edge matrix
@@ -159,6 +159,7 @@ __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const Tet
   const float l2 = fmaxf(fmaxf(dot3(Y0, Y0), dot3(Y1, Y1)), dot3(Y2, Y2));
   if (!(fabsf(G.det) > 1e-9f * l2 * sqrtf(l2))) { G.visible = false; return; }   // flat tet
   int nf = 0;
+  float Pf[4], Af[4], Bf[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int i = kFaceVerts[k][0], j = kFaceVerts[k][1], l = kFaceVerts[k][2];
@@ -171,25 +172,27 @@ __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const Tet
     G.n[k] = n;
     G.e[k] = e;
     G.sgn[k] = sg;
+    const float inv = 1.f / e;
+    Pf[k] = dot3(n, G.w - G.y[i]) * inv;
+    Af[k] = G.zr * n.x * inv;
+    Bf[k] = G.zr * n.y * inv;
     nf += (e < 0.f);
   }
   G.nf = nf;
   if (nf == 0 || nf == 4) { G.visible = false; return; }
-  int fs = 0, bs = nf;
+  // slots: front faces first, then back faces, each in face order
+  int fb = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    if (G.e[k] < 0.f) G.slot_face[fs++] = k;
-    else G.slot_face[bs++] = k;
+    const bool front = G.e[k] < 0.f;
+    G.slot_of[k] = front ? fb : nf + (k - fb);
+    fb += front;
   }
 #pragma unroll
   for (int sl = 0; sl < 4; ++sl) {
-    const int k = G.slot_face[sl];
-    const int i = kFaceVerts[k][0];
-    const float3 n = G.n[k];
-    const float inv = 1.f / G.e[k];
-    G.P[sl] = dot3(n, G.w - G.y[i]) * inv;
-    G.A[sl] = G.zr * n.x * inv;
-    G.B[sl] = G.zr * n.y * inv;
+    G.P[sl] = (G.slot_of[0] == sl) ? Pf[0] : (G.slot_of[1] == sl) ? Pf[1] : (G.slot_of[2] == sl) ? Pf[2] : Pf[3];
+    G.A[sl] = (G.slot_of[0] == sl) ? Af[0] : (G.slot_of[1] == sl) ? Af[1] : (G.slot_of[2] == sl) ? Af[2] : Af[3];
+    G.B[sl] = (G.slot_of[0] == sl) ? Bf[0] : (G.slot_of[1] == sl) ? Bf[1] : (G.slot_of[2] == sl) ? Bf[2] : Bf[3];
   }
   // affine SDF: gradient g from the edge system, value at the reference point
   const float d1 = in.f[1] - in.f[0], d2 = in.f[2] - in.f[0], d3 = in.f[3] - in.f[0];
