@@ -206,12 +206,6 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
 // (warp-reduced; one vector atomic per field group) into the per-slot record
 // gradient buffer.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-  return v;
-}
-
 template <int TILE>
 __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict__ B,
                                                        const float* __restrict__ dimage,
@@ -221,6 +215,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   __shared__ float4 st[WPB][REC_Q][32];
   __shared__ int sidx[WPB][32];
   __shared__ unsigned sslot[WPB][32];
+  __shared__ float red[WPB][32][21];   // per-lane gradient rows (odd stride: no bank conflicts)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
@@ -340,21 +335,31 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
             atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
           }
         } else {
+          // transpose through shared memory: lane j < 20 sums field j over the
+          // contributing lanes' rows and issues one atomic
+          if (contrib) {
+            float* row = red[wid][lane];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            gP[q] = warp_sum(gP[q]);
-            gA[q] = warp_sum(gA[q]);
-            gB[q] = warp_sum(gB[q]);
+            for (int q = 0; q < 4; ++q) {
+              row[q] = gP[q];
+              row[4 + q] = gA[q];
+              row[8 + q] = gB[q];
+            }
+            row[12] = gF; row[13] = gK0; row[14] = gKx; row[15] = gKy;
+            row[16] = gz; row[17] = gc0; row[18] = gc1; row[19] = gc2;
           }
-          gF = warp_sum(gF); gK0 = warp_sum(gK0); gKx = warp_sum(gKx); gKy = warp_sum(gKy);
-          gz = warp_sum(gz); gc0 = warp_sum(gc0); gc1 = warp_sum(gc1); gc2 = warp_sum(gc2);
-          if (lane == 0) {
-            atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-            atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-            atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-            atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-            atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+          __syncwarp();
+          if (lane < 20) {
+            float acc = 0.f;
+            unsigned mm = mc;
+            while (mm) {
+              const int r = __ffs(mm) - 1;
+              mm &= mm - 1u;
+              acc += red[wid][r][lane];
+            }
+            if (acc != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 1) + lane, acc);
           }
+          __syncwarp();
         }
       }
       __syncwarp();
