@@ -81,7 +81,8 @@ enum {
 
 enum {
   TTS_FLAG_PURE = 1,        /* no cap / skip / early stop / pre-filter */
-  TTS_FLAG_ACCUM_GRAD = 2   /* backward adds into dV/df/drgb instead of overwriting */
+  TTS_FLAG_ACCUM_GRAD = 2,  /* backward adds into dV/df/drgb instead of overwriting */
+  TTS_FLAG_FORWARD_ONLY = 4 /* workspace without backward state; backward calls fail */
 };
 
 #define TTS_MAX_SCENES 64

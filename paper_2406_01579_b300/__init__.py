@@ -3,8 +3,9 @@ App. A): CUDA kernels for sm_103a behind the C ABI of include/tets.h, with a
 thin PyTorch binding.  There is no CPU fallback: importing the rasterizer
 requires the built libtets.so."""
 
+from . import camera  # noqa: F401
 from ._lib import TetsError, load  # noqa: F401
 from .rasterizer import Params, Rasterizer, SceneTensors, TetRender, make_camera, render  # noqa: F401
 
 __all__ = ["Params", "Rasterizer", "SceneTensors", "TetRender", "render", "make_camera", "load",
-           "TetsError"]
+           "TetsError", "camera"]

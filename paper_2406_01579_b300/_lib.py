@@ -24,6 +24,7 @@ TTS_STATUS_TIMEOUT = 8
 
 TTS_FLAG_PURE = 1
 TTS_FLAG_ACCUM_GRAD = 2
+TTS_FLAG_FORWARD_ONLY = 4
 
 TTS_MAX_SCENES = 64
 TTS_MAX_VIEWS = 128

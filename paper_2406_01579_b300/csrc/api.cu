@@ -177,8 +177,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_rnt = take(sizeof(int) * slots);
   const size_t o_rr = take(sizeof(int4) * slots);
   const size_t o_rec = take(sizeof(float4) * REC_Q * slots);
-  P->off_rec_grad = take(sizeof(float4) * REC_Q * slots);
-  P->bytes_rec_grad = sizeof(float4) * REC_Q * slots;
+  const bool fwd_only = (pr.flags & TTS_FLAG_FORWARD_ONLY) != 0;
+  P->off_rec_grad = take(fwd_only ? 0 : sizeof(float4) * REC_Q * slots);
+  P->bytes_rec_grad = fwd_only ? 0 : sizeof(float4) * REC_Q * slots;
   const size_t o_ppb = take(sizeof(long long) * pp_chunks);
   const size_t o_k0 = take(sizeof(unsigned long long) * cap);
   const size_t o_k1 = take(sizeof(unsigned long long) * cap);
@@ -314,7 +315,7 @@ int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
 
 int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
                   tts_stream stream) {
-  if (!dimage) return TTS_ERR_ARG;
+  if (!dimage || !b || (b->params.flags & TTS_FLAG_FORWARD_ONLY)) return TTS_ERR_ARG;
   Plan P;
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;
@@ -325,7 +326,7 @@ int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, 
 
 int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
                     tts_stream stream) {
-  if (!dV || !df || !drgb) return TTS_ERR_ARG;
+  if (!dV || !df || !drgb || !b || (b->params.flags & TTS_FLAG_FORWARD_ONLY)) return TTS_ERR_ARG;
   Plan P;
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;

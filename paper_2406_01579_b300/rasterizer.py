@@ -17,7 +17,7 @@ from typing import Sequence
 import torch
 
 from . import _lib
-from ._lib import (TTS_FLAG_ACCUM_GRAD, TTS_FLAG_PURE, TTS_STATUS_BAD_INDEX,
+from ._lib import (TTS_FLAG_ACCUM_GRAD, TTS_FLAG_FORWARD_ONLY, TTS_FLAG_PURE, TTS_STATUS_BAD_INDEX,
                    TTS_STATUS_KEY_OVERFLOW, TTS_STATUS_SURV_OVERFLOW, TetsError, check)
 
 
@@ -33,6 +33,7 @@ class Params:
     alpha_cap: float = 0.99
     t_eps: float = 1e-4
     accum_grad: bool = False
+    forward_only: bool = False
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -42,7 +43,8 @@ class Params:
         p.alpha_cap = self.alpha_cap
         p.t_eps = self.t_eps
         p.tile = self.tile
-        p.flags = (TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
+        p.flags = ((TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
+                   | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0))
         p.reserved = 0
         return p
 
@@ -246,6 +248,44 @@ class Rasterizer:
                                       dV, df, dc, _stream_ptr()), "tts_render_bwd")
         del dev
         return grads
+
+    # -- whole training step (pre-filter + forward + backward) -----------------
+    def step(self, out, upstream, grads):
+        """Enqueue one step: pre-filter, forward of every view, backward into
+        ``grads`` with the upstream gradients ``upstream`` = (dimage, dalpha,
+        ddepth).  No synchronisation, no capacity check (size the workspace
+        first, e.g. with ``forward()`` + ``shrink_to_fit``)."""
+        L = self.lib
+        b = self.batch()
+        sp = _stream_ptr()
+        img, alpha, depth = out
+        gi, ga, gd = upstream
+        n = len(self.scenes)
+        dV = (ctypes.c_void_p * n)(*[g[0].data_ptr() for g in grads])
+        df = (ctypes.c_void_p * n)(*[g[1].data_ptr() for g in grads])
+        dc = (ctypes.c_void_p * n)(*[g[2].data_ptr() for g in grads])
+        check(L.tts_prepare_scene(ctypes.byref(b), sp), "tts_prepare_scene")
+        check(L.tts_render_fwd(ctypes.byref(b), img.data_ptr(), alpha.data_ptr(),
+                               depth.data_ptr(), sp), "tts_render_fwd")
+        check(L.tts_render_bwd(ctypes.byref(b), gi.data_ptr(),
+                               ga.data_ptr() if ga is not None else None,
+                               gd.data_ptr() if gd is not None else None, dV, df, dc, sp),
+              "tts_render_bwd")
+
+    def capture_step(self, out, upstream, grads, warmup: int = 2):
+        """A CUDA graph of ``step`` on these exact buffers.  Replays read the
+        current contents of the scene tensors, the upstream gradients and the
+        workspace; the scene tensors must be updated in place."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                self.step(out, upstream, grads)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.step(out, upstream, grads)
+        return g
 
     def info(self) -> _lib.tts_info:
         info = _lib.tts_info()
