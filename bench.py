@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--workload", default="spheres128", choices=["spheres128", "batched", "serve"])
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rates", default="200,500,1000,2000")
     return ap.parse_args()
 
 
@@ -241,6 +245,25 @@ def run_ours(a, rank, world):
         "pixels_per_step": pixels_per_step,
     }
 
+    # the same step captured once in a CUDA graph and replayed
+    try:
+        gstep = r.capture_step((img, alpha, depth), (gi, ga, gd), grads)
+        for _ in range(3):
+            gstep.replay()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            gstep.replay()
+        e1.record(stream)
+        barrier()
+        tg = e0.elapsed_time(e1) / 1e3
+        res["graph"] = world * pixels_per_step * a.steps / tg / 1e6
+        del gstep
+    except Exception as exc:  # capture unsupported: report eager only
+        res["graph_error"] = repr(exc)[:200]
+
     # plain single-view path: one view per call, everything per call
     if not a.no_plain and rank == 0:
         plains = [Rasterizer([st], [(c, 0)], params, device=dev) for c in sc.cams]
@@ -313,10 +336,41 @@ def run_ours(a, rank, world):
             te = float(t.item())
         res["e2e"] = {"value": world * pixels_per_step * a.steps / te / 1e6, "unit": UNIT,
                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo}
+    if not a.no_serve and rank == 0:
+        res["serve"] = quick_serve(a, st, dev)
     res["sc"] = sc
     if dist is not None:
         dist.barrier()
     return res
+
+
+def resident_scenes(rng, n_list, dev):
+    import torch
+
+    import synth
+    from paper_2406_01579_b300 import SceneTensors
+    out = []
+    for n in n_list:
+        V, T, f, rgb = synth.random_scene(rng, int(n), "sphere" if rng.uniform() < 0.5 else "torus")
+        out.append(SceneTensors(*(torch.from_numpy(x).to(dev) for x in (V, T, f, rgb))))
+    return out
+
+
+def quick_serve(a, big_scene, dev, n_requests=300, rate=200.0):
+    """Served latency on a small mix: the benchmark scene plus 7 resident
+    scenes of 32^3..96^3, 300 requests at 200 req/s, 30% forward+backward,
+    views 256^2..1024^2."""
+    from paper_2406_01579_b300 import Params
+    from paper_2406_01579_b300.serve import Server, poisson_requests
+    rng = np.random.default_rng(44)
+    scenes = [big_scene] + resident_scenes(rng, [32, 48, 64, 96, 32, 48, 64], dev)
+    srv = Server(scenes, Params(s=a.s, tile=a.tile), hbm_budget=120e9, max_views=16, streams=3)
+    srv.run(poisson_requests(np.random.default_rng(1), 48, rate, len(scenes)))   # warm-up
+    reqs = poisson_requests(np.random.default_rng(2), n_requests, rate, len(scenes))
+    _, stats = srv.run(reqs)
+    stats.update({"rate_req_s": rate, "scenes": len(scenes),
+                  "mix": "views 256..1024 px, 30% fwd+bwd, 128^3 + 7 scenes of 32..96^3"})
+    return stats
 
 
 # ---------------------------------------------------------------------------
@@ -376,6 +430,110 @@ def run_reference(a):
     print(json.dumps(out))
 
 
+def run_batched(a):
+    """16 scenes of uneven resolution (32..128)^3, 1-8 views each at
+    256^2..1024^2, tile size autotuned, one CUDA graph per step (pre-filter +
+    forward + backward of all views); compared with the plain single-view
+    path on the same views."""
+    import torch
+
+    import synth
+    from paper_2406_01579_b300 import Params, Rasterizer
+    from paper_2406_01579_b300.autotune import autotune_tile
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(3)
+    ns = [int(rng.choice([32, 48, 64, 96, 128])) for _ in range(16)]
+    scenes = resident_scenes(rng, ns, dev)
+    views = []
+    for si in range(16):
+        for _ in range(int(rng.integers(1, 9))):
+            res = int(rng.choice([256, 512, 768, 1024]))
+            views.append((synth.random_camera(rng, res, res), si))
+    params = Params(s=a.s)
+    best, times = autotune_tile(scenes, views, params, reps=2, cache_path=None)
+    params = Params(s=a.s, tile=best)
+    r = Rasterizer(scenes, views, params)
+    r.forward()
+    r.shrink_to_fit(1.15)
+    r.forward()
+    out = r._outputs()
+    up = tuple(torch.randn(n, device=dev) for n in (3 * r.total_pixels, r.total_pixels,
+                                                       r.total_pixels))
+    grads = [(torch.empty_like(x.V), torch.empty_like(x.f), torch.empty_like(x.rgb)) for x in scenes]
+    g = r.capture_step(out, up, grads)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    px = r.total_pixels
+    # plain path: every view alone, everything per call
+    plains = []
+    for c, si in views:
+        p_ = Rasterizer([scenes[si]], [(c, 0)], params)
+        p_.forward()
+        p_.shrink_to_fit(1.15)
+        plains.append(p_)
+    gr1 = [[(torch.empty_like(scenes[si].V), torch.empty_like(scenes[si].f),
+             torch.empty_like(scenes[si].rgb))] for _, si in views]
+    ups1 = [tuple(torch.randn(n, device=dev) for n in (3 * p_.total_pixels, p_.total_pixels,
+                                                          p_.total_pixels)) for p_ in plains]
+    outs1 = [p_._outputs() for p_ in plains]
+
+    def plain_step():
+        for p_, o, u_, g_ in zip(plains, outs1, ups1, gr1):
+            p_.step(o, u_, g_)
+
+    plain_step()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(max(2, a.steps // 4)):
+        plain_step()
+    e1.record()
+    torch.cuda.synchronize()
+    tp = e0.elapsed_time(e1) / 1e3 / max(2, a.steps // 4)
+    info = r.info()
+    print(json.dumps({
+        "metric": METRIC, "value": px * a.steps / t / 1e6, "unit": UNIT, "n_gpus": 1,
+        "steps": a.steps, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched uneven: 16 scenes n={ns}, {len(views)} views "
+                               f"256..1024 px, s={a.s:g}, one CUDA graph per step",
+                   "tile": best, "autotune_ms": times},
+        "plain_path_mpix_s": px / tp / 1e6, "status": int(info.status),
+        "keys": int(info.n_keys)}))
+
+
+def run_serve(a):
+    """Serving: 64 resident scenes (32..128)^3, Poisson arrivals, 30%
+    forward+backward, views 256^2..1024^2, HBM budget 120 GB."""
+    import torch
+
+    from paper_2406_01579_b300 import Params
+    from paper_2406_01579_b300.serve import Server, poisson_requests
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(4)
+    ns = [int(rng.choice([32, 48, 64, 96, 128])) for _ in range(64)]
+    scenes = resident_scenes(rng, ns, dev)
+    srv = Server(scenes, Params(s=a.s, tile=a.tile), hbm_budget=120e9, max_views=16, streams=3)
+    srv.run(poisson_requests(np.random.default_rng(1), 64, 500.0, len(scenes)))
+    out = []
+    for rate in [float(x) for x in a.serve_rates.split(",")]:
+        reqs = poisson_requests(np.random.default_rng(int(rate)), a.serve_requests, rate, len(scenes))
+        _, st = srv.run(reqs)
+        st["rate_req_s"] = rate
+        out.append(st)
+    print(json.dumps({"metric": "serve p50/p99 latency (ms) and Mpixel/s", "unit": "ms",
+                      "config": {"workload": f"serve: 64 resident scenes n={sorted(set(ns))}, "
+                                             "views 256..1024 px, 30% fwd+bwd, budget 120 GB",
+                                 "requests_per_rate": a.serve_requests}, "rates": out}))
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -383,6 +541,12 @@ def main():
     if a.impl == "reference":
         if rank == 0:
             run_reference(a)
+        return
+    if a.workload == "batched":
+        run_batched(a)
+        return
+    if a.workload == "serve":
+        run_serve(a)
         return
     res = run_ours(a, rank, world)
     if rank != 0:
@@ -416,6 +580,8 @@ def main():
         "roofline": roofline,
         "stage_ms": st, "dominant_stage": dom,
         "plain_path_mpix_s": res.get("plain"),
+        "graph_mpix_s": res.get("graph"),
+        "serve": res.get("serve"),
         "gpu_launches": res["launches"],
         "fragments_per_step": res["nfrag"], "keys_per_step": res["n_keys"],
         "survivors": res["n_surv"], "sort_passes": res["sort_passes"],

@@ -44,9 +44,9 @@ class Request:
 @dataclasses.dataclass
 class Result:
     rid: int
-    image: np.ndarray
-    alpha: np.ndarray
-    depth: np.ndarray
+    image: torch.Tensor      # (3, H, W) view of a pinned host buffer
+    alpha: torch.Tensor      # (H, W)
+    depth: torch.Tensor      # (H, W)
     grads: tuple | None
     done: float
     latency: float
@@ -161,10 +161,9 @@ class Server:
             if b.grads is not None:
                 g = b.grads[i]
             results[q.rid] = Result(
-                q.rid, img[3 * off:3 * off + 3 * H * W].view(3, H, W).numpy().copy(),
-                alpha[off:off + H * W].view(H, W).numpy().copy(),
-                depth[off:off + H * W].view(H, W).numpy().copy(), g, now, now - q.arrival,
-                len(b.reqs))
+                q.rid, img[3 * off:3 * off + 3 * H * W].view(3, H, W),
+                alpha[off:off + H * W].view(H, W), depth[off:off + H * W].view(H, W), g, now,
+                now - q.arrival, len(b.reqs))
         return True
 
     # -- the loop --------------------------------------------------------------

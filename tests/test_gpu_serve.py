@@ -48,7 +48,7 @@ def test_result_alone_equals_result_in_mix(server):
     assert res[0].batch_views > 1 or res[1].batch_views > 1
     for a, b in ((alone_f[0], res[0]), (alone_g[1], res[1])):
         for u, v in ((a.image, b.image), (a.alpha, b.alpha), (a.depth, b.depth)):
-            assert np.abs(u - v).max() <= 1e-4
+            assert (u - v).abs().max().item() <= 1e-4
     ga, gb = alone_g[1].grads, res[1].grads
     for u, v in zip(ga, gb):
         u, v = u.cpu().numpy(), v.cpu().numpy()
