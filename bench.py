@@ -264,6 +264,28 @@ def run_ours(a, rank, world):
     except Exception as exc:  # capture unsupported: report eager only
         res["graph_error"] = repr(exc)[:200]
 
+    # the paper's resort window (N_w = 5), same step
+    if not a.no_plain and rank == 0:
+        from paper_2406_01579_b300 import Params as _P
+        rw = Rasterizer([st], [(c, 0) for c in sc.cams], _P(s=a.s, tile=a.tile, resort_window=5),
+                        device=dev)
+        rw.forward()
+        rw.shrink_to_fit(1.15)
+        outw = rw._outputs()
+        for _ in range(3):
+            rw.step(outw, (gi, ga, gd), grads)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nsw = max(3, a.steps // 2)
+        for _ in range(nsw):
+            rw.step(outw, (gi, ga, gd), grads)
+        e1.record(stream)
+        barrier()
+        res["window5"] = pixels_per_step * nsw / (e0.elapsed_time(e1) / 1e3) / 1e6
+        del rw, outw
+
     # plain single-view path: one view per call, everything per call
     if not a.no_plain and rank == 0:
         plains = [Rasterizer([st], [(c, 0)], params, device=dev) for c in sc.cams]
@@ -581,6 +603,7 @@ def main():
         "stage_ms": st, "dominant_stage": dom,
         "plain_path_mpix_s": res.get("plain"),
         "graph_mpix_s": res.get("graph"),
+        "resort_window5_mpix_s": res.get("window5"),
         "serve": res.get("serve"),
         "gpu_launches": res["launches"],
         "fragments_per_step": res["nfrag"], "keys_per_step": res["n_keys"],

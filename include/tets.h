@@ -104,7 +104,10 @@ typedef struct {
   float t_eps;            /* 1e-4 */
   int32_t tile;           /* tile edge in pixels: 8, 16 or 32 */
   int32_t flags;          /* TTS_FLAG_* */
-  int32_t reserved;       /* 0 */
+  int32_t resort_window;  /* N_w of Sec. 3.3, 0..7: per pixel, fragments pass through a
+                             window of N_w kept sorted by the depth of their chord's entry
+                             point (ties: earlier first); the nearest leaves it when it holds
+                             more than N_w, the rest at the end.  0: per-tile sort order. */
 } tts_params;
 
 /* One scene: caller-owned device arrays (must outlive every call using them). */

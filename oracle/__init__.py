@@ -43,7 +43,8 @@ class OrcParams(ctypes.Structure):
     _fields_ = [("s", ctypes.c_double), ("prefilter_thresh", ctypes.c_double),
                 ("alpha_skip", ctypes.c_double), ("alpha_cap", ctypes.c_double),
                 ("t_eps", ctypes.c_double), ("band", ctypes.c_double),
-                ("tile", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("tile", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -108,7 +109,9 @@ def make_cam(cam) -> OrcCam:
 
 
 def make_params(s=175.0, tile=16, pure=False, prefilter_thresh=1.0 / 255.0,
-                alpha_skip=1.0 / 255.0, alpha_cap=0.99, t_eps=1e-4, band=1e-4) -> OrcParams:
+                alpha_skip=1.0 / 255.0, alpha_cap=0.99, t_eps=1e-4, band=1e-4,
+                window=0) -> OrcParams:
+    """``window``: resort window N_w (0: tile order, < 0: full per-pixel sort)."""
     p = OrcParams()
     p.s = s
     p.prefilter_thresh = prefilter_thresh
@@ -118,6 +121,8 @@ def make_params(s=175.0, tile=16, pure=False, prefilter_thresh=1.0 / 255.0,
     p.band = band
     p.tile = tile
     p.flags = PURE if pure else 0
+    p.window = window
+    p.pad = 0
     return p
 
 

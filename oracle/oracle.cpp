@@ -53,6 +53,8 @@ struct OrcParams {
   double band;              // relative half-width of the decision bands
   int32_t tile;             // tile edge in pixels
   int32_t flags;            // bit 0: PURE (no cap, skip, termination, pre-filter)
+  int32_t window;           // resort window N_w (Sec. 3.3); 0: tile order; <0: full per-pixel sort
+  int32_t pad;
 };
 
 }  // extern "C"
@@ -345,6 +347,7 @@ struct Frag {
   double alpha;    // Eq. 1
   double zbar;     // mean vertex depth (Eq. 2 depth term)
   double c[3];     // tet colour: mean of the vertex colours
+  double zin;      // depth of the chord's entry point (App. A.2 z_p of the nearest hit)
 };
 
 struct Blended {
@@ -362,6 +365,17 @@ struct PixelResult {
 
 // Walk the fragment list.  Decision indices count every threshold test in
 // evaluation order; flip = index of the decision to invert (-1: none).
+// Resort window (Sec. 3.3): fragments that pass the cap and skip tests enter
+// a window kept sorted by the entry depth z_in (ties: earlier first); when it
+// holds more than N_w fragments the nearest one leaves it and is blended; at
+// the end of the list the rest leave in depth order.  N_w = 0 keeps the tile
+// order; N_w < 0 sorts the whole pixel list by z_in.
+struct Staged {
+  Frag f;
+  double a;
+  bool clamped;
+};
+
 static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip, bool record,
                       PixelResult* r) {
   const bool pure = (p.flags & ORC_PURE) != 0;
@@ -378,13 +392,45 @@ static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip,
     }
     return (id == flip) ? !outcome : outcome;
   };
+  // cap and skip in list order, then the window's emission order
+  std::vector<Staged> in;
   for (const Frag& f : fr) {
     double a = f.alpha;
     bool clamped = false;
     if (!pure) {
       if (decide(a > p.alpha_cap, a, p.alpha_cap)) { a = p.alpha_cap; clamped = true; }
       if (decide(a < p.alpha_skip, a, p.alpha_skip)) continue;
+    } else if (!(a > 0.0)) {
+      continue;
     }
+    in.push_back({f, a, clamped});
+  }
+  std::vector<Staged> order;
+  if (p.window == 0) {
+    order = in;
+  } else {
+    const size_t cap = (p.window < 0) ? in.size() + 1 : (size_t)p.window;
+    std::vector<Staged> win;
+    auto near_tie = [&](double x, double y) {
+      return std::fabs(x - y) <= 1e-5 * std::max(std::fabs(x), std::fabs(y));
+    };
+    for (const Staged& st : in) {
+      size_t pos = 0;
+      while (pos < win.size() && win[pos].f.zin <= st.f.zin) ++pos;
+      for (const Staged& w : win)
+        if (near_tie(w.f.zin, st.f.zin)) r->amb += 2;  // order not decidable in FP32
+      win.insert(win.begin() + pos, st);
+      if (win.size() > cap) {
+        order.push_back(win.front());
+        win.erase(win.begin());
+      }
+    }
+    for (const Staged& w : win) order.push_back(w);
+  }
+  for (const Staged& st : order) {
+    const Frag& f = st.f;
+    const double a = st.a;
+    const bool clamped = st.clamped;
     double Tn = T * (1.0 - a);
     if (!pure) {
       if (decide(Tn < p.t_eps, Tn, p.t_eps)) break;
@@ -462,6 +508,7 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
         FragOut<double> o;
         if (!eval_fragment<double>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, &o)) continue;
         ++hits;
+        fg.zin = o.z_in;
         fg.alpha = opacity_eq1<double>(o.f_prev, o.f_next, p->s);
         fg.zbar = 0.25 * (X[0][2] + X[1][2] + X[2][2] + X[3][2]);
         for (int q = 0; q < 3; ++q)
@@ -569,6 +616,8 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
       const int tile = (j / B) * tx + (i / B);
       const double px = i + 0.5, py = j + 0.5;
       D1 Tr(1.0), C[3] = {D1(0.0), D1(0.0), D1(0.0)}, Dp(0.0);
+      struct FD { D1 a, zb, cc[3]; double zin; };
+      std::vector<FD> in;
       for (int e = ranges[2 * tile]; e < ranges[2 * tile + 1]; ++e) {
         const int32_t s = key_val[e];
         const int32_t* r4 = rect + 4 * (int64_t)s;
@@ -594,16 +643,39 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
         if (!pure) {
           if (a.v > p->alpha_cap) a = D1(p->alpha_cap);
           if (a.v < p->alpha_skip) continue;
+        } else if (!(a.v > 0.0)) {
+          continue;
         }
-        D1 Tn = Tr * (1.0 - a);
-        if (!pure && Tn.v < p->t_eps) break;
-        D1 zb = 0.25 * (((X[0][2] + X[1][2]) + X[2][2]) + X[3][2]);
+        FD fd;
+        fd.a = a;
+        fd.zin = o.z_in.v;
+        fd.zb = 0.25 * (((X[0][2] + X[1][2]) + X[2][2]) + X[3][2]);
         for (int q = 0; q < 3; ++q) {
           D1 cc = 0.25 * (((D1(fld.rgb[3 * t[0] + q]) + D1(fld.rgb[3 * t[1] + q])) + D1(fld.rgb[3 * t[2] + q])) + D1(fld.rgb[3 * t[3] + q]));
           cc.d[0] = 0.25 * (trgb[3 * t[0] + q] + trgb[3 * t[1] + q] + trgb[3 * t[2] + q] + trgb[3 * t[3] + q]);
-          C[q] = C[q] + Tr * a * cc;
+          fd.cc[q] = cc;
         }
-        Dp = Dp + Tr * a * zb;
+        in.push_back(fd);
+      }
+      std::vector<FD> order;
+      if (p->window == 0) {
+        order = in;
+      } else {
+        const size_t cap = (p->window < 0) ? in.size() + 1 : (size_t)p->window;
+        std::vector<FD> win;
+        for (const FD& fd : in) {
+          size_t pos = 0;
+          while (pos < win.size() && win[pos].zin <= fd.zin) ++pos;
+          win.insert(win.begin() + pos, fd);
+          if (win.size() > cap) { order.push_back(win.front()); win.erase(win.begin()); }
+        }
+        for (const FD& w : win) order.push_back(w);
+      }
+      for (const FD& fd : order) {
+        D1 Tn = Tr * (1.0 - fd.a);
+        if (!pure && Tn.v < p->t_eps) break;
+        for (int q = 0; q < 3; ++q) C[q] = C[q] + Tr * fd.a * fd.cc[q];
+        Dp = Dp + Tr * fd.a * fd.zb;
         Tr = Tn;
       }
       const int64_t pix = (int64_t)j * W + i;

@@ -69,6 +69,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
         pr.prefilter_thresh >= 0.f))
     return TTS_ERR_ARG;
   if (b->key_capacity < 1 || b->key_capacity > 0x7fffffffLL) return TTS_ERR_ARG;
+  if (pr.resort_window < 0 || pr.resort_window > 7) return TTS_ERR_ARG;
   std::memset(&P->hb, 0, sizeof(Batch));
   Batch& B = P->hb;
   B.n_scenes = b->n_scenes;
@@ -80,6 +81,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   B.t_eps = pr.t_eps;
   B.tile = pr.tile;
   B.flags = pr.flags;
+  B.resort_window = pr.resort_window;
   B.key_cap = b->key_capacity;
   // scenes
   long long surv_total = 0, flag_total = 0;
@@ -191,6 +193,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_pT = take(sizeof(float) * pix);
   const size_t o_pL = take(sizeof(int) * pix);
   const size_t o_pN = take(sizeof(int) * pix);
+  const size_t o_pC = take(sizeof(float4) * pix);
   P->bytes = align_up(off, 256);
   if (need_ws) {
     if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % 256) != 0)
@@ -217,6 +220,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.pix_T = reinterpret_cast<float*>(base + o_pT);
     B.pix_last = reinterpret_cast<int*>(base + o_pL);
     B.pix_nfrag = reinterpret_cast<int*>(base + o_pN);
+    B.pix_CD = reinterpret_cast<float4*>(base + o_pC);
   }
   HostPlan& H = P->hp;
   H.n_scenes = b->n_scenes;
@@ -228,6 +232,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.range_blocks = 2 * sm_count();
   H.total_tiles = tiles;
   H.tile = pr.tile;
+  H.window = pr.resort_window;
   H.tet_bwd_blocks = 2 * sm_count();
   blend_grid(pr.tile, sm_count(), &H.blend_fwd_blocks, &H.blend_bwd_blocks);
   H.total_pixels = pix;

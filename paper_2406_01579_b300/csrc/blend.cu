@@ -194,10 +194,179 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
       B->pix_T[vw.pix_base + p] = T;
       B->pix_last[vw.pix_base + p] = last;
       B->pix_nfrag[vw.pix_base + p] = nfrag;
+      B->pix_CD[vw.pix_base + p] = make_float4(C0, C1, C2, D);
     }
   }
   queue_done(&c->work_fwd, &c->done_fwd);
 }
+
+// ---------------------------------------------------------------------------
+// Resort window (Sec. 3.3).  Per pixel, fragments that pass the cap and skip
+// tests enter a window of at most N_w (kept in registers) sorted by the depth
+// of the chord's entry point, ties keeping arrival order; when it holds more
+// than N_w fragments the nearest leaves it and is blended (stop-before-T<eps
+// applies in this order); at the end of the list the rest leave nearest
+// first.  The entry depth is zbar / rho_in (the record's reference depth is
+// the tet's mean depth).
+// ---------------------------------------------------------------------------
+constexpr int WIN_MAX = 8;
+
+struct Win {
+  float k[WIN_MAX];
+  float a[WIN_MAX];
+  unsigned sl[WIN_MAX];
+  int n;
+};
+
+__device__ __forceinline__ void win_insert(Win& w, float key, float a, unsigned slot) {
+  int pos = 0;
+#pragma unroll
+  for (int i = 0; i < WIN_MAX; ++i) pos += (i < w.n) & (w.k[i] <= key);
+#pragma unroll
+  for (int i = WIN_MAX - 1; i > 0; --i) {
+    if (i > pos && i <= w.n) {
+      w.k[i] = w.k[i - 1];
+      w.a[i] = w.a[i - 1];
+      w.sl[i] = w.sl[i - 1];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < WIN_MAX; ++i) {
+    if (i == pos) {
+      w.k[i] = key;
+      w.a[i] = a;
+      w.sl[i] = slot;
+    }
+  }
+  ++w.n;
+}
+
+__device__ __forceinline__ void win_pop(Win& w) {
+#pragma unroll
+  for (int i = 0; i < WIN_MAX - 1; ++i) {
+    w.k[i] = w.k[i + 1];
+    w.a[i] = w.a[i + 1];
+    w.sl[i] = w.sl[i + 1];
+  }
+  --w.n;
+}
+
+// Blend one fragment leaving the window (forward).
+__device__ __forceinline__ void win_emit_fwd(const float4* __restrict__ rec, unsigned slot, float a,
+                                             bool pure, float eps, float& T, float& C0, float& C1,
+                                             float& C2, float& D, bool& done) {
+  const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+  if (!pure && Tn < eps) {
+    done = true;
+    return;
+  }
+  const float4 q5 = __ldg(rec + (size_t)slot * REC_Q + 5);
+  const float wgt = __fmul_rn(T, a);
+  C0 = __fmaf_rn(wgt, q5.y, C0);
+  C1 = __fmaf_rn(wgt, q5.z, C1);
+  C2 = __fmaf_rn(wgt, q5.w, C2);
+  D = __fmaf_rn(wgt, q5.x, D);
+  T = Tn;
+}
+
+template <int TILE>
+__global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restrict__ B,
+                                                           float* __restrict__ image,
+                                                           float* __restrict__ alpha,
+                                                           float* __restrict__ depth) {
+  constexpr int SB = (TILE / 8) * (TILE / 4);
+  __shared__ float4 st[WPB][REC_Q][32];
+  __shared__ unsigned sslot[WPB][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
+  Counters* c = B->ctr;
+  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const float4* __restrict__ rec = B->rec;
+  const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
+  const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
+  const int nw = B->resort_window;
+  const int total = B->total_tiles * SB;
+  for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
+    WarpBlock wb;
+    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    if (!__any_sync(FULL, wb.inimg)) continue;
+    const int2 rg = B->ranges[wb.gt];
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    int nfrag = 0;
+    bool done = !wb.inimg;
+    Win win;
+    win.n = 0;
+    for (int g = rg.x; g < rg.y; g += 32) {
+      if (!wb.cull_to(!done)) break;
+      const int idx = g + lane;
+      bool ov = false;
+      unsigned slot = 0u;
+      float4 q0;
+      if (idx < rg.y) {
+        slot = vals[idx];
+        q0 = __ldg(rec + (size_t)slot * REC_Q);
+        ov = !wb.misses(q0);
+      }
+      const unsigned m = __ballot_sync(FULL, ov);
+      if (m == 0u) continue;
+      if (ov) {
+        const int pos = __popc(m & ltm);
+        const float4* r = rec + (size_t)slot * REC_Q;
+        st[wid][0][pos] = q0;
+#pragma unroll
+        for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+        sslot[wid][pos] = slot;
+      }
+      __syncwarp();
+      const int cnt = __popc(m);
+      for (int k = 0; k < cnt; ++k) {
+        if (!done) {
+          const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k], st[wid][3][k],
+                                      wb.fpx, wb.fpy);
+          if (ch.hit) {
+            ++nfrag;
+            const Opacity o = opacity_eval(st[wid][4][k], ch);
+            const float a = pure ? o.alpha : fminf(o.alpha, cap);
+            if (pure ? (a > 0.f) : (a >= skip)) {
+              const float key = __fmul_rn(st[wid][5][k].x, __fmul_rn(o.rho_out, o.r));
+              win_insert(win, key, a, sslot[wid][k]);
+              if (win.n > nw) {
+                const unsigned s0 = win.sl[0];
+                const float a0 = win.a[0];
+                win_pop(win);
+                win_emit_fwd(rec, s0, a0, pure, eps, T, C0, C1, C2, D, done);
+              }
+            }
+          }
+        }
+        if (__all_sync(FULL, done)) break;
+      }
+      __syncwarp();
+    }
+    // flush what is left in the window, nearest first
+    while (!done && win.n > 0) {
+      const unsigned s0 = win.sl[0];
+      const float a0 = win.a[0];
+      win_pop(win);
+      win_emit_fwd(rec, s0, a0, pure, eps, T, C0, C1, C2, D, done);
+    }
+    if (wb.inimg) {
+      const long long HW = (long long)vw.W * vw.H;
+      const long long p = (long long)wb.py * vw.W + wb.px;
+      image[3 * vw.pix_base + p] = C0;
+      image[3 * vw.pix_base + HW + p] = C1;
+      image[3 * vw.pix_base + 2 * HW + p] = C2;
+      alpha[vw.pix_base + p] = 1.f - T;
+      depth[vw.pix_base + p] = D;
+      B->pix_T[vw.pix_base + p] = T;
+      B->pix_last[vw.pix_base + p] = rg.y - rg.x;
+      B->pix_nfrag[vw.pix_base + p] = nfrag;
+      B->pix_CD[vw.pix_base + p] = make_float4(C0, C1, C2, D);
+    }
+  }
+  queue_done(&c->work_fwd, &c->done_fwd);
+}
+
 
 // ---------------------------------------------------------------------------
 // K7: backward blend.  Same warp blocks; each warp re-walks its tile's list
@@ -368,6 +537,152 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   queue_done(&c->work_bwd, &c->done_bwd);
 }
 
+// Backward with the resort window: replays the forward (same walk, same
+// window, same stop) front to back.  With W = gC.C + gD.D of the final pixel
+// and the running prefix P of T_j a_j w_j, the suffix of fragment i is
+// W - P - T_i a_i w_i, so dL/da_i = T_i w_i - (suffix - gO T_final)/(1 - a_i).
+// Each emitted fragment's record is reloaded and its chord recomputed; the
+// record-field gradients leave as per-lane vector atomics.
+template <int TILE>
+__global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restrict__ B,
+                                                           const float* __restrict__ dimage,
+                                                           const float* __restrict__ dalpha,
+                                                           const float* __restrict__ ddepth) {
+  constexpr int SB = (TILE / 8) * (TILE / 4);
+  __shared__ float4 st[WPB][REC_Q][32];
+  __shared__ unsigned sslot[WPB][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned ltm = (1u << lane) - 1u;
+  Counters* c = B->ctr;
+  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const float4* __restrict__ rec = B->rec;
+  float4* __restrict__ rgrad = B->rec_grad;
+  const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
+  const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
+  const int nw = B->resort_window;
+  const int total = B->total_tiles * SB;
+  for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
+    WarpBlock wb;
+    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    if (!__any_sync(FULL, wb.inimg)) continue;
+    const int2 rg = B->ranges[wb.gt];
+    const long long HW = (long long)vw.W * vw.H;
+    const long long pp = (long long)wb.py * vw.W + wb.px;
+    float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gO = 0.f, gD = 0.f, Tfin = 1.f, Wt = 0.f;
+    if (wb.inimg) {
+      Tfin = B->pix_T[vw.pix_base + pp];
+      gC0 = dimage[3 * vw.pix_base + pp];
+      gC1 = dimage[3 * vw.pix_base + HW + pp];
+      gC2 = dimage[3 * vw.pix_base + 2 * HW + pp];
+      if (dalpha) gO = dalpha[vw.pix_base + pp];
+      if (ddepth) gD = ddepth[vw.pix_base + pp];
+      const float4 cd = B->pix_CD[vw.pix_base + pp];
+      Wt = gC0 * cd.x + gC1 * cd.y + gC2 * cd.z + gD * cd.w;
+    }
+    const float gOT = gO * Tfin;
+    float T = 1.f, Pw = 0.f;
+    bool done = !wb.inimg;
+    Win win;
+    win.n = 0;
+    // adjoint of one fragment leaving the window
+    auto emit = [&](unsigned slot, float a) {
+      const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
+      if (!pure && Tn < eps) {
+        done = true;
+        return;
+      }
+      const float4* r = rec + (size_t)slot * REC_Q;
+      const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
+      const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5);
+      const Chord ch = chord_eval(q0, q1, q2, q3, wb.fpx, wb.fpy);
+      const Opacity o = opacity_eval(q4, ch);
+      const float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+      const float twa = T * a * wv;
+      const float suffix = Wt - Pw - twa;
+      const float dLda = T * wv - (suffix - gOT) / __fsub_rn(1.f, a);
+      Pw += twa;
+      const float wgt = T * a;
+      float4* dst = rgrad + (size_t)slot * REC_Q;
+      const bool clamped = !pure && (o.alpha > cap);
+      if (!clamped) {
+        const float dx = dLda * o.e1 * o.B;
+        const float dy = -dLda * o.alpha * (1.f - o.B);
+        const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
+        const float dpin = -dx * o.sGz * iin * iin;
+        const float dpout = (dx - dy) * o.sGz * iout * iout;
+        const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
+        float gP[4], gA[4], gB[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
+          gP[q] = dp;
+          gA[q] = dp * ch.dx;
+          gB[q] = dp * ch.dy;
+        }
+        atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
+        atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
+        atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
+        atomicAdd(dst + 4, make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy));
+      }
+      atomicAdd(dst + 5, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2));
+      T = Tn;
+    };
+    for (int g = rg.x; g < rg.y; g += 32) {
+      if (!wb.cull_to(!done)) break;
+      const int idx = g + lane;
+      bool ov = false;
+      unsigned slot = 0u;
+      float4 q0;
+      if (idx < rg.y) {
+        slot = vals[idx];
+        q0 = __ldg(rec + (size_t)slot * REC_Q);
+        ov = !wb.misses(q0);
+      }
+      const unsigned m = __ballot_sync(FULL, ov);
+      if (m == 0u) continue;
+      if (ov) {
+        const int pos = __popc(m & ltm);
+        const float4* r = rec + (size_t)slot * REC_Q;
+        st[wid][0][pos] = q0;
+#pragma unroll
+        for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+        sslot[wid][pos] = slot;
+      }
+      __syncwarp();
+      const int cnt = __popc(m);
+      for (int k = 0; k < cnt; ++k) {
+        if (!done) {
+          const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k], st[wid][3][k],
+                                      wb.fpx, wb.fpy);
+          if (ch.hit) {
+            const Opacity o = opacity_eval(st[wid][4][k], ch);
+            const float a = pure ? o.alpha : fminf(o.alpha, cap);
+            if (pure ? (a > 0.f) : (a >= skip)) {
+              const float key = __fmul_rn(st[wid][5][k].x, __fmul_rn(o.rho_out, o.r));
+              win_insert(win, key, a, sslot[wid][k]);
+              if (win.n > nw) {
+                const unsigned s0 = win.sl[0];
+                const float a0 = win.a[0];
+                win_pop(win);
+                emit(s0, a0);
+              }
+            }
+          }
+        }
+        if (__all_sync(FULL, done)) break;
+      }
+      __syncwarp();
+    }
+    while (!done && win.n > 0) {
+      const unsigned s0 = win.sl[0];
+      const float a0 = win.a[0];
+      win_pop(win);
+      emit(s0, a0);
+    }
+  }
+  queue_done(&c->work_bwd, &c->done_bwd);
+}
+
 // ---------------------------------------------------------------------------
 // K8: record -> vertex adjoint.  One thread per survivor of a scene; loops
 // over the scene's views, recomputes the view's tet geometry, applies the
@@ -530,6 +845,14 @@ void blend_grid(int tile, int sms, int* fwd_blocks, int* bwd_blocks) {
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      cudaStream_t st) {
   const int g = P.blend_fwd_blocks;
+  if (P.window > 0) {
+    switch (P.tile) {
+      case 8: k_blend_fwd_win<8><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+      case 16: k_blend_fwd_win<16><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+      default: k_blend_fwd_win<32><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+    }
+    return 1;
+  }
   switch (P.tile) {
     case 8: k_blend_fwd<8><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
     case 16: k_blend_fwd<16><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
@@ -541,6 +864,14 @@ int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* al
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                      const float* ddepth, cudaStream_t st) {
   const int g = P.blend_bwd_blocks;
+  if (P.window > 0) {
+    switch (P.tile) {
+      case 8: k_blend_bwd_win<8><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+      case 16: k_blend_bwd_win<16><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+      default: k_blend_bwd_win<32><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+    }
+    return 1;
+  }
   switch (P.tile) {
     case 8: k_blend_bwd<8><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
     case 16: k_blend_bwd<16><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;

@@ -14,6 +14,7 @@ struct HostPlan {
   int range_blocks;
   int total_tiles;
   int tile;
+  int window;
   int tet_bwd_blocks;
   int blend_fwd_blocks, blend_bwd_blocks;
   long long total_pixels;

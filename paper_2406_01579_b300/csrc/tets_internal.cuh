@@ -72,6 +72,7 @@ struct Batch {
   int max_pf_chunks, max_pp_chunks;
   float s, prefilter_thresh, alpha_skip, alpha_cap, t_eps;
   int tile, flags;
+  int resort_window;
   int sort_blocks;
   long long key_cap;
   long long total_pixels;
@@ -95,6 +96,7 @@ struct Batch {
   float* pix_T;             // [total_pixels]
   int* pix_last;            // [total_pixels]
   int* pix_nfrag;           // [total_pixels]
+  float4* pix_CD;           // [total_pixels] final (C0, C1, C2, D)
   SceneD sc[TTS_MAX_SCENES];
   ViewD vw[TTS_MAX_VIEWS];
   int scene_views[TTS_MAX_VIEWS];

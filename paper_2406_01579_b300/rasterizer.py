@@ -34,6 +34,7 @@ class Params:
     t_eps: float = 1e-4
     accum_grad: bool = False
     forward_only: bool = False
+    resort_window: int = 0      # N_w of Sec. 3.3 (0..7)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -45,7 +46,7 @@ class Params:
         p.tile = self.tile
         p.flags = ((TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
                    | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0))
-        p.reserved = 0
+        p.resort_window = int(self.resort_window)
         return p
 
 

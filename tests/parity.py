@@ -41,7 +41,8 @@ def oracle_params(p: Params, band=1e-4):
     f = lambda x: float(np.float32(x))
     return oracle.make_params(s=f(p.s), tile=p.tile, pure=p.pure,
                               prefilter_thresh=f(p.prefilter_thresh), alpha_skip=f(p.alpha_skip),
-                              alpha_cap=f(p.alpha_cap), t_eps=f(p.t_eps), band=band)
+                              alpha_cap=f(p.alpha_cap), t_eps=f(p.t_eps), band=band,
+                              window=int(p.resort_window))
 
 
 def gpu_run(scenes, views, params: Params, upstream=None, lists=False):

@@ -69,6 +69,31 @@ def test_sphere16_gradients(sphere16, s):
         assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
 
 
+@pytest.mark.parametrize("nw", [1, 5])
+def test_resort_window_parity(sphere16, nw):
+    """Sec. 3.3 resort window: images and gradients against the oracle's
+    window of the same size."""
+    p = Params(s=60.0, tile=16, resort_window=nw)
+    cam = sphere16.cams[0]
+    up0 = synth.upstream_grads(6, [cam])[0]
+    orc0 = oracle_run(sphere16, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(sphere16, cam, p, upstream=up)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
+    _check_view(gpu["views"][0], orc0, f"window{nw}")
+    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"window{nw} {name}: rel err {err:.3e}"
+
+
+def test_resort_window_torus64(torus64):
+    p = Params(s=175.0, tile=16, resort_window=5)
+    cam = torus64.cams[0]
+    gpu = gpu_run([torus64], [(cam, 0)], p)
+    orc = oracle_run(torus64, cam, p)
+    _check_view(gpu["views"][0], orc, "torus64 window5")
+
+
 def test_gradients_pure_small_grids():
     for n, s in ((2, 3.0), (4, 6.0)):
         V = synth.grid_vertices(n)
