@@ -82,10 +82,10 @@ def lib():
         L.orc_fragment_grad.restype = ctypes.c_int
         L.orc_render.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P,
                                  P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int,
-                                 P, P, P]
+                                 P, P, P, P, P, P]
         L.orc_render.restype = ctypes.c_int
         L.orc_render_dirderiv.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P, P, P, P,
-                                          P, P, P, P, P, P, P]
+                                          P, P, P, P, P, P, P, P]
         L.orc_render_dirderiv.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -170,7 +170,7 @@ def bin_view(surv, T, V, cam, tile: int):
 
 
 def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=None,
-           nthreads: int = 0, V64=None, f64=None, rgb64=None):
+           nthreads: int = 0, V64=None, f64=None, rgb64=None, normals: bool = False):
     """Render one view; returns a dict with image (3,H,W), alpha, depth, amb,
     alt_*, nfrag, the binning lists and (if ``upstream`` = (dimg, dalpha,
     ddepth) is given) the FP64 gradients dV, df, drgb.  ``V64``/``f64``/``rgb64``
@@ -197,9 +197,13 @@ def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=
     nfrag = np.zeros((H, W), np.int32)
     N = len(V)
     dV = df = drgb = None
-    gi = ga = gd = None
+    gi = ga = gd = gn = None
+    nrm = np.zeros((3, H, W)) if normals else None
+    anrm = np.zeros((3, H, W)) if normals else None
     if upstream is not None:
-        gi, ga, gd = (_c(u, np.float32) for u in upstream)
+        gi, ga, gd = (_c(u, np.float32) for u in upstream[:3])
+        if len(upstream) > 3 and upstream[3] is not None:
+            gn = _c(upstream[3], np.float32)
         dV = np.zeros((N, 3))
         df = np.zeros(N)
         drgb = np.zeros((N, 3))
@@ -209,10 +213,10 @@ def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=
                           _p(bins["key_val"]), _p(bins["ranges"]), _p(img), _p(alpha), _p(depth),
                           _p(amb), _p(aimg), _p(aalpha), _p(adepth), _p(nfrag), _p(gi), _p(ga),
                           _p(gd), _p(dV), _p(df), _p(drgb), nthreads, _p(V64), _p(f64),
-                          _p(rgb64))
+                          _p(rgb64), _p(nrm), _p(anrm), _p(gn))
     assert rc == 0
     out = dict(image=img, alpha=alpha, depth=depth, amb=amb, alt_image=aimg, alt_alpha=aalpha,
-               alt_depth=adepth, nfrag=nfrag, surv=surv, bins=bins)
+               alt_depth=adepth, nfrag=nfrag, surv=surv, bins=bins, normal=nrm, alt_normal=anrm)
     if upstream is not None:
         out.update(dV=dV, df=df, drgb=drgb)
     return out
@@ -228,14 +232,15 @@ def dirderiv(V, T, f, rgb, cam, params: OrcParams, surv, bins, upstream, tV, tf,
     V64, f64, rgb64 = (None if a is None else _c(a, np.float64) for a in (V64, f64, rgb64))
     tV, tf, trgb = (_c(a, np.float64) for a in (tV, tf, trgb))
     surv = _c(surv, np.int32)
-    gi, ga, gd = (_c(u, np.float32) for u in upstream)
+    gi, ga, gd = (_c(u, np.float32) for u in upstream[:3])
+    gn = _c(upstream[3], np.float32) if len(upstream) > 3 and upstream[3] is not None else None
     c = make_cam(cam)
     out = np.zeros(2)
     lib().orc_render_dirderiv(len(V), _p(V), _p(f), _p(rgb), _p(T), len(surv),
                               _p(surv), _p(bins["rect"]), ctypes.byref(c),
                               ctypes.byref(params), _p(bins["key_val"]), _p(bins["ranges"]),
                               _p(gi), _p(ga), _p(gd), _p(tV), _p(tf), _p(trgb), _p(out),
-                              _p(V64), _p(f64), _p(rgb64))
+                              _p(V64), _p(f64), _p(rgb64), _p(gn))
     return float(out[0]), float(out[1])
 
 

@@ -86,6 +86,8 @@ template <int NT> Dual<NT> operator/(const Dual<NT>& a, double b) { return a * (
 template <int NT> Dual<NT> operator/(double a, const Dual<NT>& b) { return Dual<NT>(a) / b; }
 template <int NT> Dual<NT> dexp(const Dual<NT>& a) { double e = std::exp(a.v); Dual<NT> r(e); for (int i = 0; i < NT; ++i) r.d[i] = e * a.d[i]; return r; }
 template <int NT> Dual<NT> dexpm1(const Dual<NT>& a) { double e = std::exp(a.v); Dual<NT> r(std::expm1(a.v)); for (int i = 0; i < NT; ++i) r.d[i] = e * a.d[i]; return r; }
+template <int NT> Dual<NT> dsqrt(const Dual<NT>& a) { double r = std::sqrt(a.v); Dual<NT> o(r); for (int i = 0; i < NT; ++i) o.d[i] = (r > 0) ? a.d[i] / (2.0 * r) : 0.0; return o; }
+inline double dsqrt(double a) { return std::sqrt(a); }
 inline double dexp(double a) { return std::exp(a); }
 inline double dexpm1(double a) { return std::expm1(a); }
 template <int NT> double val(const Dual<NT>& a) { return a.v; }
@@ -189,6 +191,48 @@ struct Fields {
     for (int64_t i = 0; i < N; ++i) f[i] = f64 ? f64[i] : (double)f32[i];
   }
 };
+
+// ---------------------------------------------------------------------------
+// Per-tet normal (Sec. 3.2 "Per-tetrahedron normal", App. A.3): the SDF is
+// affine in the tet, [g; c0] = [x_j^T 1]^{-1} f.  Solved here on the
+// camera-space vertices by Gaussian elimination with partial pivoting, then
+// taken to world space (g_w = R^T g, the chain rule of x = R v + t) and
+// normalised.  Returns false for a zero gradient (normal 0).
+// ---------------------------------------------------------------------------
+template <class S>
+static bool tet_normal_world(const S X[4][3], const S F[4], const OrcCam& c, S n[3]) {
+  S M[4][5];
+  for (int j = 0; j < 4; ++j) {
+    for (int r = 0; r < 3; ++r) M[j][r] = X[j][r];
+    M[j][3] = S(1.0);
+    M[j][4] = F[j];
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (std::fabs(val(M[r][col])) > std::fabs(val(M[piv][col]))) piv = r;
+    if (val(M[piv][col]) == 0.0) return false;
+    if (piv != col)
+      for (int k = 0; k < 5; ++k) std::swap(M[piv][k], M[col][k]);
+    for (int r = col + 1; r < 4; ++r) {
+      const S fct = M[r][col] / M[col][col];
+      for (int k = col; k < 5; ++k) M[r][k] = M[r][k] - fct * M[col][k];
+    }
+  }
+  S sol[4];
+  for (int r = 3; r >= 0; --r) {
+    S acc = M[r][4];
+    for (int k = r + 1; k < 4; ++k) acc = acc - M[r][k] * sol[k];
+    sol[r] = acc / M[r][r];
+  }
+  S gw[3];
+  for (int r = 0; r < 3; ++r)
+    gw[r] = (double)c.R[r] * sol[0] + (double)c.R[3 + r] * sol[1] + (double)c.R[6 + r] * sol[2];
+  const S nn = dsqrt(gw[0] * gw[0] + gw[1] * gw[1] + gw[2] * gw[2]);
+  if (!(val(nn) > 0.0)) return false;
+  for (int r = 0; r < 3; ++r) n[r] = gw[r] / nn;
+  return true;
+}
 
 extern "C" {
 
@@ -348,16 +392,17 @@ struct Frag {
   double zbar;     // mean vertex depth (Eq. 2 depth term)
   double c[3];     // tet colour: mean of the vertex colours
   double zin;      // depth of the chord's entry point (App. A.2 z_p of the nearest hit)
+  double n[3];     // world-space unit normal (Eq. 2 normal term)
 };
 
 struct Blended {
   int32_t s;
-  double a, T, zbar, c[3];
+  double a, T, zbar, c[3], n[3];
   bool clamped;
 };
 
 struct PixelResult {
-  double C[3], D, O;
+  double C[3], D, O, N[3];
   int amb;            // ambiguous decisions met on the primary branch
   int first_amb;      // decision index of the first one (-1 none)
   std::vector<Blended> blended;
@@ -379,7 +424,7 @@ struct Staged {
 static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip, bool record,
                       PixelResult* r) {
   const bool pure = (p.flags & ORC_PURE) != 0;
-  double T = 1.0, C[3] = {0, 0, 0}, D = 0;
+  double T = 1.0, C[3] = {0, 0, 0}, D = 0, Nn[3] = {0, 0, 0};
   int dec = 0;
   r->amb = 0;
   r->first_amb = -1;
@@ -436,11 +481,15 @@ static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip,
       if (decide(Tn < p.t_eps, Tn, p.t_eps)) break;
     }
     for (int q = 0; q < 3; ++q) C[q] += T * a * f.c[q];
+    for (int q = 0; q < 3; ++q) Nn[q] += T * a * f.n[q];
     D += T * a * f.zbar;
-    if (record) r->blended.push_back({f.s, a, T, f.zbar, {f.c[0], f.c[1], f.c[2]}, clamped});
+    if (record)
+      r->blended.push_back({f.s, a, T, f.zbar, {f.c[0], f.c[1], f.c[2]}, {f.n[0], f.n[1], f.n[2]},
+                            clamped});
     T = Tn;
   }
   for (int q = 0; q < 3; ++q) r->C[q] = C[q];
+  for (int q = 0; q < 3; ++q) r->N[q] = Nn[q];
   r->D = D;
   r->O = 1.0 - T;
 }
@@ -468,7 +517,8 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
                double* alt_img, double* alt_alpha, double* alt_depth, int32_t* nfrag,
                const float* dimg, const float* dalpha, const float* ddepth,
                double* dV, double* df, double* drgb, int nthreads,
-               const double* V64, const double* f64, const double* rgb64) {
+               const double* V64, const double* f64, const double* rgb64,
+               double* nrm, double* alt_nrm, const float* dnrm) {
   const OrcCam& c = *cam;
   const Fields fld(N, V, f, rgb, V64, f64, rgb64);
   const int W = c.width, H = c.height, B = p->tile;
@@ -511,6 +561,7 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
         fg.zin = o.z_in;
         fg.alpha = opacity_eq1<double>(o.f_prev, o.f_next, p->s);
         fg.zbar = 0.25 * (X[0][2] + X[1][2] + X[2][2] + X[3][2]);
+        if (!tet_normal_world<double>(X, F, c, fg.n)) fg.n[0] = fg.n[1] = fg.n[2] = 0.0;
         for (int q = 0; q < 3; ++q)
           fg.c[q] = 0.25 * (((fld.rgb[3 * t[0] + q] + fld.rgb[3 * t[1] + q]) + fld.rgb[3 * t[2] + q]) + fld.rgb[3 * t[3] + q]);
         fr.push_back(fg);
@@ -518,6 +569,8 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
       composite(fr, *p, -1, want_grad, &pr);
       const int64_t pix = (int64_t)j * W + i;
       for (int q = 0; q < 3; ++q) img[q * HW + pix] = pr.C[q];
+      if (nrm)
+        for (int q = 0; q < 3; ++q) nrm[q * HW + pix] = pr.N[q];
       alpha[pix] = pr.O;
       depth[pix] = pr.D;
       amb[pix] = pr.amb;
@@ -525,10 +578,14 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
       if (pr.first_amb >= 0) {
         composite(fr, *p, pr.first_amb, false, &alt);
         for (int q = 0; q < 3; ++q) alt_img[q * HW + pix] = alt.C[q];
+        if (alt_nrm)
+          for (int q = 0; q < 3; ++q) alt_nrm[q * HW + pix] = alt.N[q];
         alt_alpha[pix] = alt.O;
         alt_depth[pix] = alt.D;
       } else {
         for (int q = 0; q < 3; ++q) alt_img[q * HW + pix] = pr.C[q];
+        if (alt_nrm)
+          for (int q = 0; q < 3; ++q) alt_nrm[q * HW + pix] = pr.N[q];
         alt_alpha[pix] = pr.O;
         alt_depth[pix] = pr.D;
       }
@@ -536,11 +593,14 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
       // ---- adjoint of the composite (primary branch) ----
       const double gC[3] = {dimg[pix], dimg[HW + pix], dimg[2 * HW + pix]};
       const double gO = dalpha[pix], gD = ddepth[pix];
+      const double gN[3] = {dnrm ? (double)dnrm[pix] : 0.0, dnrm ? (double)dnrm[HW + pix] : 0.0,
+                            dnrm ? (double)dnrm[2 * HW + pix] : 0.0};
       const double Tfin = 1.0 - pr.O;
       double Ssuf = 0.0;
       for (int b = (int)pr.blended.size() - 1; b >= 0; --b) {
         const Blended& bl = pr.blended[b];
-        const double w = gC[0] * bl.c[0] + gC[1] * bl.c[1] + gC[2] * bl.c[2] + gD * bl.zbar;
+        const double w = gC[0] * bl.c[0] + gC[1] * bl.c[1] + gC[2] * bl.c[2] + gD * bl.zbar +
+                         gN[0] * bl.n[0] + gN[1] * bl.n[1] + gN[2] * bl.n[2];
         const double dLda = bl.T * w - (Ssuf - gO * Tfin) / (1.0 - bl.a);
         Ssuf += bl.T * bl.a * w;
         const int32_t* t = T + 4 * (int64_t)surv[bl.s];
@@ -574,6 +634,28 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
             }
           }
         }
+        if (dnrm && (gN[0] != 0.0 || gN[1] != 0.0 || gN[2] != 0.0)) {
+          // normal term: dL/dn = T a gN through n = g_w / |g_w| (App. A.3)
+          typedef Dual<16> D16;
+          D16 X[4][3], F[4], nd[3];
+          for (int q = 0; q < 4; ++q) {
+            double xd[3];
+            cam_xform(c, &fld.V[3 * (int64_t)t[q]], xd);
+            for (int r = 0; r < 3; ++r) { X[q][r] = D16(xd[r]); X[q][r].d[3 * q + r] = 1.0; }
+            F[q] = D16(fld.f[t[q]]);
+            F[q].d[12 + q] = 1.0;
+          }
+          if (tet_normal_world<D16>(X, F, c, nd)) {
+            const double wgt = bl.T * bl.a;
+            for (int r = 0; r < 3; ++r) {
+              const double gn = wgt * gN[r];
+              for (int q = 0; q < 4; ++q) {
+                for (int k = 0; k < 3; ++k) dX[q][k] += gn * nd[r].d[3 * q + k];
+                dF[q] += gn * nd[r].d[12 + q];
+              }
+            }
+          }
+        }
         for (int q = 0; q < 4; ++q) {
           // world gradient: x_c = R v + t  ->  dv = R^T dx_c
           for (int r = 0; r < 3; ++r) {
@@ -601,7 +683,7 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
                         const int32_t* ranges, const float* dimg, const float* dalpha,
                         const float* ddepth, const double* tV, const double* tf,
                         const double* trgb, double* out, const double* V64, const double* f64,
-                        const double* rgb64) {
+                        const double* rgb64, const float* dnrm) {
   typedef Dual<1> D1;
   const OrcCam& c = *cam;
   const Fields fld(N, V, f, rgb, V64, f64, rgb64);
@@ -615,8 +697,8 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
     for (int i = 0; i < W; ++i) {
       const int tile = (j / B) * tx + (i / B);
       const double px = i + 0.5, py = j + 0.5;
-      D1 Tr(1.0), C[3] = {D1(0.0), D1(0.0), D1(0.0)}, Dp(0.0);
-      struct FD { D1 a, zb, cc[3]; double zin; };
+      D1 Tr(1.0), C[3] = {D1(0.0), D1(0.0), D1(0.0)}, Dp(0.0), Nn[3] = {D1(0.0), D1(0.0), D1(0.0)};
+      struct FD { D1 a, zb, cc[3], nn[3]; double zin; };
       std::vector<FD> in;
       for (int e = ranges[2 * tile]; e < ranges[2 * tile + 1]; ++e) {
         const int32_t s = key_val[e];
@@ -649,6 +731,7 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
         FD fd;
         fd.a = a;
         fd.zin = o.z_in.v;
+        if (!tet_normal_world<D1>(X, F, c, fd.nn)) fd.nn[0] = fd.nn[1] = fd.nn[2] = D1(0.0);
         fd.zb = 0.25 * (((X[0][2] + X[1][2]) + X[2][2]) + X[3][2]);
         for (int q = 0; q < 3; ++q) {
           D1 cc = 0.25 * (((D1(fld.rgb[3 * t[0] + q]) + D1(fld.rgb[3 * t[1] + q])) + D1(fld.rgb[3 * t[2] + q])) + D1(fld.rgb[3 * t[3] + q]));
@@ -675,12 +758,16 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
         D1 Tn = Tr * (1.0 - fd.a);
         if (!pure && Tn.v < p->t_eps) break;
         for (int q = 0; q < 3; ++q) C[q] = C[q] + Tr * fd.a * fd.cc[q];
+        for (int q = 0; q < 3; ++q) Nn[q] = Nn[q] + Tr * fd.a * fd.nn[q];
         Dp = Dp + Tr * fd.a * fd.zb;
         Tr = Tn;
       }
       const int64_t pix = (int64_t)j * W + i;
       L = L + (double)dimg[pix] * C[0] + (double)dimg[HW + pix] * C[1] + (double)dimg[2 * HW + pix] * C[2] +
           (double)dalpha[pix] * (1.0 - Tr) + (double)ddepth[pix] * Dp;
+      if (dnrm)
+        L = L + (double)dnrm[pix] * Nn[0] + (double)dnrm[HW + pix] * Nn[1] +
+            (double)dnrm[2 * HW + pix] * Nn[2];
     }
   out[0] = L.v;
   out[1] = L.d[0];

@@ -89,3 +89,40 @@ def test_window_adjoint_matches_dual_numbers():
     L, dL = oracle.dirderiv(sc.V, sc.T, sc.f, sc.rgb, cam, p, r["surv"], r["bins"], up, tV, tf, tr)
     pred = (r["dV"] * tV).sum() + (r["df"] * tf).sum() + (r["drgb"] * tr).sum()
     assert pred == pytest.approx(dL, rel=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# normal channel of Eq. 2 (Sec. 3.2 per-tet normal, App. A.3)
+# ---------------------------------------------------------------------------
+
+def test_normal_map_of_affine_sdf_is_its_unit_gradient():
+    """An affine SDF has one normal everywhere: N = O * n with n = grad/|grad|."""
+    rng = np.random.default_rng(21)
+    nvec = rng.normal(size=3)
+    nvec /= np.linalg.norm(nvec)
+    V = synth.grid_vertices(3)
+    T = synth.grid_tets(3)
+    f = (2.0 * (V.astype(np.float64) @ nvec) - 0.1).astype(np.float32)
+    rgb = np.ones((len(V), 3), np.float32)
+    cam = synth.orbit_camera(35.0, 25.0, 40, 40)
+    p = oracle.make_params(s=5.0, tile=8, pure=True)
+    r = oracle.render(V, T, f, rgb, cam, p, surv=np.arange(len(T), dtype=np.int32), normals=True)
+    expect = r["alpha"][None] * nvec[:, None, None]
+    assert np.abs(r["normal"] - expect).max() < 1e-6
+    assert (r["alpha"] > 0.05).sum() > 100
+
+
+def test_normal_adjoint_matches_dual_numbers():
+    sc = synth.scene_sphere16()
+    cam = sc.cams[0]
+    p = oracle.make_params(s=60.0)
+    up = list(synth.upstream_grads(8, [cam])[0])
+    up.append(np.random.default_rng(9).normal(size=(3, cam.height, cam.width)).astype(np.float32))
+    r = oracle.render(sc.V, sc.T, sc.f, sc.rgb, cam, p, upstream=up, normals=True)
+    rng = np.random.default_rng(10)
+    tV, tf, tr = rng.normal(size=sc.V.shape), rng.normal(size=sc.N), rng.normal(size=sc.rgb.shape)
+    L, dL = oracle.dirderiv(sc.V, sc.T, sc.f, sc.rgb, cam, p, r["surv"], r["bins"], up, tV, tf, tr)
+    pred = (r["dV"] * tV).sum() + (r["df"] * tf).sum() + (r["drgb"] * tr).sum()
+    assert pred == pytest.approx(dL, rel=1e-9)
+    Lr = sum((u * x).sum() for u, x in zip(up, (r["image"], r["alpha"], r["depth"], r["normal"])))
+    assert L == pytest.approx(Lr, rel=1e-12)
