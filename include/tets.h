@@ -17,6 +17,12 @@
  *   tts_render_bwd      gradients of a scalar loss through the forward, given
  *                       dL/dimage, dL/dalpha, dL/ddepth: written to the vertex
  *                       positions, vertex SDF values and vertex colours.
+ *   tts_render_fwd_ex / tts_render_bwd_ex
+ *                       the same with the normal map of Eq. 2 as a fourth
+ *                       channel (TTS_FLAG_NORMALS): N = sum_i T_i alpha_i n_i
+ *                       with n_i the world-space unit gradient of tet i's
+ *                       affine SDF (Sec. 3.2 "per-tetrahedron normal",
+ *                       App. A.3), computed once per scene preparation.
  *
  * Everything runs on one CUDA device, asynchronously on the caller's stream.
  * No entry point allocates device memory: the caller provides one workspace
@@ -82,7 +88,8 @@ enum {
 enum {
   TTS_FLAG_PURE = 1,        /* no cap / skip / early stop / pre-filter */
   TTS_FLAG_ACCUM_GRAD = 2,  /* backward adds into dV/df/drgb instead of overwriting */
-  TTS_FLAG_FORWARD_ONLY = 4 /* workspace without backward state; backward calls fail */
+  TTS_FLAG_FORWARD_ONLY = 4, /* workspace without backward state; backward calls fail */
+  TTS_FLAG_NORMALS = 8       /* also render the normal map: use the _ex calls */
 };
 
 #define TTS_MAX_SCENES 64
@@ -129,7 +136,7 @@ typedef struct {
 
 /* A batch: any number of scenes and views (up to the maxima above).  The
  * workspace layout is a pure function of (scenes' N, K, surv_capacity; views'
- * sizes and scenes; tile; key_capacity). */
+ * sizes and scenes; tile; flags; key_capacity). */
 typedef struct {
   const tts_scene* scenes; /* host array */
   int32_t n_scenes;
@@ -167,6 +174,30 @@ int tts_prepare_scene(const tts_batch* b, tts_stream stream);
 int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
                    tts_stream stream);
 
+/* Outputs of a forward (device, layouts as above).  normal: 3 * sum(H W)
+ * floats, planar like image; required with TTS_FLAG_NORMALS and NULL
+ * without it (TTS_ERR_ARG otherwise). */
+typedef struct {
+  float* image;
+  float* alpha;
+  float* depth;
+  float* normal;
+} tts_outputs;
+
+/* Upstream gradients of a backward (device, the layouts of tts_outputs).
+ * dalpha, ddepth and dnormal may be NULL (zero); dnormal must be NULL
+ * without TTS_FLAG_NORMALS. */
+typedef struct {
+  const float* dimage;
+  const float* dalpha;
+  const float* ddepth;
+  const float* dnormal;
+} tts_upstream;
+
+/* tts_render_fwd with a tts_outputs (the only forward that can write the
+ * normal map).  tts_render_fwd(b, i, a, d, s) equals this with normal NULL. */
+int tts_render_fwd_ex(const tts_batch* b, const tts_outputs* out, tts_stream stream);
+
 /* Backward of the last forward on this workspace.  dimage/dalpha/ddepth have
  * the layouts of the forward outputs; ddepth or dalpha may be NULL (zero).
  * dV, df, drgb: host arrays of n_scenes device pointers (N_s x 3, N_s,
@@ -174,6 +205,11 @@ int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
 int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha,
                    const float* ddepth, float* const* dV, float* const* df,
                    float* const* drgb, tts_stream stream);
+
+/* tts_render_bwd with a tts_upstream (adds dL/dnormal's contribution, which
+ * reaches V and f through each tet's normal). */
+int tts_render_bwd_ex(const tts_batch* b, const tts_upstream* up, float* const* dV,
+                      float* const* df, float* const* drgb, tts_stream stream);
 
 /* The forward and backward as their stages, for callers that interleave
  * their own work or time the stages: tts_render_fwd == tts_bin_views then
@@ -188,6 +224,8 @@ int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha,
                   const float* ddepth, tts_stream stream);       /* per-tile adjoint */
 int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df,
                     float* const* drgb, tts_stream stream);      /* record -> vertex */
+int tts_blend_fwd_ex(const tts_batch* b, const tts_outputs* out, tts_stream stream);
+int tts_blend_bwd_ex(const tts_batch* b, const tts_upstream* up, tts_stream stream);
 
 /* Number of kernels this library has launched in this process so far
  * (host-side counter, all threads). */

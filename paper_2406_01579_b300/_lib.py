@@ -25,6 +25,7 @@ TTS_STATUS_TIMEOUT = 8
 TTS_FLAG_PURE = 1
 TTS_FLAG_ACCUM_GRAD = 2
 TTS_FLAG_FORWARD_ONLY = 4
+TTS_FLAG_NORMALS = 8
 
 TTS_MAX_SCENES = 64
 TTS_MAX_VIEWS = 128
@@ -61,6 +62,16 @@ class tts_batch(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
+class tts_outputs(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_void_p), ("alpha", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p)]
+
+
+class tts_upstream(ctypes.Structure):
+    _fields_ = [("dimage", ctypes.c_void_p), ("dalpha", ctypes.c_void_p),
+                ("ddepth", ctypes.c_void_p), ("dnormal", ctypes.c_void_p)]
+
+
 class tts_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("n_scenes", ctypes.c_int32),
                 ("n_keys", ctypes.c_int64), ("n_surv", ctypes.c_int64 * TTS_MAX_SCENES),
@@ -68,7 +79,8 @@ class tts_info(ctypes.Structure):
 
 
 ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene", "tts_render_fwd",
-                "tts_render_bwd", "tts_bin_views", "tts_blend_fwd", "tts_blend_bwd",
+                "tts_render_bwd", "tts_render_fwd_ex", "tts_render_bwd_ex", "tts_bin_views",
+                "tts_blend_fwd", "tts_blend_bwd", "tts_blend_fwd_ex", "tts_blend_bwd_ex",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
                 "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
                 "tts_error_string", "tts_version")
@@ -97,6 +109,12 @@ def load():
     L.tts_prepare_scene.argtypes = [B, P]
     L.tts_render_fwd.argtypes = [B, P, P, P, P]
     L.tts_render_bwd.argtypes = [B, P, P, P, P, P, P, P]
+    O = ctypes.POINTER(tts_outputs)
+    U = ctypes.POINTER(tts_upstream)
+    L.tts_render_fwd_ex.argtypes = [B, O, P]
+    L.tts_render_bwd_ex.argtypes = [B, U, P, P, P, P]
+    L.tts_blend_fwd_ex.argtypes = [B, O, P]
+    L.tts_blend_bwd_ex.argtypes = [B, U, P]
     L.tts_bin_views.argtypes = [B, P]
     L.tts_blend_fwd.argtypes = [B, P, P, P, P]
     L.tts_blend_bwd.argtypes = [B, P, P, P, P]

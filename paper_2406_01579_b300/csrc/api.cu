@@ -70,6 +70,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     return TTS_ERR_ARG;
   if (b->key_capacity < 1 || b->key_capacity > 0x7fffffffLL) return TTS_ERR_ARG;
   if (pr.resort_window < 0 || pr.resort_window > 7) return TTS_ERR_ARG;
+  if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS))
+    return TTS_ERR_ARG;
   std::memset(&P->hb, 0, sizeof(Batch));
   Batch& B = P->hb;
   B.n_scenes = b->n_scenes;
@@ -84,7 +86,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   B.resort_window = pr.resort_window;
   B.key_cap = b->key_capacity;
   // scenes
-  long long surv_total = 0, flag_total = 0;
+  long long surv_total = 0, flag_total = 0, max_surv = 1;
   int pf_chunks = 0, max_pf = 1;
   std::vector<int> views_of(b->n_scenes, 0);
   for (int v = 0; v < b->n_views; ++v) {
@@ -108,6 +110,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     S.surv_cap = (sc.surv_capacity > 0) ? std::min<long long>(sc.surv_capacity, sc.K) : sc.K;
     S.surv_off = surv_total;
     surv_total += S.surv_cap;
+    max_surv = std::max(max_surv, S.surv_cap);
     S.flag_off = flag_total;
     flag_total += align_up(sc.K, 16);
     S.pf_chunks = (int)((sc.K + PF_CHUNK - 1) / PF_CHUNK);
@@ -194,6 +197,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_pL = take(sizeof(int) * pix);
   const size_t o_pN = take(sizeof(int) * pix);
   const size_t o_pC = take(sizeof(float4) * pix);
+  const bool normals = (pr.flags & TTS_FLAG_NORMALS) != 0;
+  const size_t o_sn = take(normals ? sizeof(float4) * surv_total : 0);
+  const size_t o_pNm = take((normals && !fwd_only) ? sizeof(float4) * pix : 0);
   P->bytes = align_up(off, 256);
   if (need_ws) {
     if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % 256) != 0)
@@ -221,6 +227,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.pix_last = reinterpret_cast<int*>(base + o_pL);
     B.pix_nfrag = reinterpret_cast<int*>(base + o_pN);
     B.pix_CD = reinterpret_cast<float4*>(base + o_pC);
+    B.surv_n = normals ? reinterpret_cast<float4*>(base + o_sn) : nullptr;
+    B.pix_N = (normals && !fwd_only) ? reinterpret_cast<float4*>(base + o_pNm) : nullptr;
   }
   HostPlan& H = P->hp;
   H.n_scenes = b->n_scenes;
@@ -233,8 +241,11 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.total_tiles = tiles;
   H.tile = pr.tile;
   H.window = pr.resort_window;
+  H.normals = normals;
+  H.normal_blocks = (int)std::min<long long>((max_surv + 255) / 256, 8LL * sm_count());
   H.tet_bwd_blocks = 2 * sm_count();
-  blend_grid(pr.tile, sm_count(), &H.blend_fwd_blocks, &H.blend_bwd_blocks);
+  blend_grid(pr.tile, normals, pr.resort_window, sm_count(), &H.blend_fwd_blocks,
+             &H.blend_bwd_blocks);
   H.total_pixels = pix;
   return TTS_OK;
 }
@@ -301,32 +312,60 @@ int tts_bin_views(const tts_batch* b, tts_stream stream) {
   return check_launch();
 }
 
-int tts_blend_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
-  if (!image || !alpha || !depth) return TTS_ERR_ARG;
+static bool outputs_ok(const tts_batch* b, const tts_outputs* o) {
+  if (!b || !o || !o->image || !o->alpha || !o->depth) return false;
+  const bool normals = (b->params.flags & TTS_FLAG_NORMALS) != 0;
+  return normals == (o->normal != nullptr);
+}
+
+static bool upstream_ok(const tts_batch* b, const tts_upstream* u) {
+  if (!b || !u || !u->dimage || (b->params.flags & TTS_FLAG_FORWARD_ONLY)) return false;
+  return u->dnormal == nullptr || (b->params.flags & TTS_FLAG_NORMALS) != 0;
+}
+
+int tts_blend_fwd_ex(const tts_batch* b, const tts_outputs* out, tts_stream stream) {
+  if (!outputs_ok(b, out)) return TTS_ERR_ARG;
   Plan P;
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  g_launches += launch_blend_fwd(P.hp, dev_desc(b, P), image, alpha, depth, st);
+  g_launches += launch_blend_fwd(P.hp, dev_desc(b, P), out->image, out->alpha, out->depth,
+                                 out->normal, st);
   return check_launch();
 }
 
-int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
-  if (!image || !alpha || !depth) return TTS_ERR_ARG;
+int tts_blend_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
+  const tts_outputs o = {image, alpha, depth, nullptr};
+  return tts_blend_fwd_ex(b, &o, stream);
+}
+
+int tts_render_fwd_ex(const tts_batch* b, const tts_outputs* out, tts_stream stream) {
+  if (!outputs_ok(b, out)) return TTS_ERR_ARG;
   int rc = tts_bin_views(b, stream);
   if (rc != TTS_OK) return rc;
-  return tts_blend_fwd(b, image, alpha, depth, stream);
+  return tts_blend_fwd_ex(b, out, stream);
+}
+
+int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth, tts_stream stream) {
+  const tts_outputs o = {image, alpha, depth, nullptr};
+  return tts_render_fwd_ex(b, &o, stream);
+}
+
+int tts_blend_bwd_ex(const tts_batch* b, const tts_upstream* up, tts_stream stream) {
+  if (!upstream_ok(b, up)) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  g_launches += launch_blend_bwd(P.hp, dev_desc(b, P), up->dimage, up->dalpha, up->ddepth,
+                                 up->dnormal, st);
+  return check_launch();
 }
 
 int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
                   tts_stream stream) {
-  if (!dimage || !b || (b->params.flags & TTS_FLAG_FORWARD_ONLY)) return TTS_ERR_ARG;
-  Plan P;
-  int rc = make_plan(b, &P, true);
-  if (rc != TTS_OK) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  g_launches += launch_blend_bwd(P.hp, dev_desc(b, P), dimage, dalpha, ddepth, st);
-  return check_launch();
+  const tts_upstream u = {dimage, dalpha, ddepth, nullptr};
+  return tts_blend_bwd_ex(b, &u, stream);
 }
 
 int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
@@ -357,12 +396,18 @@ int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, floa
   return check_launch();
 }
 
-int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
-                   float* const* dV, float* const* df, float* const* drgb, tts_stream stream) {
-  if (!dimage || !dV || !df || !drgb) return TTS_ERR_ARG;
-  int rc = tts_blend_bwd(b, dimage, dalpha, ddepth, stream);
+int tts_render_bwd_ex(const tts_batch* b, const tts_upstream* up, float* const* dV,
+                      float* const* df, float* const* drgb, tts_stream stream) {
+  if (!upstream_ok(b, up) || !dV || !df || !drgb) return TTS_ERR_ARG;
+  int rc = tts_blend_bwd_ex(b, up, stream);
   if (rc != TTS_OK) return rc;
   return tts_scatter_bwd(b, dV, df, drgb, stream);
+}
+
+int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
+                   float* const* dV, float* const* df, float* const* drgb, tts_stream stream) {
+  const tts_upstream u = {dimage, dalpha, ddepth, nullptr};
+  return tts_render_bwd_ex(b, &u, dV, df, drgb, stream);
 }
 
 int64_t tts_launch_count(void) { return g_launches.load(); }

@@ -160,6 +160,32 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* _
   }
 }
 
+// Per-survivor world unit normal n = g / |g| of the tet's affine SDF (Sec. 3.2
+// per-tet normal, App. A.3), view independent and hoisted into the scene
+// preparation (App. B.1).  grid (blocks, n_scenes)
+__global__ void __launch_bounds__(256) k_tet_normals(const Batch* __restrict__ B) {
+  const int s = blockIdx.y;
+  const SceneD& S = B->sc[s];
+  const int nsurv = B->ctr->n_surv[s];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
+    const int4 t = __ldg(&S.T[B->surv[S.surv_off + k]]);
+    const int id[4] = {t.x, t.y, t.z, t.w};
+    float3 v[4];
+    float f[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float* p = S.V + 3ll * id[j];
+      v[j] = f3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+      f[j] = __ldg(S.f + id[j]);
+    }
+    TetGrad G;
+    tet_grad(v, f, G);
+    float ih, sg;
+    const float3 n = tet_unit_normal(G, &ih, &sg);
+    B->surv_n[S.surv_off + k] = make_float4(n.x, n.y, n.z, 0.f);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // K2: per-view preprocess.  grid (max_pp_chunks, n_views)
 // ---------------------------------------------------------------------------
@@ -496,6 +522,10 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   k_prefilter_flags<<<g, PF_THREADS, 0, st>>>(dB);
   k_prefilter_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
   k_prefilter_compact<<<g, PF_THREADS, 0, st>>>(dB);
+  if (P.normals) {
+    k_tet_normals<<<dim3(P.normal_blocks, P.n_scenes), 256, 0, st>>>(dB);
+    return 4;
+  }
   return 3;
 }
 

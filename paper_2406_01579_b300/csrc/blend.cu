@@ -88,6 +88,27 @@ __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B,
   return vw;
 }
 
+// Per-slot normals of a view's tile lists: the survivor normals of its scene
+// (slot - rec_base is the survivor index).
+template <bool NRM>
+__device__ __forceinline__ const float4* surv_normals(const Batch* __restrict__ B,
+                                                      const ViewD& vw) {
+  if constexpr (NRM) return B->surv_n + (B->sc[vw.scene].surv_off - vw.rec_base);
+  return nullptr;
+}
+
+// Normal map output (planar like the image) and, when a backward follows,
+// the final per-pixel normal.
+__device__ __forceinline__ void store_normal(const Batch* __restrict__ B, const ViewD& vw,
+                                             long long p, float* __restrict__ normal, float N0,
+                                             float N1, float N2) {
+  const long long HW = (long long)vw.W * vw.H;
+  normal[3 * vw.pix_base + p] = N0;
+  normal[3 * vw.pix_base + HW + p] = N1;
+  normal[3 * vw.pix_base + 2 * HW + p] = N2;
+  if (B->pix_N) B->pix_N[vw.pix_base + p] = make_float4(N0, N1, N2, 0.f);
+}
+
 // ---------------------------------------------------------------------------
 // K6: forward blend.  Persistent warps; each takes 8x4 pixel blocks of tiles
 // from a queue (longest tile lists first), scans the tile's list 32 entries
@@ -95,13 +116,14 @@ __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B,
 // their records in its own shared-memory slice and blends them front to back
 // (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions).
 // ---------------------------------------------------------------------------
-template <int TILE>
+template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict__ B,
                                                        float* __restrict__ image,
                                                        float* __restrict__ alpha,
-                                                       float* __restrict__ depth) {
+                                                       float* __restrict__ depth,
+                                                       float* __restrict__ normal) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  __shared__ float4 st[WPB][REC_Q][32];
+  __shared__ float4 st[WPB][REC_Q + NRM][32];
   __shared__ int sidx[WPB][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
@@ -116,7 +138,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
     const ViewD& vw = decode_item<TILE>(B, item, wb);
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
     int last = 0, nfrag = 0;
     bool done = !wb.inimg;
     // one group of lookahead on (slot, bbox)
@@ -139,6 +162,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
           st[wid][0][pos] = q0;
 #pragma unroll
           for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+          if constexpr (NRM) st[wid][REC_Q][pos] = __ldg(nrm + slot);
           sidx[wid][pos] = lane;
         }
         __syncwarp();
@@ -169,6 +193,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
                   C1 = __fmaf_rn(wgt, q5.z, C1);
                   C2 = __fmaf_rn(wgt, q5.w, C2);
                   D = __fmaf_rn(wgt, q5.x, D);
+                  if constexpr (NRM) {
+                    const float4 n = st[wid][REC_Q][k];
+                    N0 = __fmaf_rn(wgt, n.x, N0);
+                    N1 = __fmaf_rn(wgt, n.y, N1);
+                    N2 = __fmaf_rn(wgt, n.z, N2);
+                  }
                   T = Tn;
                   last = g - rg.x + sidx[wid][k] + 1;
                 }
@@ -195,6 +225,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
       B->pix_last[vw.pix_base + p] = last;
       B->pix_nfrag[vw.pix_base + p] = nfrag;
       B->pix_CD[vw.pix_base + p] = make_float4(C0, C1, C2, D);
+      if constexpr (NRM) store_normal(B, vw, p, normal, N0, N1, N2);
     }
   }
   queue_done(&c->work_fwd, &c->done_fwd);
@@ -252,9 +283,12 @@ __device__ __forceinline__ void win_pop(Win& w) {
 }
 
 // Blend one fragment leaving the window (forward).
-__device__ __forceinline__ void win_emit_fwd(const float4* __restrict__ rec, unsigned slot, float a,
+template <bool NRM>
+__device__ __forceinline__ void win_emit_fwd(const float4* __restrict__ rec,
+                                             const float4* __restrict__ nrm, unsigned slot, float a,
                                              bool pure, float eps, float& T, float& C0, float& C1,
-                                             float& C2, float& D, bool& done) {
+                                             float& C2, float& D, float& N0, float& N1, float& N2,
+                                             bool& done) {
   const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
   if (!pure && Tn < eps) {
     done = true;
@@ -266,14 +300,21 @@ __device__ __forceinline__ void win_emit_fwd(const float4* __restrict__ rec, uns
   C1 = __fmaf_rn(wgt, q5.z, C1);
   C2 = __fmaf_rn(wgt, q5.w, C2);
   D = __fmaf_rn(wgt, q5.x, D);
+  if constexpr (NRM) {
+    const float4 n = __ldg(nrm + slot);
+    N0 = __fmaf_rn(wgt, n.x, N0);
+    N1 = __fmaf_rn(wgt, n.y, N1);
+    N2 = __fmaf_rn(wgt, n.z, N2);
+  }
   T = Tn;
 }
 
-template <int TILE>
+template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restrict__ B,
                                                            float* __restrict__ image,
                                                            float* __restrict__ alpha,
-                                                           float* __restrict__ depth) {
+                                                           float* __restrict__ depth,
+                                                           float* __restrict__ normal) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q][32];
   __shared__ unsigned sslot[WPB][32];
@@ -291,7 +332,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
     const ViewD& vw = decode_item<TILE>(B, item, wb);
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f;
+    const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
+    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
     int nfrag = 0;
     bool done = !wb.inimg;
     Win win;
@@ -334,7 +376,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
                 const unsigned s0 = win.sl[0];
                 const float a0 = win.a[0];
                 win_pop(win);
-                win_emit_fwd(rec, s0, a0, pure, eps, T, C0, C1, C2, D, done);
+                win_emit_fwd<NRM>(rec, nrm, s0, a0, pure, eps, T, C0, C1, C2, D, N0, N1, N2, done);
               }
             }
           }
@@ -348,7 +390,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
       const unsigned s0 = win.sl[0];
       const float a0 = win.a[0];
       win_pop(win);
-      win_emit_fwd(rec, s0, a0, pure, eps, T, C0, C1, C2, D, done);
+      win_emit_fwd<NRM>(rec, nrm, s0, a0, pure, eps, T, C0, C1, C2, D, N0, N1, N2, done);
     }
     if (wb.inimg) {
       const long long HW = (long long)vw.W * vw.H;
@@ -362,6 +404,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
       B->pix_last[vw.pix_base + p] = rg.y - rg.x;
       B->pix_nfrag[vw.pix_base + p] = nfrag;
       B->pix_CD[vw.pix_base + p] = make_float4(C0, C1, C2, D);
+      if constexpr (NRM) store_normal(B, vw, p, normal, N0, N1, N2);
     }
   }
   queue_done(&c->work_fwd, &c->done_fwd);
@@ -375,16 +418,19 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
 // (warp-reduced; one vector atomic per field group) into the per-slot record
 // gradient buffer.
 // ---------------------------------------------------------------------------
-template <int TILE>
+template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict__ B,
                                                        const float* __restrict__ dimage,
                                                        const float* __restrict__ dalpha,
-                                                       const float* __restrict__ ddepth) {
+                                                       const float* __restrict__ ddepth,
+                                                       const float* __restrict__ dnormal) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  __shared__ float4 st[WPB][REC_Q][32];
+  constexpr int NF = NRM ? 23 : 20;          // gradient fields per fragment
+  constexpr int RS = NRM ? 23 : 21;          // row stride (odd: no bank conflicts)
+  __shared__ float4 st[WPB][REC_Q + NRM][32];
   __shared__ int sidx[WPB][32];
   __shared__ unsigned sslot[WPB][32];
-  __shared__ float red[WPB][32][21];   // per-lane gradient rows (odd stride: no bank conflicts)
+  __shared__ float red[WPB][32][RS];         // per-lane gradient rows
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
@@ -400,7 +446,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;
     const long long p = (long long)wb.py * vw.W + wb.px;
+    const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
     float Tfin = 1.f, gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gO = 0.f, gD = 0.f;
+    float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
     int last = 0;
     if (wb.inimg) {
       Tfin = B->pix_T[vw.pix_base + p];
@@ -410,6 +458,11 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
       gC2 = dimage[3 * vw.pix_base + 2 * HW + p];
       if (dalpha) gO = dalpha[vw.pix_base + p];
       if (ddepth) gD = ddepth[vw.pix_base + p];
+      if (NRM && dnormal) {
+        gN0 = dnormal[3 * vw.pix_base + p];
+        gN1 = dnormal[3 * vw.pix_base + HW + p];
+        gN2 = dnormal[3 * vw.pix_base + 2 * HW + p];
+      }
     }
     int maxlast = last;
 #pragma unroll
@@ -438,6 +491,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         st[wid][0][pos] = q0;
 #pragma unroll
         for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
+        if constexpr (NRM) st[wid][REC_Q][pos] = __ldg(nrm + slot);
         sidx[wid][pos] = lane;
         sslot[wid][pos] = slot;
       }
@@ -459,11 +513,16 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         if (mc == 0u) continue;
         float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
         float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+        float gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
         if (contrib) {
           const float4 q5 = st[wid][5][k];
           const float om = __fsub_rn(1.f, a);
           const float Ti = __fdiv_rn(T, om);
-          const float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+          float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+          if constexpr (NRM) {
+            const float4 n = st[wid][REC_Q][k];
+            wv += gN0 * n.x + gN1 * n.y + gN2 * n.z;
+          }
           const float dLda = Ti * wv - (S - gOT) / om;
           S += Ti * a * wv;
           T = Ti;
@@ -472,6 +531,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
           gc0 = wgt * gC0;
           gc1 = wgt * gC1;
           gc2 = wgt * gC2;
+          gn0 = wgt * gN0;
+          gn1 = wgt * gN1;
+          gn2 = wgt * gN2;
           const bool clamped = !pure && (o.alpha > cap);
           if (!clamped) {
             // alpha = (1 - e1) B with x = s (f_prev - f_next), y = s f_next
@@ -502,10 +564,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
             atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
             atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
             atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+            if constexpr (NRM) atomicAdd(dst, make_float4(gn0, gn1, gn2, 0.f));
           }
         } else {
-          // transpose through shared memory: lane j < 20 sums field j over the
-          // contributing lanes' rows and issues one atomic
+          // transpose through shared memory: lane j < NF sums field j over the
+          // contributing lanes' rows and issues one atomic (fields 0..19 are
+          // record components 4..23, fields 20..22 the normal gradient at 0..2)
           if (contrib) {
             float* row = red[wid][lane];
 #pragma unroll
@@ -516,9 +580,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
             }
             row[12] = gF; row[13] = gK0; row[14] = gKx; row[15] = gKy;
             row[16] = gz; row[17] = gc0; row[18] = gc1; row[19] = gc2;
+            if constexpr (NRM) {
+              row[20] = gn0; row[21] = gn1; row[22] = gn2;
+            }
           }
           __syncwarp();
-          if (lane < 20) {
+          if (lane < NF) {
             float acc = 0.f;
             unsigned mm = mc;
             while (mm) {
@@ -526,7 +593,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
               mm &= mm - 1u;
               acc += red[wid][r][lane];
             }
-            if (acc != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 1) + lane, acc);
+            if (acc != 0.f)
+              atomicAdd(reinterpret_cast<float*>(dst) + (lane < 20 ? 4 + lane : lane - 20), acc);
           }
           __syncwarp();
         }
@@ -543,11 +611,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
 // W - P - T_i a_i w_i, so dL/da_i = T_i w_i - (suffix - gO T_final)/(1 - a_i).
 // Each emitted fragment's record is reloaded and its chord recomputed; the
 // record-field gradients leave as per-lane vector atomics.
-template <int TILE>
+template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restrict__ B,
                                                            const float* __restrict__ dimage,
                                                            const float* __restrict__ dalpha,
-                                                           const float* __restrict__ ddepth) {
+                                                           const float* __restrict__ ddepth,
+                                                           const float* __restrict__ dnormal) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q][32];
   __shared__ unsigned sslot[WPB][32];
@@ -568,7 +637,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;
     const long long pp = (long long)wb.py * vw.W + wb.px;
+    const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
     float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gO = 0.f, gD = 0.f, Tfin = 1.f, Wt = 0.f;
+    float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
     if (wb.inimg) {
       Tfin = B->pix_T[vw.pix_base + pp];
       gC0 = dimage[3 * vw.pix_base + pp];
@@ -578,6 +649,13 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       if (ddepth) gD = ddepth[vw.pix_base + pp];
       const float4 cd = B->pix_CD[vw.pix_base + pp];
       Wt = gC0 * cd.x + gC1 * cd.y + gC2 * cd.z + gD * cd.w;
+      if (NRM && dnormal) {
+        gN0 = dnormal[3 * vw.pix_base + pp];
+        gN1 = dnormal[3 * vw.pix_base + HW + pp];
+        gN2 = dnormal[3 * vw.pix_base + 2 * HW + pp];
+        const float4 nf = B->pix_N[vw.pix_base + pp];
+        Wt += gN0 * nf.x + gN1 * nf.y + gN2 * nf.z;
+      }
     }
     const float gOT = gO * Tfin;
     float T = 1.f, Pw = 0.f;
@@ -596,7 +674,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       const float4 q4 = __ldg(r + 4), q5 = __ldg(r + 5);
       const Chord ch = chord_eval(q0, q1, q2, q3, wb.fpx, wb.fpy);
       const Opacity o = opacity_eval(q4, ch);
-      const float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+      float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
+      float4 n = make_float4(0.f, 0.f, 0.f, 0.f);
+      if constexpr (NRM) {
+        n = __ldg(nrm + slot);
+        wv += gN0 * n.x + gN1 * n.y + gN2 * n.z;
+      }
       const float twa = T * a * wv;
       const float suffix = Wt - Pw - twa;
       const float dLda = T * wv - (suffix - gOT) / __fsub_rn(1.f, a);
@@ -625,6 +708,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
         atomicAdd(dst + 4, make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy));
       }
       atomicAdd(dst + 5, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2));
+      if constexpr (NRM) atomicAdd(dst, make_float4(wgt * gN0, wgt * gN1, wgt * gN2, 0.f));
       T = Tn;
     };
     for (int g = rg.x; g < rg.y; g += 32) {
@@ -690,6 +774,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
 // clears the record gradient slot, and scatters into dV, df, drgb.
 // The reference point x_r (ray through the bbox corner pixel at the centroid
 // depth) is held constant: the fragment opacity does not depend on it.
+// With the normal map channel, the per-view dL/dn (record gradient q0.xyz)
+// is summed over the views and pushed once through the world-space
+// n = g / |g| of the tet's affine SDF.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
   const int s = blockIdx.y;
@@ -699,6 +786,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
   float* __restrict__ gV = go.dV[s];
   float* __restrict__ gf = go.df[s];
   float* __restrict__ gc = go.drgb[s];
+  const bool nrm = (B->flags & TTS_FLAG_NORMALS) != 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
     const int tet = B->surv[S.surv_off + k];
     TetIn in;
@@ -706,6 +794,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
     float3 dv[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
     float dfv[4] = {0.f, 0.f, 0.f, 0.f};
     float3 dcol = f3(0, 0, 0);
+    float3 dnw = f3(0, 0, 0);
     bool any = false;
     for (int vi = 0; vi < S.view_cnt; ++vi) {
       const int v = B->scene_views[S.view_off + vi];
@@ -713,14 +802,17 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       const long long slot = vw.rec_base + k;
       if (B->rec_nt[slot] == 0) continue;
       float4* gq = B->rec_grad + slot * REC_Q;
+      const float4 g0 = nrm ? gq[0] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4], g5 = gq[5];
-      const float mag = fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
+      const float mag = fabsf(g0.x) + fabsf(g0.y) + fabsf(g0.z) + fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
                         fabsf(g2.y) + fabsf(g2.z) + fabsf(g2.w) + fabsf(g3.x) + fabsf(g3.y) +
                         fabsf(g3.z) + fabsf(g3.w) + fabsf(g4.x) + fabsf(g4.y) + fabsf(g4.z) +
                         fabsf(g4.w) + fabsf(g5.x) + fabsf(g5.y) + fabsf(g5.z) + fabsf(g5.w);
       if (mag == 0.f) continue;
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (nrm) gq[0] = z4;
       gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
+      dnw = dnw + f3(g0.x, g0.y, g0.z);
       if (!loaded) { load_tet(S, tet, in); loaded = true; }
       Geo G;
       tet_geometry(vw, sv, in, G);
@@ -786,6 +878,17 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       }
       dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
     }
+    if (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f) {
+      if (!loaded) { load_tet(S, tet, in); loaded = true; }
+      TetGrad TG;
+      tet_grad(in.v, in.f, TG);
+      float ih, sg;
+      const float3 n = tet_unit_normal(TG, &ih, &sg);
+      if (ih > 0.f) {
+        tet_grad_adjoint(TG, tet_normal_adjoint(n, ih, sg, dnw), 0.f, dv, dfv);
+        any = true;
+      }
+    }
     if (!any) continue;
     const int4 t = __ldg(&S.T[tet]);
     const int id[4] = {t.x, t.y, t.z, t.w};
@@ -813,69 +916,81 @@ static int occ_blocks(K kern, int sms) {
   return per * sms;
 }
 
-void blend_grid(int tile, int sms, int* fwd_blocks, int* bwd_blocks) {
-  static int cache[3][2] = {{0, 0}, {0, 0}, {0, 0}};
-  const int ti = (tile == 8) ? 0 : (tile == 16) ? 1 : 2;
-  if (cache[ti][0] > 0) {
-    *fwd_blocks = cache[ti][0];
-    *bwd_blocks = cache[ti][1];
-    return;
-  }
-  switch (tile) {
-    case 8:
-      *fwd_blocks = occ_blocks(k_blend_fwd<8>, sms);
-      *bwd_blocks = occ_blocks(k_blend_bwd<8>, sms);
-      break;
-    case 16:
-      *fwd_blocks = occ_blocks(k_blend_fwd<16>, sms);
-      *bwd_blocks = occ_blocks(k_blend_bwd<16>, sms);
-      break;
-    default:
-      *fwd_blocks = occ_blocks(k_blend_fwd<32>, sms);
-      *bwd_blocks = occ_blocks(k_blend_bwd<32>, sms);
-      break;
-  }
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) {
-    cache[ti][0] = *fwd_blocks;
-    cache[ti][1] = *bwd_blocks;
+template <int TILE, bool NRM>
+static void blend_grid_t(int sms, int window, int* fwd_blocks, int* bwd_blocks) {
+  if (window > 0) {
+    *fwd_blocks = occ_blocks(k_blend_fwd_win<TILE, NRM>, sms);
+    *bwd_blocks = occ_blocks(k_blend_bwd_win<TILE, NRM>, sms);
+  } else {
+    *fwd_blocks = occ_blocks(k_blend_fwd<TILE, NRM>, sms);
+    *bwd_blocks = occ_blocks(k_blend_bwd<TILE, NRM>, sms);
   }
 }
 
-int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
-                     cudaStream_t st) {
-  const int g = P.blend_fwd_blocks;
-  if (P.window > 0) {
-    switch (P.tile) {
-      case 8: k_blend_fwd_win<8><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
-      case 16: k_blend_fwd_win<16><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
-      default: k_blend_fwd_win<32><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
-    }
-    return 1;
+void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, int* bwd_blocks) {
+  static int cache[3][2][2][2] = {};
+  const int ti = (tile == 8) ? 0 : (tile == 16) ? 1 : 2;
+  const int ni = normals ? 1 : 0, wi = (window > 0) ? 1 : 0;
+  int* c = cache[ti][ni][wi];
+  if (c[0] > 0) {
+    *fwd_blocks = c[0];
+    *bwd_blocks = c[1];
+    return;
   }
-  switch (P.tile) {
-    case 8: k_blend_fwd<8><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
-    case 16: k_blend_fwd<16><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
-    default: k_blend_fwd<32><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth); break;
+  switch (tile * 2 + ni) {
+    case 16: blend_grid_t<8, false>(sms, window, fwd_blocks, bwd_blocks); break;
+    case 17: blend_grid_t<8, true>(sms, window, fwd_blocks, bwd_blocks); break;
+    case 32: blend_grid_t<16, false>(sms, window, fwd_blocks, bwd_blocks); break;
+    case 33: blend_grid_t<16, true>(sms, window, fwd_blocks, bwd_blocks); break;
+    case 64: blend_grid_t<32, false>(sms, window, fwd_blocks, bwd_blocks); break;
+    default: blend_grid_t<32, true>(sms, window, fwd_blocks, bwd_blocks); break;
+  }
+  c[0] = *fwd_blocks;
+  c[1] = *bwd_blocks;
+}
+
+template <int TILE, bool NRM>
+static void fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
+                  float* normal, cudaStream_t st) {
+  const int g = P.blend_fwd_blocks;
+  if (P.window > 0)
+    k_blend_fwd_win<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+  else
+    k_blend_fwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+}
+
+template <int TILE, bool NRM>
+static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
+                  const float* ddepth, const float* dnormal, cudaStream_t st) {
+  const int g = P.blend_bwd_blocks;
+  if (P.window > 0)
+    k_blend_bwd_win<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth, dnormal);
+  else
+    k_blend_bwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth, dnormal);
+}
+
+int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
+                     float* normal, cudaStream_t st) {
+  switch (P.tile * 2 + (P.normals ? 1 : 0)) {
+    case 16: fwd_t<8, false>(P, dB, image, alpha, depth, normal, st); break;
+    case 17: fwd_t<8, true>(P, dB, image, alpha, depth, normal, st); break;
+    case 32: fwd_t<16, false>(P, dB, image, alpha, depth, normal, st); break;
+    case 33: fwd_t<16, true>(P, dB, image, alpha, depth, normal, st); break;
+    case 64: fwd_t<32, false>(P, dB, image, alpha, depth, normal, st); break;
+    default: fwd_t<32, true>(P, dB, image, alpha, depth, normal, st); break;
   }
   return 1;
 }
 
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                     const float* ddepth, cudaStream_t st) {
-  const int g = P.blend_bwd_blocks;
-  if (P.window > 0) {
-    switch (P.tile) {
-      case 8: k_blend_bwd_win<8><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-      case 16: k_blend_bwd_win<16><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-      default: k_blend_bwd_win<32><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-    }
-    return 1;
-  }
-  switch (P.tile) {
-    case 8: k_blend_bwd<8><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-    case 16: k_blend_bwd<16><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
-    default: k_blend_bwd<32><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth); break;
+                     const float* ddepth, const float* dnormal, cudaStream_t st) {
+  switch (P.tile * 2 + (P.normals ? 1 : 0)) {
+    case 16: bwd_t<8, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    case 17: bwd_t<8, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    case 32: bwd_t<16, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    case 33: bwd_t<16, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    case 64: bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    default: bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
   }
   return 1;
 }

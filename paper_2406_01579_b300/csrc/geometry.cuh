@@ -220,6 +220,72 @@ __device__ __forceinline__ void write_record(const ViewD& vw, float s, const Tet
   out[5] = make_float4(G.zbar, c.x, c.y, c.z);
 }
 
+// World-space SDF gradient of a tet (App. A.3).  With edge rows
+// y_j = v_j - v_0 and d_j = f_j - f_0 (j = 1..3) the affine field has
+// g = Y^-1 d = h / det, h = d_1 c_1 + d_2 c_2 + d_3 c_3, where c_1 = y_2 x y_3,
+// c_2 = y_3 x y_1, c_3 = y_1 x y_2 are the cofactor columns and det = y_1 . c_1.
+struct TetGrad {
+  float3 y[3], c[3];
+  float d[3];
+  float3 h;      // det * g
+  float det;
+};
+
+__device__ __forceinline__ void tet_grad(const float3 v[4], const float f[4], TetGrad& G) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    G.y[j] = v[j + 1] - v[0];
+    G.d[j] = f[j + 1] - f[0];
+  }
+  G.c[0] = cross3(G.y[1], G.y[2]);
+  G.c[1] = cross3(G.y[2], G.y[0]);
+  G.c[2] = cross3(G.y[0], G.y[1]);
+  G.h = G.d[0] * G.c[0] + G.d[1] * G.c[1] + G.d[2] * G.c[2];
+  G.det = dot3(G.y[0], G.c[0]);
+}
+
+// Unit normal n = g / |g| = sign(det) h / |h| (Sec. 3.2 per-tet normal); zero
+// for a flat tet or a constant field.  *inv_h = 1/|h| (0 when degenerate),
+// *sg = sign(det).
+__device__ __forceinline__ float3 tet_unit_normal(const TetGrad& G, float* inv_h, float* sg) {
+  const float hh = dot3(G.h, G.h);
+  *sg = (G.det < 0.f) ? -1.f : 1.f;
+  if (!(hh > 0.f) || G.det == 0.f) {
+    *inv_h = 0.f;
+    return f3(0.f, 0.f, 0.f);
+  }
+  const float ih = 1.f / sqrtf(hh);
+  *inv_h = ih;
+  return (*sg * ih) * G.h;
+}
+
+// Adjoint of (h, det) -> (v, f): adds dL/dv_j and dL/df_j given dL/dh, dL/ddet.
+__device__ __forceinline__ void tet_grad_adjoint(const TetGrad& G, float3 dh, float ddet,
+                                                 float3 dv[4], float df[4]) {
+  float3 dc[3], dy[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float dd = dot3(G.c[j], dh);
+    df[j + 1] += dd;
+    df[0] -= dd;
+    dc[j] = G.d[j] * dh;
+  }
+  // det = y_0 . c_0 with d det / d y_j = c_j
+  dy[0] = cross3(dc[1], G.y[2]) + cross3(G.y[1], dc[2]) + ddet * G.c[0];
+  dy[1] = cross3(G.y[2], dc[0]) + cross3(dc[2], G.y[0]) + ddet * G.c[1];
+  dy[2] = cross3(dc[0], G.y[1]) + cross3(G.y[0], dc[1]) + ddet * G.c[2];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    dv[j + 1] = dv[j + 1] + dy[j];
+    dv[0] = dv[0] - dy[j];
+  }
+}
+
+// Adjoint of the unit normal: dL/dh from dL/dn.
+__device__ __forceinline__ float3 tet_normal_adjoint(float3 n, float inv_h, float sg, float3 dn) {
+  return (sg * inv_h) * (dn - dot3(n, dn) * n);
+}
+
 __device__ __forceinline__ void load_tet(const SceneD& S, int tet, TetIn& in) {
   const int4 t = __ldg(&S.T[tet]);
   const int id[4] = {t.x, t.y, t.z, t.w};

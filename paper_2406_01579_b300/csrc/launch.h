@@ -15,6 +15,8 @@ struct HostPlan {
   int total_tiles;
   int tile;
   int window;
+  bool normals;
+  int normal_blocks;
   int tet_bwd_blocks;
   int blend_fwd_blocks, blend_bwd_blocks;
   long long total_pixels;
@@ -30,12 +32,12 @@ struct GradOut {
 int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
-                     cudaStream_t st);
+                     float* normal, cudaStream_t st);
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                     const float* ddepth, cudaStream_t st);
+                     const float* ddepth, const float* dnormal, cudaStream_t st);
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);
 // persistent grid sizes of the blend kernels for a tile size (occupancy based)
-void blend_grid(int tile, int sms, int* fwd_blocks, int* bwd_blocks);
+void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, int* bwd_blocks);
 
 }  // namespace tts

@@ -97,6 +97,8 @@ struct Batch {
   int* pix_last;            // [total_pixels]
   int* pix_nfrag;           // [total_pixels]
   float4* pix_CD;           // [total_pixels] final (C0, C1, C2, D)
+  float4* surv_n;           // [sum surv_cap] world unit normal per survivor (normals only)
+  float4* pix_N;            // [total_pixels] final normal (normals with a backward)
   SceneD sc[TTS_MAX_SCENES];
   ViewD vw[TTS_MAX_VIEWS];
   int scene_views[TTS_MAX_VIEWS];
@@ -117,7 +119,8 @@ struct Batch {
 //       x_r = z_r * ray(i0+.5, j0+.5).  Along the pixel ray, with
 //       lin = Kx dx + Ky dy:  s f(t) = (F + lin) + (K0 + lin) (t - z_r) / z_r.
 //   q5  (zbar, r, g, b): mean vertex depth (Eq. 2 depth) and mean colour.
-// The record gradient buffer has the same layout (q0 unused).
+// The record gradient buffer has the same layout; its q0.xyz holds dL/dn of
+// the tet's world unit normal (normal map channel).
 // ---------------------------------------------------------------------------
 constexpr int REC_Q = 6;
 

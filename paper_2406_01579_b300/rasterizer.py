@@ -17,8 +17,9 @@ from typing import Sequence
 import torch
 
 from . import _lib
-from ._lib import (TTS_FLAG_ACCUM_GRAD, TTS_FLAG_FORWARD_ONLY, TTS_FLAG_PURE, TTS_STATUS_BAD_INDEX,
-                   TTS_STATUS_KEY_OVERFLOW, TTS_STATUS_SURV_OVERFLOW, TetsError, check)
+from ._lib import (TTS_FLAG_ACCUM_GRAD, TTS_FLAG_FORWARD_ONLY, TTS_FLAG_NORMALS, TTS_FLAG_PURE,
+                   TTS_STATUS_BAD_INDEX, TTS_STATUS_KEY_OVERFLOW, TTS_STATUS_SURV_OVERFLOW,
+                   TetsError, check)
 
 
 @dataclasses.dataclass
@@ -35,6 +36,7 @@ class Params:
     accum_grad: bool = False
     forward_only: bool = False
     resort_window: int = 0      # N_w of Sec. 3.3 (0..7)
+    normals: bool = False       # also render the Eq. 2 normal map
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -45,7 +47,8 @@ class Params:
         p.t_eps = self.t_eps
         p.tile = self.tile
         p.flags = ((TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
-                   | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0))
+                   | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0)
+                   | (TTS_FLAG_NORMALS if self.normals else 0))
         p.resort_window = int(self.resort_window)
         return p
 
@@ -180,19 +183,40 @@ class Rasterizer:
         check(self.lib.tts_prepare_scene(ctypes.byref(b), _stream_ptr()), "tts_prepare_scene")
 
     def _outputs(self):
+        """Flat output tensors: (image, alpha, depth) and, with
+        ``params.normals``, the normal map (3 planes per view, like image)."""
         dev = self.device
         img = torch.empty(3 * self.total_pixels, dtype=torch.float32, device=dev)
         alpha = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
         depth = torch.empty(self.total_pixels, dtype=torch.float32, device=dev)
+        if self.params.normals:
+            return img, alpha, depth, torch.empty(3 * self.total_pixels, dtype=torch.float32,
+                                                  device=dev)
         return img, alpha, depth
+
+    @staticmethod
+    def _c_outputs(out) -> _lib.tts_outputs:
+        o = _lib.tts_outputs()
+        o.image, o.alpha, o.depth = out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr()
+        o.normal = out[3].data_ptr() if len(out) > 3 else None
+        return o
+
+    @staticmethod
+    def _c_upstream(upstream) -> _lib.tts_upstream:
+        ptr = [(x.data_ptr() if x is not None else None) for x in upstream]
+        ptr += [None] * (4 - len(ptr))
+        u = _lib.tts_upstream()
+        u.dimage, u.dalpha, u.ddepth, u.dnormal = ptr
+        return u
 
     def forward_raw(self, out=None):
         """Enqueue the forward (no synchronisation, no capacity check)."""
-        img, alpha, depth = out if out is not None else self._outputs()
+        out = tuple(out) if out is not None else self._outputs()
         b = self.batch()
-        check(self.lib.tts_render_fwd(ctypes.byref(b), img.data_ptr(), alpha.data_ptr(),
-                                      depth.data_ptr(), _stream_ptr()), "tts_render_fwd")
-        return img, alpha, depth
+        o = self._c_outputs(out)
+        check(self.lib.tts_render_fwd_ex(ctypes.byref(b), ctypes.byref(o), _stream_ptr()),
+              "tts_render_fwd_ex")
+        return out
 
     def forward(self, prepare: bool = True, check_status: bool = True, out=None):
         """prepare (optional) + forward; with ``check_status`` the status word
@@ -229,9 +253,8 @@ class Rasterizer:
         self.key_capacity = int(math.ceil(max(info.n_keys, 1) * slack)) + 4096
         self._alloc()
 
-    def backward(self, dimage, dalpha=None, ddepth=None, grads=None):
+    def backward(self, dimage, dalpha=None, ddepth=None, grads=None, dnormal=None):
         """Gradients of the last forward; returns [(dV, df, drgb)] per scene."""
-        dev = self.device
         if grads is None:
             grads = [(torch.empty_like(s.V), torch.empty_like(s.f), torch.empty_like(s.rgb))
                      for s in self.scenes]
@@ -239,39 +262,34 @@ class Rasterizer:
         dV = (ctypes.c_void_p * n)(*[g[0].data_ptr() for g in grads])
         df = (ctypes.c_void_p * n)(*[g[1].data_ptr() for g in grads])
         dc = (ctypes.c_void_p * n)(*[g[2].data_ptr() for g in grads])
-        dimage = dimage.contiguous()
-        da = dalpha.contiguous() if dalpha is not None else None
-        dd = ddepth.contiguous() if ddepth is not None else None
+        up = tuple(x.contiguous() if x is not None else None
+                   for x in (dimage, dalpha, ddepth, dnormal))
         b = self.batch()
-        check(self.lib.tts_render_bwd(ctypes.byref(b), dimage.data_ptr(),
-                                      da.data_ptr() if da is not None else None,
-                                      dd.data_ptr() if dd is not None else None,
-                                      dV, df, dc, _stream_ptr()), "tts_render_bwd")
-        del dev
+        u = self._c_upstream(up)
+        check(self.lib.tts_render_bwd_ex(ctypes.byref(b), ctypes.byref(u), dV, df, dc,
+                                         _stream_ptr()), "tts_render_bwd_ex")
         return grads
 
     # -- whole training step (pre-filter + forward + backward) -----------------
     def step(self, out, upstream, grads):
         """Enqueue one step: pre-filter, forward of every view, backward into
         ``grads`` with the upstream gradients ``upstream`` = (dimage, dalpha,
-        ddepth).  No synchronisation, no capacity check (size the workspace
+        ddepth[, dnormal]) for the outputs ``out`` (as from ``_outputs``).  No
+        synchronisation, no capacity check (size the workspace
         first, e.g. with ``forward()`` + ``shrink_to_fit``)."""
         L = self.lib
         b = self.batch()
         sp = _stream_ptr()
-        img, alpha, depth = out
-        gi, ga, gd = upstream
         n = len(self.scenes)
         dV = (ctypes.c_void_p * n)(*[g[0].data_ptr() for g in grads])
         df = (ctypes.c_void_p * n)(*[g[1].data_ptr() for g in grads])
         dc = (ctypes.c_void_p * n)(*[g[2].data_ptr() for g in grads])
+        o = self._c_outputs(out)
+        u = self._c_upstream(upstream)
         check(L.tts_prepare_scene(ctypes.byref(b), sp), "tts_prepare_scene")
-        check(L.tts_render_fwd(ctypes.byref(b), img.data_ptr(), alpha.data_ptr(),
-                               depth.data_ptr(), sp), "tts_render_fwd")
-        check(L.tts_render_bwd(ctypes.byref(b), gi.data_ptr(),
-                               ga.data_ptr() if ga is not None else None,
-                               gd.data_ptr() if gd is not None else None, dV, df, dc, sp),
-              "tts_render_bwd")
+        check(L.tts_render_fwd_ex(ctypes.byref(b), ctypes.byref(o), sp), "tts_render_fwd_ex")
+        check(L.tts_render_bwd_ex(ctypes.byref(b), ctypes.byref(u), dV, df, dc, sp),
+              "tts_render_bwd_ex")
 
     def capture_step(self, out, upstream, grads, warmup: int = 2):
         """A CUDA graph of ``step`` on these exact buffers.  Replays read the
@@ -324,19 +342,24 @@ class Rasterizer:
         return dict(keys=keys, vals=vals, ranges=ranges, surv=surv, zmin_bits=int(zmin.value),
                     depth_bits=int(db.value), n_keys=n, info=info)
 
-    def view_outputs(self, img, alpha, depth):
-        """Split flat outputs into per-view (3,H,W), (H,W), (H,W) tensors."""
+    def view_outputs(self, img, alpha, depth, normal=None):
+        """Split flat outputs into per-view (3,H,W), (H,W), (H,W) tensors
+        (and a (3,H,W) normal map when given)."""
         out = []
         for (cam, _), off in zip(self.views, self.pix_off):
             H, W = int(cam.height), int(cam.width)
-            out.append((img[3 * off:3 * off + 3 * H * W].view(3, H, W),
-                        alpha[off:off + H * W].view(H, W), depth[off:off + H * W].view(H, W)))
+            v = (img[3 * off:3 * off + 3 * H * W].view(3, H, W),
+                 alpha[off:off + H * W].view(H, W), depth[off:off + H * W].view(H, W))
+            if normal is not None:
+                v = v + (normal[3 * off:3 * off + 3 * H * W].view(3, H, W),)
+            out.append(v)
         return out
 
 
 class TetRender(torch.autograd.Function):
-    """(V, f, rgb) -> (image, alpha, depth) for the views of a single-scene
-    ``Rasterizer``; outputs are flat view-major planar tensors."""
+    """(V, f, rgb) -> (image, alpha, depth[, normal]) for the views of a
+    single-scene ``Rasterizer``; outputs are flat view-major planar tensors
+    (the normal map when the rasterizer's params ask for it)."""
 
     @staticmethod
     def forward(ctx, V, f, rgb, raster: Rasterizer, check_status: bool = True):
@@ -344,15 +367,15 @@ class TetRender(torch.autograd.Function):
         if V.data_ptr() != sc.V.data_ptr() or f.data_ptr() != sc.f.data_ptr() or \
                 rgb.data_ptr() != sc.rgb.data_ptr():
             raster.set_scenes([SceneTensors(V.detach(), sc.T, f.detach(), rgb.detach())])
-        img, alpha, depth = raster.forward(prepare=True, check_status=check_status)
+        out = raster.forward(prepare=True, check_status=check_status)
         ctx.raster = raster
-        return img, alpha, depth
+        return tuple(out)
 
     @staticmethod
-    def backward(ctx, gimg, galpha, gdepth):
+    def backward(ctx, gimg, galpha, gdepth, gnormal=None):
         raster = ctx.raster
         gimg = gimg if gimg is not None else torch.zeros(3 * raster.total_pixels, device=raster.device)
-        (dV, df, drgb), = raster.backward(gimg, galpha, gdepth)
+        (dV, df, drgb), = raster.backward(gimg, galpha, gdepth, dnormal=gnormal)
         return dV, df, drgb, None, None
 
 
@@ -361,8 +384,8 @@ _cache: dict = {}
 
 def render(V, T, f, rgb, cams, params: Params | None = None, check_status: bool = True):
     """Renders the views ``cams`` of one scene and returns a list of
-    (image (3,H,W), alpha (H,W), depth (H,W)) per view; differentiable with
-    respect to V, f and rgb."""
+    (image (3,H,W), alpha (H,W), depth (H,W)[, normal (3,H,W)]) per view;
+    differentiable with respect to V, f and rgb."""
     params = params or Params()
     key = (tuple(V.shape), tuple(T.shape), T.data_ptr(), len(cams),
            tuple((int(c.width), int(c.height)) for c in cams), dataclasses.astuple(params))
@@ -375,5 +398,5 @@ def render(V, T, f, rgb, cams, params: Params | None = None, check_status: bool 
     else:
         for i, c in enumerate(cams):
             raster._c_views[i].cam = make_camera(c)
-    img, alpha, depth = TetRender.apply(V, f, rgb, raster, check_status)
-    return raster.view_outputs(img, alpha, depth)
+    out = TetRender.apply(V, f, rgb, raster, check_status)
+    return raster.view_outputs(*out)

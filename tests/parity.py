@@ -50,9 +50,9 @@ def gpu_run(scenes, views, params: Params, upstream=None, lists=False):
     Returns per-view outputs (numpy), optional gradients per scene, lists."""
     st = [to_dev(s) for s in scenes]
     r = Rasterizer(st, views, params)
-    img, alpha, depth = r.forward()
+    res = r.forward()
     out = dict(raster=r, views=[tuple(x.cpu().numpy() for x in v)
-                                for v in r.view_outputs(img, alpha, depth)])
+                                for v in r.view_outputs(*res)])
     if lists:
         out["lists"] = {k: (v.cpu().numpy() if torch.is_tensor(v) else v)
                         for k, v in r.debug_lists().items() if k not in ("surv", "info")}
@@ -62,7 +62,10 @@ def gpu_run(scenes, views, params: Params, upstream=None, lists=False):
         gi = torch.from_numpy(np.concatenate([u[0].reshape(-1) for u in upstream])).cuda()
         ga = torch.from_numpy(np.concatenate([u[1].reshape(-1) for u in upstream])).cuda()
         gd = torch.from_numpy(np.concatenate([u[2].reshape(-1) for u in upstream])).cuda()
-        grads = r.backward(gi, ga, gd)
+        gn = None
+        if len(upstream[0]) > 3:
+            gn = torch.from_numpy(np.concatenate([u[3].reshape(-1) for u in upstream])).cuda()
+        grads = r.backward(gi, ga, gd, dnormal=gn)
         out["grads"] = [tuple(g.cpu().numpy().astype(np.float64) for g in gs) for gs in grads]
     torch.cuda.synchronize()
     return out
@@ -76,7 +79,8 @@ def oracle_run(scene, cam, params: Params, upstream=None):
     op = oracle_params(params)
     surv, amb_t, amax = oracle.prefilter(T, f, op)
     bins = oracle.bin_view(surv, T, V, cam, params.tile)
-    r = oracle.render(V, T, f, rgb, cam, op, surv=surv, bins=bins, upstream=upstream)
+    r = oracle.render(V, T, f, rgb, cam, op, surv=surv, bins=bins, upstream=upstream,
+                      normals=params.normals)
     r["amb_tets"] = amb_t
     return r
 
@@ -84,15 +88,24 @@ def oracle_run(scene, cam, params: Params, upstream=None):
 def masked_upstream(up, amb):
     """Zero the upstream gradient at band pixels."""
     m = amb > 0
-    return (up[0] * ~m[None], up[1] * ~m, up[2] * ~m)
+    out = (up[0] * ~m[None], up[1] * ~m, up[2] * ~m)
+    if len(up) > 3:
+        out = out + (up[3] * ~m[None],)
+    return out
 
 
 def compare_images(gpu_view, orc, tol=IMG_TOL):
     """Returns (n_bad, n_amb_pixels, max_err_on_unambiguous)."""
-    gi, ga, gd = gpu_view
-    prim = np.concatenate([orc["image"], orc["alpha"][None], orc["depth"][None]], 0)
-    alt = np.concatenate([orc["alt_image"], orc["alt_alpha"][None], orc["alt_depth"][None]], 0)
-    got = np.concatenate([gi, ga[None], gd[None]], 0).astype(np.float64)
+    gi, ga, gd = gpu_view[:3]
+    prim = [orc["image"], orc["alpha"][None], orc["depth"][None]]
+    alt = [orc["alt_image"], orc["alt_alpha"][None], orc["alt_depth"][None]]
+    got = [gi, ga[None], gd[None]]
+    if len(gpu_view) > 3:           # normal map channel
+        prim.append(orc["normal"])
+        alt.append(orc["alt_normal"])
+        got.append(gpu_view[3])
+    prim, alt = np.concatenate(prim, 0), np.concatenate(alt, 0)
+    got = np.concatenate(got, 0).astype(np.float64)
     e1 = np.abs(got - prim).max(0)
     e2 = np.abs(got - alt).max(0)
     amb = orc["amb"] > 0

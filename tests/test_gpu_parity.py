@@ -86,6 +86,47 @@ def test_resort_window_parity(sphere16, nw):
         assert err < GRAD_TOL, f"window{nw} {name}: rel err {err:.3e}"
 
 
+@pytest.mark.parametrize("tile,nw,pure", [(8, 0, False), (16, 0, False), (16, 0, True),
+                                          (32, 5, False)])
+def test_normal_map_and_gradients(sphere16, tile, nw, pure):
+    """Eq. 2 normal channel (per-tet normal of Sec. 3.2 / App. A.3): the
+    normal map and the gradients of all four upstream channels."""
+    p = Params(s=60.0, tile=tile, resort_window=nw, pure=pure, normals=True)
+    cam = sphere16.cams[0]
+    up0 = tuple(synth.upstream_grads(11, [cam])[0])
+    up0 = up0 + (np.random.default_rng(12).normal(size=(3, cam.height, cam.width))
+                 .astype(np.float32),)
+    orc0 = oracle_run(sphere16, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(sphere16, cam, p, upstream=up)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
+    assert len(gpu["views"][0]) == 4
+    assert np.abs(orc0["normal"]).max() > 0.5
+    _check_view(gpu["views"][0], orc0, f"normals tile{tile} nw{nw}")
+    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"normals {name}: rel err {err:.3e}"
+
+
+def test_normal_gradient_alone(sphere16):
+    """Only dL/dnormal nonzero: the gradient reaches V and f through the
+    per-tet normals and through the opacities."""
+    p = Params(s=60.0, tile=16, normals=True)
+    cam = sphere16.cams[0]
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(13)
+    up0 = (np.zeros((3, H, W), np.float32), np.zeros((H, W), np.float32),
+           np.zeros((H, W), np.float32), rng.normal(size=(3, H, W)).astype(np.float32))
+    orc0 = oracle_run(sphere16, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(sphere16, cam, p, upstream=up)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
+    assert np.abs(orc["drgb"]).max() == 0.0
+    for name, g, o in zip(("dV", "df"), gpu["grads"][0][:2], (orc["dV"], orc["df"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"normal-only {name}: rel err {err:.3e}"
+
+
 def test_resort_window_torus64(torus64):
     p = Params(s=175.0, tile=16, resort_window=5)
     cam = torus64.cams[0]
