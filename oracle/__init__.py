@@ -14,6 +14,9 @@ What each function restates (paper sections):
               Eq. 1 opacity, Eq. 2 front-to-back blending (3DGS conventions),
               and the exact adjoint (compositing adjoint + dual numbers).
   fragment    one ray against one tet (App. A.1/A.2), for closed-form tests.
+  tet_edges, regularizers
+              Sec. 4 eikonal and normal-consistency losses of the grid's SDF
+              with their gradients (``geometry_terms.cpp``).
 
 Parity status: pinned by the tests under ``tests/test_oracle_*.py``.
 """
@@ -27,7 +30,8 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.cpp")
+_SRCS = [os.path.join(_HERE, n) for n in ("oracle.cpp", "geometry_terms.cpp")]
+_DEPS = _SRCS + [os.path.join(_HERE, "dual.h")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 PURE = 1
@@ -48,13 +52,13 @@ class OrcParams(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.cpp into liboracle.so (FP contraction off: the key path
-    is an exact FP32 op sequence)."""
+    """Compile the oracle sources into liboracle.so (FP contraction off: the
+    key path is an exact FP32 op sequence)."""
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB) >= os.path.getmtime(d) for d in _DEPS)):
         return _LIB
     cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp"]
+           "-fPIC", "-shared", *_SRCS, "-o", _LIB + ".tmp"]
     subprocess.check_call(cmd)
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
@@ -87,6 +91,12 @@ def lib():
         L.orc_render_dirderiv.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P, P, P, P,
                                           P, P, P, P, P, P, P, P]
         L.orc_render_dirderiv.restype = ctypes.c_int
+        L.orc_tet_edges.argtypes = [i64, i64, P, P]
+        L.orc_tet_edges.restype = i64
+        L.orc_regularizers.argtypes = [i64, P, i64, P, P, i64, P, f64, f64, P, P, P]
+        L.orc_regularizers.restype = None
+        L.orc_regularizers_dirderiv.argtypes = [i64, P, i64, P, P, i64, P, f64, f64, P, P, P]
+        L.orc_regularizers_dirderiv.restype = None
         _lib = L
     return _lib
 
@@ -262,3 +272,42 @@ def fragment_grad(X, F, px, py, fx, fy, cx, cy, s):
     g = np.zeros(16)
     hit = lib().orc_fragment_grad(_p(X), _p(F), px, py, fx, fy, cx, cy, s, _p(a), _p(g))
     return (float(a[0]), g) if hit else None
+
+
+def tet_edges(T, N=None):
+    """Unique edges of a tet grid as an (E, 2) int32 array of (lo, hi) pairs
+    sorted lexicographically."""
+    T = _c(T, np.int32)
+    N = int(T.max()) + 1 if N is None else int(N)
+    out = np.zeros((6 * len(T), 2), np.int32)
+    n = lib().orc_tet_edges(N, len(T), _p(T), _p(out))
+    if n < 0:
+        raise ValueError("tet index outside [0, N)")
+    return out[:n].copy()
+
+
+def regularizers(V, T, f, edges, w_eik=1.0, w_nc=1.0, grad=True):
+    """Sec. 4 eikonal and normal-consistency losses (FP64) and the gradients
+    of w_eik L_eik + w_nc L_nc with respect to V and f."""
+    V = _c(V, np.float64)
+    f = _c(f, np.float64)
+    T = _c(T, np.int32)
+    edges = _c(edges, np.int32)
+    out = np.zeros(2)
+    dV = np.zeros_like(V) if grad else None
+    df = np.zeros_like(f) if grad else None
+    lib().orc_regularizers(len(V), _p(V), len(T), _p(T), _p(f), len(edges), _p(edges),
+                           float(w_eik), float(w_nc), _p(out), _p(dV), _p(df))
+    return dict(L_eik=float(out[0]), L_nc=float(out[1]), dV=dV, df=df)
+
+
+def regularizers_dirderiv(V, T, f, edges, w_eik, w_nc, tV, tf):
+    """(value, directional derivative along (tV, tf)) of w_eik L_eik + w_nc
+    L_nc by dual numbers."""
+    V, f, tV, tf = (_c(x, np.float64) for x in (V, f, tV, tf))
+    T = _c(T, np.int32)
+    edges = _c(edges, np.int32)
+    out = np.zeros(2)
+    lib().orc_regularizers_dirderiv(len(V), _p(V), len(T), _p(T), _p(f), len(edges), _p(edges),
+                                    float(w_eik), float(w_nc), _p(tV), _p(tf), _p(out))
+    return float(out[0]), float(out[1])
