@@ -272,6 +272,49 @@ int tts_debug_records(const tts_batch* b, const void** records, tts_stream strea
 int tts_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                            uint32_t* vals_out, int64_t n, int32_t key_bits, tts_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Geometry-stage terms (Sec. 4): the unique edges of a tet grid and the
+ * eikonal and normal-consistency regularizers of its SDF.  Same conventions:
+ * caller-owned device arrays and workspace (256-byte aligned), asynchronous
+ * on the stream, argument errors found before anything is enqueued.  A tet or
+ * edge with an index outside [0, N) is skipped and sets TTS_STATUS_BAD_INDEX
+ * in the workspace's status word (tts_geometry_status).
+ * ------------------------------------------------------------------------ */
+
+/* Workspace bytes of tts_tet_edges for N vertices and K tets (6 K < 2^31). */
+int tts_tet_edges_workspace_size(int64_t N, int64_t K, size_t* bytes);
+
+/* The unique edges of the grid T (K x 4 int32, 16-byte aligned): the pairs
+ * (lo, hi), lo < hi, of vertices that share a tet, sorted by (lo, hi).
+ * edges: device int32 pairs (8-byte aligned), at most edge_capacity written
+ * (6 K always suffices); *n_edges (device int64) receives the number of
+ * edges, or -1 when an index was out of range. */
+int tts_tet_edges(const int32_t* T, int64_t K, int64_t N, int32_t* edges, int64_t edge_capacity,
+                  int64_t* n_edges, void* workspace, size_t workspace_bytes, tts_stream stream);
+
+/* Workspace bytes of tts_regularizers for N vertices. */
+int tts_regularizers_workspace_size(int64_t N, size_t* bytes);
+
+/* Sec. 4 regularizers of the SDF f on the grid (V, T):
+ *   L_eik = sum over tets k of (|g_k| - 1)^2, g_k the gradient of tet k's
+ *           affine SDF (App. A.3);
+ *   L_nc  = sum over the given edges (a, b) of 1 - cos(m_a, m_b), m_v the sum
+ *           of the unit normals g_k / |g_k| of the tets containing v.
+ * A flat tet (zero volume) contributes to neither; a tet with g = 0 adds 1 to
+ * L_eik and nothing to m; an edge with m_a = 0 or m_b = 0 adds 1 to L_nc.
+ * losses: device double[2] = (L_eik, L_nc), overwritten.  dV (N x 3), df (N):
+ * device gradients of w_eik L_eik + w_nc L_nc, both NULL for losses only;
+ * overwritten unless flags has TTS_FLAG_ACCUM_GRAD.  edges: E int32 pairs
+ * (8-byte aligned), e.g. from tts_tet_edges. */
+int tts_regularizers(const float* V, const int32_t* T, const float* f, int64_t N, int64_t K,
+                     const int32_t* edges, int64_t E, float w_eik, float w_nc, double* losses,
+                     float* dV, float* df, int32_t flags, void* workspace, size_t workspace_bytes,
+                     tts_stream stream);
+
+/* Synchronises the stream and reads the status word of a tts_tet_edges or
+ * tts_regularizers workspace. */
+int tts_geometry_status(const void* workspace, uint32_t* status, tts_stream stream);
+
 const char* tts_error_string(int code);
 
 /* Library version and the GPU architecture it was built for. */

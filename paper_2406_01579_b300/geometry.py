@@ -1,0 +1,101 @@
+"""Geometry-stage terms of Sec. 4 over the C ABI: the unique edges of a tet
+grid and the eikonal / normal-consistency regularizers of its SDF.  Device
+memory comes from PyTorch; the work runs in libtets' kernels."""
+
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import TTS_FLAG_ACCUM_GRAD, TTS_STATUS_BAD_INDEX, TetsError, check
+
+
+def _stream_ptr():
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator hands out 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def tet_edges(T: torch.Tensor, N: int) -> torch.Tensor:
+    """(E, 2) int32 tensor of the grid's unique edges (lo < hi), sorted."""
+    L = _lib.load()
+    if T.dtype != torch.int32 or not T.is_contiguous() or T.dim() != 2 or T.shape[1] != 4:
+        raise TetsError("T must be a contiguous K x 4 int32 CUDA tensor")
+    K = int(T.shape[0])
+    nb = ctypes.c_size_t(0)
+    check(L.tts_tet_edges_workspace_size(int(N), K, ctypes.byref(nb)), "tts_tet_edges_workspace_size")
+    ws = _ws(nb.value, T.device)
+    edges = torch.empty((6 * K, 2), dtype=torch.int32, device=T.device)
+    n = torch.empty(1, dtype=torch.int64, device=T.device)
+    check(L.tts_tet_edges(T.data_ptr(), K, int(N), edges.data_ptr(), 6 * K, n.data_ptr(),
+                          ws.data_ptr(), ws.numel(), _stream_ptr()), "tts_tet_edges")
+    count = int(n.item())
+    if count < 0:
+        raise TetsError("a tet index is outside [0, N)")
+    return edges[:count].clone()
+
+
+class Regularizers:
+    """Workspace + call for the Sec. 4 regularizers of one grid size."""
+
+    def __init__(self, N: int, device):
+        self.lib = _lib.load()
+        self.N = int(N)
+        nb = ctypes.c_size_t(0)
+        check(self.lib.tts_regularizers_workspace_size(self.N, ctypes.byref(nb)),
+              "tts_regularizers_workspace_size")
+        self.ws = _ws(nb.value, device)
+        self.losses = torch.zeros(2, dtype=torch.float64, device=device)
+
+    def __call__(self, V, T, f, edges, w_eik=1.0, w_nc=1.0, grads=None, accumulate=False):
+        """Enqueues the call.  Returns the device (L_eik, L_nc) float64 tensor
+        (a view of a buffer reused by the next call) and, when ``grads`` =
+        (dV, df) is given, fills it with the gradients of w_eik L_eik +
+        w_nc L_nc."""
+        dV, df = grads if grads is not None else (None, None)
+        E = int(edges.shape[0]) if edges is not None else 0
+        check(self.lib.tts_regularizers(
+            V.data_ptr(), T.data_ptr(), f.data_ptr(), self.N, int(T.shape[0]),
+            edges.data_ptr() if E else None, E, float(w_eik), float(w_nc), self.losses.data_ptr(),
+            dV.data_ptr() if dV is not None else None, df.data_ptr() if df is not None else None,
+            TTS_FLAG_ACCUM_GRAD if accumulate else 0, self.ws.data_ptr(), self.ws.numel(),
+            _stream_ptr()), "tts_regularizers")
+        return self.losses
+
+    def status(self) -> int:
+        st = ctypes.c_uint32(0)
+        check(self.lib.tts_geometry_status(self.ws.data_ptr(), ctypes.byref(st), _stream_ptr()),
+              "tts_geometry_status")
+        return int(st.value)
+
+
+class RegularizerLoss(torch.autograd.Function):
+    """(V, f) -> w_eik L_eik + w_nc L_nc (float64 scalar) with gradients."""
+
+    @staticmethod
+    def forward(ctx, V, f, T, edges, w_eik, w_nc, reg: Regularizers):
+        dV = torch.empty_like(V)
+        df = torch.empty_like(f)
+        losses = reg(V.detach(), T, f.detach(), edges, w_eik, w_nc, grads=(dV, df))
+        ctx.save_for_backward(dV, df)
+        return w_eik * losses[0] + w_nc * losses[1]
+
+    @staticmethod
+    def backward(ctx, g):
+        dV, df = ctx.saved_tensors
+        gf = g.to(torch.float32)
+        return dV * gf, df * gf, None, None, None, None, None
+
+
+def regularizer_loss(V, f, T, edges, w_eik=1.0, w_nc=1.0, reg: Regularizers | None = None):
+    reg = reg or Regularizers(V.shape[0], V.device)
+    return RegularizerLoss.apply(V, f, T, edges, w_eik, w_nc, reg)
+
+
+__all__ = ["tet_edges", "Regularizers", "RegularizerLoss", "regularizer_loss",
+           "TTS_STATUS_BAD_INDEX"]
