@@ -273,7 +273,7 @@ int tts_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* vals_in, uin
                            uint32_t* vals_out, int64_t n, int32_t key_bits, tts_stream stream);
 
 /* ------------------------------------------------------------------------
- * Geometry-stage terms (Sec. 4): the unique edges of a tet grid and the
+ * Geometry-stage terms (Sec. 4.2): the unique edges of a tet grid and the
  * eikonal and normal-consistency regularizers of its SDF.  Same conventions:
  * caller-owned device arrays and workspace (256-byte aligned), asynchronous
  * on the stream, argument errors found before anything is enqueued.  A tet or
@@ -295,7 +295,7 @@ int tts_tet_edges(const int32_t* T, int64_t K, int64_t N, int32_t* edges, int64_
 /* Workspace bytes of tts_regularizers for N vertices. */
 int tts_regularizers_workspace_size(int64_t N, size_t* bytes);
 
-/* Sec. 4 regularizers of the SDF f on the grid (V, T):
+/* Sec. 4.2 regularizers of the SDF f on the grid (V, T):
  *   L_eik = sum over tets k of (|g_k| - 1)^2, g_k the gradient of tet k's
  *           affine SDF (App. A.3);
  *   L_nc  = sum over the given edges (a, b) of 1 - cos(m_a, m_b), m_v the sum

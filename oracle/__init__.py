@@ -15,8 +15,10 @@ What each function restates (paper sections):
               and the exact adjoint (compositing adjoint + dual numbers).
   fragment    one ray against one tet (App. A.1/A.2), for closed-form tests.
   tet_edges, regularizers
-              Sec. 4 eikonal and normal-consistency losses of the grid's SDF
+              Sec. 4.2 eikonal and normal-consistency losses of the grid's SDF
               with their gradients (``geometry_terms.cpp``).
+  marching_tets
+              Marching Tetrahedra mesh extraction (Sec. 3.1).
 
 Parity status: pinned by the tests under ``tests/test_oracle_*.py``.
 """
@@ -97,6 +99,8 @@ def lib():
         L.orc_regularizers.restype = None
         L.orc_regularizers_dirderiv.argtypes = [i64, P, i64, P, P, i64, P, f64, f64, P, P, P]
         L.orc_regularizers_dirderiv.restype = None
+        L.orc_marching_tets.argtypes = [i64, P, i64, P, P, i64, P, P, P, i64, P, i64, P]
+        L.orc_marching_tets.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -287,7 +291,7 @@ def tet_edges(T, N=None):
 
 
 def regularizers(V, T, f, edges, w_eik=1.0, w_nc=1.0, grad=True):
-    """Sec. 4 eikonal and normal-consistency losses (FP64) and the gradients
+    """Sec. 4.2 eikonal and normal-consistency losses (FP64) and the gradients
     of w_eik L_eik + w_nc L_nc with respect to V and f."""
     V = _c(V, np.float64)
     f = _c(f, np.float64)
@@ -311,3 +315,24 @@ def regularizers_dirderiv(V, T, f, edges, w_eik, w_nc, tV, tf):
     lib().orc_regularizers_dirderiv(len(V), _p(V), len(T), _p(T), _p(f), len(edges), _p(edges),
                                     float(w_eik), float(w_nc), _p(tV), _p(tf), _p(out))
     return float(out[0]), float(out[1])
+
+
+def marching_tets(V, T, f, edges=None):
+    """Marching Tetrahedra: returns dict(verts (nv, 3) float64, vert_edge
+    (nv,) int32 index into ``edges``, tris (nt, 3) int32, edges)."""
+    V = _c(V, np.float64)
+    f = _c(f, np.float64)
+    T = _c(T, np.int32)
+    edges = tet_edges(T, len(V)) if edges is None else _c(edges, np.int32)
+    E = len(edges)
+    verts = np.zeros((E, 3))
+    vedge = np.zeros(E, np.int32)
+    tris = np.zeros((2 * len(T), 3), np.int32)
+    counts = np.zeros(2, np.int64)
+    rc = lib().orc_marching_tets(len(V), _p(V), len(T), _p(T), _p(f), E, _p(edges), _p(verts),
+                                 _p(vedge), E, _p(tris), 2 * len(T), _p(counts))
+    if rc != 0:
+        raise ValueError("a tet edge is missing from the edge list")
+    nv, nt = int(counts[0]), int(counts[1])
+    return dict(verts=verts[:nv].copy(), vert_edge=vedge[:nv].copy(), tris=tris[:nt].copy(),
+                edges=edges)

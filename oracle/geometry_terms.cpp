@@ -4,16 +4,23 @@
 //
 //   tet_edges       the unique edges of a tetrahedral grid (each tet has six),
 //                   as (lo, hi) vertex pairs sorted lexicographically.
-//   regularizers    Sec. 4 "Eikonal loss": L_eik = sum over tets k of
+//   regularizers    Sec. 4.2 "Eikonal loss": L_eik = sum over tets k of
 //                   (|g_k| - 1)^2, with g_k the gradient of tet k's affine SDF
 //                   obtained from the 4 x 4 system of App. A.3 (rows
 //                   [v_i^T 1], right-hand side f_i), solved here by Gaussian
 //                   elimination with partial pivoting.
-//                   Sec. 4 "Normal consistency loss": the per-tet normals
+//                   Sec. 4.2 "Normal consistency loss": the per-tet normals
 //                   n_k = g_k / |g_k| are carried to the vertices and
 //                   L_nc = sum over edges (a, b) of (1 - cos(m_a, m_b)).
 //                   FP64; gradients by the hand-written adjoint (the transposed
 //                   4 x 4 solve), checked against forward-mode dual numbers.
+//   marching_tets   Marching Tetrahedra (Sec. 3.1, the mesh extraction the
+//                   representation keeps): a vertex on every grid edge whose
+//                   end points lie on different sides of the zero level set
+//                   (positive: f > 0), at the zero of the linear interpolation;
+//                   one triangle per tet with a 1-3 sign split and two per tet
+//                   with a 2-2 split, wound so that the normal points towards
+//                   increasing f.
 //
 // Readings where the paper is silent:
 //   * "project the tet normals onto vertices": m_v = unweighted sum of the
@@ -24,9 +31,19 @@
 //     nothing to m; an edge with a zero vertex sum contributes 1 to L_nc
 //     (cos taken as 0) with zero gradient.
 //
+//   * Marching Tetrahedra: vertices are numbered by the order of their edges
+//     in the sorted unique-edge list; triangles follow the tets in order.  A
+//     2-2 tet with positive local vertices p < q and negative r < s has the
+//     quad (pr, ps, qs, qr) (each a crossing edge), split along pr-qs into
+//     (pr, ps, qs) and (pr, qs, qr).  A 1-3 tet with odd vertex o and others
+//     a < b < c gives (oa, ob, oc).  The winding is then chosen from the sign
+//     of a vertex determinant (see orc_marching_tets) so that the normal
+//     points towards increasing f.
+//
 // Parity status: pinned by closed forms (affine fields, the two-tet
-// configuration, the Kuhn-grid edge count), invariances, dual numbers and
-// finite differences.
+// configuration, the Kuhn-grid edge count, a hand-cut single tet),
+// invariances, dual numbers, finite differences, and for the extracted mesh
+// by watertightness, Euler characteristic and enclosed volume.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -240,6 +257,108 @@ void orc_regularizers_dirderiv(int64_t N, const double* V, int64_t K, const int3
   const D1 L = w_eik * le + w_nc * ln;
   out[0] = L.v;
   out[1] = L.d[0];
+}
+
+// Marching Tetrahedra.  edges: the sorted unique edges (E pairs).  Writes up
+// to vcap vertices (x, y, z) with their source edge index and up to tcap
+// triangles; counts = (vertices, triangles) needed.  Returns 0, or -1 when a
+// tet edge is missing from the edge list.
+int orc_marching_tets(int64_t N, const double* V, int64_t K, const int32_t* T, const double* f,
+                      int64_t E, const int32_t* edges, double* verts, int32_t* vert_edge,
+                      int64_t vcap, int32_t* tris, int64_t tcap, int64_t* counts) {
+  (void)N;
+  // vertex id of each crossing edge, in edge order
+  std::vector<int64_t> vid(E, -1);
+  int64_t nv = 0;
+  for (int64_t e = 0; e < E; ++e) {
+    const int32_t a = edges[2 * e], b = edges[2 * e + 1];
+    if ((f[a] > 0.0) == (f[b] > 0.0)) continue;
+    vid[e] = nv;
+    if (nv < vcap) {
+      // zero of the linear interpolation along the edge
+      for (int r = 0; r < 3; ++r)
+        verts[3 * nv + r] = (V[3 * a + r] * f[b] - V[3 * b + r] * f[a]) / (f[b] - f[a]);
+      if (vert_edge) vert_edge[nv] = (int32_t)e;
+    }
+    ++nv;
+  }
+  auto lookup = [&](int32_t x, int32_t y) -> int64_t {
+    const std::pair<int32_t, int32_t> key(std::min(x, y), std::max(x, y));
+    int64_t lo = 0, hi = E;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      const std::pair<int32_t, int32_t> m(edges[2 * mid], edges[2 * mid + 1]);
+      if (m < key) lo = mid + 1; else hi = mid;
+    }
+    if (lo >= E || edges[2 * lo] != key.first || edges[2 * lo + 1] != key.second) return -1;
+    return vid[lo];
+  };
+  auto det3 = [&](const int32_t o, const int32_t a, const int32_t b, const int32_t c) {
+    double m[3][3];
+    for (int r = 0; r < 3; ++r) {
+      m[0][r] = V[3 * a + r] - V[3 * o + r];
+      m[1][r] = V[3 * b + r] - V[3 * o + r];
+      m[2][r] = V[3 * c + r] - V[3 * o + r];
+    }
+    return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+           m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+           m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+  };
+  int64_t nt = 0;
+  auto emit = [&](int64_t x, int64_t y, int64_t z) {
+    if (nt < tcap) {
+      tris[3 * nt] = (int32_t)x;
+      tris[3 * nt + 1] = (int32_t)y;
+      tris[3 * nt + 2] = (int32_t)z;
+    }
+    ++nt;
+  };
+  for (int64_t k = 0; k < K; ++k) {
+    const int32_t* t = T + 4 * k;
+    bool pos[4];
+    int np = 0;
+    for (int i = 0; i < 4; ++i) {
+      pos[i] = f[t[i]] > 0.0;
+      np += pos[i] ? 1 : 0;
+    }
+    if (np == 0 || np == 4) continue;
+    if (np == 1 || np == 3) {
+      int o = -1, oth[3], m = 0;
+      for (int i = 0; i < 4; ++i) {
+        if (pos[i] == (np == 1)) o = i; else oth[m++] = i;
+      }
+      const int64_t x = lookup(t[o], t[oth[0]]), y = lookup(t[o], t[oth[1]]),
+                    z = lookup(t[o], t[oth[2]]);
+      if (x < 0 || y < 0 || z < 0) return -1;
+      // (oa, ob, oc) faces away from o iff det(a - o, b - o, c - o) > 0; the
+      // normal must point towards the positive side
+      const double D = det3(t[o], t[oth[0]], t[oth[1]], t[oth[2]]);
+      const bool flip = (np == 1) ? (D > 0.0) : (D < 0.0);
+      if (flip) emit(x, z, y); else emit(x, y, z);
+    } else {
+      int P[2], Q[2], mp = 0, mq = 0;
+      for (int i = 0; i < 4; ++i) {
+        if (pos[i]) P[mp++] = i; else Q[mq++] = i;
+      }
+      const int p = P[0], q = P[1], r = Q[0], s_ = Q[1];
+      const int64_t pr = lookup(t[p], t[r]), ps = lookup(t[p], t[s_]), qs = lookup(t[q], t[s_]),
+                    qr = lookup(t[q], t[r]);
+      if (pr < 0 || ps < 0 || qs < 0 || qr < 0) return -1;
+      // (pr, ps, qs) and (pr, qs, qr) face the positive pair iff
+      // det(q - p, r - p, s - p) < 0
+      const double D = det3(t[p], t[q], t[r], t[s_]);
+      if (D > 0.0) {
+        emit(pr, qs, ps);
+        emit(pr, qr, qs);
+      } else {
+        emit(pr, ps, qs);
+        emit(pr, qs, qr);
+      }
+    }
+  }
+  counts[0] = nv;
+  counts[1] = nt;
+  return 0;
 }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-// Geometry-stage terms of Sec. 4 on the GPU: the unique edges of a tet grid
+// Geometry-stage terms of Sec. 4.2 on the GPU: the unique edges of a tet grid
 // and the eikonal / normal-consistency regularizers of its SDF with their
 // gradients.
 //

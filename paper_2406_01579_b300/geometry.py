@@ -1,4 +1,4 @@
-"""Geometry-stage terms of Sec. 4 over the C ABI: the unique edges of a tet
+"""Geometry-stage terms of Sec. 4.2 over the C ABI: the unique edges of a tet
 grid and the eikonal / normal-consistency regularizers of its SDF.  Device
 memory comes from PyTorch; the work runs in libtets' kernels."""
 
@@ -41,7 +41,7 @@ def tet_edges(T: torch.Tensor, N: int) -> torch.Tensor:
 
 
 class Regularizers:
-    """Workspace + call for the Sec. 4 regularizers of one grid size."""
+    """Workspace + call for the Sec. 4.2 regularizers of one grid size."""
 
     def __init__(self, N: int, device):
         self.lib = _lib.load()

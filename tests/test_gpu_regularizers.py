@@ -1,4 +1,4 @@
-"""Parity of the GPU geometry-stage terms (Sec. 4 eikonal and normal
+"""Parity of the GPU geometry-stage terms (Sec. 4.2 eikonal and normal
 consistency, unique grid edges) with the oracle, through the C ABI."""
 
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the oracle's geometry-stage terms (Sec. 4 eikonal and normal
+"""Pins of the oracle's geometry-stage terms (Sec. 4.2 eikonal and normal
 consistency losses, App. A.3 per-tet gradient) against closed forms,
 invariances, dual numbers and finite differences."""
 
