@@ -311,8 +311,32 @@ int tts_regularizers(const float* V, const int32_t* T, const float* f, int64_t N
                      float* dV, float* df, int32_t flags, void* workspace, size_t workspace_bytes,
                      tts_stream stream);
 
-/* Synchronises the stream and reads the status word of a tts_tet_edges or
- * tts_regularizers workspace. */
+/* Workspace bytes of tts_marching_tets for K tets and E edges. */
+int tts_marching_tets_workspace_size(int64_t K, int64_t E, size_t* bytes);
+
+/* Marching Tetrahedra (Sec. 3.1, DMTet's extraction of the zero level set):
+ * every edge of the sorted unique edge list (E pairs, e.g. from
+ * tts_tet_edges) whose end points lie on different sides (positive: f > 0)
+ * gets a vertex at the zero of the linear interpolation
+ * (v_a f_b - v_b f_a) / (f_b - f_a); vertices are numbered in edge order.
+ * Each tet with a 1-3 sign split gives one triangle (the cut edges of the odd
+ * vertex o, in ascending order of the others' local index), each 2-2 tet two
+ * (positive local vertices p < q, negative r < s: the quad pr, ps, qs, qr
+ * split into (pr, ps, qs) and (pr, qs, qr)); triangles follow the tets in
+ * order, wound so that their normal points towards increasing f (decided by
+ * the sign of one FP32 vertex determinant per tet).
+ * verts: device float (x, y, z) per vertex, vert_edge: its edge index
+ * (nullable), at most vert_capacity written; tris: device int32 vertex index
+ * triples, at most tri_capacity written.  counts: device int64[2] receives
+ * (vertices, triangles) needed, so a call with zero capacities sizes the
+ * outputs.  A tet edge missing from the list sets TTS_STATUS_BAD_INDEX. */
+int tts_marching_tets(const float* V, const int32_t* T, const float* f, int64_t N, int64_t K,
+                      const int32_t* edges, int64_t E, float* verts, int32_t* vert_edge,
+                      int64_t vert_capacity, int32_t* tris, int64_t tri_capacity, int64_t* counts,
+                      void* workspace, size_t workspace_bytes, tts_stream stream);
+
+/* Synchronises the stream and reads the status word of a tts_tet_edges,
+ * tts_regularizers or tts_marching_tets workspace. */
 int tts_geometry_status(const void* workspace, uint32_t* status, tts_stream stream);
 
 const char* tts_error_string(int code);

@@ -84,7 +84,8 @@ ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
                 "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
                 "tts_tet_edges_workspace_size", "tts_tet_edges", "tts_regularizers_workspace_size",
-                "tts_regularizers", "tts_geometry_status",
+                "tts_regularizers", "tts_marching_tets_workspace_size", "tts_marching_tets",
+                "tts_geometry_status",
                 "tts_error_string", "tts_version")
 
 _lib = None
@@ -135,6 +136,9 @@ def load():
     L.tts_regularizers_workspace_size.argtypes = [i64, ctypes.POINTER(ctypes.c_size_t)]
     L.tts_regularizers.argtypes = [P, P, P, i64, i64, P, i64, ctypes.c_float, ctypes.c_float, P,
                                    P, P, ctypes.c_int32, P, ctypes.c_size_t, P]
+    L.tts_marching_tets_workspace_size.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.tts_marching_tets.argtypes = [P, P, P, i64, i64, P, i64, P, P, i64, P, i64, P, P,
+                                    ctypes.c_size_t, P]
     L.tts_geometry_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint32), P]
     L.tts_error_string.argtypes = [ctypes.c_int]
     L.tts_error_string.restype = ctypes.c_char_p

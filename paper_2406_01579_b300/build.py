@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtets.so")
-SOURCES = ["bin.cu", "blend.cu", "api.cu", "sort_noalloc.cu", "regularize.cu"]
+SOURCES = ["bin.cu", "blend.cu", "api.cu", "sort_noalloc.cu", "regularize.cu", "marching.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -19,118 +19,10 @@
 #include <cmath>
 #include <cstring>
 
-#include "geometry.cuh"
+#include "geo_common.cuh"
 
 namespace tts {
 namespace {
-
-constexpr int RT = 256;          // threads per block
-constexpr int SCAN_T = 1024;     // scan block size
-constexpr int SCAN_CHUNK = 4096; // elements per scan block
-
-struct GeoStatus {
-  unsigned int status;
-  unsigned int pad[3];
-  long long total;               // scan total (edges)
-  double acc[2];                 // L_eik, L_nc accumulators
-};
-
-__device__ __forceinline__ bool valid4(int4 t, long long N) {
-  return (unsigned long long)t.x < (unsigned long long)N && (unsigned long long)t.y < (unsigned long long)N &&
-         (unsigned long long)t.z < (unsigned long long)N && (unsigned long long)t.w < (unsigned long long)N;
-}
-
-// the six vertex pairs of a tet: (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
-__device__ __forceinline__ int pair_a(int e) { return e < 3 ? 0 : (e < 5 ? 1 : 2); }
-__device__ __forceinline__ int pair_b(int e) { return e < 3 ? e + 1 : (e < 5 ? e - 1 : 3); }
-
-// ---------------------------------------------------------------------------
-// device-wide exclusive scan of int counts (N entries) into off[0..N], with
-// off[N] = total; three kernels (block sums, scan of the sums, block scans)
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T block_scan_excl(T v, T* total) {
-  __shared__ T ws[SCAN_T / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  if (lane == 31) ws[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    T s = (lane < SCAN_T / 32) ? ws[lane] : T(0);
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T u = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += u;
-    }
-    if (lane < SCAN_T / 32) ws[lane] = s;
-  }
-  __syncthreads();
-  const T base = (wid > 0) ? ws[wid - 1] : T(0);
-  *total = ws[SCAN_T / 32 - 1];
-  __syncthreads();
-  return base + inc - v;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_sums(const int* __restrict__ cnt, long long n,
-                                                      long long* __restrict__ sums) {
-  const long long b0 = (long long)blockIdx.x * SCAN_CHUNK;
-  long long acc = 0;
-  for (long long i = b0 + threadIdx.x; i < min(n, b0 + SCAN_CHUNK); i += SCAN_T) acc += cnt[i];
-  long long tot;
-  block_scan_excl<long long>(acc, &tot);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_top(long long* __restrict__ sums, int nb,
-                                                     GeoStatus* st) {
-  long long carry = 0;
-  for (int base = 0; base < nb; base += SCAN_T) {
-    const int i = base + threadIdx.x;
-    const long long v = (i < nb) ? sums[i] : 0;
-    long long tot;
-    const long long ex = block_scan_excl<long long>(v, &tot);
-    if (i < nb) sums[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) st->total = carry;
-}
-
-__global__ void __launch_bounds__(SCAN_T) k_scan_blocks(const int* __restrict__ cnt, long long n,
-                                                        const long long* __restrict__ sums,
-                                                        long long* __restrict__ off) {
-  const long long b0 = (long long)blockIdx.x * SCAN_CHUNK;
-  constexpr int PER = SCAN_CHUNK / SCAN_T;
-  const long long i0 = b0 + (long long)threadIdx.x * PER;
-  int v[PER];
-  long long acc = 0;
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    v[q] = (i0 + q < n) ? cnt[i0 + q] : 0;
-    acc += v[q];
-  }
-  long long tot;
-  long long run = block_scan_excl<long long>(acc, &tot) + sums[blockIdx.x];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    if (i0 + q < n) off[i0 + q] = run;
-    run += v[q];
-  }
-  if (i0 <= n - 1 && n - 1 < i0 + PER) off[n] = run;   // the thread holding the last entry
-}
-
-int scan_counts(const int* cnt, long long n, long long* sums, long long* off, GeoStatus* st,
-                cudaStream_t s) {
-  const int nb = (int)((n + SCAN_CHUNK - 1) / SCAN_CHUNK);
-  k_scan_sums<<<nb, SCAN_T, 0, s>>>(cnt, n, sums);
-  k_scan_top<<<1, SCAN_T, 0, s>>>(sums, nb, st);
-  k_scan_blocks<<<nb, SCAN_T, 0, s>>>(cnt, n, sums, off);
-  return 3;
-}
 
 // ---------------------------------------------------------------------------
 // edges
@@ -352,20 +244,6 @@ __global__ void k_reg_finish(const GeoStatus* st, double* losses) {
   losses[1] = st->acc[1];
 }
 
-size_t align256(size_t x) { return (x + 255) / 256 * 256; }
-
-int grid_for(long long n) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
-      sms = 148;
-  }
-  const long long b = (n + RT - 1) / RT;
-  return (int)std::max<long long>(1, std::min<long long>(b, 8LL * sms));
-}
-
 struct EdgeWs {
   size_t bytes;
   size_t o_st, o_cnt, o_off, o_sums, o_bucket, o_ucnt, o_uoff, o_usums;
@@ -404,14 +282,7 @@ RegWs reg_layout(long long N) {
   return w;
 }
 
-bool sizes_ok(long long N, long long K) {
-  return N >= 1 && K >= 1 && N <= 0x7fffffffLL && 6 * K <= 0x7fffffffLL;
-}
-
 }  // namespace
-
-// launch counter shared with the other entry points
-void count_launches(long long n);
 
 }  // namespace tts
 
@@ -449,11 +320,11 @@ int tts_tet_edges(const int32_t* T, int64_t K, int64_t N, int32_t* edges, int64_
     return TTS_ERR_CUDA;
   long long n = 0;
   k_edge_count<<<grid_for(K), RT, 0, s>>>(T4, K, N, cnt, st);
-  n += 1 + scan_counts(cnt, N, sums, off, st, s);
+  n += 1 + scan_counts(cnt, N, sums, off, &st->total, s);
   if (cudaMemsetAsync(cnt, 0, sizeof(int) * N, s) != cudaSuccess) return TTS_ERR_CUDA;
   k_edge_fill<<<grid_for(K), RT, 0, s>>>(T4, K, N, off, cnt, bucket);
   k_edge_unique<<<grid_for(N), RT, 0, s>>>(N, off, bucket, ucnt);
-  n += 2 + scan_counts(ucnt, N, usums, uoff, st, s);
+  n += 2 + scan_counts(ucnt, N, usums, uoff, &st->total, s);
   k_edge_write<<<grid_for(N), RT, 0, s>>>(N, off, bucket, uoff, reinterpret_cast<int2*>(edges),
                                           edge_capacity, st, reinterpret_cast<long long*>(n_edges));
   count_launches(n + 1);

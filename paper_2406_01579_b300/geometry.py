@@ -1,6 +1,7 @@
-"""Geometry-stage terms of Sec. 4.2 over the C ABI: the unique edges of a tet
-grid and the eikonal / normal-consistency regularizers of its SDF.  Device
-memory comes from PyTorch; the work runs in libtets' kernels."""
+"""Geometry terms over the C ABI: the unique edges of a tet grid, the
+eikonal / normal-consistency regularizers of its SDF (Sec. 4.2) and Marching
+Tetrahedra mesh extraction (Sec. 3.1).  Device memory comes from PyTorch; the
+work runs in libtets' kernels."""
 
 from __future__ import annotations
 
@@ -97,5 +98,37 @@ def regularizer_loss(V, f, T, edges, w_eik=1.0, w_nc=1.0, reg: Regularizers | No
     return RegularizerLoss.apply(V, f, T, edges, w_eik, w_nc, reg)
 
 
-__all__ = ["tet_edges", "Regularizers", "RegularizerLoss", "regularizer_loss",
+def marching_tets(V, T, f, edges):
+    """Marching Tetrahedra: (verts (nv, 3) float32, tris (nt, 3) int32,
+    vert_edge (nv,) int32) for the zero level set of f.  Two calls: the first
+    sizes the outputs (one stream synchronisation), the second fills them."""
+    L = _lib.load()
+    N, K, E = int(V.shape[0]), int(T.shape[0]), int(edges.shape[0])
+    nb = ctypes.c_size_t(0)
+    check(L.tts_marching_tets_workspace_size(K, E, ctypes.byref(nb)),
+          "tts_marching_tets_workspace_size")
+    ws = _ws(nb.value, V.device)
+    counts = torch.zeros(2, dtype=torch.int64, device=V.device)
+    dummy_v = torch.empty(3, dtype=torch.float32, device=V.device)
+    dummy_t = torch.empty(3, dtype=torch.int32, device=V.device)
+    args = (V.data_ptr(), T.data_ptr(), f.data_ptr(), N, K, edges.data_ptr(), E)
+    check(L.tts_marching_tets(*args, dummy_v.data_ptr(), None, 0, dummy_t.data_ptr(), 0,
+                              counts.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()),
+          "tts_marching_tets")
+    nv, nt = (int(x) for x in counts.cpu())
+    verts = torch.empty((max(nv, 1), 3), dtype=torch.float32, device=V.device)
+    vedge = torch.empty(max(nv, 1), dtype=torch.int32, device=V.device)
+    tris = torch.empty((max(nt, 1), 3), dtype=torch.int32, device=V.device)
+    check(L.tts_marching_tets(*args, verts.data_ptr(), vedge.data_ptr(), nv, tris.data_ptr(), nt,
+                              counts.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr()),
+          "tts_marching_tets")
+    st = ctypes.c_uint32(0)
+    check(L.tts_geometry_status(ws.data_ptr(), ctypes.byref(st), _stream_ptr()),
+          "tts_geometry_status")
+    if st.value & TTS_STATUS_BAD_INDEX:
+        raise TetsError("an index is out of range or a tet edge is missing from the edge list")
+    return verts[:nv], tris[:nt], vedge[:nv]
+
+
+__all__ = ["tet_edges", "Regularizers", "RegularizerLoss", "regularizer_loss", "marching_tets",
            "TTS_STATUS_BAD_INDEX"]
