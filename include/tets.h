@@ -169,6 +169,21 @@ int tts_workspace_init(const tts_batch* b, tts_stream stream);
  * the workspace. */
 int tts_prepare_scene(const tts_batch* b, tts_stream stream);
 
+/* Coarse-to-fine pre-filter (App. B.1), first round: the axis-aligned bounds
+ * of the vertices of each scene's survivors of the last tts_prepare_scene.
+ * aabb: device float[6 * n_scenes], (xmin, ymin, zmin, xmax, ymax, zmax) per
+ * scene; a scene without survivors gets (+inf x3, -inf x3). */
+int tts_survivor_bounds(const tts_batch* b, float* aabb, tts_stream stream);
+
+/* Coarse-to-fine pre-filter, the resize between the rounds: maps the grid's
+ * box [grid_lo, grid_hi] (host float[3] each) affinely, per axis, onto the
+ * bounds aabb (device float[6], e.g. from tts_survivor_bounds) widened by
+ * pad times its extent on each side: V_out = V_in * scale + offset
+ * (N x 3, device; may alias V_in).  Empty bounds leave V_out = V_in.  The
+ * caller then evaluates the SDF at the new vertices and prepares again. */
+int tts_fit_grid(const float* V_in, int64_t N, const float grid_lo[3], const float grid_hi[3],
+                 const float* aabb, float pad, float* V_out, tts_stream stream);
+
 /* Forward for every view of the batch (needs tts_prepare_scene first).
  * image: 3 * sum(H W) floats, alpha and depth: sum(H W) floats (device). */
 int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,

@@ -19,6 +19,8 @@ What each function restates (paper sections):
               with their gradients (``geometry_terms.cpp``).
   marching_tets
               Marching Tetrahedra mesh extraction (Sec. 3.1).
+  survivor_bounds, fit_grid
+              the coarse-to-fine pre-filter of App. B.1.
 
 Parity status: pinned by the tests under ``tests/test_oracle_*.py``.
 """
@@ -101,6 +103,10 @@ def lib():
         L.orc_regularizers_dirderiv.restype = None
         L.orc_marching_tets.argtypes = [i64, P, i64, P, P, i64, P, P, P, i64, P, i64, P]
         L.orc_marching_tets.restype = ctypes.c_int
+        L.orc_survivor_bounds.argtypes = [P, P, P, i64, P]
+        L.orc_survivor_bounds.restype = None
+        L.orc_fit_grid.argtypes = [i64, P, P, P, P, f64, P]
+        L.orc_fit_grid.restype = None
         _lib = L
     return _lib
 
@@ -336,3 +342,25 @@ def marching_tets(V, T, f, edges=None):
     nv, nt = int(counts[0]), int(counts[1])
     return dict(verts=verts[:nv].copy(), vert_edge=vedge[:nv].copy(), tris=tris[:nt].copy(),
                 edges=edges)
+
+
+def survivor_bounds(V, T, surv):
+    """(xmin, ymin, zmin, xmax, ymax, zmax) of the survivors' vertices."""
+    V = _c(V, np.float32)
+    T = _c(T, np.int32)
+    surv = _c(surv, np.int32)
+    out = np.zeros(6, np.float32)
+    lib().orc_survivor_bounds(_p(V), _p(T), _p(surv), len(surv), _p(out))
+    return out
+
+
+def fit_grid(V, grid_lo, grid_hi, aabb, pad=0.05):
+    """Grid vertices mapped per axis from [grid_lo, grid_hi] onto the bounds
+    widened by pad * extent (FP64)."""
+    V = _c(V, np.float32)
+    lo = _c(grid_lo, np.float64)
+    hi = _c(grid_hi, np.float64)
+    aabb = _c(aabb, np.float32)
+    out = np.zeros(V.shape, np.float64)
+    lib().orc_fit_grid(len(V), _p(V), _p(lo), _p(hi), _p(aabb), float(pad), _p(out))
+    return out

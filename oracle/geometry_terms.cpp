@@ -21,6 +21,11 @@
 //                   one triangle per tet with a 1-3 sign split and two per tet
 //                   with a 2-2 split, wound so that the normal points towards
 //                   increasing f.
+//   survivor_bounds, fit_grid
+//                   the coarse-to-fine pre-filter of App. B.1: the axis-aligned
+//                   bounds of the first round's survivors, and the grid mapped
+//                   per axis onto those bounds (widened by a pad fraction of
+//                   their extent) for the second round.
 //
 // Readings where the paper is silent:
 //   * "project the tet normals onto vertices": m_v = unweighted sum of the
@@ -359,6 +364,44 @@ int orc_marching_tets(int64_t N, const double* V, int64_t K, const int32_t* T, c
   counts[0] = nv;
   counts[1] = nt;
   return 0;
+}
+
+// Bounds of the vertices of the survivor tets (float min / max, exact):
+// out = (xmin, ymin, zmin, xmax, ymax, zmax); (+inf, -inf) when empty.
+void orc_survivor_bounds(const float* V, const int32_t* T, const int32_t* surv, int64_t nsurv,
+                         float* out) {
+  for (int r = 0; r < 3; ++r) {
+    out[r] = INFINITY;
+    out[3 + r] = -INFINITY;
+  }
+  for (int64_t i = 0; i < nsurv; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const int64_t id = T[4 * (int64_t)surv[i] + j];
+      for (int r = 0; r < 3; ++r) {
+        out[r] = std::min(out[r], V[3 * id + r]);
+        out[3 + r] = std::max(out[3 + r], V[3 * id + r]);
+      }
+    }
+}
+
+// The grid box [lo, hi] mapped per axis onto [b_lo, b_hi] = the bounds
+// widened by pad * extent on each side (FP64); identity when the bounds are
+// empty.
+void orc_fit_grid(int64_t N, const float* V, const double* lo, const double* hi,
+                  const float* aabb, double pad, double* out) {
+  bool empty = false;
+  for (int r = 0; r < 3; ++r) empty |= !(aabb[r] <= aabb[3 + r]);
+  for (int64_t i = 0; i < N; ++i)
+    for (int r = 0; r < 3; ++r) {
+      const double x = V[3 * i + r];
+      if (empty) {
+        out[3 * i + r] = x;
+        continue;
+      }
+      const double ext = (double)aabb[3 + r] - (double)aabb[r];
+      const double blo = aabb[r] - pad * ext, bhi = aabb[3 + r] + pad * ext;
+      out[3 * i + r] = blo + (x - lo[r]) * (bhi - blo) / (hi[r] - lo[r]);
+    }
 }
 
 }  // extern "C"

@@ -78,7 +78,8 @@ class tts_info(ctypes.Structure):
                 ("sort_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32)]
 
 
-ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene", "tts_render_fwd",
+ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
+                "tts_survivor_bounds", "tts_fit_grid", "tts_render_fwd",
                 "tts_render_bwd", "tts_render_fwd_ex", "tts_render_bwd_ex", "tts_bin_views",
                 "tts_blend_fwd", "tts_blend_bwd", "tts_blend_fwd_ex", "tts_blend_bwd_ex",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
@@ -118,6 +119,9 @@ def load():
     L.tts_render_bwd_ex.argtypes = [B, U, P, P, P, P]
     L.tts_blend_fwd_ex.argtypes = [B, O, P]
     L.tts_blend_bwd_ex.argtypes = [B, U, P]
+    L.tts_survivor_bounds.argtypes = [B, P, P]
+    F3 = ctypes.c_float * 3
+    L.tts_fit_grid.argtypes = [P, ctypes.c_int64, F3, F3, P, ctypes.c_float, P, P]
     L.tts_bin_views.argtypes = [B, P]
     L.tts_blend_fwd.argtypes = [B, P, P, P, P]
     L.tts_blend_bwd.argtypes = [B, P, P, P, P]

@@ -179,6 +179,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   P->off_ctr = take(sizeof(Counters));
   const size_t o_pfb = take(sizeof(int) * pf_chunks);
   const size_t o_pff = take((size_t)flag_total);
+  const size_t o_bnd = take(sizeof(unsigned) * 6 * b->n_scenes);
   const size_t o_surv = take(sizeof(int) * surv_total);
   const size_t o_rz = take(sizeof(unsigned) * slots);
   const size_t o_rnt = take(sizeof(int) * slots);
@@ -211,6 +212,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.ctr = reinterpret_cast<Counters*>(base + P->off_ctr);
     B.pf_blocksum = reinterpret_cast<int*>(base + o_pfb);
     B.pf_flags = reinterpret_cast<unsigned char*>(base + o_pff);
+    B.bounds = reinterpret_cast<unsigned*>(base + o_bnd);
     B.surv = reinterpret_cast<int*>(base + o_surv);
     B.rec_z = reinterpret_cast<unsigned*>(base + o_rz);
     B.rec_nt = reinterpret_cast<int*>(base + o_rnt);
@@ -299,6 +301,31 @@ int tts_prepare_scene(const tts_batch* b, tts_stream stream) {
   long long n = launch_upload(P.hb, dB, st);
   n += launch_prefilter(P.hp, dB, st);
   g_launches += n;
+  return check_launch();
+}
+
+int tts_survivor_bounds(const tts_batch* b, float* aabb, tts_stream stream) {
+  if (!aabb) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  g_launches += launch_bounds(P.hp, dev_desc(b, P), aabb, st);
+  return check_launch();
+}
+
+int tts_fit_grid(const float* V_in, int64_t N, const float grid_lo[3], const float grid_hi[3],
+                 const float* aabb, float pad, float* V_out, tts_stream stream) {
+  if (!V_in || !V_out || !aabb || !grid_lo || !grid_hi || N < 1 || N > 0x7fffffffLL) return TTS_ERR_ARG;
+  if (!(std::isfinite(pad) && pad >= 0.f)) return TTS_ERR_ARG;
+  float lo[3], hi[3];
+  for (int i = 0; i < 3; ++i) {
+    lo[i] = grid_lo[i];
+    hi[i] = grid_hi[i];
+    if (!(std::isfinite(lo[i]) && std::isfinite(hi[i]) && hi[i] > lo[i])) return TTS_ERR_ARG;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  g_launches += launch_fit_grid(V_in, N, lo, hi, aabb, pad, V_out, st);
   return check_launch();
 }
 

@@ -1,5 +1,7 @@
 // Pre-filter (Sec. 3.2), per-view preprocess and tile binning with a device
 // radix sort of (tile id, mean depth) keys (Sec. 3.3).
+#include <algorithm>
+
 #include "geometry.cuh"
 #include "launch.h"
 
@@ -184,6 +186,112 @@ __global__ void __launch_bounds__(256) k_tet_normals(const Batch* __restrict__ B
     const float3 n = tet_unit_normal(G, &ih, &sg);
     B->surv_n[S.surv_off + k] = make_float4(n.x, n.y, n.z, 0.f);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse-to-fine pre-filter (App. B.1): the axis-aligned bounds of the
+// survivors' vertices after a first round, and the affine refit of the grid
+// into those bounds for the second round.  Float min / max go through
+// order-preserving unsigned keys so that plain integer atomics apply.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned float_key(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_bounds_init(const Batch* __restrict__ B) {
+  const int i = threadIdx.x;
+  if (i < 6 * B->n_scenes) B->bounds[i] = (i % 6 < 3) ? 0xffffffffu : 0u;
+}
+
+// grid (blocks, n_scenes)
+__global__ void __launch_bounds__(256) k_bounds(const Batch* __restrict__ B) {
+  const int s = blockIdx.y;
+  const SceneD& S = B->sc[s];
+  const int nsurv = B->ctr->n_surv[s];
+  unsigned mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
+    const int4 t = __ldg(&S.T[B->surv[S.surv_off + k]]);
+    const int id[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const unsigned key = float_key(__ldg(S.V + 3ll * id[j] + r));
+        mn[r] = min(mn[r], key);
+        mx[r] = max(mx[r], key);
+      }
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    mn[r] = __reduce_min_sync(0xffffffffu, mn[r]);
+    mx[r] = __reduce_max_sync(0xffffffffu, mx[r]);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      if (mn[r] != 0xffffffffu) atomicMin(&B->bounds[6 * s + r], mn[r]);
+      if (mx[r] != 0u) atomicMax(&B->bounds[6 * s + 3 + r], mx[r]);
+    }
+  }
+}
+
+// empty scenes read back as (+inf, +inf, +inf, -inf, -inf, -inf)
+__global__ void k_bounds_finish(const Batch* __restrict__ B, float* __restrict__ aabb) {
+  const int i = threadIdx.x;
+  if (i >= 6 * B->n_scenes) return;
+  const unsigned k = B->bounds[i];
+  const bool empty = (i % 6 < 3) ? (k == 0xffffffffu) : (k == 0u);
+  aabb[i] = empty ? ((i % 6 < 3) ? __int_as_float(0x7f800000) : __int_as_float(0xff800000))
+                  : key_float(k);
+}
+
+int launch_bounds(const HostPlan& P, const Batch* dB, float* aabb, cudaStream_t st) {
+  k_bounds_init<<<1, 6 * TTS_MAX_SCENES, 0, st>>>(dB);
+  k_bounds<<<dim3(P.normal_blocks, P.n_scenes), 256, 0, st>>>(dB);
+  k_bounds_finish<<<1, 6 * TTS_MAX_SCENES, 0, st>>>(dB, aabb);
+  return 3;
+}
+
+struct FitArgs {
+  float lo[3], hi[3];
+};
+
+// V_out = b_lo + (V_in - lo) * (b_hi - b_lo) / (hi - lo) per axis, [b_lo, b_hi]
+// the bounds widened by pad * extent on each side; unchanged when empty.
+__global__ void __launch_bounds__(256) k_fit_grid(const float* __restrict__ Vin, long long N,
+                                                  FitArgs a, const float* __restrict__ aabb,
+                                                  float pad, float* __restrict__ Vout) {
+  float scale[3], off[3];
+  bool empty = false;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) empty |= !(aabb[r] <= aabb[3 + r]);
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const float ext = aabb[3 + r] - aabb[r];
+    const float blo = aabb[r] - pad * ext, bhi = aabb[3 + r] + pad * ext;
+    scale[r] = empty ? 1.f : (bhi - blo) / (a.hi[r] - a.lo[r]);
+    off[r] = empty ? 0.f : blo - a.lo[r] * scale[r];
+  }
+  for (long long i = blockIdx.x * 256ll + threadIdx.x; i < 3 * N; i += (long long)gridDim.x * 256) {
+    const int r = (int)(i % 3);
+    Vout[i] = __fmaf_rn(Vin[i], scale[r], off[r]);
+  }
+}
+
+int launch_fit_grid(const float* V_in, long long N, const float lo[3], const float hi[3],
+                    const float* aabb, float pad, float* V_out, cudaStream_t st) {
+  FitArgs a;
+  for (int r = 0; r < 3; ++r) {
+    a.lo[r] = lo[r];
+    a.hi[r] = hi[r];
+  }
+  const long long blocks = std::min<long long>((3 * N + 255) / 256, 4096);
+  k_fit_grid<<<(int)blocks, 256, 0, st>>>(V_in, N, a, aabb, pad, V_out);
+  return 1;
 }
 
 // ---------------------------------------------------------------------------

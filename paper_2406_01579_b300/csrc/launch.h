@@ -31,6 +31,9 @@ struct GradOut {
 // Each launcher returns the number of kernels it launched.
 int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st);
+int launch_bounds(const HostPlan& P, const Batch* dB, float* aabb, cudaStream_t st);
+int launch_fit_grid(const float* V_in, long long N, const float lo[3], const float hi[3],
+                    const float* aabb, float pad, float* V_out, cudaStream_t st);
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      float* normal, cudaStream_t st);
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,

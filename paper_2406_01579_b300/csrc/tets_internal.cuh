@@ -81,6 +81,7 @@ struct Batch {
   Counters* ctr;
   int* pf_blocksum;         // [pf_chunks_total]
   unsigned char* pf_flags;  // [sum K]
+  unsigned int* bounds;     // [6 * n_scenes] survivor AABB as order-preserving float keys
   int* surv;                // [sum surv_cap]
   unsigned int* rec_z;      // [slots] FP32 mean depth bits
   int* rec_nt;              // [slots] tiles overlapped (0: culled)

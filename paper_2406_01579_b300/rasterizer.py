@@ -182,6 +182,16 @@ class Rasterizer:
         b = self.batch()
         check(self.lib.tts_prepare_scene(ctypes.byref(b), _stream_ptr()), "tts_prepare_scene")
 
+    def survivor_bounds(self, out=None) -> torch.Tensor:
+        """(n_scenes, 6) device tensor of the survivors' axis-aligned bounds
+        after the last ``prepare`` (App. B.1 coarse-to-fine pre-filter)."""
+        out = out if out is not None else torch.empty((len(self.scenes), 6), dtype=torch.float32,
+                                                      device=self.device)
+        b = self.batch()
+        check(self.lib.tts_survivor_bounds(ctypes.byref(b), out.data_ptr(), _stream_ptr()),
+              "tts_survivor_bounds")
+        return out
+
     def _outputs(self):
         """Flat output tensors: (image, alpha, depth) and, with
         ``params.normals``, the normal map (3 planes per view, like image)."""
@@ -354,6 +364,21 @@ class Rasterizer:
                 v = v + (normal[3 * off:3 * off + 3 * H * W].view(3, H, W),)
             out.append(v)
         return out
+
+
+def fit_grid(V: torch.Tensor, grid_lo, grid_hi, aabb: torch.Tensor, pad: float = 0.05,
+             out: torch.Tensor | None = None) -> torch.Tensor:
+    """Second round of the coarse-to-fine pre-filter (App. B.1): the grid's
+    vertices V (inside the box [grid_lo, grid_hi]) mapped per axis onto the
+    survivor bounds ``aabb`` (6 floats, device) widened by ``pad`` times
+    their extent on each side.  Runs on the device without synchronising."""
+    lib = _lib.load()
+    out = out if out is not None else torch.empty_like(V)
+    lo = (ctypes.c_float * 3)(*[float(x) for x in grid_lo])
+    hi = (ctypes.c_float * 3)(*[float(x) for x in grid_hi])
+    check(lib.tts_fit_grid(V.data_ptr(), int(V.shape[0]), lo, hi, aabb.data_ptr(), float(pad),
+                           out.data_ptr(), _stream_ptr()), "tts_fit_grid")
+    return out
 
 
 class TetRender(torch.autograd.Function):
