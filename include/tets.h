@@ -115,6 +115,12 @@ typedef struct {
                              window of N_w kept sorted by the depth of their chord's entry
                              point (ties: earlier first); the nearest leaves it when it holds
                              more than N_w, the rest at the end.  0: per-tile sort order. */
+  int32_t blend_segment;  /* list entries per backward work unit: 0 (library default, 1024)
+                             or a multiple of 32 in 32..65536.  The forward walks each tile
+                             list whole and records its state every blend_segment entries;
+                             the backward walks the segments of a longer list in parallel
+                             from those states (equal to the unsplit walk up to FP32
+                             rounding).  Ignored with a resort window. */
 } tts_params;
 
 /* One scene: caller-owned device arrays (must outlive every call using them). */
@@ -155,6 +161,8 @@ typedef struct {
   int64_t n_surv[TTS_MAX_SCENES]; /* survivors per scene of the last prepare */
   int32_t sort_bits;        /* key bits sorted by the last forward */
   int32_t sort_passes;
+  int32_t blend_units;      /* blend work units (tile lists and list segments) */
+  int32_t reserved;
 } tts_info;
 
 /* Bytes of workspace the batch needs (host only; nothing is enqueued). */

@@ -42,7 +42,7 @@ class tts_params(ctypes.Structure):
     _fields_ = [("s", ctypes.c_float), ("prefilter_thresh", ctypes.c_float),
                 ("alpha_skip", ctypes.c_float), ("alpha_cap", ctypes.c_float),
                 ("t_eps", ctypes.c_float), ("tile", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("resort_window", ctypes.c_int32)]
+                ("resort_window", ctypes.c_int32), ("blend_segment", ctypes.c_int32)]
 
 
 class tts_scene(ctypes.Structure):
@@ -75,7 +75,8 @@ class tts_upstream(ctypes.Structure):
 class tts_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("n_scenes", ctypes.c_int32),
                 ("n_keys", ctypes.c_int64), ("n_surv", ctypes.c_int64 * TTS_MAX_SCENES),
-                ("sort_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32)]
+                ("sort_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
+                ("blend_units", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",

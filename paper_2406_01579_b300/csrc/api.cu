@@ -33,6 +33,8 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+constexpr int kBlendSegment = 1024;   // default list entries per blend work unit
+
 int bit_length(long long x) {
   int b = 0;
   while (x > 0) { ++b; x >>= 1; }
@@ -72,6 +74,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     return TTS_ERR_ARG;
   if (b->key_capacity < 1 || b->key_capacity > 0x7fffffffLL) return TTS_ERR_ARG;
   if (pr.resort_window < 0 || pr.resort_window > 7) return TTS_ERR_ARG;
+  if (pr.blend_segment != 0 &&
+      (pr.blend_segment < 32 || pr.blend_segment > 65536 || pr.blend_segment % 32 != 0))
+    return TTS_ERR_ARG;
   if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS))
     return TTS_ERR_ARG;
   std::memset(&P->hb, 0, sizeof(Batch));
@@ -86,6 +91,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   B.tile = pr.tile;
   B.flags = pr.flags;
   B.resort_window = pr.resort_window;
+  B.seg_len = (pr.resort_window > 0) ? 0 : (pr.blend_segment > 0 ? pr.blend_segment : kBlendSegment);
   B.key_cap = b->key_capacity;
   // scenes
   long long surv_total = 0, flag_total = 0, max_surv = 1;
@@ -195,7 +201,16 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_v1 = take(sizeof(unsigned) * cap);
   const size_t o_hist = take(sizeof(unsigned) * RADIX * (B.sort_blocks + 1));
   const size_t o_rng = take(sizeof(int2) * tiles);
-  const size_t o_wl = take(sizeof(int) * tiles);
+  // split-tile segments: at most 2 * keys / seg_len (each split tile has more
+  // than seg_len keys, so ceil(len / seg_len) <= 2 len / seg_len); one
+  // checkpoint of 32 B per pixel and segment
+  B.seg_cap = B.seg_len > 0 ? (int)std::min<long long>(2 * cap / B.seg_len + 1, 0x3fffffffLL) : 0;
+  const long long tt = (long long)pr.tile * pr.tile;
+  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + B.seg_cap));
+  const size_t o_tseg = take(sizeof(int2) * tiles);
+  const size_t o_psa = take(sizeof(float4) * B.seg_cap * tt);
+  const size_t o_psb = take(sizeof(float4) * B.seg_cap * tt);
+
   const size_t o_pT = take(sizeof(float) * pix);
   const size_t o_pL = take(sizeof(int) * pix);
   const size_t o_pN = take(sizeof(int) * pix);
@@ -226,7 +241,11 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.vals[1] = reinterpret_cast<unsigned*>(base + o_v1);
     B.hist = reinterpret_cast<unsigned*>(base + o_hist);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
-    B.worklist = reinterpret_cast<int*>(base + o_wl);
+    B.worklist = reinterpret_cast<int2*>(base + o_wl);
+    B.tseg = reinterpret_cast<int2*>(base + o_tseg);
+    B.pseg_a = reinterpret_cast<float4*>(base + o_psa);
+    B.pseg_b = reinterpret_cast<float4*>(base + o_psb);
+
     B.pix_T = reinterpret_cast<float*>(base + o_pT);
     B.pix_last = reinterpret_cast<int*>(base + o_pL);
     B.pix_nfrag = reinterpret_cast<int*>(base + o_pN);
@@ -289,6 +308,7 @@ int tts_workspace_init(const tts_batch* b, tts_stream stream) {
   if (P.bytes_rec_grad &&
       cudaMemsetAsync(base + P.off_rec_grad, 0, P.bytes_rec_grad, st) != cudaSuccess)
     return TTS_ERR_CUDA;
+
   return TTS_OK;
 }
 
@@ -470,6 +490,7 @@ int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream) {
   for (int s = 0; s < b->n_scenes; ++s) info->n_surv[s] = c.n_surv[s];
   info->sort_bits = c.total_bits;
   info->sort_passes = c.n_passes;
+  info->blend_units = c.n_units;
   return TTS_OK;
 }
 

@@ -596,29 +596,50 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
   }
 }
 
-// Work list for the persistent blend kernels: tiles in decreasing order of
-// list length (bucketed by bit length), so the longest lists start first.
+// Work list for the persistent blend kernels.  A tile whose list is longer
+// than seg_len entries is split into segments of seg_len entries: the forward
+// walks the whole list (segment 0's unit) and records its state at each
+// segment end, and the backward walks the segments in parallel from those
+// states (one warp per 8x4 block walking a long list back to front would
+// otherwise bound its duration).  Units (tile, segment) are ordered by
+// decreasing length (bucketed by bit length), so the longest start first.
 __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __restrict__ B) {
   __shared__ int cnt[33], off[33];
+  __shared__ int nseg_total;
   if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
+  if (threadIdx.x == 0) nseg_total = 0;
   __syncthreads();
   const int nt = B->total_tiles;
+  const int L = B->seg_len;
   for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
     const int2 r = B->ranges[t];
     const int len = r.y - r.x;
-    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], 1);
+    int nseg = (L > 0 && len > L) ? (len + L - 1) / L : 1;
+    int base = -1;
+    if (nseg > 1) {
+      base = atomicAdd(&nseg_total, nseg);
+      if (base + nseg > B->seg_cap) {   // outside the sizing bound: blend unsplit
+        nseg = 1;
+        base = -1;
+      }
+    }
+    B->tseg[t] = make_int2(base, nseg);
+    const int w = (nseg > 1) ? L : len;
+    atomicAdd(&cnt[w > 0 ? 32 - __clz(w) : 0], nseg);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     int run = 0;
     for (int b = 32; b >= 0; --b) { off[b] = run; run += cnt[b]; }
+    B->ctr->n_units = run;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
     const int2 r = B->ranges[t];
-    const int len = r.y - r.x;
-    const int pos = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], 1);
-    B->worklist[pos] = t;
+    const int2 ts = B->tseg[t];
+    const int w = (ts.y > 1) ? L : (r.y - r.x);
+    const int pos = atomicAdd(&off[w > 0 ? 32 - __clz(w) : 0], ts.y);
+    for (int j = 0; j < ts.y; ++j) B->worklist[pos + j] = make_int2(t, j);
   }
 }
 

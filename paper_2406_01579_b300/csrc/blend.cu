@@ -40,6 +40,8 @@ __device__ __forceinline__ void queue_done(unsigned* counter, unsigned* done) {
 // A warp's work item: one 8x4 pixel block of one tile, lanes row-major.
 struct WarpBlock {
   int gt;
+  int seg;                    // segment of a split tile list (0 otherwise)
+  int sb;                     // 8x4 block within the tile
   int px, py;
   bool inimg;
   float fpx, fpy;
@@ -65,12 +67,14 @@ struct WarpBlock {
   }
 };
 
+// The warp block (tile gt, 8x4 block sb, list segment seg).
 template <int TILE>
-__device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
-                                                    WarpBlock& wb) {
-  constexpr int SBX = TILE / 8, SB = SBX * (TILE / 4);
-  wb.gt = B->worklist[item / SB];
-  const int sb = item - (item / SB) * SB;
+__device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B, int gt, int seg,
+                                                     int sb, WarpBlock& wb) {
+  constexpr int SBX = TILE / 8;
+  wb.gt = gt;
+  wb.seg = seg;
+  wb.sb = sb;
   const ViewD& vw = B->vw[find_view(B, wb.gt)];
   const int lt = wb.gt - vw.tile_base;
   const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
@@ -86,6 +90,15 @@ __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B,
   wb.wy0 = (float)by + 0.5f;
   wb.wy1 = wb.wy0 + 3.f;
   return vw;
+}
+
+// Work item -> warp block: item / SB indexes the (tile, segment) unit list.
+template <int TILE>
+__device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
+                                                    WarpBlock& wb) {
+  constexpr int SB = (TILE / 8) * (TILE / 4);
+  const int2 u = B->worklist[item / SB];
+  return decode_block<TILE>(B, u.x, u.y, item - (item / SB) * SB, wb);
 }
 
 // Per-slot normals of a view's tile lists: the survivor normals of its scene
@@ -109,12 +122,140 @@ __device__ __forceinline__ void store_normal(const Batch* __restrict__ B, const 
   if (B->pix_N) B->pix_N[vw.pix_base + p] = make_float4(N0, N1, N2, 0.f);
 }
 
+// Per-pixel compositing state of the forward.
+struct FwdState {
+  float T, C0, C1, C2, D, N0, N1, N2;
+  int last, nfrag;
+  bool done;
+};
+
+// Walks the list entries [lo, hi) of the warp's tile front to back for the
+// lanes that are not done: the entries whose bbox meets a live pixel are
+// staged (ballot) in the warp's shared-memory slice and blended in order
+// (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions).  With `stop` a pixel
+// stops before the fragment that would take T below eps.  `last` counts list
+// entries from rg_x.
+// Final per-pixel outputs of the forward.
+template <bool NRM>
+__device__ __forceinline__ void store_pixel(const Batch* __restrict__ B, const ViewD& vw,
+                                            const WarpBlock& wb, const FwdState& S,
+                                            float* __restrict__ image, float* __restrict__ alpha,
+                                            float* __restrict__ depth, float* __restrict__ normal) {
+  const long long HW = (long long)vw.W * vw.H;
+  const long long p = (long long)wb.py * vw.W + wb.px;
+  image[3 * vw.pix_base + p] = S.C0;
+  image[3 * vw.pix_base + HW + p] = S.C1;
+  image[3 * vw.pix_base + 2 * HW + p] = S.C2;
+  alpha[vw.pix_base + p] = 1.f - S.T;
+  depth[vw.pix_base + p] = S.D;
+  B->pix_T[vw.pix_base + p] = S.T;
+  B->pix_last[vw.pix_base + p] = S.last;
+  B->pix_nfrag[vw.pix_base + p] = S.nfrag;
+  B->pix_CD[vw.pix_base + p] = make_float4(S.C0, S.C1, S.C2, S.D);
+  if constexpr (NRM) store_normal(B, vw, p, normal, S.N0, S.N1, S.N2);
+}
+
+// Walks the list entries [lo, hi) of the warp's tile front to back for the
+// lanes that are not done: the entries whose bbox meets a live pixel are
+// staged (ballot) in the warp's shared-memory slice and blended in order
+// (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions); a pixel stops before
+// the fragment that would take T below eps (not in PURE mode).  `last` counts
+// list entries from lo.  When the list is split into segments for the
+// backward (ts.y > 1), the state at the end of each segment is stored as the
+// walk passes it.
+template <bool NRM>
+__device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock wb,
+                                         const unsigned* __restrict__ vals,
+                                         const float4* __restrict__ rec,
+                                         const float4* __restrict__ nrm, int lo, int hi, int2 ts,
+                                         int tt, bool pure, float cap, float skip, float eps,
+                                         float4 (*st)[32], int* sidx, FwdState& S) {
+  const int lane = threadIdx.x & 31;
+  const unsigned ltm = (1u << lane) - 1u;
+  const int L = B->seg_len;
+  const bool split = ts.y > 1;
+  // one group of lookahead on (slot, bbox)
+  int idx = lo + lane;
+  unsigned slot = (idx < hi) ? vals[idx] : 0u;
+  float4 q0 = (idx < hi) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
+  unsigned slot_n = (idx + 32 < hi) ? vals[idx + 32] : 0u;
+  for (int g = lo; g < hi; g += 32) {
+    if (split && g > lo && (g - lo) % L == 0) {
+      const long long pi = ((long long)ts.x + (g - lo) / L - 1) * tt + wb.sb * 32 + lane;
+      B->pseg_a[pi] = make_float4(S.T, S.C0, S.C1, S.C2);
+      B->pseg_b[pi] = make_float4(S.D, S.N0, S.N1, S.N2);
+    }
+    if (!wb.cull_to(!S.done)) break;
+    const int idn = g + 32 + lane;
+    const float4 q0_n = (idn < hi) ? __ldg(rec + (size_t)slot_n * REC_Q)
+                                   : make_float4(0.f, 0.f, -1.f, -1.f);
+    const unsigned slot_nn = (idn + 32 < hi) ? vals[idn + 32] : 0u;
+    const bool ov = (g + lane < hi) && !wb.misses(q0);
+    const unsigned m = __ballot_sync(FULL, ov);
+    if (m != 0u) {
+      if (ov) {
+        const int pos = __popc(m & ltm);
+        const float4* r = rec + (size_t)slot * REC_Q;
+        st[0][pos] = q0;
+#pragma unroll
+        for (int q = 1; q < REC_Q; ++q) st[q][pos] = __ldg(r + q);
+        if constexpr (NRM) st[REC_Q][pos] = __ldg(nrm + slot);
+        sidx[pos] = lane;
+      }
+      __syncwarp();
+      const int cnt = __popc(m);
+      for (int k = 0; k < cnt; ++k) {
+        if (!S.done) {
+          const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
+          if (ch.hit) {
+            ++S.nfrag;
+            const Opacity o = opacity_eval(st[4][k], ch);
+            float a = o.alpha;
+            bool use = true;
+            if (!pure) {
+              a = fminf(a, cap);
+              use = a >= skip;
+            } else {
+              use = a > 0.f;
+            }
+            if (use) {
+              const float Tn = __fmul_rn(S.T, __fsub_rn(1.f, a));
+              if (!pure && Tn < eps) {
+                S.done = true;
+              } else {
+                const float4 q5 = st[5][k];
+                const float wgt = __fmul_rn(S.T, a);
+                S.C0 = __fmaf_rn(wgt, q5.y, S.C0);
+                S.C1 = __fmaf_rn(wgt, q5.z, S.C1);
+                S.C2 = __fmaf_rn(wgt, q5.w, S.C2);
+                S.D = __fmaf_rn(wgt, q5.x, S.D);
+                if constexpr (NRM) {
+                  const float4 n = st[REC_Q][k];
+                  S.N0 = __fmaf_rn(wgt, n.x, S.N0);
+                  S.N1 = __fmaf_rn(wgt, n.y, S.N1);
+                  S.N2 = __fmaf_rn(wgt, n.z, S.N2);
+                }
+                S.T = Tn;
+                S.last = g - lo + sidx[k] + 1;
+              }
+            }
+          }
+        }
+        if (__all_sync(FULL, S.done)) break;
+      }
+      __syncwarp();
+    }
+    slot = slot_n;
+    q0 = q0_n;
+    slot_n = slot_nn;
+  }
+}
+
 // ---------------------------------------------------------------------------
-// K6: forward blend.  Persistent warps; each takes 8x4 pixel blocks of tiles
-// from a queue (longest tile lists first), scans the tile's list 32 entries
-// at a time, keeps (ballot) the entries whose bbox meets the block, stages
-// their records in its own shared-memory slice and blends them front to back
-// (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions).
+// K6: forward blend.  Persistent warps take work items from a queue (longest
+// lists first), each one 8x4 pixel block of one tile list, and walk the list
+// front to back (fwd_walk).  Units of the backward's later list segments
+// (segment index > 0) have no forward work.
 // ---------------------------------------------------------------------------
 template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict__ B,
@@ -125,108 +266,25 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q + NRM][32];
   __shared__ int sidx[WPB][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned ltm = (1u << lane) - 1u;
+  const int wid = threadIdx.x >> 5;
   Counters* c = B->ctr;
   const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
   const float4* __restrict__ rec = B->rec;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
-  const int total = B->total_tiles * SB;
+  const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, item, wb);
+    if (wb.seg > 0) continue;
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
+    const int2 ts = B->tseg[wb.gt];
     const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f, D = 0.f, N0 = 0.f, N1 = 0.f, N2 = 0.f;
-    int last = 0, nfrag = 0;
-    bool done = !wb.inimg;
-    // one group of lookahead on (slot, bbox)
-    int idx = rg.x + lane;
-    unsigned slot = (idx < rg.y) ? vals[idx] : 0u;
-    float4 q0 = (idx < rg.y) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
-    unsigned slot_n = (idx + 32 < rg.y) ? vals[idx + 32] : 0u;
-    for (int g = rg.x; g < rg.y; g += 32) {
-      if (!wb.cull_to(!done)) break;
-      const int idn = g + 32 + lane;
-      const float4 q0_n = (idn < rg.y) ? __ldg(rec + (size_t)slot_n * REC_Q)
-                                       : make_float4(0.f, 0.f, -1.f, -1.f);
-      const unsigned slot_nn = (idn + 32 < rg.y) ? vals[idn + 32] : 0u;
-      const bool ov = (g + lane < rg.y) && !wb.misses(q0);
-      const unsigned m = __ballot_sync(FULL, ov);
-      if (m != 0u) {
-        if (ov) {
-          const int pos = __popc(m & ltm);
-          const float4* r = rec + (size_t)slot * REC_Q;
-          st[wid][0][pos] = q0;
-#pragma unroll
-          for (int q = 1; q < REC_Q; ++q) st[wid][q][pos] = __ldg(r + q);
-          if constexpr (NRM) st[wid][REC_Q][pos] = __ldg(nrm + slot);
-          sidx[wid][pos] = lane;
-        }
-        __syncwarp();
-        const int cnt = __popc(m);
-        for (int k = 0; k < cnt; ++k) {
-          if (!done) {
-            const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k],
-                                        st[wid][3][k], wb.fpx, wb.fpy);
-            if (ch.hit) {
-              ++nfrag;
-              const Opacity o = opacity_eval(st[wid][4][k], ch);
-              float a = o.alpha;
-              bool use = true;
-              if (!pure) {
-                a = fminf(a, cap);
-                use = a >= skip;
-              } else {
-                use = a > 0.f;
-              }
-              if (use) {
-                const float Tn = __fmul_rn(T, __fsub_rn(1.f, a));
-                if (!pure && Tn < eps) {
-                  done = true;
-                } else {
-                  const float4 q5 = st[wid][5][k];
-                  const float wgt = __fmul_rn(T, a);
-                  C0 = __fmaf_rn(wgt, q5.y, C0);
-                  C1 = __fmaf_rn(wgt, q5.z, C1);
-                  C2 = __fmaf_rn(wgt, q5.w, C2);
-                  D = __fmaf_rn(wgt, q5.x, D);
-                  if constexpr (NRM) {
-                    const float4 n = st[wid][REC_Q][k];
-                    N0 = __fmaf_rn(wgt, n.x, N0);
-                    N1 = __fmaf_rn(wgt, n.y, N1);
-                    N2 = __fmaf_rn(wgt, n.z, N2);
-                  }
-                  T = Tn;
-                  last = g - rg.x + sidx[wid][k] + 1;
-                }
-              }
-            }
-          }
-          if (__all_sync(FULL, done)) break;
-        }
-        __syncwarp();
-      }
-      slot = slot_n;
-      q0 = q0_n;
-      slot_n = slot_nn;
-    }
-    if (wb.inimg) {
-      const long long HW = (long long)vw.W * vw.H;
-      const long long p = (long long)wb.py * vw.W + wb.px;
-      image[3 * vw.pix_base + p] = C0;
-      image[3 * vw.pix_base + HW + p] = C1;
-      image[3 * vw.pix_base + 2 * HW + p] = C2;
-      alpha[vw.pix_base + p] = 1.f - T;
-      depth[vw.pix_base + p] = D;
-      B->pix_T[vw.pix_base + p] = T;
-      B->pix_last[vw.pix_base + p] = last;
-      B->pix_nfrag[vw.pix_base + p] = nfrag;
-      B->pix_CD[vw.pix_base + p] = make_float4(C0, C1, C2, D);
-      if constexpr (NRM) store_normal(B, vw, p, normal, N0, N1, N2);
-    }
+    FwdState S = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, !wb.inimg};
+    fwd_walk<NRM>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
+                  st[wid], sidx[wid], S);
+    if (wb.inimg) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
   }
   queue_done(&c->work_fwd, &c->done_fwd);
 }
@@ -326,7 +384,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
   const int nw = B->resort_window;
-  const int total = B->total_tiles * SB;
+  const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, item, wb);
@@ -439,7 +497,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   float4* __restrict__ rgrad = B->rec_grad;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip;
-  const int total = B->total_tiles * SB;
+  const int total = c->n_units * SB;
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, item, wb);
@@ -464,15 +522,44 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         gN2 = dnormal[3 * vw.pix_base + 2 * HW + p];
       }
     }
-    int maxlast = last;
+    // the list range of this item: the whole list, or one segment of a split
+    // one; T and the suffix S start at the range's end
+    const int2 ts = B->tseg[wb.gt];
+    int lo = rg.x, hi = rg.y;
+    float T = Tfin, S = 0.f;
+    if (ts.y > 1) {
+      lo = rg.x + wb.seg * B->seg_len;
+      hi = min(lo + B->seg_len, rg.y);
+      if (wb.inimg && last > hi - rg.x) {
+        // the pixel blends past this segment: T and the colour / depth /
+        // normal at its end were stored by the forward; the suffix after it
+        // is S = W - (gC.C + gD.D + gN.N at the end), W the same of the
+        // final pixel
+        const long long pj = ((long long)ts.x + wb.seg) * (TILE * TILE) + wb.sb * 32 + lane;
+        const float4 a = __ldcg(B->pseg_a + pj);
+        const float4 b4 = __ldcg(B->pseg_b + pj);
+        float P = gC0 * a.y + gC1 * a.z + gC2 * a.w + gD * b4.x;
+        if constexpr (NRM) P += gN0 * b4.y + gN1 * b4.z + gN2 * b4.w;
+        const float4 cd = B->pix_CD[vw.pix_base + p];
+        float W = gC0 * cd.x + gC1 * cd.y + gC2 * cd.z + gD * cd.w;
+        if constexpr (NRM) {
+          if (dnormal) {
+            const float4 nf = B->pix_N[vw.pix_base + p];
+            W += gN0 * nf.x + gN1 * nf.y + gN2 * nf.z;
+          }
+        }
+        T = a.x;
+        S = W - P;
+      }
+    }
+    int maxlast = min(last, hi - rg.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) maxlast = max(maxlast, __shfl_xor_sync(FULL, maxlast, o));
-    if (maxlast == 0) continue;
-    float T = Tfin, S = 0.f;
+    if (maxlast <= lo - rg.x) continue;
     const float gOT = gO * Tfin;
     const int top = rg.x + maxlast;
-    for (int ge = top; ge > rg.x; ge -= 32) {
-      const int g0 = max(rg.x, ge - 32);
+    for (int ge = top; ge > lo; ge -= 32) {
+      const int g0 = max(lo, ge - 32);
       if (!wb.cull_to(last > g0 - rg.x)) continue;
       const int idx = g0 + lane;
       bool ov = false;
@@ -629,7 +716,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
   const int nw = B->resort_window;
-  const int total = B->total_tiles * SB;
+  const int total = c->n_units * SB;
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, item, wb);
@@ -950,13 +1037,15 @@ void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, in
 }
 
 template <int TILE, bool NRM>
-static void fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
-                  float* normal, cudaStream_t st) {
+static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
+                 float* normal, cudaStream_t st) {
   const int g = P.blend_fwd_blocks;
-  if (P.window > 0)
+  if (P.window > 0) {
     k_blend_fwd_win<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
-  else
-    k_blend_fwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+    return 1;
+  }
+  k_blend_fwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+  return 1;
 }
 
 template <int TILE, bool NRM>
@@ -972,14 +1061,13 @@ static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      float* normal, cudaStream_t st) {
   switch (P.tile * 2 + (P.normals ? 1 : 0)) {
-    case 16: fwd_t<8, false>(P, dB, image, alpha, depth, normal, st); break;
-    case 17: fwd_t<8, true>(P, dB, image, alpha, depth, normal, st); break;
-    case 32: fwd_t<16, false>(P, dB, image, alpha, depth, normal, st); break;
-    case 33: fwd_t<16, true>(P, dB, image, alpha, depth, normal, st); break;
-    case 64: fwd_t<32, false>(P, dB, image, alpha, depth, normal, st); break;
-    default: fwd_t<32, true>(P, dB, image, alpha, depth, normal, st); break;
+    case 16: return fwd_t<8, false>(P, dB, image, alpha, depth, normal, st);
+    case 17: return fwd_t<8, true>(P, dB, image, alpha, depth, normal, st);
+    case 32: return fwd_t<16, false>(P, dB, image, alpha, depth, normal, st);
+    case 33: return fwd_t<16, true>(P, dB, image, alpha, depth, normal, st);
+    case 64: return fwd_t<32, false>(P, dB, image, alpha, depth, normal, st);
+    default: return fwd_t<32, true>(P, dB, image, alpha, depth, normal, st);
   }
-  return 1;
 }
 
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,

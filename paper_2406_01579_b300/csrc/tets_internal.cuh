@@ -35,7 +35,8 @@ struct Counters {
   int n_surv[TTS_MAX_SCENES];
   unsigned int work_fwd, work_bwd;      // persistent blend work queues
   unsigned int done_fwd, done_bwd;      // warps finished (last one resets)
-  int pad[12];
+  int n_units;              // blend work units (tile segments) of the last binning
+  int pad[11];
 };
 
 struct SceneD {
@@ -73,6 +74,8 @@ struct Batch {
   float s, prefilter_thresh, alpha_skip, alpha_cap, t_eps;
   int tile, flags;
   int resort_window;
+  int seg_len;              // list entries per blend work unit (0: no splitting)
+  int seg_cap;              // segment slots of the split-tile checkpoints
   int sort_blocks;
   long long key_cap;
   long long total_pixels;
@@ -93,7 +96,10 @@ struct Batch {
   unsigned int* vals[2];
   unsigned int* hist;       // [RADIX * sort_blocks]
   int2* ranges;             // [total_tiles]
-  int* worklist;            // [total_tiles] tiles by decreasing list length
+  int2* worklist;           // [units] (tile, segment), longest first
+  int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)
+  float4* pseg_a;           // [seg_cap * tile^2] forward state at each segment end: (T, C0, C1, C2)
+  float4* pseg_b;           // [seg_cap * tile^2] (D, N0, N1, N2)
   float* pix_T;             // [total_pixels]
   int* pix_last;            // [total_pixels]
   int* pix_nfrag;           // [total_pixels]

@@ -37,6 +37,7 @@ class Params:
     forward_only: bool = False
     resort_window: int = 0      # N_w of Sec. 3.3 (0..7)
     normals: bool = False       # also render the Eq. 2 normal map
+    blend_segment: int = 0      # list entries per backward work unit (0: library default)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -50,6 +51,7 @@ class Params:
                    | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0)
                    | (TTS_FLAG_NORMALS if self.normals else 0))
         p.resort_window = int(self.resort_window)
+        p.blend_segment = int(self.blend_segment)
         return p
 
 

@@ -127,6 +127,29 @@ def test_normal_gradient_alone(sphere16):
         assert err < GRAD_TOL, f"normal-only {name}: rel err {err:.3e}"
 
 
+@pytest.mark.parametrize("seg", [32, 96])
+@pytest.mark.parametrize("s,pure", [(20.0, False), (175.0, False), (20.0, True)])
+def test_split_tile_lists(sphere16, seg, s, pure):
+    """Tile lists split into segments of `seg` entries (the forward records
+    its state at every segment end, the backward walks the segments in
+    parallel from those states): image, normal map and gradients against the
+    oracle."""
+    p = Params(s=s, tile=16, pure=pure, normals=True, blend_segment=seg)
+    cam = sphere16.cams[0]
+    up0 = tuple(synth.upstream_grads(21, [cam])[0])
+    up0 = up0 + (np.random.default_rng(22).normal(size=(3, cam.height, cam.width))
+                 .astype(np.float32),)
+    orc0 = oracle_run(sphere16, cam, p)
+    up = masked_upstream(up0, orc0["amb"])
+    orc = oracle_run(sphere16, cam, p, upstream=up)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up], lists=True)
+    assert int(np.diff(gpu["lists"]["ranges"], axis=1).max()) > 4 * seg
+    _check_view(gpu["views"][0], orc0, f"split{seg} s{s}")
+    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"split{seg} {name}: rel err {err:.3e}"
+
+
 def test_resort_window_torus64(torus64):
     p = Params(s=175.0, tile=16, resort_window=5)
     cam = torus64.cams[0]
