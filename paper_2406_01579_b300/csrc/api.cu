@@ -260,7 +260,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.max_pp_chunks = max_pp;
   H.sort_blocks = B.sort_blocks;
   H.max_passes = (32 + B.tile_bits + RADIX_BITS - 1) / RADIX_BITS;
-  H.range_blocks = 2 * sm_count();
+  H.range_blocks = 16 * sm_count();
   H.total_tiles = tiles;
   H.tile = pr.tile;
   H.window = pr.resort_window;

@@ -76,10 +76,14 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __r
   const long long k1 = min(k0 + PF_CHUNK, S.K);
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float sv = B->s, thr = B->prefilter_thresh;
+  // alpha_max <= sigmoid(-s f_min) < T_f once f_min > ln(1/T_f - 1)/s: such a
+  // tet (most of the grid, away from the surface) needs no exponentials
+  const float fcut = (thr > 0.f && thr < 1.f) ? logf(1.f / thr - 1.f) / sv : __int_as_float(0x7f800000);
   const unsigned N = (unsigned)S.N;
   unsigned char* flags = B->pf_flags + S.flag_off;
   int cnt = 0;
   bool bad = false;
+#pragma unroll 4
   for (long long k = k0 + threadIdx.x; k < k1; k += PF_THREADS) {
     const int4 t = __ldg(&S.T[k]);
     unsigned char keep = 0;
@@ -92,8 +96,10 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __r
         const float fmx = fmaxf(fmaxf(fa, fb), fmaxf(fc, fd));
         const float fmn = fminf(fminf(fa, fb), fminf(fc, fd));
         // Eq. 1 at (f_max, f_min): -expm1(-s (fmax - fmin)) * sigmoid(-s fmin)
-        const float amax = (fmx > fmn) ? -expm1f(-sv * (fmx - fmn)) / (1.f + expf(sv * fmn)) : 0.f;
-        keep = (amax >= thr) ? 1 : 0;
+        if (fmx > fmn && fmn <= fcut) {
+          const float amax = -expm1f(-sv * (fmx - fmn)) / (1.f + expf(sv * fmn));
+          keep = (amax >= thr) ? 1 : 0;
+        }
       }
     } else {
       bad = true;
@@ -297,7 +303,7 @@ int launch_fit_grid(const float* V_in, long long N, const float lo[3], const flo
 // ---------------------------------------------------------------------------
 // K2: per-view preprocess.  grid (max_pp_chunks, n_views)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PP_THREADS) k_preprocess(const Batch* __restrict__ B) {
+__global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
   const int v = blockIdx.y;
   const ViewD& vw = B->vw[v];
   const int chunk = blockIdx.x;

@@ -900,7 +900,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       if (nrm) gq[0] = z4;
       gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
       dnw = dnw + f3(g0.x, g0.y, g0.z);
-      if (!loaded) { load_tet(S, tet, in); loaded = true; }
+      if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
       Geo G;
       tet_geometry(vw, sv, in, G);
       if (!G.visible) continue;
@@ -966,7 +966,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
     }
     if (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f) {
-      if (!loaded) { load_tet(S, tet, in); loaded = true; }
+      if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
       TetGrad TG;
       tet_grad(in.v, in.f, TG);
       float ih, sg;

@@ -286,6 +286,8 @@ __device__ __forceinline__ float3 tet_normal_adjoint(float3 n, float inv_h, floa
   return (sg * inv_h) * (dn - dot3(n, dn) * n);
 }
 
+// The tet's vertices, SDF values and (when COLOURS) vertex colours.
+template <bool COLOURS = true>
 __device__ __forceinline__ void load_tet(const SceneD& S, int tet, TetIn& in) {
   const int4 t = __ldg(&S.T[tet]);
   const int id[4] = {t.x, t.y, t.z, t.w};
@@ -294,8 +296,10 @@ __device__ __forceinline__ void load_tet(const SceneD& S, int tet, TetIn& in) {
     const float* v = S.V + 3ll * id[j];
     in.v[j] = f3(__ldg(v), __ldg(v + 1), __ldg(v + 2));
     in.f[j] = __ldg(S.f + id[j]);
-    const float* c = S.rgb + 3ll * id[j];
-    in.c[j] = f3(__ldg(c), __ldg(c + 1), __ldg(c + 2));
+    if constexpr (COLOURS) {
+      const float* c = S.rgb + 3ll * id[j];
+      in.c[j] = f3(__ldg(c), __ldg(c + 1), __ldg(c + 2));
+    }
   }
 }
 
