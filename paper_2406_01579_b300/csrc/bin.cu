@@ -608,7 +608,7 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
 // segment end, and the backward walks the segments in parallel from those
 // states (one warp per 8x4 block walking a long list back to front would
 // otherwise bound its duration).  Units (tile, segment) are ordered by
-// decreasing length (bucketed by bit length), so the longest start first.
+// decreasing work (bucketed by bit length), so the longest start first.
 __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __restrict__ B) {
   __shared__ int cnt[33], off[33];
   __shared__ int nseg_total;
@@ -630,8 +630,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __
       }
     }
     B->tseg[t] = make_int2(base, nseg);
-    const int w = (nseg > 1) ? L : len;
-    atomicAdd(&cnt[w > 0 ? 32 - __clz(w) : 0], nseg);
+    // segment 0 carries the forward's walk of the whole list: ordered by the
+    // list length; the later segments by the segment length
+    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], 1);
+    if (nseg > 1) atomicAdd(&cnt[32 - __clz(L)], nseg - 1);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -643,9 +645,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __
   for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
     const int2 r = B->ranges[t];
     const int2 ts = B->tseg[t];
-    const int w = (ts.y > 1) ? L : (r.y - r.x);
-    const int pos = atomicAdd(&off[w > 0 ? 32 - __clz(w) : 0], ts.y);
-    for (int j = 0; j < ts.y; ++j) B->worklist[pos + j] = make_int2(t, j);
+    const int len = r.y - r.x;
+    B->worklist[atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], 1)] = make_int2(t, 0);
+    if (ts.y > 1) {
+      const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
+      for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
+    }
   }
 }
 

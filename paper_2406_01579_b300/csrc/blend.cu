@@ -204,20 +204,27 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
       }
       __syncwarp();
       const int cnt = __popc(m);
-      for (int k = 0; k < cnt; ++k) {
-        if (!S.done) {
+      // candidates in pairs: both chords and opacities are evaluated branch
+      // free back to back (independent, so their latencies overlap), then
+      // composited in order
+      for (int k0 = 0; k0 < cnt; k0 += 2) {
+        float av[2];
+        bool hv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = min(k0 + u, cnt - 1);   // past the end: evaluated again, masked
           const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
-          if (ch.hit) {
+          const Opacity o = opacity_eval(st[4][k], ch);
+          hv[u] = ch.hit && (k0 + u < cnt);
+          av[u] = pure ? o.alpha : fminf(o.alpha, cap);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = k0 + u;
+          if (hv[u] && !S.done) {
             ++S.nfrag;
-            const Opacity o = opacity_eval(st[4][k], ch);
-            float a = o.alpha;
-            bool use = true;
-            if (!pure) {
-              a = fminf(a, cap);
-              use = a >= skip;
-            } else {
-              use = a > 0.f;
-            }
+            const float a = av[u];
+            const bool use = pure ? (a > 0.f) : (a >= skip);
             if (use) {
               const float Tn = __fmul_rn(S.T, __fsub_rn(1.f, a));
               if (!pure && Tn < eps) {
