@@ -36,6 +36,20 @@ UNIT = "Mpixel/s"
 FWD_FLOP_PER_FRAG = 48
 BWD_FLOP_PER_FRAG = 150
 
+# DRAM bytes (read + write) per launch of the blend kernels on this workload,
+# from one ncu capture (profiles/blend_spheres128_4x512.md), keyed by the
+# sha256 prefix of the kernel source they were taken on: a changed kernel
+# reports no traffic until it is captured again.
+KERNEL_TRAFFIC = {
+    "f03d76669c909381": {"blend_fwd": 194834944, "blend_bwd": 241210112},
+}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2406_01579_b300", "csrc", "blend.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -51,6 +65,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the normal-map step and the geometry-term timings")
     ap.add_argument("--workload", default="spheres128", choices=["spheres128", "batched", "serve"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
@@ -317,6 +333,9 @@ def run_ours(a, rank, world):
         res["plain"] = pixels_per_step * ns / tp / 1e6
         del plains
 
+    if not a.no_extras and rank == 0:
+        res["extras"] = extras(a, st, sc, params, ups, dev, barrier)
+
     # end to end through the public API with host buffers
     if not a.no_e2e:
         hV = torch.from_numpy(sc.V).pin_memory()
@@ -364,6 +383,87 @@ def run_ours(a, rank, world):
     if dist is not None:
         dist.barrier()
     return res
+
+
+def extras(a, st, sc, params, ups, dev, barrier):
+    """Timings beside the headline step on the same 128^3 grid: the step with
+    the Eq. 2 normal map as a fourth channel, and the geometry terms (unique
+    edges, Sec. 4.2 regularizers with gradients, Marching Tetrahedra, the
+    App. B.1 coarse-to-fine bounds and refit)."""
+    import ctypes
+    import dataclasses
+
+    import torch
+
+    from paper_2406_01579_b300 import Rasterizer, _lib, fit_grid
+    from paper_2406_01579_b300.geometry import Regularizers, tet_edges
+
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+
+    def timed(fn, n):
+        for _ in range(2):
+            fn()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / n
+
+    # the step with the normal map (upstream dL/dnormal ~ N(0, 1))
+    rn = Rasterizer([st], [(c, 0) for c in sc.cams], dataclasses.replace(params, normals=True),
+                    device=dev)
+    rn.forward()
+    rn.shrink_to_fit(1.15)
+    on = rn._outputs()
+    g = np.random.default_rng(7)
+    upn = [torch.from_numpy(np.concatenate([u[i].ravel() for u in ups])).to(dev) for i in range(3)]
+    upn.append(torch.from_numpy(g.normal(size=3 * rn.total_pixels).astype(np.float32)).to(dev))
+    gr = [(torch.empty_like(st.V), torch.empty_like(st.f), torch.empty_like(st.rgb))]
+    ms = timed(lambda: rn.step(on, upn, gr), max(3, a.steps // 2))
+    out["normals_step_mpix_s"] = rn.total_pixels / (ms / 1e3) / 1e6
+    del rn, on
+    # unique edges (topology, once per grid) and the regularizers
+    N, K = st.V.shape[0], st.T.shape[0]
+    out["edges_ms"] = timed(lambda: tet_edges(st.T, N), 2)
+    E = tet_edges(st.T, N)
+    reg = Regularizers(N, dev)
+    dV, df = torch.empty_like(st.V), torch.empty_like(st.f)
+    out["regularizers_ms"] = timed(lambda: reg(st.V, st.T, st.f, E, 1.0, 1.0, grads=(dV, df)), 5)
+    out["n_edges"] = int(E.shape[0])
+    # Marching Tetrahedra: outputs sized by a first call, then the timed calls
+    L = _lib.load()
+    nb = ctypes.c_size_t(0)
+    _lib.check(L.tts_marching_tets_workspace_size(K, E.shape[0], ctypes.byref(nb)))
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device=dev)
+    counts = torch.zeros(2, dtype=torch.int64, device=dev)
+    dummy = torch.empty(3, dtype=torch.float32, device=dev)
+    dummyi = torch.empty(3, dtype=torch.int32, device=dev)
+    args = (st.V.data_ptr(), st.T.data_ptr(), st.f.data_ptr(), N, K, E.data_ptr(), E.shape[0])
+    _lib.check(L.tts_marching_tets(*args, dummy.data_ptr(), None, 0, dummyi.data_ptr(), 0,
+                                   counts.data_ptr(), ws.data_ptr(), ws.numel(), stream.cuda_stream))
+    nv, nt = (int(x) for x in counts.cpu())
+    verts = torch.empty((nv, 3), dtype=torch.float32, device=dev)
+    tris = torch.empty((nt, 3), dtype=torch.int32, device=dev)
+
+    def mt():
+        _lib.check(L.tts_marching_tets(*args, verts.data_ptr(), None, nv, tris.data_ptr(), nt,
+                                       counts.data_ptr(), ws.data_ptr(), ws.numel(),
+                                       stream.cuda_stream))
+    out["marching_tets_ms"] = timed(mt, 5)
+    out["mesh"] = {"vertices": nv, "triangles": nt}
+    # coarse-to-fine pre-filter: bounds of the first round's survivors, refit
+    rb = Rasterizer([st], [(sc.cams[0], 0)], params, device=dev)
+    rb.prepare()
+    V2 = torch.empty_like(st.V)
+    out["coarse_to_fine_ms"] = timed(
+        lambda: fit_grid(st.V, [-1.0] * 3, [1.0] * 3, rb.survivor_bounds()[0], 0.05, out=V2), 5)
+    del rb
+    return out
 
 
 def resident_scenes(rng, n_list, dev):
@@ -587,8 +687,9 @@ def main():
              "blend_bwd": res["nfrag"] * BWD_FLOP_PER_FRAG}
     rk = dom if dom in flops else "blend_bwd"
     achieved = flops[rk] / (launch_s[rk] / 1e3) / 1e12
+    traffic = KERNEL_TRAFFIC.get(kernel_source_hash(), {}).get(rk)
     roofline = {"kernel": rk, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
     out = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
@@ -611,6 +712,8 @@ def main():
         "mtet_per_s": 12582912 * a.steps / res["elapsed"] / 1e6,
         "clocks": res["clocks"],
     }
+    if "extras" in res:
+        out["extras"] = res["extras"]
     if "e2e" in res:
         out["e2e"] = res["e2e"]
     if not a.no_cpu_baseline:
