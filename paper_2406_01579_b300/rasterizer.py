@@ -111,8 +111,12 @@ class Rasterizer:
 
     def __init__(self, scenes: Sequence[SceneTensors], views: Sequence, params: Params,
                  key_capacity: int | None = None, surv_capacity: Sequence[int] | None = None,
-                 device=None):
+                 device=None, workspace: torch.Tensor | None = None):
+        """``workspace``: an optional uint8 device buffer to use (its leading
+        bytes) when it is large enough, or a callable that returns one for a
+        byte count, instead of allocating one."""
         self.lib = _lib.load()
+        self._ext_ws = workspace
         self.params = params
         self.device = torch.device(device) if device is not None else scenes[0].V.device
         self.views = [(c, int(s)) for c, s in views]
@@ -174,7 +178,11 @@ class Rasterizer:
     def _alloc(self):
         self.ws = None
         nbytes = self.workspace_bytes()
-        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        ext = self._ext_ws(nbytes) if callable(self._ext_ws) else self._ext_ws
+        if ext is not None and ext.numel() >= nbytes and ext.data_ptr() % 256 == 0:
+            self.ws = ext[:nbytes]
+        else:
+            self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.ws_bytes = nbytes
         b = self.batch()
         check(self.lib.tts_workspace_init(ctypes.byref(b), _stream_ptr()), "tts_workspace_init")

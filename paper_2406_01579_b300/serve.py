@@ -8,7 +8,11 @@ pre-filter per scene entry, one sort, one blend queue for all the views) and
 launched asynchronously on that slot's stream, so batches overlap on the
 device.  Gradient requests get their own scene entry, hence their own
 gradient buffers; forward-only requests of the same scene share one entry.
-Images come back to pinned host memory; gradients stay on the device.
+Each stream slot keeps its workspace, output and pinned host staging buffers
+across batches (grown when a batch needs more), so the steady state
+allocates no device or pinned memory per batch.  Images come back through
+the slot's pinned buffer into host tensors of their own; gradients stay on
+the device.
 """
 
 from __future__ import annotations
@@ -44,7 +48,7 @@ class Request:
 @dataclasses.dataclass
 class Result:
     rid: int
-    image: torch.Tensor      # (3, H, W) view of a pinned host buffer
+    image: torch.Tensor      # (3, H, W) host
     alpha: torch.Tensor      # (H, W)
     depth: torch.Tensor      # (H, W)
     grads: tuple | None
@@ -53,17 +57,42 @@ class Result:
     batch_views: int
 
 
+class _Slot:
+    """A stream with buffers that persist across the batches it runs."""
+
+    def __init__(self, device):
+        self.stream = torch.cuda.Stream(device=device)
+        self.device = device
+        self.ws = None          # uint8 device workspace
+        self.dev = None         # float32 device outputs / upstream gradients
+        self.host = None        # float32 pinned host staging
+
+    def workspace(self, ws_bytes: int):
+        """The slot's workspace, grown (x1.5) when too small."""
+        if self.ws is None or self.ws.numel() < ws_bytes:
+            self.ws = None
+            self.ws = torch.empty(int(ws_bytes * 1.5) + 4096, dtype=torch.uint8, device=self.device)
+        return self.ws
+
+    def buffers(self, n_float: int):
+        """Device and pinned host float buffers of at least n_float, grown
+        (x1.5) when too small."""
+        if self.dev is None or self.dev.numel() < n_float:
+            self.dev = torch.empty(int(n_float * 1.5) + 4096, dtype=torch.float32,
+                                   device=self.device)
+            self.host = torch.empty(self.dev.numel(), dtype=torch.float32, pin_memory=True)
+        return self.dev, self.host
+
+
 class _Inflight:
-    def __init__(self, reqs, raster, out_host, out_dev, grads, event, nbytes, stream, keep):
+    def __init__(self, reqs, raster, slot, n_out, grads, event, nbytes):
         self.reqs = reqs
         self.raster = raster
-        self.out_host = out_host
-        self.out_dev = out_dev
+        self.slot = slot
+        self.n_out = n_out      # floats of image + alpha + depth at the slot's buffers' start
         self.grads = grads
         self.event = event
         self.nbytes = nbytes
-        self.stream = stream
-        self.keep = keep
 
 
 class Server:
@@ -75,21 +104,29 @@ class Server:
         self.device = torch.device(device) if device is not None else self.scenes[0].V.device
         self.budget = float(hbm_budget)
         self.max_views = int(max_views)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.slots = [_Slot(self.device) for _ in range(streams)]
         self.surv = []
-        self.keys_per_px = []
+        self.key_scale = []     # per scene: c in keys ~ surv (1 + c res / tile)^2
+        self.key_margin = []    # per scene: safety factor, doubled after an overflow
         self._register(ref_res)
 
     def _register(self, res: int):
-        """Survivors of each resident scene and keys per pixel at a reference
-        view (capacity estimates)."""
+        """Survivors of each resident scene and its keys at a reference view
+        (capacity estimates).  A tet whose bbox spans w pixels overlaps about
+        (1 + w / tile)^2 tiles and w grows with the image size, so the keys of
+        a view of size res are modelled as surv (1 + c res / tile)^2 with c
+        fitted at the reference view."""
         cam = _camera.orbit(30.0, 20.0, res, res)
+        T = float(self.params.tile)
         for sc in self.scenes:
             r = Rasterizer([sc], [(cam, 0)], dataclasses.replace(self.params, forward_only=True))
             r.forward()
             info = r.info()
-            self.surv.append(int(info.n_surv[0]))
-            self.keys_per_px.append(max(1.0, info.n_keys / float(res * res)))
+            surv = max(1, int(info.n_surv[0]))
+            self.surv.append(surv)
+            ratio = max(1.0, info.n_keys / float(surv))
+            self.key_scale.append((ratio ** 0.5 - 1.0) * T / res)
+            self.key_margin.append(1.5)
             del r
 
     # -- batching ------------------------------------------------------------
@@ -106,7 +143,9 @@ class Server:
         px = 0
         for (cam, e), q in zip(views, reqs):
             npx = int(cam.width) * int(cam.height)
-            keys += 2.0 * self.keys_per_px[q.scene] * npx
+            res = max(int(cam.width), int(cam.height))
+            grow = (1.0 + self.key_scale[q.scene] * res / float(self.params.tile)) ** 2
+            keys += self.key_margin[q.scene] * self.surv[q.scene] * grow
             slots += surv_cap[e]
             px += npx
         key_cap = int(keys) + 65536
@@ -114,55 +153,55 @@ class Server:
             key_cap * KEY_BYTES + px * PIXEL_BYTES
         return scenes, views, surv_cap, key_cap, nbytes
 
-    def _launch(self, reqs, want_grad, stream) -> _Inflight:
+    def _launch(self, reqs, want_grad, slot: _Slot) -> _Inflight:
         scenes, views, surv_cap, key_cap, nbytes = self._estimate(reqs, want_grad)
         p = dataclasses.replace(self.params, forward_only=not want_grad)
-        keep = []
+        stream = slot.stream
         with torch.cuda.stream(stream):
             r = Rasterizer([self.scenes[s] for s in scenes], views, p, key_capacity=key_cap,
-                           surv_capacity=surv_cap, device=self.device)
-            out = r._outputs()
+                           surv_capacity=surv_cap, device=self.device, workspace=slot.workspace)
+            P = r.total_pixels
+            n_out = 5 * P
+            dev, host = slot.buffers(2 * n_out if want_grad else n_out)
+            out = (dev[:3 * P], dev[3 * P:4 * P], dev[4 * P:5 * P])
             grads = None
             if want_grad:
-                gi = torch.empty(3 * r.total_pixels, dtype=torch.float32, device=self.device)
-                ga = torch.empty(r.total_pixels, dtype=torch.float32, device=self.device)
-                gd = torch.empty(r.total_pixels, dtype=torch.float32, device=self.device)
+                # upstream gradients staged through the slot's pinned buffer
+                hu = host[n_out:2 * n_out]
                 for q, off in zip(reqs, r.pix_off):
                     H, W = int(q.camera.height), int(q.camera.width)
-                    hi, ha, hd = (torch.from_numpy(np.ascontiguousarray(x, np.float32)).pin_memory()
+                    ui, ua, ud = (torch.from_numpy(np.ascontiguousarray(x, np.float32)).view(-1)
                                   for x in q.upstream)
-                    keep += [hi, ha, hd]
-                    gi[3 * off:3 * off + 3 * H * W].copy_(hi.view(-1), non_blocking=True)
-                    ga[off:off + H * W].copy_(ha.view(-1), non_blocking=True)
-                    gd[off:off + H * W].copy_(hd.view(-1), non_blocking=True)
+                    hu[3 * off:3 * off + 3 * H * W].copy_(ui)
+                    hu[3 * P + off:3 * P + off + H * W].copy_(ua)
+                    hu[4 * P + off:4 * P + off + H * W].copy_(ud)
+                du = dev[n_out:2 * n_out]
+                du.copy_(hu, non_blocking=True)
                 grads = [(torch.empty_like(self.scenes[s].V), torch.empty_like(self.scenes[s].f),
                           torch.empty_like(self.scenes[s].rgb)) for s in scenes]
-                r.step(out, (gi, ga, gd), grads)
-                keep += [gi, ga, gd]
+                r.step(out, (du[:3 * P], du[3 * P:4 * P], du[4 * P:5 * P]), grads)
             else:
                 r.prepare()
                 r.forward_raw(out)
-            host = tuple(torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in out)
-            for h, d in zip(host, out):
-                h.copy_(d, non_blocking=True)
+            host[:n_out].copy_(dev[:n_out], non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(stream)
-        return _Inflight(reqs, r, host, out, grads, ev, nbytes, stream, keep)
+        return _Inflight(reqs, r, slot, n_out, grads, ev, nbytes)
 
     def _finish(self, b: _Inflight, now: float, results: dict):
-        with torch.cuda.stream(b.stream):
+        with torch.cuda.stream(b.slot.stream):
             info = b.raster.info()   # the batch is complete: this does not wait
         if info.status & (TTS_STATUS_KEY_OVERFLOW | TTS_STATUS_SURV_OVERFLOW):
             return False         # capacity estimate too small: caller re-runs the batch
-        img, alpha, depth = b.out_host
+        P = b.raster.total_pixels
+        host = b.slot.host
         for i, (q, off) in enumerate(zip(b.reqs, b.raster.pix_off)):
             H, W = int(q.camera.height), int(q.camera.width)
-            g = None
-            if b.grads is not None:
-                g = b.grads[i]
+            g = b.grads[i] if b.grads is not None else None
             results[q.rid] = Result(
-                q.rid, img[3 * off:3 * off + 3 * H * W].view(3, H, W),
-                alpha[off:off + H * W].view(H, W), depth[off:off + H * W].view(H, W), g, now,
+                q.rid, host[3 * off:3 * off + 3 * H * W].clone().view(3, H, W),
+                host[3 * P + off:3 * P + off + H * W].clone().view(H, W),
+                host[4 * P + off:4 * P + off + H * W].clone().view(H, W), g, now,
                 now - q.arrival, len(b.reqs))
         return True
 
@@ -174,9 +213,10 @@ class Server:
         ready = collections.deque()
         inflight: list[_Inflight] = []
         results: dict = {}
-        free = list(range(len(self.streams)))
+        free = list(range(len(self.slots)))
         busy_bytes = 0.0
         n_batches = 0
+        retries = 0
         max_inflight = 0
         t0 = time.perf_counter()
         clock = (lambda: time.perf_counter() - t0) if realtime else (lambda: float("inf"))
@@ -190,11 +230,15 @@ class Server:
                     t = time.perf_counter() - t0
                     inflight.remove(b)
                     busy_bytes -= b.nbytes
-                    free.append(self.streams.index(b.stream))
+                    free.append(self.slots.index(b.slot))
                     if not self._finish(b, t, results):
+                        # a capacity estimate was too small: grow the
+                        # estimates of this batch's scenes and run it again
                         for q in reversed(b.reqs):
                             ready.appendleft(q)
-                        self.keys_per_px = [2.0 * k for k in self.keys_per_px]
+                        for sc in {q.scene for q in b.reqs}:
+                            self.key_margin[sc] *= 2.0
+                        retries += 1
                     progressed = True
             while ready and free:
                 kind = ready[0].want_grad
@@ -213,7 +257,7 @@ class Server:
                         ready.appendleft(q)
                     break
                 si = free.pop(0)
-                b = self._launch(batch, kind, self.streams[si])
+                b = self._launch(batch, kind, self.slots[si])
                 busy_bytes += b.nbytes
                 inflight.append(b)
                 n_batches += 1
@@ -228,7 +272,8 @@ class Server:
         lat = np.array([r.latency for r in results.values()]) * 1e3
         px = sum(int(q.camera.width) * int(q.camera.height) for q in requests)
         first = min(q.arrival for q in requests) if requests else 0.0
-        stats = {"requests": len(requests), "batches": n_batches, "max_inflight": max_inflight,
+        stats = {"requests": len(requests), "batches": n_batches, "retries": retries,
+                 "max_inflight": max_inflight,
                  "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                  "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                  "mpix_s": px / max(t_end - first, 1e-9) / 1e6, "wall_s": t_end}
