@@ -129,12 +129,6 @@ struct FwdState {
   bool done;
 };
 
-// Walks the list entries [lo, hi) of the warp's tile front to back for the
-// lanes that are not done: the entries whose bbox meets a live pixel are
-// staged (ballot) in the warp's shared-memory slice and blended in order
-// (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions).  With `stop` a pixel
-// stops before the fragment that would take T below eps.  `last` counts list
-// entries from rg_x.
 // Final per-pixel outputs of the forward.
 template <bool NRM>
 __device__ __forceinline__ void store_pixel(const Batch* __restrict__ B, const ViewD& vw,
@@ -204,18 +198,24 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
       }
       __syncwarp();
       const int cnt = __popc(m);
-      // candidates in pairs: both chords and opacities are evaluated branch
-      // free back to back (independent, so their latencies overlap), then
-      // composited in order
+      // candidates in pairs: both chords, then (when either meets a live
+      // lane) both opacities are evaluated branch free back to back
+      // (independent, so their latencies overlap), then composited in order
       for (int k0 = 0; k0 < cnt; k0 += 2) {
         float av[2];
         bool hv[2];
+        Chord chs[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int k = min(k0 + u, cnt - 1);   // past the end: evaluated again, masked
-          const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
-          const Opacity o = opacity_eval(st[4][k], ch);
-          hv[u] = ch.hit && (k0 + u < cnt);
+          chs[u] = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
+          hv[u] = chs[u].hit && (k0 + u < cnt);
+        }
+        if (!__any_sync(FULL, (hv[0] || hv[1]) && !S.done)) continue;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = min(k0 + u, cnt - 1);
+          const Opacity o = opacity_eval(st[4][k], chs[u]);
           av[u] = pure ? o.alpha : fminf(o.alpha, cap);
         }
 #pragma unroll
