@@ -206,7 +206,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   // checkpoint of 32 B per pixel and segment
   B.seg_cap = B.seg_len > 0 ? (int)std::min<long long>(2 * cap / B.seg_len + 1, 0x3fffffffLL) : 0;
   const long long tt = (long long)pr.tile * pr.tile;
-  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + B.seg_cap));
+  // units: one per tile, one per later segment, one more per split tile
+  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + 2 * (size_t)B.seg_cap));
   const size_t o_tseg = take(sizeof(int2) * tiles);
   const size_t o_psa = take(sizeof(float4) * B.seg_cap * tt);
   const size_t o_psb = take(sizeof(float4) * B.seg_cap * tt);

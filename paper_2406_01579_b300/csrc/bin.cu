@@ -602,9 +602,10 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
   }
 }
 
-// Work list for the persistent blend kernels.  A tile whose list is longer
-// than seg_len entries is split into segments of seg_len entries: the forward
-// walks the whole list (segment 0's unit) and records its state at each
+// Work list for the persistent blend kernels, units (tile, segment | part << 24).
+// A tile whose list is longer than seg_len entries is split into segments of
+// seg_len entries: the forward walks the whole list (the segment-0 units,
+// parts 0 and 1 covering its 4x4 blocks) and records its state at each
 // segment end, and the backward walks the segments in parallel from those
 // states (one warp per 8x4 block walking a long list back to front would
 // otherwise bound its duration).  Units (tile, segment) are ordered by
@@ -630,9 +631,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __
       }
     }
     B->tseg[t] = make_int2(base, nseg);
-    // segment 0 carries the forward's walk of the whole list: ordered by the
-    // list length; the later segments by the segment length
-    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], 1);
+    // segment 0 carries the forward's walk of the whole list (two parts for
+    // a split list: its 4x4 blocks, two lanes per pixel): ordered by the list
+    // length; the later segments (backward only) by the segment length
+    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], nseg > 1 ? 2 : 1);
     if (nseg > 1) atomicAdd(&cnt[32 - __clz(L)], nseg - 1);
   }
   __syncthreads();
@@ -646,8 +648,10 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __
     const int2 r = B->ranges[t];
     const int2 ts = B->tseg[t];
     const int len = r.y - r.x;
-    B->worklist[atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], 1)] = make_int2(t, 0);
+    const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], ts.y > 1 ? 2 : 1);
+    B->worklist[pos0] = make_int2(t, 0);
     if (ts.y > 1) {
+      B->worklist[pos0 + 1] = make_int2(t, 1 << 24);   // part 1: forward only
       const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
       for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
     }

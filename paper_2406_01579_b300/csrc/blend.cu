@@ -42,6 +42,8 @@ struct WarpBlock {
   int gt;
   int seg;                    // segment of a split tile list (0 otherwise)
   int sb;                     // 8x4 block within the tile
+  int part;                   // forward part of a long list (4x4 blocks part*SB ..)
+  int tpix;                   // the lane's pixel within the tile, row-major
   int px, py;
   bool inimg;
   float fpx, fpy;
@@ -67,7 +69,7 @@ struct WarpBlock {
   }
 };
 
-// The warp block (tile gt, 8x4 block sb, list segment seg).
+// The warp block (tile gt, 8x4 block sb, list segment seg), lanes row-major.
 template <int TILE>
 __device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B, int gt, int seg,
                                                      int sb, WarpBlock& wb) {
@@ -75,11 +77,14 @@ __device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B
   wb.gt = gt;
   wb.seg = seg;
   wb.sb = sb;
+  wb.part = 0;
   const ViewD& vw = B->vw[find_view(B, wb.gt)];
   const int lt = wb.gt - vw.tile_base;
   const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
-  const int bx = txi * TILE + (sb % SBX) * 8, by = tyi * TILE + (sb / SBX) * 4;
+  const int ox = (sb % SBX) * 8, oy = (sb / SBX) * 4;
   const int lane = threadIdx.x & 31;
+  wb.tpix = (oy + (lane >> 3)) * TILE + ox + (lane & 7);
+  const int bx = txi * TILE + ox, by = tyi * TILE + oy;
   wb.px = bx + (lane & 7);
   wb.py = by + (lane >> 3);
   wb.inimg = (wb.px < vw.W) & (wb.py < vw.H);
@@ -92,13 +97,47 @@ __device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B
   return vw;
 }
 
+// A 4x4 pixel block (b4 in tile-local row-major order of 4x4 blocks) with two
+// lanes per pixel: lane = 2 * (4 * row + column) + sub.
+template <int TILE>
+__device__ __forceinline__ const ViewD& decode_block4(const Batch* __restrict__ B, int gt, int b4,
+                                                      WarpBlock& wb) {
+  constexpr int BX = TILE / 4;
+  wb.gt = gt;
+  wb.seg = 0;
+  wb.sb = 0;
+  wb.part = 1;
+  const ViewD& vw = B->vw[find_view(B, wb.gt)];
+  const int lt = wb.gt - vw.tile_base;
+  const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
+  const int ox = (b4 % BX) * 4, oy = (b4 / BX) * 4;
+  const int pix = (threadIdx.x & 31) >> 1;
+  wb.tpix = (oy + (pix >> 2)) * TILE + ox + (pix & 3);
+  const int bx = txi * TILE + ox, by = tyi * TILE + oy;
+  wb.px = bx + (pix & 3);
+  wb.py = by + (pix >> 2);
+  wb.inimg = (wb.px < vw.W) & (wb.py < vw.H);
+  wb.fpx = (float)wb.px + 0.5f;
+  wb.fpy = (float)wb.py + 0.5f;
+  wb.wx0 = (float)bx + 0.5f;
+  wb.wx1 = wb.wx0 + 3.f;
+  wb.wy0 = (float)by + 0.5f;
+  wb.wy1 = wb.wy0 + 3.f;
+  return vw;
+}
+
 // Work item -> warp block: item / SB indexes the (tile, segment) unit list.
+// Units are (tile, segment | part << 24): segment > 0 units are backward
+// work only, part > 0 units forward work only (the further 4x4 blocks of a
+// long list).
 template <int TILE>
 __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
                                                     WarpBlock& wb) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
   const int2 u = B->worklist[item / SB];
-  return decode_block<TILE>(B, u.x, u.y, item - (item / SB) * SB, wb);
+  const ViewD& vw = decode_block<TILE>(B, u.x, u.y & 0xffffff, item - (item / SB) * SB, wb);
+  wb.part = u.y >> 24;
+  return vw;
 }
 
 // Per-slot normals of a view's tile lists: the survivor normals of its scene
@@ -149,15 +188,66 @@ __device__ __forceinline__ void store_pixel(const Batch* __restrict__ B, const V
   if constexpr (NRM) store_normal(B, vw, p, normal, S.N0, S.N1, S.N2);
 }
 
+// Fragment codes handed between the lanes of a pixel: alpha' > 0 (blend),
+// FRAG_ZERO (blend with alpha' = 0), FRAG_SKIP (a chord, not blended), 0 (no
+// chord).
+constexpr float FRAG_ZERO = -2.f;
+constexpr float FRAG_SKIP = -1.f;
+
+// One fragment of the pixel's compositing (Eq. 2, 3DGS conventions), given
+// its code v: counts the chord, blends alpha' or stops the pixel.
+template <bool NRM>
+__device__ __forceinline__ void composite(float v, int k, int base, bool pure, float eps,
+                                          float4 (*st)[32], const int* sidx, FwdState& S) {
+  if (v == 0.f || S.done) return;
+  ++S.nfrag;
+  if (v == FRAG_SKIP) return;
+  const float a = fmaxf(v, 0.f);
+  const float Tn = __fmul_rn(S.T, __fsub_rn(1.f, a));
+  if (!pure && Tn < eps) {
+    S.done = true;
+    return;
+  }
+  const float4 q5 = st[5][k];
+  const float wgt = __fmul_rn(S.T, a);
+  S.C0 = __fmaf_rn(wgt, q5.y, S.C0);
+  S.C1 = __fmaf_rn(wgt, q5.z, S.C1);
+  S.C2 = __fmaf_rn(wgt, q5.w, S.C2);
+  S.D = __fmaf_rn(wgt, q5.x, S.D);
+  if constexpr (NRM) {
+    const float4 n = st[REC_Q][k];
+    S.N0 = __fmaf_rn(wgt, n.x, S.N0);
+    S.N1 = __fmaf_rn(wgt, n.y, S.N1);
+    S.N2 = __fmaf_rn(wgt, n.z, S.N2);
+  }
+  S.T = Tn;
+  S.last = base + sidx[k] + 1;
+}
+
+// Eq. 1 with the cap and skip decisions, as a fragment code.
+__device__ __forceinline__ float fragment_code(const float4& q4, const Chord& ch, bool pure,
+                                               float cap, float skip) {
+  const Opacity o = opacity_eval(q4, ch);
+  const float a = pure ? o.alpha : fminf(o.alpha, cap);
+  const bool use = pure ? (a > 0.f) : (a >= skip);
+  return use ? (a > 0.f ? a : FRAG_ZERO) : FRAG_SKIP;
+}
+
 // Walks the list entries [lo, hi) of the warp's tile front to back for the
 // lanes that are not done: the entries whose bbox meets a live pixel are
 // staged (ballot) in the warp's shared-memory slice and blended in order
 // (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions); a pixel stops before
-// the fragment that would take T below eps (not in PURE mode).  `last` counts
-// list entries from lo.  When the list is split into segments for the
-// backward (ts.y > 1), the state at the end of each segment is stored as the
-// walk passes it.
-template <bool NRM>
+// the fragment that would take T below eps (not in PURE mode).  Candidates
+// are taken in pairs.  LPP = 1 (an 8x4 block, one lane per pixel): each lane
+// evaluates both chords, then (when either meets a live lane) both
+// opacities, then composites the two in order.  LPP = 2 (a 4x4 block, two
+// lanes per pixel): each lane of a pixel evaluates one candidate of the
+// pair, the two exchange their fragment codes and both composite the pair
+// in order, which halves the chain a long list puts on one warp.  `last`
+// counts list entries from lo.  When the list is split into segments for
+// the backward (ts.y > 1), the state at the end of each segment is stored as
+// the walk passes it.
+template <bool NRM, int LPP>
 __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock wb,
                                          const unsigned* __restrict__ vals,
                                          const float4* __restrict__ rec,
@@ -165,6 +255,7 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
                                          int tt, bool pure, float cap, float skip, float eps,
                                          float4 (*st)[32], int* sidx, FwdState& S) {
   const int lane = threadIdx.x & 31;
+  const int sub = (LPP == 2) ? (lane & 1) : 0;
   const unsigned ltm = (1u << lane) - 1u;
   const int L = B->seg_len;
   const bool split = ts.y > 1;
@@ -174,8 +265,8 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
   float4 q0 = (idx < hi) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
   unsigned slot_n = (idx + 32 < hi) ? vals[idx + 32] : 0u;
   for (int g = lo; g < hi; g += 32) {
-    if (split && g > lo && (g - lo) % L == 0) {
-      const long long pi = ((long long)ts.x + (g - lo) / L - 1) * tt + wb.sb * 32 + lane;
+    if (split && g > lo && (g - lo) % L == 0 && sub == 0) {
+      const long long pi = ((long long)ts.x + (g - lo) / L - 1) * tt + wb.tpix;
       B->pseg_a[pi] = make_float4(S.T, S.C0, S.C1, S.C2);
       B->pseg_b[pi] = make_float4(S.D, S.N0, S.N1, S.N2);
     }
@@ -198,55 +289,27 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
       }
       __syncwarp();
       const int cnt = __popc(m);
-      // candidates in pairs: both chords, then (when either meets a live
-      // lane) both opacities are evaluated branch free back to back
-      // (independent, so their latencies overlap), then composited in order
+      const int base = g - lo;
       for (int k0 = 0; k0 < cnt; k0 += 2) {
-        float av[2];
-        bool hv[2];
-        Chord chs[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int k = min(k0 + u, cnt - 1);   // past the end: evaluated again, masked
-          chs[u] = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
-          hv[u] = chs[u].hit && (k0 + u < cnt);
-        }
-        if (!__any_sync(FULL, (hv[0] || hv[1]) && !S.done)) continue;
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int k = min(k0 + u, cnt - 1);
-          const Opacity o = opacity_eval(st[4][k], chs[u]);
-          av[u] = pure ? o.alpha : fminf(o.alpha, cap);
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int k = k0 + u;
-          if (hv[u] && !S.done) {
-            ++S.nfrag;
-            const float a = av[u];
-            const bool use = pure ? (a > 0.f) : (a >= skip);
-            if (use) {
-              const float Tn = __fmul_rn(S.T, __fsub_rn(1.f, a));
-              if (!pure && Tn < eps) {
-                S.done = true;
-              } else {
-                const float4 q5 = st[5][k];
-                const float wgt = __fmul_rn(S.T, a);
-                S.C0 = __fmaf_rn(wgt, q5.y, S.C0);
-                S.C1 = __fmaf_rn(wgt, q5.z, S.C1);
-                S.C2 = __fmaf_rn(wgt, q5.w, S.C2);
-                S.D = __fmaf_rn(wgt, q5.x, S.D);
-                if constexpr (NRM) {
-                  const float4 n = st[REC_Q][k];
-                  S.N0 = __fmaf_rn(wgt, n.x, S.N0);
-                  S.N1 = __fmaf_rn(wgt, n.y, S.N1);
-                  S.N2 = __fmaf_rn(wgt, n.z, S.N2);
-                }
-                S.T = Tn;
-                S.last = g - lo + sidx[k] + 1;
-              }
-            }
-          }
+        if constexpr (LPP == 1) {
+          const int ka = k0, kb = min(k0 + 1, cnt - 1);   // past the end: evaluated again, masked
+          const Chord cha = chord_eval(st[0][ka], st[1][ka], st[2][ka], st[3][ka], wb.fpx, wb.fpy);
+          const Chord chb = chord_eval(st[0][kb], st[1][kb], st[2][kb], st[3][kb], wb.fpx, wb.fpy);
+          const bool ha = cha.hit, hb = chb.hit && (k0 + 1 < cnt);
+          if (!__any_sync(FULL, (ha || hb) && !S.done)) continue;
+          const float va = fragment_code(st[4][ka], cha, pure, cap, skip);
+          const float vb = fragment_code(st[4][kb], chb, pure, cap, skip);
+          composite<NRM>(ha ? va : 0.f, ka, base, pure, eps, st, sidx, S);
+          composite<NRM>(hb ? vb : 0.f, kb, base, pure, eps, st, sidx, S);
+        } else {
+          const int k = min(k0 + sub, cnt - 1);
+          const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
+          const bool h = ch.hit && (k0 + sub < cnt);
+          if (!__any_sync(FULL, h && !S.done)) continue;
+          const float mine = h ? fragment_code(st[4][k], ch, pure, cap, skip) : 0.f;
+          const float other = __shfl_xor_sync(FULL, mine, 1);
+          composite<NRM>(sub ? other : mine, k0, base, pure, eps, st, sidx, S);
+          composite<NRM>(sub ? mine : other, min(k0 + 1, cnt - 1), base, pure, eps, st, sidx, S);
         }
         if (__all_sync(FULL, S.done)) break;
       }
@@ -282,16 +345,25 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
   const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
-    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    const ViewD* vwp = &decode_item<TILE>(B, item, wb);
     if (wb.seg > 0) continue;
+    const int2 ts = B->tseg[wb.gt];
+    const bool two = ts.y > 1;   // a long list: 4x4 blocks with two lanes per pixel
+    if (two) vwp = &decode_block4<TILE>(B, wb.gt, wb.part * SB + wb.sb, wb);
+    const ViewD& vw = *vwp;
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
-    const int2 ts = B->tseg[wb.gt];
     const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
     FwdState S = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, !wb.inimg};
-    fwd_walk<NRM>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
-                  st[wid], sidx[wid], S);
-    if (wb.inimg) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+    if (two) {
+      fwd_walk<NRM, 2>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
+                       st[wid], sidx[wid], S);
+      if (wb.inimg && (threadIdx.x & 1) == 0) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+    } else {
+      fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
+                       st[wid], sidx[wid], S);
+      if (wb.inimg) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+    }
   }
   queue_done(&c->work_fwd, &c->done_fwd);
 }
@@ -508,6 +580,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, item, wb);
+    if (wb.part > 0) continue;                 // forward-only unit
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;
     const long long p = (long long)wb.py * vw.W + wb.px;
@@ -542,7 +615,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         // normal at its end were stored by the forward; the suffix after it
         // is S = W - (gC.C + gD.D + gN.N at the end), W the same of the
         // final pixel
-        const long long pj = ((long long)ts.x + wb.seg) * (TILE * TILE) + wb.sb * 32 + lane;
+        const long long pj = ((long long)ts.x + wb.seg) * (TILE * TILE) + wb.tpix;
         const float4 a = __ldcg(B->pseg_a + pj);
         const float4 b4 = __ldcg(B->pseg_b + pj);
         float P = gC0 * a.y + gC1 * a.z + gC2 * a.w + gD * b4.x;
