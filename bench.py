@@ -38,10 +38,10 @@ BWD_FLOP_PER_FRAG = 150
 
 # DRAM bytes (read + write) per launch of the blend kernels on this workload,
 # from one ncu capture (profiles/blend_spheres128_4x512.md), keyed by the
-# sha256 prefix of the kernel source they were taken on: a changed kernel
-# reports no traffic until it is captured again.
+# sha256 prefix of the kernel source they were taken on and the tile size: a
+# changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "f03d76669c909381": {"blend_fwd": 194834944, "blend_bwd": 241210112},
+    "f03d76669c909381": {16: {"blend_fwd": 194834944, "blend_bwd": 241210112}},
 }
 
 
@@ -58,7 +58,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--s", type=float, default=175.0)
-    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="tile edge 8, 16 or 32; 0: picked by the library's autotuner on this batch")
+    ap.add_argument("--blend-segment", type=int, default=0,
+                    help="list entries per backward segment (0: library default)")
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--views", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -170,7 +173,14 @@ def run_ours(a, rank, world):
         rng = np.random.default_rng(1000 + rank)
         sc.cams = [synth.random_camera(rng, a.res, a.res) for _ in range(a.views)]
     st = SceneTensors(*(torch.from_numpy(x).to(dev) for x in (sc.V, sc.T, sc.f, sc.rgb)))
-    params = Params(s=a.s, tile=a.tile)
+    tune = None
+    if a.tile == 0:
+        from paper_2406_01579_b300.autotune import autotune_tile
+        best, times = autotune_tile([st], [(c, 0) for c in sc.cams],
+                                    Params(s=a.s, blend_segment=a.blend_segment), cache_path=None)
+        a.tile = best
+        tune = {str(k): round(v, 4) for k, v in times.items()}
+    params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment)
     r = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
     r.forward()
     r.shrink_to_fit(1.15)
@@ -255,6 +265,7 @@ def run_ours(a, rank, world):
     nfrag = int(r._ws_slice(Np.value, 4 * r.total_pixels, torch.int32).sum().item())
     lasts = int(r._ws_slice(Lp.value, 4 * r.total_pixels, torch.int32).sum().item())
     res = {
+        "autotune_ms": tune,
         "elapsed": elapsed, "value": value, "stage_ms": stage_ms, "launches": launches,
         "clocks": clocks, "nfrag": nfrag, "entries_walked": lasts, "n_keys": int(info.n_keys),
         "n_surv": int(info.n_surv[0]), "sort_passes": int(info.sort_passes),
@@ -699,7 +710,7 @@ def main():
              "blend_bwd": res["nfrag"] * BWD_FLOP_PER_FRAG}
     rk = dom if dom in flops else "blend_bwd"
     achieved = flops[rk] / (launch_s[rk] / 1e3) / 1e12
-    traffic = KERNEL_TRAFFIC.get(kernel_source_hash(), {}).get(rk)
+    traffic = KERNEL_TRAFFIC.get(kernel_source_hash(), {}).get(a.tile, {}).get(rk)
     roofline = {"kernel": rk, "bound": "alu", "achieved": achieved, "peak": alu_peak,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
                 "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
@@ -711,7 +722,8 @@ def main():
         "config": {"workload": workload_name(a), "global_views": a.views * world,
                    "l2": "inputs larger than L2 (tet indices 201 MB, per-step records "
                          f"{res['n_surv'] * a.views * 96 / 1e6:.0f} MB)",
-                   "parallelism": f"dp{world} (independent views per GPU)"},
+                   "parallelism": f"dp{world} (independent views per GPU)",
+                   "tile_autotune_ms_per_step": res.get("autotune_ms")},
         "roofline": roofline,
         "stage_ms": st, "dominant_stage": dom,
         "plain_path_mpix_s": res.get("plain"),

@@ -60,7 +60,7 @@ def _time_step(r: Rasterizer, with_backward: bool, reps: int) -> float:
 
 
 def autotune_tile(scenes, views, params: Params, candidates=(8, 16, 32), with_backward=True,
-                  reps: int = 3, cache_path: str | None = DEFAULT_CACHE):
+                  reps: int = 5, cache_path: str | None = DEFAULT_CACHE):
     """Returns (best tile, {tile: ms per step}).  Uses and updates the cache."""
     probe = Rasterizer(scenes, views, dataclasses.replace(params, tile=16))
     probe.forward()

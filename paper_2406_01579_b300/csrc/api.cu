@@ -33,7 +33,7 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-constexpr int kBlendSegment = 1024;   // default list entries per blend work unit
+constexpr int kBlendSegment = 256;    // default list entries per backward segment
 
 int bit_length(long long x) {
   int b = 0;
