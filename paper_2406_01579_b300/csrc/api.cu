@@ -199,7 +199,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_k1 = take(sizeof(unsigned long long) * cap);
   const size_t o_v0 = take(sizeof(unsigned) * cap);
   const size_t o_v1 = take(sizeof(unsigned) * cap);
-  const size_t o_hist = take(sizeof(unsigned) * RADIX * (B.sort_blocks + 1));
+  B.sort_tiles = (int)((cap + SORT_TILE - 1) / SORT_TILE);
+  const size_t o_ghist = take(sizeof(unsigned) * MAX_PASSES * RADIX);
+  const size_t o_look = take(sizeof(unsigned long long) * RADIX * (size_t)B.sort_tiles);
   const size_t o_rng = take(sizeof(int2) * tiles);
   // split-tile segments: at most 2 * keys / seg_len (each split tile has more
   // than seg_len keys, so ceil(len / seg_len) <= 2 len / seg_len); one
@@ -209,6 +211,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   // units: one per tile, one per later segment, one more per split tile
   const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + 2 * (size_t)B.seg_cap));
   const size_t o_tseg = take(sizeof(int2) * tiles);
+  const int wl_blocks = (tiles + 255) / 256;
+  const size_t o_wlc = take(sizeof(int) * 34 * (size_t)wl_blocks);
+  const size_t o_wlb = take(sizeof(int) * 34);
   const size_t o_psa = take(sizeof(float4) * B.seg_cap * tt);
   const size_t o_psb = take(sizeof(float4) * B.seg_cap * tt);
 
@@ -240,10 +245,13 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.keys[1] = reinterpret_cast<unsigned long long*>(base + o_k1);
     B.vals[0] = reinterpret_cast<unsigned*>(base + o_v0);
     B.vals[1] = reinterpret_cast<unsigned*>(base + o_v1);
-    B.hist = reinterpret_cast<unsigned*>(base + o_hist);
+    B.ghist = reinterpret_cast<unsigned*>(base + o_ghist);
+    B.look = reinterpret_cast<unsigned long long*>(base + o_look);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
     B.worklist = reinterpret_cast<int2*>(base + o_wl);
     B.tseg = reinterpret_cast<int2*>(base + o_tseg);
+    B.wl_blockcnt = reinterpret_cast<int*>(base + o_wlc);
+    B.wl_base = reinterpret_cast<int*>(base + o_wlb);
     B.pseg_a = reinterpret_cast<float4*>(base + o_psa);
     B.pseg_b = reinterpret_cast<float4*>(base + o_psb);
 
@@ -260,6 +268,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.max_pf_chunks = max_pf;
   H.max_pp_chunks = max_pp;
   H.sort_blocks = B.sort_blocks;
+  H.sort_tiles = B.sort_tiles;
+  H.wl_blocks = wl_blocks;
   H.max_passes = (32 + B.tile_bits + RADIX_BITS - 1) / RADIX_BITS;
   H.range_blocks = 16 * sm_count();
   H.total_tiles = tiles;

@@ -57,9 +57,14 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->status &= ~(unsigned)TTS_STATUS_KEY_OVERFLOW;
     c->work_fwd = c->work_bwd = 0u;
     c->done_fwd = c->done_bwd = 0u;
+    c->sort_epoch += 1u;
+    c->seg_total = 0;
+    for (int p = 0; p < MAX_PASSES; ++p) c->sort_ticket[p] = 0u;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
     B->ranges[t] = make_int2(0, 0);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MAX_PASSES * RADIX; i += gridDim.x * blockDim.x)
+    B->ghist[i] = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -431,84 +436,72 @@ __global__ void __launch_bounds__(PP_THREADS) k_duplicate(const Batch* __restric
 }
 
 // ---------------------------------------------------------------------------
-// K4: LSD radix sort, 8-bit digits, stable.  Per pass: histogram per block,
-// per-digit row scan, stable scatter (warp multisplit ranks).
+// K4: LSD radix sort, 8-bit digits, stable, one kernel per digit pass.  The
+// global digit counts of every pass come from one read of the keys
+// (k_radix_ghist).  A pass takes tiles of SORT_TILE keys in ticket order,
+// ranks them per digit inside the block (warp multisplit), publishes the
+// tile's digit counts, finds the counts of all earlier tiles by decoupled
+// look-back (each earlier tile's aggregate, or the inclusive prefix where one
+// is published), publishes its own inclusive prefix and scatters the tile in
+// digit runs.  The look-back waits are bounded: past the limit the pass sets
+// TTS_STATUS_TIMEOUT and goes on (its output is then undefined).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void sort_chunk(const Batch* B, long long n, long long* lo, long long* hi) {
-  const int nb = B->sort_blocks;
-  long long per = (n + nb - 1) / nb;
-  per = (per + SORT_TILE - 1) / SORT_TILE * SORT_TILE;
-  *lo = min(n, per * blockIdx.x);
-  *hi = min(n, *lo + per);
+constexpr unsigned long long LB_AGG = 1ull << 32;      // flag bits above the 32-bit count
+constexpr unsigned long long LB_PREFIX = 2ull << 32;
+constexpr long long LB_SPIN_LIMIT = 1ll << 22;
+
+__device__ __forceinline__ unsigned long long lb_word(unsigned tag, unsigned long long flag,
+                                                      unsigned value) {
+  return ((unsigned long long)tag << 34) | flag | value;
 }
 
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_hist(const Batch* __restrict__ B, int pass) {
+// grid: sort_blocks; each block adds its keys' digits of every live pass
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_ghist(const Batch* __restrict__ B) {
   const Counters* c = B->ctr;
-  if (pass >= c->n_passes) return;
+  const int np = c->n_passes;
+  if (np == 0) return;
   const long long n = c->n_keys_used;
-  long long lo, hi;
-  sort_chunk(B, n, &lo, &hi);
-  __shared__ unsigned h[SORT_THREADS / 32][RADIX];
-  for (int i = threadIdx.x; i < (SORT_THREADS / 32) * RADIX; i += SORT_THREADS) (&h[0][0])[i] = 0;
+  constexpr int NH = SORT_THREADS / 64;   // one histogram per two warps (32 KB)
+  __shared__ unsigned h[NH][MAX_PASSES][RADIX];
+  for (int i = threadIdx.x; i < NH * MAX_PASSES * RADIX; i += SORT_THREADS) (&h[0][0][0])[i] = 0;
   __syncthreads();
-  const unsigned long long* src = B->keys[pass & 1];
-  const int sh = pass * RADIX_BITS;
-  const int wid = threadIdx.x >> 5;
-  for (long long i = lo + threadIdx.x; i < hi; i += SORT_THREADS) {
-    const unsigned d = (unsigned)(src[i] >> sh) & (RADIX - 1);
-    atomicAdd(&h[wid][d], 1u);
+  const unsigned long long* src = B->keys[0];
+  const int wid = threadIdx.x >> 6;
+  for (long long i = blockIdx.x * (long long)SORT_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * SORT_THREADS) {
+    const unsigned long long k = src[i];
+    for (int p = 0; p < np; ++p) atomicAdd(&h[wid][p][(unsigned)(k >> (p * RADIX_BITS)) & (RADIX - 1)], 1u);
   }
   __syncthreads();
-  const int nb = B->sort_blocks;
-  for (int d = threadIdx.x; d < RADIX; d += SORT_THREADS) {
+  for (int i = threadIdx.x; i < np * RADIX; i += SORT_THREADS) {
     unsigned t = 0;
 #pragma unroll
-    for (int w = 0; w < SORT_THREADS / 32; ++w) t += h[w][d];
-    B->hist[(size_t)d * (nb + 1) + blockIdx.x] = t;
+    for (int w = 0; w < NH; ++w) t += (&h[w][0][0])[i];
+    if (t) atomicAdd(&B->ghist[i], t);
   }
 }
 
-// grid RADIX blocks: exclusive scan of one digit's row over the blocks; the
-// row total goes to the extra last column.
-__global__ void __launch_bounds__(SCAN_THREADS) k_radix_rowscan(const Batch* __restrict__ B, int pass) {
-  if (pass >= B->ctr->n_passes) return;
-  const int nb = B->sort_blocks;
-  unsigned* row = B->hist + (size_t)blockIdx.x * (nb + 1);
-  unsigned carry = 0;
-  for (int base = 0; base < nb; base += SCAN_THREADS) {
-    const int i = base + threadIdx.x;
-    const unsigned v = (i < nb) ? row[i] : 0u;
-    unsigned tot;
-    const unsigned ex = block_excl_scan<unsigned, SCAN_THREADS>(v, &tot);
-    if (i < nb) row[i] = carry + ex;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) row[nb] = carry;
-}
-
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __restrict__ B, int pass) {
-  const Counters* c = B->ctr;
+// grid: sort_tiles (the key capacity's tiles); blocks past the live tiles exit
+__global__ void __launch_bounds__(SORT_THREADS) k_radix_onesweep(const Batch* __restrict__ B, int pass) {
+  Counters* c = B->ctr;
   if (pass >= c->n_passes) return;
   const long long n = c->n_keys_used;
-  long long lo, hi;
-  sort_chunk(B, n, &lo, &hi);
-  const int nb = B->sort_blocks;
+  const int ntiles = (int)((n + SORT_TILE - 1) / SORT_TILE);
   constexpr int NW = SORT_THREADS / 32;
-  __shared__ unsigned base[RADIX];
+  __shared__ int s_tile;
+  __shared__ unsigned dbase[RADIX];
   __shared__ unsigned wcnt[NW][RADIX];
   __shared__ unsigned tstart[RADIX];
   __shared__ unsigned long long sk[SORT_TILE];
   __shared__ unsigned sv[SORT_TILE];
-  // digit base = (exclusive scan of digit totals) + this block's row prefix
-  {
-    const int d = threadIdx.x;  // SORT_THREADS == RADIX
-    const unsigned tot = B->hist[(size_t)d * (nb + 1) + nb];
-    unsigned t;
-    const unsigned ex = block_excl_scan<unsigned, SORT_THREADS>(tot, &t);
-    base[d] = ex + B->hist[(size_t)d * (nb + 1) + blockIdx.x];
-  }
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(&c->sort_ticket[pass], 1u);
   for (int i = threadIdx.x; i < NW * RADIX; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
+  const int tile = s_tile;
+  if (tile >= ntiles) return;
+  const unsigned tag = (c->sort_epoch * MAX_PASSES + pass) % 0xffffu + 1u;
+  const long long t0 = (long long)tile * SORT_TILE;
+  const int tn = (int)min((long long)SORT_TILE, n - t0);
   const unsigned long long* ksrc = B->keys[pass & 1];
   const unsigned* vsrc = B->vals[pass & 1];
   unsigned long long* kdst = B->keys[(pass + 1) & 1];
@@ -516,75 +509,94 @@ __global__ void __launch_bounds__(SORT_THREADS) k_radix_scatter(const Batch* __r
   const int sh = pass * RADIX_BITS;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
-  for (long long t0 = lo; t0 < hi; t0 += SORT_TILE) {
-    const int tn = (int)min((long long)SORT_TILE, hi - t0);
-    unsigned long long k[SORT_KPT];
-    unsigned val[SORT_KPT];
-    unsigned dg[SORT_KPT];
-    unsigned off[SORT_KPT];
+  unsigned long long k[SORT_KPT];
+  unsigned val[SORT_KPT], dg[SORT_KPT], off[SORT_KPT];
 #pragma unroll
-    for (int j = 0; j < SORT_KPT; ++j) {
-      const long long i = t0 + (long long)wid * (32 * SORT_KPT) + j * 32 + lane;
-      if (i < hi) {
-        k[j] = ksrc[i];
-        val[j] = vsrc[i];
-        dg[j] = (unsigned)(k[j] >> sh) & (RADIX - 1);
-      } else {
-        dg[j] = RADIX;  // sentinel: not scattered
+  for (int j = 0; j < SORT_KPT; ++j) {
+    const int i = wid * (32 * SORT_KPT) + j * 32 + lane;
+    if (i < tn) {
+      k[j] = ksrc[t0 + i];
+      val[j] = vsrc[t0 + i];
+      dg[j] = (unsigned)(k[j] >> sh) & (RADIX - 1);
+    } else {
+      dg[j] = RADIX;  // sentinel: not scattered
+    }
+  }
+  // ranks inside each warp (warp multisplit), digit counts per warp
+#pragma unroll
+  for (int j = 0; j < SORT_KPT; ++j) {
+    const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
+    const unsigned rank = __popc(peers & lt_mask);
+    const unsigned d = dg[j] & (RADIX - 1);
+    const unsigned before = (dg[j] < RADIX) ? wcnt[wid][d] : 0u;
+    __syncwarp();
+    if (dg[j] < RADIX && rank == 0) wcnt[wid][d] = before + __popc(peers);
+    __syncwarp();
+    off[j] = before + rank;
+  }
+  __syncthreads();
+  {
+    const int d = threadIdx.x;   // SORT_THREADS == RADIX
+    unsigned run = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+      const unsigned x = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += x;
+    }
+    unsigned t;
+    tstart[d] = block_excl_scan<unsigned, SORT_THREADS>(run, &t);
+    // publish this tile's count of digit d, then look back over the earlier
+    // tiles for their counts
+    unsigned long long* look = B->look + (size_t)tile * RADIX + d;
+    if (tile > 0) atomicExch(look, lb_word(tag, LB_AGG, run));
+    unsigned excl = 0;
+    bool timed_out = false;
+    for (int tp = tile - 1; tp >= 0;) {
+      const unsigned long long w =
+          *reinterpret_cast<volatile unsigned long long*>(B->look + (size_t)tp * RADIX + d);
+      if ((unsigned)(w >> 34) == tag && (w & (LB_AGG | LB_PREFIX))) {
+        excl += (unsigned)w;
+        if (w & LB_PREFIX) break;
+        --tp;
+        continue;
       }
-    }
-#pragma unroll
-    for (int j = 0; j < SORT_KPT; ++j) {
-      const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
-      const unsigned rank = __popc(peers & lt_mask);
-      const unsigned d = dg[j] & (RADIX - 1);
-      const unsigned before = (dg[j] < RADIX) ? wcnt[wid][d] : 0u;
-      __syncwarp();
-      if (dg[j] < RADIX && rank == 0) wcnt[wid][d] = before + __popc(peers);
-      __syncwarp();
-      off[j] = before + rank;
-    }
-    __syncthreads();
-    unsigned tcnt;
-    {
-      const int d = threadIdx.x;
-      unsigned run = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        const unsigned x = wcnt[w][d];
-        wcnt[w][d] = run;
-        run += x;
+      long long spins = 0;
+      while (true) {   // the earlier tile has not published yet: bounded wait
+        const unsigned long long w2 =
+            *reinterpret_cast<volatile unsigned long long*>(B->look + (size_t)tp * RADIX + d);
+        if ((unsigned)(w2 >> 34) == tag && (w2 & (LB_AGG | LB_PREFIX))) break;
+        if (++spins > LB_SPIN_LIMIT) {
+          timed_out = true;
+          break;
+        }
       }
-      tcnt = run;
-      unsigned t;
-      tstart[d] = block_excl_scan<unsigned, SORT_THREADS>(run, &t);
+      if (timed_out) break;
     }
-    __syncthreads();
-    // stage the tile in digit order, then write each digit's run contiguously
+    if (timed_out) set_status(c, TTS_STATUS_TIMEOUT);
+    atomicExch(look, lb_word(tag, LB_PREFIX, excl + run));
+    // digit base: all smaller digits of the whole pass, then the earlier tiles
+    const unsigned g = B->ghist[pass * RADIX + d];
+    unsigned tg;
+    dbase[d] = block_excl_scan<unsigned, SORT_THREADS>(g, &tg) + excl;
+  }
+  __syncthreads();
+  // stage the tile in digit order, then write each digit's run contiguously
 #pragma unroll
-    for (int j = 0; j < SORT_KPT; ++j) {
-      if (dg[j] < RADIX) {
-        const unsigned lp = tstart[dg[j]] + wcnt[wid][dg[j]] + off[j];
-        sk[lp] = k[j];
-        sv[lp] = val[j];
-      }
+  for (int j = 0; j < SORT_KPT; ++j) {
+    if (dg[j] < RADIX) {
+      const unsigned lp = tstart[dg[j]] + wcnt[wid][dg[j]] + off[j];
+      sk[lp] = k[j];
+      sv[lp] = val[j];
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < tn; q += SORT_THREADS) {
-      const unsigned long long key = sk[q];
-      const unsigned d = (unsigned)(key >> sh) & (RADIX - 1);
-      const unsigned pos = base[d] + (unsigned)q - tstart[d];
-      kdst[pos] = key;
-      vdst[pos] = sv[q];
-    }
-    __syncthreads();
-    {
-      const int d = threadIdx.x;
-      base[d] += tcnt;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) wcnt[w][d] = 0;
-    }
-    __syncthreads();
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < tn; q += SORT_THREADS) {
+    const unsigned long long key = sk[q];
+    const unsigned d = (unsigned)(key >> sh) & (RADIX - 1);
+    const unsigned pos = dbase[d] + (unsigned)q - tstart[d];
+    kdst[pos] = key;
+    vdst[pos] = sv[q];
   }
 }
 
@@ -609,52 +621,112 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
 // segment end, and the backward walks the segments in parallel from those
 // states (one warp per 8x4 block walking a long list back to front would
 // otherwise bound its duration).  Units (tile, segment) are ordered by
-// decreasing work (bucketed by bit length), so the longest start first.
-__global__ void __launch_bounds__(SCAN_THREADS) k_build_worklist(const Batch* __restrict__ B) {
-  __shared__ int cnt[33], off[33];
-  __shared__ int nseg_total;
-  if (threadIdx.x < 33) cnt[threadIdx.x] = 0;
-  if (threadIdx.x == 0) nseg_total = 0;
+// decreasing work (bucketed by bit length), so the longest start first; the
+// order inside a bucket is arbitrary.
+// Warp-level exclusive scan of v (all lanes), returning the warp total.
+__device__ __forceinline__ int warp_excl_scan(int v, int* total) {
+  const int lane = threadIdx.x & 31;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  *total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
+constexpr int WL_BUCKETS = 34;      // bit length of a work amount (0..32), 33: unused
+constexpr int WL_THREADS = 256;     // one tile per thread
+
+// Work-list step 1 (one tile per thread): segment count and checkpoint slots
+// of each tile, and per block the units of each length bucket.
+__global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __restrict__ B) {
+  __shared__ int cnt[WL_BUCKETS];
+  if (threadIdx.x < WL_BUCKETS) cnt[threadIdx.x] = 0;
   __syncthreads();
+  const int t = blockIdx.x * WL_THREADS + threadIdx.x;
   const int nt = B->total_tiles;
   const int L = B->seg_len;
-  for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
-    const int2 r = B->ranges[t];
-    const int len = r.y - r.x;
-    int nseg = (L > 0 && len > L) ? (len + L - 1) / L : 1;
-    int base = -1;
-    if (nseg > 1) {
-      base = atomicAdd(&nseg_total, nseg);
-      if (base + nseg > B->seg_cap) {   // outside the sizing bound: blend unsplit
-        nseg = 1;
-        base = -1;
-      }
+  const int lane = threadIdx.x & 31;
+  const bool in = t < nt;
+  const int2 r = in ? B->ranges[t] : make_int2(0, 0);
+  const int len = r.y - r.x;
+  int nseg = (in && L > 0 && len > L) ? (len + L - 1) / L : 1;
+  // checkpoint slots, one atomic per warp
+  int tot;
+  const int ex = warp_excl_scan(nseg > 1 ? nseg : 0, &tot);
+  int base0 = 0;
+  if (lane == 31 && tot > 0) base0 = atomicAdd(&B->ctr->seg_total, tot);
+  base0 = __shfl_sync(0xffffffffu, base0, 31);
+  int base = -1;
+  if (nseg > 1) {
+    base = base0 + ex;
+    if (base + nseg > B->seg_cap) {   // outside the sizing bound: blend unsplit
+      nseg = 1;
+      base = -1;
     }
+  }
+  if (in) {
     B->tseg[t] = make_int2(base, nseg);
     // segment 0 carries the forward's walk of the whole list (two parts for
-    // a split list: its 4x4 blocks, two lanes per pixel): ordered by the list
-    // length; the later segments (backward only) by the segment length
+    // a split list): bucketed by the list length; the later segments
+    // (backward only) by the segment length
     atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], nseg > 1 ? 2 : 1);
     if (nseg > 1) atomicAdd(&cnt[32 - __clz(L)], nseg - 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    int run = 0;
-    for (int b = 32; b >= 0; --b) { off[b] = run; run += cnt[b]; }
-    B->ctr->n_units = run;
+  if (threadIdx.x < WL_BUCKETS) B->wl_blockcnt[blockIdx.x * WL_BUCKETS + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// Work-list step 2 (one block of 17 warps, two buckets each): per bucket,
+// the exclusive prefix of the blocks' unit counts (in place) and, over the
+// buckets from the longest down, the first unit of each bucket.
+__global__ void __launch_bounds__(17 * 32) k_worklist_scan(const Batch* __restrict__ B, int nb) {
+  __shared__ int total[WL_BUCKETS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < WL_BUCKETS; j += 17) {
+    int carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 32) {
+      const int b = b0 + lane;
+      const int v = (b < nb) ? B->wl_blockcnt[b * WL_BUCKETS + j] : 0;
+      int tot;
+      const int ex = warp_excl_scan(v, &tot);
+      if (b < nb) B->wl_blockcnt[b * WL_BUCKETS + j] = carry + ex;
+      carry += tot;
+    }
+    if (lane == 0) total[j] = carry;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < nt; t += SCAN_THREADS) {
-    const int2 r = B->ranges[t];
-    const int2 ts = B->tseg[t];
-    const int len = r.y - r.x;
-    const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], ts.y > 1 ? 2 : 1);
-    B->worklist[pos0] = make_int2(t, 0);
-    if (ts.y > 1) {
-      B->worklist[pos0 + 1] = make_int2(t, 1 << 24);   // part 1: forward only
-      const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
-      for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
+  if (threadIdx.x == 0) {
+    int run = 0;
+    for (int j = WL_BUCKETS - 1; j >= 0; --j) {
+      B->wl_base[j] = run;
+      run += total[j];
     }
+    B->ctr->n_units = run;
+  }
+}
+
+// Work-list step 3 (one tile per thread): each tile's units go after all
+// units of longer buckets and after the earlier blocks' units of its bucket.
+__global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __restrict__ B) {
+  __shared__ int off[WL_BUCKETS];
+  if (threadIdx.x < WL_BUCKETS)
+    off[threadIdx.x] = B->wl_base[threadIdx.x] + B->wl_blockcnt[blockIdx.x * WL_BUCKETS + threadIdx.x];
+  __syncthreads();
+  const int t = blockIdx.x * WL_THREADS + threadIdx.x;
+  if (t >= B->total_tiles) return;
+  const int L = B->seg_len;
+  const int2 r = B->ranges[t];
+  const int2 ts = B->tseg[t];
+  const int len = r.y - r.x;
+  const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], ts.y > 1 ? 2 : 1);
+  B->worklist[pos0] = make_int2(t, 0);
+  if (ts.y > 1) {
+    B->worklist[pos0 + 1] = make_int2(t, 1 << 24);   // part 1: forward only
+    const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
+    for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
   }
 }
 
@@ -679,14 +751,15 @@ int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   k_preprocess<<<g, PP_THREADS, 0, st>>>(dB);
   k_preprocess_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
   k_duplicate<<<g, PP_THREADS, 0, st>>>(dB);
+  k_radix_ghist<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB);
   for (int p = 0; p < P.max_passes; ++p) {
-    k_radix_hist<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB, p);
-    k_radix_rowscan<<<RADIX, SCAN_THREADS, 0, st>>>(dB, p);
-    k_radix_scatter<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB, p);
+    k_radix_onesweep<<<P.sort_tiles, SORT_THREADS, 0, st>>>(dB, p);
   }
   k_tile_ranges<<<P.range_blocks, 256, 0, st>>>(dB);
-  k_build_worklist<<<1, SCAN_THREADS, 0, st>>>(dB);
-  return 6 + 3 * P.max_passes;
+  k_worklist_count<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
+  k_worklist_scan<<<1, 17 * 32, 0, st>>>(dB, P.wl_blocks);
+  k_worklist_place<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
+  return 9 + P.max_passes;
 }
 
 }  // namespace tts

@@ -10,7 +10,8 @@ namespace tts {
 struct HostPlan {
   int n_scenes, n_views;
   int max_pf_chunks, max_pp_chunks;
-  int sort_blocks, max_passes;
+  int sort_blocks, max_passes, sort_tiles;
+  int wl_blocks;
   int range_blocks;
   int total_tiles;
   int tile;

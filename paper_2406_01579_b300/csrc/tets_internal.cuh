@@ -36,7 +36,10 @@ struct Counters {
   unsigned int work_fwd, work_bwd;      // persistent blend work queues
   unsigned int done_fwd, done_bwd;      // warps finished (last one resets)
   int n_units;              // blend work units (tile segments) of the last binning
-  int pad[11];
+  unsigned int sort_epoch;  // binnings so far (tags the look-back words of each pass)
+  unsigned int sort_ticket[MAX_PASSES];   // next tile of each radix pass
+  int seg_total;            // checkpoint slots handed out by the work-list builder
+  int pad[1];
 };
 
 struct SceneD {
@@ -94,10 +97,14 @@ struct Batch {
   long long* pp_blocksum;   // [pp_chunks_total]
   unsigned long long* keys[2];
   unsigned int* vals[2];
-  unsigned int* hist;       // [RADIX * sort_blocks]
+  unsigned int* ghist;      // [MAX_PASSES * RADIX] global digit counts of the keys
+  unsigned long long* look; // [sort_tiles * RADIX] look-back words of the running pass
+  int sort_tiles;           // tiles of SORT_TILE keys the key capacity holds
   int2* ranges;             // [total_tiles]
   int2* worklist;           // [units] (tile, segment), longest first
   int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)
+  int* wl_blockcnt;         // [work-list blocks * 34] units per length bucket and block
+  int* wl_base;             // [34] first unit of each length bucket
   float4* pseg_a;           // [seg_cap * tile^2] forward state at each segment end: (T, C0, C1, C2)
   float4* pseg_b;           // [seg_cap * tile^2] (D, N0, N1, N2)
   float* pix_T;             // [total_pixels]

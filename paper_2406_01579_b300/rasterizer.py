@@ -251,6 +251,8 @@ class Rasterizer:
             info = self.info()
             if info.status & TTS_STATUS_BAD_INDEX:
                 raise TetsError("a tet index is outside [0, N)")
+            if info.status & _lib.TTS_STATUS_TIMEOUT:
+                raise TetsError("a bounded device wait gave up (the outputs are undefined)")
             grow = False
             if info.status & TTS_STATUS_SURV_OVERFLOW:
                 self.surv_capacity = [int(s.T.shape[0]) for s in self.scenes]
