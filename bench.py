@@ -268,7 +268,7 @@ def run_ours(a, rank, world):
         "autotune_ms": tune,
         "elapsed": elapsed, "value": value, "stage_ms": stage_ms, "launches": launches,
         "clocks": clocks, "nfrag": nfrag, "entries_walked": lasts, "n_keys": int(info.n_keys),
-        "n_surv": int(info.n_surv[0]), "sort_passes": int(info.sort_passes),
+        "n_surv": int(info.n_surv[0]), "long_lists": int(info.long_lists),
         "pixels_per_step": pixels_per_step,
     }
 
@@ -732,7 +732,7 @@ def main():
         "serve": res.get("serve"),
         "gpu_launches": res["launches"],
         "fragments_per_step": res["nfrag"], "keys_per_step": res["n_keys"],
-        "survivors": res["n_surv"], "sort_passes": res["sort_passes"],
+        "survivors": res["n_surv"], "long_lists": res["long_lists"],
         "mtet_per_s": 12582912 * a.steps / res["elapsed"] / 1e6,
         "clocks": res["clocks"],
     }

@@ -10,7 +10,8 @@
  *                       alpha_max >= T_f, in their original order.
  *   tts_render_fwd      per view: project and cull the survivors, build one
  *                       (tile id, mean vertex depth) key per overlapped tile,
- *                       radix sort the keys (Sec. 3.3), then per pixel blend the
+ *                       sort the keys (Sec. 3.3: bucketed by tile, each tile's
+ *                       list ordered by depth on chip), then per pixel blend the
  *                       tile's tets front to back with the Eq. 1 opacity of the
  *                       ray's chord through the tet and Eq. 2 compositing
  *                       (3DGS conventions), writing image, alpha and depth.
@@ -160,8 +161,9 @@ typedef struct {
   int32_t n_scenes;
   int64_t n_keys;           /* keys produced by the last forward (needed capacity) */
   int64_t n_surv[TTS_MAX_SCENES]; /* survivors per scene of the last prepare */
-  int32_t sort_bits;        /* key bits sorted by the last forward */
-  int32_t sort_passes;
+  int32_t sort_bits;        /* bits of the (tile, depth) keys of the last forward */
+  int32_t long_lists;       /* tiles of the last forward whose list exceeded the
+                               on-chip sort (sorted by merging runs in global memory) */
   int32_t blend_units;      /* blend work units (tile lists and list segments) */
   int32_t reserved;
 } tts_info;
@@ -269,7 +271,10 @@ int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream);
  * keys (uint64: (global tile << depth_bits) | (zbits - zmin_bits)), values
  * (uint32 record slot), per-tile ranges (int32 pairs [start, end) per global
  * tile), survivor list of scene 0.., and the key encoding (zmin_bits,
- * depth_bits).  Synchronises the stream. */
+ * depth_bits).  A render keeps only the values and ranges: asking for keys
+ * enqueues a kernel that rebuilds them into a scratch buffer of the workspace
+ * from those and the slots' depth bits (valid until the next render).
+ * Synchronises the stream. */
 int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
                     const void** ranges, const void** surv, uint32_t* zmin_bits,
                     int32_t* depth_bits, tts_stream stream);
@@ -279,7 +284,7 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
 int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
 
 /* Sorts n (key, value) pairs by the low key_bits bits of the key, stably
- * (the LSD radix sort used for tile binning), without allocating anything.
+ * (an LSD radix sort), without allocating anything.
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory themselves (code inside a host callback or an
  * allocator hook, plugin hosts that own every device allocation, loops that

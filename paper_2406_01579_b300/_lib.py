@@ -75,7 +75,7 @@ class tts_upstream(ctypes.Structure):
 class tts_info(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("n_scenes", ctypes.c_int32),
                 ("n_keys", ctypes.c_int64), ("n_surv", ctypes.c_int64 * TTS_MAX_SCENES),
-                ("sort_bits", ctypes.c_int32), ("sort_passes", ctypes.c_int32),
+                ("sort_bits", ctypes.c_int32), ("long_lists", ctypes.c_int32),
                 ("blend_units", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 

@@ -8,7 +8,6 @@
 
 namespace tts {
 
-static_assert(SORT_THREADS == RADIX, "scatter maps one thread per digit");
 static_assert(sizeof(Batch) < 30000, "descriptor must fit in kernel parameters");
 
 // Copies the by-value descriptor into the workspace (kernel parameters are
@@ -131,7 +130,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   }
   // views
   long long slots = 0, pix = 0;
-  int tiles = 0, pp_chunks = 0, max_pp = 1;
+  int tiles = 0, max_pp = 1;
   for (int v = 0; v < b->n_views; ++v) {
     const tts_view& tv = b->views[v];
     const tts_camera& c = tv.cam;
@@ -156,8 +155,6 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     const long long cap = B.sc[tv.scene].surv_cap;
     slots += cap;
     V.pp_chunks = (int)((cap + PP_CHUNK - 1) / PP_CHUNK);
-    V.pp_chunk_base = pp_chunks;
-    pp_chunks += V.pp_chunks;
     max_pp = std::max(max_pp, V.pp_chunks);
     SceneD& S = B.sc[tv.scene];
     B.scene_views[S.view_off + S.view_cnt++] = v;
@@ -166,12 +163,10 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   B.total_tiles = tiles;
   B.tile_bits = std::max(1, bit_length(tiles - 1));
   B.pf_chunks_total = pf_chunks;
-  B.pp_chunks_total = pp_chunks;
   B.max_pf_chunks = max_pf;
   B.max_pp_chunks = max_pp;
   B.total_pixels = pix;
   B.total_slots = slots;
-  B.sort_blocks = 4 * sm_count();
   // layout
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -194,14 +189,11 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const bool fwd_only = (pr.flags & TTS_FLAG_FORWARD_ONLY) != 0;
   P->off_rec_grad = take(fwd_only ? 0 : sizeof(float4) * REC_Q * slots);
   P->bytes_rec_grad = fwd_only ? 0 : sizeof(float4) * REC_Q * slots;
-  const size_t o_ppb = take(sizeof(long long) * pp_chunks);
   const size_t o_k0 = take(sizeof(unsigned long long) * cap);
   const size_t o_k1 = take(sizeof(unsigned long long) * cap);
-  const size_t o_v0 = take(sizeof(unsigned) * cap);
-  const size_t o_v1 = take(sizeof(unsigned) * cap);
-  B.sort_tiles = (int)((cap + SORT_TILE - 1) / SORT_TILE);
-  const size_t o_ghist = take(sizeof(unsigned) * MAX_PASSES * RADIX);
-  const size_t o_look = take(sizeof(unsigned long long) * RADIX * (size_t)B.sort_tiles);
+  const size_t o_v = take(sizeof(unsigned) * cap);
+  const size_t o_tc = take(sizeof(int) * tiles);
+  const size_t o_tcl = take(sizeof(int) * TSORT_CLASSES * (size_t)tiles);
   const size_t o_rng = take(sizeof(int2) * tiles);
   // split-tile segments: at most 2 * keys / seg_len (each split tile has more
   // than seg_len keys, so ceil(len / seg_len) <= 2 len / seg_len); one
@@ -240,13 +232,11 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.rec_rect = reinterpret_cast<int4*>(base + o_rr);
     B.rec = reinterpret_cast<float4*>(base + o_rec);
     B.rec_grad = reinterpret_cast<float4*>(base + P->off_rec_grad);
-    B.pp_blocksum = reinterpret_cast<long long*>(base + o_ppb);
     B.keys[0] = reinterpret_cast<unsigned long long*>(base + o_k0);
     B.keys[1] = reinterpret_cast<unsigned long long*>(base + o_k1);
-    B.vals[0] = reinterpret_cast<unsigned*>(base + o_v0);
-    B.vals[1] = reinterpret_cast<unsigned*>(base + o_v1);
-    B.ghist = reinterpret_cast<unsigned*>(base + o_ghist);
-    B.look = reinterpret_cast<unsigned long long*>(base + o_look);
+    B.vals = reinterpret_cast<unsigned*>(base + o_v);
+    B.tile_cnt = reinterpret_cast<int*>(base + o_tc);
+    B.tile_class = reinterpret_cast<int*>(base + o_tcl);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
     B.worklist = reinterpret_cast<int2*>(base + o_wl);
     B.tseg = reinterpret_cast<int2*>(base + o_tseg);
@@ -267,11 +257,12 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.n_views = b->n_views;
   H.max_pf_chunks = max_pf;
   H.max_pp_chunks = max_pp;
-  H.sort_blocks = B.sort_blocks;
-  H.sort_tiles = B.sort_tiles;
+  H.tsort_blocks[0] = std::max(1, std::min((tiles + 7) / 8, 8 * sm_count()));
+  H.tsort_blocks[1] = std::max(1, std::min(tiles, 8 * sm_count()));
+  H.tsort_blocks[2] = std::max(1, std::min(tiles, 4 * sm_count()));
+  H.tsort_blocks[3] = std::max(1, std::min(tiles, 2 * sm_count()));
+  H.tsort_blocks[4] = std::max(1, std::min(tiles, sm_count()));
   H.wl_blocks = wl_blocks;
-  H.max_passes = (32 + B.tile_bits + RADIX_BITS - 1) / RADIX_BITS;
-  H.range_blocks = 16 * sm_count();
   H.total_tiles = tiles;
   H.tile = pr.tile;
   H.window = pr.resort_window;
@@ -500,7 +491,7 @@ int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream) {
   info->n_keys = c.n_keys;
   for (int s = 0; s < b->n_scenes; ++s) info->n_surv[s] = c.n_surv[s];
   info->sort_bits = c.total_bits;
-  info->sort_passes = c.n_passes;
+  info->long_lists = c.long_lists;
   info->blend_units = c.n_units;
   return TTS_OK;
 }
@@ -511,12 +502,16 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals, co
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (keys) {
+    g_launches += launch_debug_keys(P.hp, dev_desc(b, P), st);
+    if (check_launch() != TTS_OK) return TTS_ERR_CUDA;
+  }
   Counters c;
   if (cudaMemcpyAsync(&c, P.hb.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return TTS_ERR_CUDA;
   if (cudaStreamSynchronize(st) != cudaSuccess) return TTS_ERR_CUDA;
-  if (keys) *keys = P.hb.keys[c.n_passes & 1];
-  if (vals) *vals = P.hb.vals[c.n_passes & 1];
+  if (keys) *keys = P.hb.keys[0];
+  if (vals) *vals = P.hb.vals;
   if (ranges) *ranges = P.hb.ranges;
   if (surv) *surv = P.hb.surv;
   if (zmin_bits) *zmin_bits = c.zmin_bits;

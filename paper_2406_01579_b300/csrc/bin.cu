@@ -1,5 +1,5 @@
-// Pre-filter (Sec. 3.2), per-view preprocess and tile binning with a device
-// radix sort of (tile id, mean depth) keys (Sec. 3.3).
+// Pre-filter (Sec. 3.2), per-view preprocess and tile binning (Sec. 3.3): keys
+// bucketed by tile, then each tile's list sorted by mean depth on chip.
 #include <algorithm>
 
 #include "geometry.cuh"
@@ -41,6 +41,19 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
   return base + inc - v;
 }
 
+// Warp-level exclusive scan of v (all lanes), returning the warp total.
+__device__ __forceinline__ int warp_excl_scan(int v, int* total) {
+  const int lane = threadIdx.x & 31;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  *total = __shfl_sync(0xffffffffu, inc, 31);
+  return inc - v;
+}
+
 // ---------------------------------------------------------------------------
 // per-call resets
 // ---------------------------------------------------------------------------
@@ -51,20 +64,17 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->zmax_bits = 0u;
     c->depth_bits = 0;
     c->total_bits = 0;
-    c->n_passes = 0;
+    c->long_lists = 0;
     c->n_keys = 0;
     c->n_keys_used = 0;
     c->status &= ~(unsigned)TTS_STATUS_KEY_OVERFLOW;
     c->work_fwd = c->work_bwd = 0u;
     c->done_fwd = c->done_bwd = 0u;
-    c->sort_epoch += 1u;
     c->seg_total = 0;
-    for (int p = 0; p < MAX_PASSES; ++p) c->sort_ticket[p] = 0u;
+    for (int q = 0; q < TSORT_CLASSES; ++q) c->class_n[q] = 0;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
-    B->ranges[t] = make_int2(0, 0);
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MAX_PASSES * RADIX; i += gridDim.x * blockDim.x)
-    B->ghist[i] = 0u;
+    B->tile_cnt[t] = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -306,7 +316,28 @@ int launch_fit_grid(const float* V_in, long long N, const float lo[3], const flo
 }
 
 // ---------------------------------------------------------------------------
-// K2: per-view preprocess.  grid (max_pp_chunks, n_views)
+// Warp-aggregated bucket counter: every active lane adds one to bucket[gt];
+// lanes with equal gt share one atomic.  Returns the lane's position among
+// the bucket's additions (the old value plus its rank in its group).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned active, bool want_pos) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(active, gt);
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) {
+    if (want_pos) base = atomicAdd(bucket + gt, __popc(peers));
+    else atomicAdd(bucket + gt, __popc(peers));
+  }
+  if (!want_pos) return 0;
+  base = __shfl_sync(active, base, leader);
+  return base + __popc(peers & ((1u << lane) - 1u));
+}
+
+// ---------------------------------------------------------------------------
+// K2: per-view preprocess.  grid (max_pp_chunks, n_views).  Writes each
+// slot's record, tile rect and depth bits, and counts the keys of every
+// tile the slot's rect overlaps.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
   const int v = blockIdx.y;
@@ -317,300 +348,396 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   const int nsurv = B->ctr->n_surv[vw.scene];
   const float s = B->s;
   const int tile = B->tile;
-  long long nt_sum = 0;
+  int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
   unsigned zmn = 0xffffffffu, zmx = 0u;
   for (int q = threadIdx.x; q < PP_CHUNK; q += PP_THREADS) {
     const int k = chunk * PP_CHUNK + q;
-    if (k >= nsurv) break;
-    const long long slot = vw.rec_base + k;
-    const int tet = B->surv[S.surv_off + k];
-    TetIn in;
-    load_tet(S, tet, in);
-    Geo G;
-    tet_geometry(vw, s, in, G);
-    int nt = 0;
-    if (G.visible) {
-      const int tx0 = G.i0 / tile, tx1 = G.i1 / tile, ty0 = G.j0 / tile, ty1 = G.j1 / tile;
-      nt = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-      B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
-      write_record(vw, s, in, G, B->rec + slot * REC_Q);
-      zmn = min(zmn, G.zbits);
-      zmx = max(zmx, G.zbits);
+    if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
+    int tx0 = 0, ty0 = 0, ntx = 0, nt = 0;
+    if (k < nsurv) {
+      const long long slot = vw.rec_base + k;
+      const int tet = B->surv[S.surv_off + k];
+      TetIn in;
+      load_tet(S, tet, in);
+      Geo G;
+      tet_geometry(vw, s, in, G);
+      if (G.visible) {
+        tx0 = G.i0 / tile;
+        ty0 = G.j0 / tile;
+        const int tx1 = G.i1 / tile, ty1 = G.j1 / tile;
+        ntx = tx1 - tx0 + 1;
+        nt = ntx * (ty1 - ty0 + 1);
+        B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
+        write_record(vw, s, in, G, B->rec + slot * REC_Q);
+        zmn = min(zmn, G.zbits);
+        zmx = max(zmx, G.zbits);
+      }
+      B->rec_nt[slot] = nt;
+      B->rec_z[slot] = G.zbits;
     }
-    B->rec_nt[slot] = nt;
-    B->rec_z[slot] = G.zbits;
-    nt_sum += nt;
+    // key counts per tile, one atomic per (warp, tile) and round
+    for (int r = 0; __any_sync(0xffffffffu, r < nt); ++r) {
+      const unsigned act = __ballot_sync(0xffffffffu, r < nt);
+      if (r < nt) warp_bucket_add(cnt, (ty0 + r / ntx) * vw.tiles_x + tx0 + r % ntx, act, false);
+    }
   }
-  long long tot;
-  block_excl_scan<long long, PP_THREADS>(nt_sum, &tot);
   // block min/max of the depth bits
   __shared__ unsigned smn, smx;
   if (threadIdx.x == 0) { smn = 0xffffffffu; smx = 0u; }
   __syncthreads();
   if (zmn != 0xffffffffu) { atomicMin(&smn, zmn); atomicMax(&smx, zmx); }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    B->pp_blocksum[vw.pp_chunk_base + chunk] = tot;
-    if (smn != 0xffffffffu) {
-      atomicMin(&B->ctr->zmin_bits, smn);
-      atomicMax(&B->ctr->zmax_bits, smx);
-    }
+  if (threadIdx.x == 0 && smn != 0xffffffffu) {
+    atomicMin(&B->ctr->zmin_bits, smn);
+    atomicMax(&B->ctr->zmax_bits, smx);
   }
 }
 
-// Single block: exclusive scan of all preprocess block sums (views in order)
-// -> key offsets; total -> n_keys; key encoding bit counts.
-__global__ void __launch_bounds__(SCAN_THREADS) k_preprocess_scan(const Batch* __restrict__ B) {
-  long long* a = B->pp_blocksum;
-  const int n = B->pp_chunks_total;
+// ---------------------------------------------------------------------------
+// K3: tile scan (one block).  Exclusive prefix of the per-tile key counts ->
+// each tile's [start, end) ((0, 0) when empty) and its placement cursor
+// (= start); the total is the key count.  Past the key capacity every range
+// is left empty and the overflow status is set.  Also fixes the key
+// encoding's depth bit count.
+// ---------------------------------------------------------------------------
+constexpr int TS_ITEMS = 16;
+
+// List-length class of the per-tile depth sort (see K5).
+__device__ __forceinline__ int tsort_class(int n) {
+  return n <= 256 ? 0 : n <= 2048 ? 1 : n <= 4096 ? 2 : n <= 8192 ? 3 : 4;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const Batch* __restrict__ B) {
+  const int n = B->total_tiles;
+  int* __restrict__ cnt = B->tile_cnt;
+  int2* __restrict__ ranges = B->ranges;
   long long carry = 0;
-  for (int base = 0; base < n; base += SCAN_THREADS) {
-    const int i = base + threadIdx.x;
-    const long long v = (i < n) ? a[i] : 0;
+  for (int base = 0; base < n; base += SCAN_THREADS * TS_ITEMS) {
+    const int i0 = base + threadIdx.x * TS_ITEMS;
+    int v[TS_ITEMS];
+    long long sum = 0;
+    if (i0 + TS_ITEMS <= n) {
+      const int4* p = reinterpret_cast<const int4*>(cnt + i0);
+#pragma unroll
+      for (int j = 0; j < TS_ITEMS / 4; ++j) {
+        const int4 x = p[j];
+        v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < TS_ITEMS; ++j) v[j] = (i0 + j < n) ? cnt[i0 + j] : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) sum += v[j];
     long long tot;
-    const long long ex = block_excl_scan<long long, SCAN_THREADS>(v, &tot);
-    if (i < n) a[i] = carry + ex;
+    long long ex = carry + block_excl_scan<long long, SCAN_THREADS>(sum, &tot);
+    int cls[TS_ITEMS];
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) {
+      cls[j] = -1;
+      if (i0 + j < n) {
+        const bool keep = v[j] > 0 && ex + v[j] <= B->key_cap;
+        ranges[i0 + j] = keep ? make_int2((int)ex, (int)(ex + v[j])) : make_int2(0, 0);
+        cnt[i0 + j] = (int)min(ex, (long long)0x7fffffff);
+        if (keep) cls[j] = tsort_class(v[j]);
+      }
+      ex += v[j];
+    }
     carry += tot;
+    // the non-empty tiles by list-length class (one atomic per warp and class)
+#pragma unroll
+    for (int q = 0; q < TSORT_CLASSES; ++q) {
+      int nq = 0;
+#pragma unroll
+      for (int j = 0; j < TS_ITEMS; ++j) nq += (cls[j] == q);
+      int wt;
+      const int wx = warp_excl_scan(nq, &wt);
+      int b0 = 0;
+      if ((threadIdx.x & 31) == 0 && wt > 0) b0 = atomicAdd(&B->ctr->class_n[q], wt);
+      int pos = __shfl_sync(0xffffffffu, b0, 0) + wx;
+      int* list = B->tile_class + (size_t)q * n;
+#pragma unroll
+      for (int j = 0; j < TS_ITEMS; ++j)
+        if (cls[j] == q) list[pos++] = i0 + j;
+    }
+  }
+  const bool over = carry > B->key_cap;
+  if (over) {   // rare: no list at all
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += SCAN_THREADS) ranges[i] = make_int2(0, 0);
   }
   if (threadIdx.x == 0) {
     Counters* c = B->ctr;
     c->n_keys = carry;
-    long long used = carry;
-    if (carry > B->key_cap) {
-      set_status(c, TTS_STATUS_KEY_OVERFLOW);
-      used = 0;
-    }
-    c->n_keys_used = used;
+    c->n_keys_used = over ? 0 : carry;
+    if (over) set_status(c, TTS_STATUS_KEY_OVERFLOW);
     unsigned span = (c->zmax_bits >= c->zmin_bits) ? (c->zmax_bits - c->zmin_bits) : 0u;
     if (c->zmin_bits == 0xffffffffu) span = 0;
     const int db = (span == 0) ? 0 : (32 - __clz(span));
     c->depth_bits = db;
     c->total_bits = db + B->tile_bits;
-    c->n_passes = (used > 1) ? (c->total_bits + RADIX_BITS - 1) / RADIX_BITS : 0;
   }
 }
 
 // ---------------------------------------------------------------------------
-// K3: duplicate.  One key per (slot, overlapped tile), in slot order and
-// row-major tile order within the slot's rect.  grid (max_pp_chunks, n_views)
+// K4: key placement.  grid (max_pp_chunks, n_views).  Each (slot, overlapped
+// tile) pair takes the next position of its tile's bucket (one atomic per
+// warp and tile) and stores the composite (zbits << 32 | slot) there: the
+// buckets hold the right keys, in an arbitrary order that the per-tile sort
+// removes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PP_THREADS) k_duplicate(const Batch* __restrict__ B) {
+__global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ B) {
   const int v = blockIdx.y;
   const ViewD& vw = B->vw[v];
   const int chunk = blockIdx.x;
   if (chunk >= vw.pp_chunks) return;
   const Counters* c = B->ctr;
-  if (c->n_keys_used == 0) return;
+  const long long used = c->n_keys_used;
+  if (used == 0) return;
   const int nsurv = c->n_surv[vw.scene];
-  constexpr int PER = PP_CHUNK / PP_THREADS;
-  // thread handles PER consecutive slots so that key order follows slot order
-  const int k0 = chunk * PP_CHUNK + threadIdx.x * PER;
-  int nt[PER];
-  long long cnt = 0;
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int k = k0 + q;
-    nt[q] = (k < nsurv) ? B->rec_nt[vw.rec_base + k] : 0;
-    cnt += nt[q];
-  }
-  long long tot;
-  long long off = block_excl_scan<long long, PP_THREADS>(cnt, &tot) + B->pp_blocksum[vw.pp_chunk_base + chunk];
-  const unsigned zmin = c->zmin_bits;
-  const int db = c->depth_bits;
-  unsigned long long* keys = B->keys[0];
-  unsigned int* vals = B->vals[0];
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    if (nt[q] == 0) continue;
-    const long long slot = vw.rec_base + k0 + q;
-    const int4 r = B->rec_rect[slot];
-    const unsigned long long zrel = (unsigned long long)(B->rec_z[slot] - zmin);
-    for (int ty = r.z; ty <= r.w; ++ty)
-      for (int tx = r.x; tx <= r.y; ++tx) {
-        const unsigned long long gt = (unsigned long long)(vw.tile_base + ty * vw.tiles_x + tx);
-        keys[off] = (gt << db) | zrel;
-        vals[off] = (unsigned)slot;
-        ++off;
+  int* __restrict__ cur = B->tile_cnt + vw.tile_base;
+  unsigned long long* __restrict__ out = B->keys[1];
+  for (int q = threadIdx.x; q < PP_CHUNK; q += PP_THREADS) {
+    const int k = chunk * PP_CHUNK + q;
+    if (!__any_sync(0xffffffffu, k < nsurv)) break;
+    int nt = 0, ntx = 1;
+    int4 r = make_int4(0, 0, 0, 0);
+    unsigned long long comp = 0;
+    if (k < nsurv) {
+      const long long slot = vw.rec_base + k;
+      nt = B->rec_nt[slot];
+      if (nt > 0) {
+        r = B->rec_rect[slot];
+        ntx = r.y - r.x + 1;
+        comp = ((unsigned long long)B->rec_z[slot] << 32) | (unsigned)slot;
       }
+    }
+    for (int j = 0; __any_sync(0xffffffffu, j < nt); ++j) {
+      const unsigned act = __ballot_sync(0xffffffffu, j < nt);
+      if (j < nt) {
+        const int pos = warp_bucket_add(cur, (r.z + j / ntx) * vw.tiles_x + r.x + j % ntx, act, true);
+        if (pos < used) out[pos] = comp;
+      }
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
-// K4: LSD radix sort, 8-bit digits, stable, one kernel per digit pass.  The
-// global digit counts of every pass come from one read of the keys
-// (k_radix_ghist).  A pass takes tiles of SORT_TILE keys in ticket order,
-// ranks them per digit inside the block (warp multisplit), publishes the
-// tile's digit counts, finds the counts of all earlier tiles by decoupled
-// look-back (each earlier tile's aggregate, or the inclusive prefix where one
-// is published), publishes its own inclusive prefix and scatters the tile in
-// digit runs.  The look-back waits are bounded: past the limit the pass sets
-// TTS_STATUS_TIMEOUT and goes on (its output is then undefined).
+// K5: per-tile depth sort.  Within a tile the keys are ordered by the mean
+// depth bits and, for equal depths, by slot (that is, survivor order): the
+// order of a stable sort of the (tile, depth) keys in slot order.  Composite
+// keys are distinct, so any correct sort gives that one order.
+//
+// A merge sort per list: each thread sorts K keys in registers, then runs of
+// K, 2K, ... are merged pairwise through shared memory (each thread finds
+// where its K outputs start on the merge path by binary search, then merges
+// them sequentially).  The tile scan lists the tiles of each length class;
+// a class goes to a warp (<= 256 keys), 256 threads (<= 2,048), 512 threads
+// (<= 4,096), 1024 threads (<= 8,192) or 1024 threads with 16 keys each
+// (<= 16,384; longer lists: sorted runs of 16,384 merged in global memory).  Padding keys are all ones (no real key: the depth bits of
+// a kept slot are those of a finite positive float).
 // ---------------------------------------------------------------------------
-constexpr unsigned long long LB_AGG = 1ull << 32;      // flag bits above the 32-bit count
-constexpr unsigned long long LB_PREFIX = 2ull << 32;
-constexpr long long LB_SPIN_LIMIT = 1ll << 22;
-
-__device__ __forceinline__ unsigned long long lb_word(unsigned tag, unsigned long long flag,
-                                                      unsigned value) {
-  return ((unsigned long long)tag << 34) | flag | value;
+template <int NT>
+__device__ __forceinline__ void group_sync() {
+  if constexpr (NT == 32) __syncwarp();
+  else __syncthreads();
 }
 
-// grid: sort_blocks; each block adds its keys' digits of every live pass
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_ghist(const Batch* __restrict__ B) {
-  const Counters* c = B->ctr;
-  const int np = c->n_passes;
-  if (np == 0) return;
-  const long long n = c->n_keys_used;
-  constexpr int NH = SORT_THREADS / 64;   // one histogram per two warps (32 KB)
-  __shared__ unsigned h[NH][MAX_PASSES][RADIX];
-  for (int i = threadIdx.x; i < NH * MAX_PASSES * RADIX; i += SORT_THREADS) (&h[0][0][0])[i] = 0;
-  __syncthreads();
-  const unsigned long long* src = B->keys[0];
-  const int wid = threadIdx.x >> 6;
-  for (long long i = blockIdx.x * (long long)SORT_THREADS + threadIdx.x; i < n;
-       i += (long long)gridDim.x * SORT_THREADS) {
-    const unsigned long long k = src[i];
-    for (int p = 0; p < np; ++p) atomicAdd(&h[wid][p][(unsigned)(k >> (p * RADIX_BITS)) & (RADIX - 1)], 1u);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < np * RADIX; i += SORT_THREADS) {
-    unsigned t = 0;
+// Shared-memory slot of key e: one pad key after every 16, so that the
+// blocked accesses (thread t, key t K + q) of a half warp meet 16 distinct
+// 8-byte bank pairs.
+__device__ __forceinline__ int spad(int e) { return e + (e >> 4); }
+template <int N>
+__host__ __device__ constexpr int spad_size() { return N + N / 16; }
+
+// Sorts the NT * K keys held K per thread (any arrangement) ascending; on
+// return thread tid holds outputs [tid K, tid K + K).  s: spad_size(NT * K)
+// keys of shared memory.
+template <int NT, int K>
+__device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], unsigned long long* s,
+                                                 int tid) {
 #pragma unroll
-    for (int w = 0; w < NH; ++w) t += (&h[w][0][0])[i];
-    if (t) atomicAdd(&B->ghist[i], t);
+  for (int r = 0; r < K; ++r) {       // odd-even transposition network
+#pragma unroll
+    for (int i = r & 1; i + 1 < K; i += 2) {
+      const unsigned long long x = k[i], y = k[i + 1];
+      const bool sw = y < x;
+      k[i] = sw ? y : x;
+      k[i + 1] = sw ? x : y;
+    }
+  }
+  for (int run = K; run < NT * K; run <<= 1) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) s[spad(tid * K + i)] = k[i];
+    group_sync<NT>();
+    const int d0 = tid * K;
+    const int start = d0 & ~(2 * run - 1);
+    const int d = d0 - start;
+    const int a0 = start, b0 = start + run;
+    int lo = max(0, d - run), hi = min(d, run);
+    while (lo < hi) {                   // first i with b[d-1-i] < a[i]
+      const int mid = (lo + hi) >> 1;
+      if (!(s[spad(b0 + d - 1 - mid)] < s[spad(a0 + mid)])) lo = mid + 1;
+      else hi = mid;
+    }
+    int i = lo, j = d - lo;
+    unsigned long long va = (i < run) ? s[spad(a0 + i)] : ~0ull;
+    unsigned long long vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const bool ta = (i < run) && (j >= run || !(vb < va));
+      k[q] = ta ? va : vb;
+      if (ta) {
+        ++i;
+        va = (i < run) ? s[spad(a0 + i)] : ~0ull;
+      } else {
+        ++j;
+        vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
+      }
+    }
+    group_sync<NT>();
   }
 }
 
-// grid: sort_tiles (the key capacity's tiles); blocks past the live tiles exit
-__global__ void __launch_bounds__(SORT_THREADS) k_radix_onesweep(const Batch* __restrict__ B, int pass) {
+// Loads in[0, n) (n <= NT * K, padded), sorts, and writes the slots of the
+// sorted keys to out[0, n) (through shared memory, so the stores coalesce)
+// or, when keys_out is given, the sorted keys there.
+template <int NT, int K>
+__device__ __forceinline__ void group_sort_list(const unsigned long long* in, int n, unsigned* out,
+                                                unsigned long long* keys_out, unsigned long long* s,
+                                                int tid) {
+  unsigned long long k[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int i = q * NT + tid;
+    k[q] = (i < n) ? in[i] : ~0ull;
+  }
+  group_merge_sort<NT, K>(k, s, tid);
+#pragma unroll
+  for (int q = 0; q < K; ++q) s[spad(tid * K + q)] = k[q];
+  group_sync<NT>();
+  for (int i = tid; i < n; i += NT) {
+    if (keys_out) keys_out[i] = s[spad(i)];
+    else out[i] = (unsigned)s[spad(i)];
+  }
+  group_sync<NT>();
+}
+
+constexpr int TSORT_K = 8;
+
+// dynamic shared memory of a class 1..3 block of nt threads
+constexpr int tsort_smem(int nt) { return (nt * TSORT_K + nt * TSORT_K / 16) * 8; }
+
+// Class 0, lists of 1..256 keys: one warp per list, 8 warps per block.
+__global__ void __launch_bounds__(256) k_tile_sort_warp(const Batch* __restrict__ B) {
+  __shared__ unsigned long long s[8][spad_size<32 * TSORT_K>()];
+  const Counters* c = B->ctr;
+  if (c->n_keys_used == 0) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nc = c->class_n[0];
+  for (int e = blockIdx.x * 8 + w; e < nc; e += gridDim.x * 8) {
+    const int2 r = B->ranges[B->tile_class[e]];
+    const int n = r.y - r.x;
+    if (n == 1) {
+      if (lane == 0) B->vals[r.x] = (unsigned)B->keys[1][r.x];
+      continue;
+    }
+    group_sort_list<32, TSORT_K>(B->keys[1] + r.x, n, B->vals + r.x, nullptr, s[w], lane);
+  }
+}
+
+// Classes 1..3: one block of NT threads per list of up to NT * K keys
+// (NT * K keys of dynamic shared memory).
+template <int NT, int K, int CLS>
+__global__ void __launch_bounds__(NT) k_tile_sort_block(const Batch* __restrict__ B) {
+  extern __shared__ unsigned long long sb[];
+  const Counters* c = B->ctr;
+  if (c->n_keys_used == 0) return;
+  const int nc = c->class_n[CLS];
+  const int* list = B->tile_class + (size_t)CLS * B->total_tiles;
+  for (int e = blockIdx.x; e < nc; e += gridDim.x) {
+    const int2 r = B->ranges[list[e]];
+    group_sort_list<NT, K>(B->keys[1] + r.x, r.y - r.x, B->vals + r.x, nullptr, sb, threadIdx.x);
+  }
+}
+
+// Merge of the sorted runs a[0, la) and b[0, lb) into o[0, la + lb) by all
+// threads of the block (merge path in global memory).
+template <int NT>
+__device__ void block_merge(const unsigned long long* a, int la, const unsigned long long* b, int lb,
+                            unsigned long long* o) {
+  const int total = la + lb;
+  const int per = (total + NT - 1) / NT;
+  const int d0 = threadIdx.x * per;
+  if (d0 >= total) return;
+  const int d1 = min(d0 + per, total);
+  int lo = max(0, d0 - lb), hi = min(d0, la);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (!(b[d0 - 1 - mid] < a[mid])) lo = mid + 1;
+    else hi = mid;
+  }
+  int i = lo, j = d0 - lo;
+  for (int d = d0; d < d1; ++d) {
+    const bool take_a = (i < la) && (j >= lb || !(b[j] < a[i]));
+    o[d] = take_a ? a[i++] : b[j++];
+  }
+}
+
+constexpr int TSORT_L_K = TSORT_L_CAP / TSORT_L_THREADS;
+
+// Class 4, lists longer than 8,192 keys; persistent blocks of 1024 threads.
+// Up to TSORT_L_CAP keys: one on-chip sort.  Longer: sorted runs of
+// TSORT_L_CAP keys, then block merges of run pairs between keys[1] and
+// keys[0] (the block owns the tile's range in both).
+__global__ void __launch_bounds__(TSORT_L_THREADS) k_tile_sort_long(const Batch* __restrict__ B) {
+  extern __shared__ unsigned long long sl[];
   Counters* c = B->ctr;
-  if (pass >= c->n_passes) return;
-  const long long n = c->n_keys_used;
-  const int ntiles = (int)((n + SORT_TILE - 1) / SORT_TILE);
-  constexpr int NW = SORT_THREADS / 32;
-  __shared__ int s_tile;
-  __shared__ unsigned dbase[RADIX];
-  __shared__ unsigned wcnt[NW][RADIX];
-  __shared__ unsigned tstart[RADIX];
-  __shared__ unsigned long long sk[SORT_TILE];
-  __shared__ unsigned sv[SORT_TILE];
-  if (threadIdx.x == 0) s_tile = (int)atomicAdd(&c->sort_ticket[pass], 1u);
-  for (int i = threadIdx.x; i < NW * RADIX; i += SORT_THREADS) (&wcnt[0][0])[i] = 0;
-  __syncthreads();
-  const int tile = s_tile;
-  if (tile >= ntiles) return;
-  const unsigned tag = (c->sort_epoch * MAX_PASSES + pass) % 0xffffu + 1u;
-  const long long t0 = (long long)tile * SORT_TILE;
-  const int tn = (int)min((long long)SORT_TILE, n - t0);
-  const unsigned long long* ksrc = B->keys[pass & 1];
-  const unsigned* vsrc = B->vals[pass & 1];
-  unsigned long long* kdst = B->keys[(pass + 1) & 1];
-  unsigned* vdst = B->vals[(pass + 1) & 1];
-  const int sh = pass * RADIX_BITS;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned long long k[SORT_KPT];
-  unsigned val[SORT_KPT], dg[SORT_KPT], off[SORT_KPT];
-#pragma unroll
-  for (int j = 0; j < SORT_KPT; ++j) {
-    const int i = wid * (32 * SORT_KPT) + j * 32 + lane;
-    if (i < tn) {
-      k[j] = ksrc[t0 + i];
-      val[j] = vsrc[t0 + i];
-      dg[j] = (unsigned)(k[j] >> sh) & (RADIX - 1);
-    } else {
-      dg[j] = RADIX;  // sentinel: not scattered
+  if (c->n_keys_used == 0) return;
+  const int nc = c->class_n[4];
+  const int* list = B->tile_class + 4 * (size_t)B->total_tiles;
+  for (int e = blockIdx.x; e < nc; e += gridDim.x) {
+    const int2 r = B->ranges[list[e]];
+    const int n = r.y - r.x;
+    unsigned long long* A = B->keys[1] + r.x;
+    if (n <= TSORT_L_CAP) {
+      group_sort_list<TSORT_L_THREADS, TSORT_L_K>(A, n, B->vals + r.x, nullptr, sl, threadIdx.x);
+      continue;
     }
-  }
-  // ranks inside each warp (warp multisplit), digit counts per warp
-#pragma unroll
-  for (int j = 0; j < SORT_KPT; ++j) {
-    const unsigned peers = __match_any_sync(0xffffffffu, dg[j]);
-    const unsigned rank = __popc(peers & lt_mask);
-    const unsigned d = dg[j] & (RADIX - 1);
-    const unsigned before = (dg[j] < RADIX) ? wcnt[wid][d] : 0u;
-    __syncwarp();
-    if (dg[j] < RADIX && rank == 0) wcnt[wid][d] = before + __popc(peers);
-    __syncwarp();
-    off[j] = before + rank;
-  }
-  __syncthreads();
-  {
-    const int d = threadIdx.x;   // SORT_THREADS == RADIX
-    unsigned run = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      const unsigned x = wcnt[w][d];
-      wcnt[w][d] = run;
-      run += x;
-    }
-    unsigned t;
-    tstart[d] = block_excl_scan<unsigned, SORT_THREADS>(run, &t);
-    // publish this tile's count of digit d, then look back over the earlier
-    // tiles for their counts
-    unsigned long long* look = B->look + (size_t)tile * RADIX + d;
-    if (tile > 0) atomicExch(look, lb_word(tag, LB_AGG, run));
-    unsigned excl = 0;
-    bool timed_out = false;
-    for (int tp = tile - 1; tp >= 0;) {
-      const unsigned long long w =
-          *reinterpret_cast<volatile unsigned long long*>(B->look + (size_t)tp * RADIX + d);
-      if ((unsigned)(w >> 34) == tag && (w & (LB_AGG | LB_PREFIX))) {
-        excl += (unsigned)w;
-        if (w & LB_PREFIX) break;
-        --tp;
-        continue;
+    if (threadIdx.x == 0) atomicAdd(&c->long_lists, 1);
+    for (int c0 = 0; c0 < n; c0 += TSORT_L_CAP)
+      group_sort_list<TSORT_L_THREADS, TSORT_L_K>(A + c0, min(TSORT_L_CAP, n - c0), nullptr, A + c0,
+                                                  sl, threadIdx.x);
+    __syncthreads();
+    unsigned long long* src = A;
+    unsigned long long* dst = B->keys[0] + r.x;
+    for (int w = TSORT_L_CAP; w < n; w <<= 1) {
+      for (int lo = 0; lo < n; lo += 2 * w) {
+        const int mid = min(lo + w, n), hi = min(lo + 2 * w, n);
+        block_merge<TSORT_L_THREADS>(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
       }
-      long long spins = 0;
-      while (true) {   // the earlier tile has not published yet: bounded wait
-        const unsigned long long w2 =
-            *reinterpret_cast<volatile unsigned long long*>(B->look + (size_t)tp * RADIX + d);
-        if ((unsigned)(w2 >> 34) == tag && (w2 & (LB_AGG | LB_PREFIX))) break;
-        if (++spins > LB_SPIN_LIMIT) {
-          timed_out = true;
-          break;
-        }
-      }
-      if (timed_out) break;
+      __syncthreads();
+      unsigned long long* x = src;
+      src = dst;
+      dst = x;
     }
-    if (timed_out) set_status(c, TTS_STATUS_TIMEOUT);
-    atomicExch(look, lb_word(tag, LB_PREFIX, excl + run));
-    // digit base: all smaller digits of the whole pass, then the earlier tiles
-    const unsigned g = B->ghist[pass * RADIX + d];
-    unsigned tg;
-    dbase[d] = block_excl_scan<unsigned, SORT_THREADS>(g, &tg) + excl;
-  }
-  __syncthreads();
-  // stage the tile in digit order, then write each digit's run contiguously
-#pragma unroll
-  for (int j = 0; j < SORT_KPT; ++j) {
-    if (dg[j] < RADIX) {
-      const unsigned lp = tstart[dg[j]] + wcnt[wid][dg[j]] + off[j];
-      sk[lp] = k[j];
-      sv[lp] = val[j];
-    }
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < tn; q += SORT_THREADS) {
-    const unsigned long long key = sk[q];
-    const unsigned d = (unsigned)(key >> sh) & (RADIX - 1);
-    const unsigned pos = dbase[d] + (unsigned)q - tstart[d];
-    kdst[pos] = key;
-    vdst[pos] = sv[q];
+    for (int i = threadIdx.x; i < n; i += TSORT_L_THREADS) B->vals[r.x + i] = (unsigned)src[i];
+    __syncthreads();
   }
 }
 
-// K5: per-tile [start, end) from the sorted keys.
-__global__ void k_tile_ranges(const Batch* __restrict__ B) {
+// Debug view of the sorted lists as 64-bit keys (global tile << depth_bits |
+// zbits - zmin_bits), rebuilt into keys[0] from the ranges and the slots'
+// depth bits.  Not part of a render.
+__global__ void k_debug_keys(const Batch* __restrict__ B) {
   const Counters* c = B->ctr;
-  const long long n = c->n_keys_used;
+  if (c->n_keys_used == 0) return;
   const int db = c->depth_bits;
-  const unsigned long long* keys = B->keys[c->n_passes & 1];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int t = (int)(keys[i] >> db);
-    if (i == 0 || (int)(keys[i - 1] >> db) != t) B->ranges[t].x = (int)i;
-    if (i == n - 1 || (int)(keys[i + 1] >> db) != t) B->ranges[t].y = (int)(i + 1);
+  const unsigned zmin = c->zmin_bits;
+  for (int t = blockIdx.x; t < B->total_tiles; t += gridDim.x) {
+    const int2 r = B->ranges[t];
+    for (int i = r.x + threadIdx.x; i < r.y; i += blockDim.x)
+      B->keys[0][i] = ((unsigned long long)t << db) | (unsigned long long)(B->rec_z[B->vals[i]] - zmin);
   }
 }
 
@@ -623,18 +750,6 @@ __global__ void k_tile_ranges(const Batch* __restrict__ B) {
 // otherwise bound its duration).  Units (tile, segment) are ordered by
 // decreasing work (bucketed by bit length), so the longest start first; the
 // order inside a bucket is arbitrary.
-// Warp-level exclusive scan of v (all lanes), returning the warp total.
-__device__ __forceinline__ int warp_excl_scan(int v, int* total) {
-  const int lane = threadIdx.x & 31;
-  int inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  *total = __shfl_sync(0xffffffffu, inc, 31);
-  return inc - v;
-}
 
 constexpr int WL_BUCKETS = 34;      // bit length of a work amount (0..32), 33: unused
 constexpr int WL_THREADS = 256;     // one tile per thread
@@ -745,21 +860,42 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   return 3;
 }
 
+static int binning_setup();
+
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
+  binning_setup();
   k_fwd_reset<<<64, 256, 0, st>>>(dB);
   dim3 g(P.max_pp_chunks, P.n_views);
   k_preprocess<<<g, PP_THREADS, 0, st>>>(dB);
-  k_preprocess_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
-  k_duplicate<<<g, PP_THREADS, 0, st>>>(dB);
-  k_radix_ghist<<<P.sort_blocks, SORT_THREADS, 0, st>>>(dB);
-  for (int p = 0; p < P.max_passes; ++p) {
-    k_radix_onesweep<<<P.sort_tiles, SORT_THREADS, 0, st>>>(dB, p);
-  }
-  k_tile_ranges<<<P.range_blocks, 256, 0, st>>>(dB);
+  k_tile_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
+  k_place<<<g, PP_THREADS, 0, st>>>(dB);
+  k_tile_sort_warp<<<P.tsort_blocks[0], 256, 0, st>>>(dB);
+  k_tile_sort_block<256, TSORT_K, 1><<<P.tsort_blocks[1], 256, tsort_smem(256), st>>>(dB);
+  k_tile_sort_block<512, TSORT_K, 2><<<P.tsort_blocks[2], 512, tsort_smem(512), st>>>(dB);
+  k_tile_sort_block<1024, TSORT_K, 3><<<P.tsort_blocks[3], 1024, tsort_smem(1024), st>>>(dB);
+  k_tile_sort_long<<<P.tsort_blocks[4], TSORT_L_THREADS, TSORT_L_SMEM, st>>>(dB);
   k_worklist_count<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
   k_worklist_scan<<<1, 17 * 32, 0, st>>>(dB, P.wl_blocks);
   k_worklist_place<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
-  return 9 + P.max_passes;
+  return 12;
+}
+
+// Opt-in of the long-list sort to its dynamic shared memory (once per
+// process; a failure shows as the launch error of that kernel).
+static int binning_setup() {
+  static int rc = -1;
+  if (rc < 0)
+    rc = (cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               TSORT_L_SMEM) == cudaSuccess &&
+          cudaFuncSetAttribute(k_tile_sort_block<1024, TSORT_K, 3>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               tsort_smem(1024)) == cudaSuccess) ? 0 : 1;
+  return rc;
+}
+
+int launch_debug_keys(const HostPlan& P, const Batch* dB, cudaStream_t st) {
+  k_debug_keys<<<P.tsort_blocks[1], 256, 0, st>>>(dB);
+  return 1;
 }
 
 }  // namespace tts

@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
   __shared__ int sidx[WPB][32];
   const int wid = threadIdx.x >> 5;
   Counters* c = B->ctr;
-  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
-  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
-  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   float4* __restrict__ rgrad = B->rec_grad;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
-  const unsigned* __restrict__ vals = B->vals[c->n_passes & 1];
+  const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   float4* __restrict__ rgrad = B->rec_grad;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;

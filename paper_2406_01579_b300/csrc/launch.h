@@ -10,9 +10,8 @@ namespace tts {
 struct HostPlan {
   int n_scenes, n_views;
   int max_pf_chunks, max_pp_chunks;
-  int sort_blocks, max_passes, sort_tiles;
+  int tsort_blocks[TSORT_CLASSES];   // persistent grid of each depth-sort class
   int wl_blocks;
-  int range_blocks;
   int total_tiles;
   int tile;
   int window;
@@ -32,6 +31,7 @@ struct GradOut {
 // Each launcher returns the number of kernels it launched.
 int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st);
+int launch_debug_keys(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_bounds(const HostPlan& P, const Batch* dB, float* aabb, cudaStream_t st);
 int launch_fit_grid(const float* V_in, long long N, const float lo[3], const float hi[3],
                     const float* aabb, float pad, float* V_out, cudaStream_t st);

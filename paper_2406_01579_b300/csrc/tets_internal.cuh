@@ -12,15 +12,16 @@ namespace tts {
 
 constexpr int PF_CHUNK = 4096;      // tets per pre-filter block
 constexpr int PF_THREADS = 256;
-constexpr int PP_CHUNK = 512;       // survivors per preprocess / duplicate block
+constexpr int PP_CHUNK = 512;       // survivors per preprocess / key placement block
 constexpr int PP_THREADS = 256;
-constexpr int RADIX_BITS = 8;
-constexpr int RADIX = 1 << RADIX_BITS;
-constexpr int MAX_PASSES = 8;       // 64-bit keys
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_KPT = 8;         // keys per thread per tile
-constexpr int SORT_TILE = SORT_THREADS * SORT_KPT;
 constexpr int SCAN_THREADS = 1024;
+// Per-tile depth sort of the longest lists: a 1024-thread block with
+// TSORT_L_CAP keys of dynamic shared memory (lists longer than that: sorted
+// runs of TSORT_L_CAP keys merged in global memory).
+constexpr int TSORT_L_THREADS = 1024;
+constexpr int TSORT_CLASSES = 5;    // list lengths (0,256] (256,2K] (2K,4K] (4K,8K] (8K,...)
+constexpr int TSORT_L_CAP = 16384;
+constexpr int TSORT_L_SMEM = (TSORT_L_CAP + TSORT_L_CAP / 16) * 8;   // one pad key per 16
 
 // Counters at the start of the workspace (after the descriptor).
 struct Counters {
@@ -29,17 +30,15 @@ struct Counters {
   unsigned int zmax_bits;
   int depth_bits;           // bits of (zbits - zmin_bits)
   int total_bits;           // depth_bits + tile_bits
-  int n_passes;             // radix passes actually needed
+  int long_lists;           // tiles sorted by the global-memory merge
   long long n_keys;         // keys produced (may exceed capacity: then overflow)
   long long n_keys_used;    // keys the sort and blend see (0 on overflow)
   int n_surv[TTS_MAX_SCENES];
   unsigned int work_fwd, work_bwd;      // persistent blend work queues
   unsigned int done_fwd, done_bwd;      // warps finished (last one resets)
   int n_units;              // blend work units (tile segments) of the last binning
-  unsigned int sort_epoch;  // binnings so far (tags the look-back words of each pass)
-  unsigned int sort_ticket[MAX_PASSES];   // next tile of each radix pass
   int seg_total;            // checkpoint slots handed out by the work-list builder
-  int pad[1];
+  int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
 };
 
 struct SceneD {
@@ -65,21 +64,19 @@ struct ViewD {
   int tile_base;            // first global tile id
   long long pix_base;       // first output pixel
   long long rec_base;       // first record slot
-  int pp_chunk_base;        // first preprocess block-sum slot
-  int pp_chunks;
+  int pp_chunks;            // preprocess / key placement blocks
 };
 
 struct Batch {
   int n_scenes, n_views;
   int total_tiles, tile_bits;
-  int pf_chunks_total, pp_chunks_total;
+  int pf_chunks_total;
   int max_pf_chunks, max_pp_chunks;
   float s, prefilter_thresh, alpha_skip, alpha_cap, t_eps;
   int tile, flags;
   int resort_window;
   int seg_len;              // list entries per blend work unit (0: no splitting)
   int seg_cap;              // segment slots of the split-tile checkpoints
-  int sort_blocks;
   long long key_cap;
   long long total_pixels;
   long long total_slots;
@@ -94,12 +91,11 @@ struct Batch {
   int4* rec_rect;           // [slots] tile rect (tx0, tx1, ty0, ty1)
   float4* rec;              // [slots * 6]
   float4* rec_grad;         // [slots * 6]
-  long long* pp_blocksum;   // [pp_chunks_total]
-  unsigned long long* keys[2];
-  unsigned int* vals[2];
-  unsigned int* ghist;      // [MAX_PASSES * RADIX] global digit counts of the keys
-  unsigned long long* look; // [sort_tiles * RADIX] look-back words of the running pass
-  int sort_tiles;           // tiles of SORT_TILE keys the key capacity holds
+  unsigned long long* keys[2];   // [key_cap] each: [1] (zbits << 32 | slot) bucketed by
+                                 // tile; [0] merge scratch, debug keys on request
+  unsigned int* vals;       // [key_cap] record slot of each key, sorted per tile
+  int* tile_cnt;            // [total_tiles] keys per tile, then the placement cursor
+  int* tile_class;          // [TSORT_CLASSES * total_tiles] non-empty tiles by list length
   int2* ranges;             // [total_tiles]
   int2* worklist;           // [units] (tile, segment), longest first
   int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)

@@ -13,7 +13,7 @@ import oracle
 import synth
 from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors
 from parity import (GRAD_TOL, IMG_TOL, compare_images, compare_keys, gpu_run, grad_rel_err,
-                    masked_upstream, oracle_run, to_dev)
+                    masked_upstream, oracle_params, oracle_run, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -283,16 +283,38 @@ def test_torus64_gradients(torus64):
         assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
 
 
+@pytest.mark.parametrize("res,tile,lo,hi", [(64, 32, 16385, None), (256, 32, 2049, 16384),
+                                            (96, 8, 1, 2048)])
+def test_long_tile_lists(res, tile, lo, hi):
+    """Tile lists of every length class of the per-tile depth sort: up to
+    2,048 keys (256-thread on-chip sort), 2,049..16,384 (one 1024-thread
+    on-chip sort) and longer (sorted runs of 16,384 merged in global memory).
+    The 64^3 torus seen at a low resolution piles many tets into each tile.
+    Keys, values and ranges bit for bit against the oracle's sort."""
+    sc = synth.scene_torus64(res=res)
+    p = Params(s=60.0, tile=tile)
+    cam = sc.cams[0]
+    gpu = gpu_run([sc], [(cam, 0)], p, lists=True)
+    surv, amb_t, _ = oracle.prefilter(sc.T, sc.f, oracle_params(p))
+    orc = {"surv": surv, "amb_tets": amb_t, "bins": oracle.bin_view(surv, sc.T, sc.V, cam, tile)}
+    compare_keys(gpu, orc)
+    r = gpu["lists"]["ranges"]
+    lens = r[:, 1] - r[:, 0]
+    assert ((lens >= lo) & (lens <= (hi or lens.max()))).sum() >= 1, lens.max()
+    assert (gpu["info"].long_lists > 0) == (lens.max() > 16384)
+
+
 @pytest.fixture(scope="module")
 def spheres128():
     return synth.scene_spheres128()
 
 
-def test_spheres128_bench_workload(spheres128):
+@pytest.mark.parametrize("tile", [8, 16])
+def test_spheres128_bench_workload(spheres128, tile):
     """The benchmark's configuration: 128^3 grid, 4 views at 512^2, s = 175,
-    one batched call.  Keys are compared bit for bit per view; images pixel
-    by pixel."""
-    p = Params(s=175.0, tile=16)
+    one batched call (tile 8 is the size the benchmark's autotuner picks).
+    Keys are compared bit for bit per view; images pixel by pixel."""
+    p = Params(s=175.0, tile=tile)
     sc = spheres128
     views = [(c, 0) for c in sc.cams]
     gpu = gpu_run([sc], views, p, lists=True)
@@ -301,7 +323,7 @@ def test_spheres128_bench_workload(spheres128):
     keys = lists["keys"].view(np.uint64)
     db = lists["depth_bits"]
     gtile = (keys >> np.uint64(db)).astype(np.int64)
-    tiles_per_view = (512 // 16) ** 2
+    tiles_per_view = (512 // tile) ** 2
     for vi, cam in enumerate(sc.cams):
         orc = oracle_run(sc, cam, p)
         sel = (gtile >= vi * tiles_per_view) & (gtile < (vi + 1) * tiles_per_view)
