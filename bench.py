@@ -41,7 +41,7 @@ BWD_FLOP_PER_FRAG = 150
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "f03d76669c909381": {16: {"blend_fwd": 194834944, "blend_bwd": 241210112}},
+    "a855f4c8816633ff": {8: {"blend_fwd": 124839424, "blend_bwd": 225387008}},
 }
 
 
