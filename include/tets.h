@@ -163,7 +163,8 @@ typedef struct {
   int64_t n_surv[TTS_MAX_SCENES]; /* survivors per scene of the last prepare */
   int32_t sort_bits;        /* bits of the (tile, depth) keys of the last forward */
   int32_t long_lists;       /* tiles of the last forward whose list exceeded the
-                               on-chip sort (sorted by merging runs in global memory) */
+                               on-chip sort of 4,096 keys (sorted by merging runs
+                               in global memory) */
   int32_t blend_units;      /* blend work units (tile lists and list segments) */
   int32_t reserved;
 } tts_info;

@@ -257,11 +257,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.n_views = b->n_views;
   H.max_pf_chunks = max_pf;
   H.max_pp_chunks = max_pp;
-  H.tsort_blocks[0] = std::max(1, std::min((tiles + 7) / 8, 8 * sm_count()));
-  H.tsort_blocks[1] = std::max(1, std::min(tiles, 8 * sm_count()));
-  H.tsort_blocks[2] = std::max(1, std::min(tiles, 4 * sm_count()));
-  H.tsort_blocks[3] = std::max(1, std::min(tiles, 2 * sm_count()));
-  H.tsort_blocks[4] = std::max(1, std::min(tiles, sm_count()));
+  H.tsort_blocks = std::max(1, std::min(tiles, 3 * sm_count()));
   H.wl_blocks = wl_blocks;
   H.total_tiles = tiles;
   H.tile = pr.tile;

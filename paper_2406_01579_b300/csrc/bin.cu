@@ -72,6 +72,7 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->done_fwd = c->done_bwd = 0u;
     c->seg_total = 0;
     for (int q = 0; q < TSORT_CLASSES; ++q) c->class_n[q] = 0;
+    for (int q = 0; q < 3; ++q) c->sort_q[q] = 0;
   }
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
     B->tile_cnt[t] = 0;
@@ -402,9 +403,10 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
 // ---------------------------------------------------------------------------
 constexpr int TS_ITEMS = 16;
 
-// List-length class of the per-tile depth sort (see K5).
+// List-length class of the per-tile depth sort (see K5): up to 256 keys,
+// 2,048, 4,096, more.
 __device__ __forceinline__ int tsort_class(int n) {
-  return n <= 256 ? 0 : n <= 2048 ? 1 : n <= 4096 ? 2 : n <= 8192 ? 3 : 4;
+  return n <= 256 ? 0 : n <= 2048 ? 1 : n <= 4096 ? 2 : 3;
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const Batch* __restrict__ B) {
@@ -531,16 +533,31 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
 // A merge sort per list: each thread sorts K keys in registers, then runs of
 // K, 2K, ... are merged pairwise through shared memory (each thread finds
 // where its K outputs start on the merge path by binary search, then merges
-// them sequentially).  The tile scan lists the tiles of each length class;
-// a class goes to a warp (<= 256 keys), 256 threads (<= 2,048), 512 threads
-// (<= 4,096), 1024 threads (<= 8,192) or 1024 threads with 16 keys each
-// (<= 16,384; longer lists: sorted runs of 16,384 merged in global memory).  Padding keys are all ones (no real key: the depth bits of
-// a kept slot are those of a finite positive float).
+// them sequentially).  Padding keys are all ones (no real key: the depth
+// bits of a kept slot are those of a finite positive float).
+//
+// One persistent kernel of 512-thread blocks sorts every list, longest
+// first: the tile scan lists the tiles by length class, and the blocks take
+// (1) lists of more than 2,048 keys, one per block (more than 4,096: sorted
+// runs of 4,096 merged in global memory), then (2) lists of 257..2,048
+// keys, one per half block, then (3) lists of up to 256 keys, one per warp,
+// each from its own device queue.
 // ---------------------------------------------------------------------------
+constexpr int TSORT_NT = 512;
+
+// Barrier of a group of NT threads: the warp, the whole block, or (NT = 256)
+// the named barrier bar (1 or 2) of a half block.
 template <int NT>
-__device__ __forceinline__ void group_sync() {
-  if constexpr (NT == 32) __syncwarp();
-  else __syncthreads();
+__device__ __forceinline__ void group_sync(int bar) {
+  if constexpr (NT == 32) {
+    __syncwarp();
+  } else if constexpr (NT == TSORT_NT) {
+    __syncthreads();
+  } else if (bar == 1) {
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+  } else {
+    asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+  }
 }
 
 // Shared-memory slot of key e: one pad key after every 16, so that the
@@ -555,7 +572,7 @@ __host__ __device__ constexpr int spad_size() { return N + N / 16; }
 // keys of shared memory.
 template <int NT, int K>
 __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], unsigned long long* s,
-                                                 int tid) {
+                                                 int tid, int bar) {
 #pragma unroll
   for (int r = 0; r < K; ++r) {       // odd-even transposition network
 #pragma unroll
@@ -569,7 +586,7 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
   for (int run = K; run < NT * K; run <<= 1) {
 #pragma unroll
     for (int i = 0; i < K; ++i) s[spad(tid * K + i)] = k[i];
-    group_sync<NT>();
+    group_sync<NT>(bar);
     const int d0 = tid * K;
     const int start = d0 & ~(2 * run - 1);
     const int d = d0 - start;
@@ -595,7 +612,7 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
         vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
       }
     }
-    group_sync<NT>();
+    group_sync<NT>(bar);
   }
 }
 
@@ -605,61 +622,28 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
 template <int NT, int K>
 __device__ __forceinline__ void group_sort_list(const unsigned long long* in, int n, unsigned* out,
                                                 unsigned long long* keys_out, unsigned long long* s,
-                                                int tid) {
+                                                int tid, int bar) {
   unsigned long long k[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     const int i = q * NT + tid;
     k[q] = (i < n) ? in[i] : ~0ull;
   }
-  group_merge_sort<NT, K>(k, s, tid);
+  group_merge_sort<NT, K>(k, s, tid, bar);
 #pragma unroll
   for (int q = 0; q < K; ++q) s[spad(tid * K + q)] = k[q];
-  group_sync<NT>();
+  group_sync<NT>(bar);
   for (int i = tid; i < n; i += NT) {
     if (keys_out) keys_out[i] = s[spad(i)];
     else out[i] = (unsigned)s[spad(i)];
   }
-  group_sync<NT>();
+  group_sync<NT>(bar);
 }
 
 constexpr int TSORT_K = 8;
-
-// dynamic shared memory of a class 1..3 block of nt threads
-constexpr int tsort_smem(int nt) { return (nt * TSORT_K + nt * TSORT_K / 16) * 8; }
-
-// Class 0, lists of 1..256 keys: one warp per list, 8 warps per block.
-__global__ void __launch_bounds__(256) k_tile_sort_warp(const Batch* __restrict__ B) {
-  __shared__ unsigned long long s[8][spad_size<32 * TSORT_K>()];
-  const Counters* c = B->ctr;
-  if (c->n_keys_used == 0) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nc = c->class_n[0];
-  for (int e = blockIdx.x * 8 + w; e < nc; e += gridDim.x * 8) {
-    const int2 r = B->ranges[B->tile_class[e]];
-    const int n = r.y - r.x;
-    if (n == 1) {
-      if (lane == 0) B->vals[r.x] = (unsigned)B->keys[1][r.x];
-      continue;
-    }
-    group_sort_list<32, TSORT_K>(B->keys[1] + r.x, n, B->vals + r.x, nullptr, s[w], lane);
-  }
-}
-
-// Classes 1..3: one block of NT threads per list of up to NT * K keys
-// (NT * K keys of dynamic shared memory).
-template <int NT, int K, int CLS>
-__global__ void __launch_bounds__(NT) k_tile_sort_block(const Batch* __restrict__ B) {
-  extern __shared__ unsigned long long sb[];
-  const Counters* c = B->ctr;
-  if (c->n_keys_used == 0) return;
-  const int nc = c->class_n[CLS];
-  const int* list = B->tile_class + (size_t)CLS * B->total_tiles;
-  for (int e = blockIdx.x; e < nc; e += gridDim.x) {
-    const int2 r = B->ranges[list[e]];
-    group_sort_list<NT, K>(B->keys[1] + r.x, r.y - r.x, B->vals + r.x, nullptr, sb, threadIdx.x);
-  }
-}
+constexpr int TSORT_BLOCK_CAP = TSORT_NT * TSORT_K;        // 4,096
+constexpr int TSORT_HALF_CAP = TSORT_NT / 2 * TSORT_K;     // 2,048
+constexpr int TSORT_WARP_CAP = 32 * TSORT_K;               // 256
 
 // Merge of the sorted runs a[0, la) and b[0, lb) into o[0, la + lb) by all
 // threads of the block (merge path in global memory).
@@ -684,45 +668,84 @@ __device__ void block_merge(const unsigned long long* a, int la, const unsigned 
   }
 }
 
-constexpr int TSORT_L_K = TSORT_L_CAP / TSORT_L_THREADS;
+// A list of more than TSORT_BLOCK_CAP keys, by the whole block: sorted runs
+// of TSORT_BLOCK_CAP keys, then block merges of run pairs between keys[1]
+// and keys[0] (the block owns the tile's range in both).
+__device__ void sort_long_list(const Batch* __restrict__ B, int2 r, unsigned long long* s) {
+  const int n = r.y - r.x;
+  unsigned long long* A = B->keys[1] + r.x;
+  for (int c0 = 0; c0 < n; c0 += TSORT_BLOCK_CAP)
+    group_sort_list<TSORT_NT, TSORT_K>(A + c0, min(TSORT_BLOCK_CAP, n - c0), nullptr, A + c0, s,
+                                       threadIdx.x, 0);
+  unsigned long long* src = A;
+  unsigned long long* dst = B->keys[0] + r.x;
+  for (int w = TSORT_BLOCK_CAP; w < n; w <<= 1) {
+    for (int lo = 0; lo < n; lo += 2 * w) {
+      const int mid = min(lo + w, n), hi = min(lo + 2 * w, n);
+      block_merge<TSORT_NT>(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
+    }
+    __syncthreads();
+    unsigned long long* x = src;
+    src = dst;
+    dst = x;
+  }
+  for (int i = threadIdx.x; i < n; i += TSORT_NT) B->vals[r.x + i] = (unsigned)src[i];
+  __syncthreads();
+}
 
-// Class 4, lists longer than 8,192 keys; persistent blocks of 1024 threads.
-// Up to TSORT_L_CAP keys: one on-chip sort.  Longer: sorted runs of
-// TSORT_L_CAP keys, then block merges of run pairs between keys[1] and
-// keys[0] (the block owns the tile's range in both).
-__global__ void __launch_bounds__(TSORT_L_THREADS) k_tile_sort_long(const Batch* __restrict__ B) {
-  extern __shared__ unsigned long long sl[];
+__global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restrict__ B) {
+  __shared__ unsigned long long s[spad_size<TSORT_BLOCK_CAP>()];
+  __shared__ int s_item[2];
   Counters* c = B->ctr;
   if (c->n_keys_used == 0) return;
-  const int nc = c->class_n[4];
-  const int* list = B->tile_class + 4 * (size_t)B->total_tiles;
-  for (int e = blockIdx.x; e < nc; e += gridDim.x) {
-    const int2 r = B->ranges[list[e]];
+  const int nt = B->total_tiles;
+  const int* list = B->tile_class;
+  const int n3 = c->class_n[3], n2 = c->class_n[2], n1 = c->class_n[1], n0 = c->class_n[0];
+  const unsigned long long* in = B->keys[1];
+  // (1) lists of more than 2,048 keys (the longest class first), a block each
+  for (;;) {
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(&c->sort_q[0], 1);
+    __syncthreads();
+    const int it = s_item[0];
+    __syncthreads();
+    if (it >= n3 + n2) break;
+    const int t = (it < n3) ? list[3 * nt + it] : list[2 * nt + it - n3];
+    const int2 r = B->ranges[t];
+    if (r.y - r.x > TSORT_BLOCK_CAP) {
+      if (threadIdx.x == 0) atomicAdd(&c->long_lists, 1);
+      sort_long_list(B, r, s);
+    } else {
+      group_sort_list<TSORT_NT, TSORT_K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, s,
+                                         threadIdx.x, 0);
+    }
+  }
+  // (2) lists of 257..2,048 keys, a half block each (named barriers 1, 2)
+  const int h = threadIdx.x >> 8, htid = threadIdx.x & 255;
+  unsigned long long* sh = s + h * spad_size<TSORT_HALF_CAP>();
+  for (;;) {
+    if (htid == 0) s_item[h] = atomicAdd(&c->sort_q[1], 1);
+    group_sync<256>(1 + h);
+    const int it = s_item[h];
+    group_sync<256>(1 + h);
+    if (it >= n1) break;
+    const int2 r = B->ranges[list[nt + it]];
+    group_sort_list<256, TSORT_K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, sh, htid, 1 + h);
+  }
+  // (3) lists of up to 256 keys, a warp each, inside the warp's half
+  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
+  unsigned long long* sw = sh + w * spad_size<TSORT_WARP_CAP>();
+  for (;;) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&c->sort_q[2], 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n0) break;
+    const int2 r = B->ranges[list[it]];
     const int n = r.y - r.x;
-    unsigned long long* A = B->keys[1] + r.x;
-    if (n <= TSORT_L_CAP) {
-      group_sort_list<TSORT_L_THREADS, TSORT_L_K>(A, n, B->vals + r.x, nullptr, sl, threadIdx.x);
+    if (n == 1) {
+      if (lane == 0) B->vals[r.x] = (unsigned)in[r.x];
       continue;
     }
-    if (threadIdx.x == 0) atomicAdd(&c->long_lists, 1);
-    for (int c0 = 0; c0 < n; c0 += TSORT_L_CAP)
-      group_sort_list<TSORT_L_THREADS, TSORT_L_K>(A + c0, min(TSORT_L_CAP, n - c0), nullptr, A + c0,
-                                                  sl, threadIdx.x);
-    __syncthreads();
-    unsigned long long* src = A;
-    unsigned long long* dst = B->keys[0] + r.x;
-    for (int w = TSORT_L_CAP; w < n; w <<= 1) {
-      for (int lo = 0; lo < n; lo += 2 * w) {
-        const int mid = min(lo + w, n), hi = min(lo + 2 * w, n);
-        block_merge<TSORT_L_THREADS>(src + lo, mid - lo, src + mid, hi - mid, dst + lo);
-      }
-      __syncthreads();
-      unsigned long long* x = src;
-      src = dst;
-      dst = x;
-    }
-    for (int i = threadIdx.x; i < n; i += TSORT_L_THREADS) B->vals[r.x + i] = (unsigned)src[i];
-    __syncthreads();
+    group_sort_list<32, TSORT_K>(in + r.x, n, B->vals + r.x, nullptr, sw, lane, 0);
   }
 }
 
@@ -860,41 +883,21 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   return 3;
 }
 
-static int binning_setup();
-
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
-  binning_setup();
   k_fwd_reset<<<64, 256, 0, st>>>(dB);
   dim3 g(P.max_pp_chunks, P.n_views);
   k_preprocess<<<g, PP_THREADS, 0, st>>>(dB);
   k_tile_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
   k_place<<<g, PP_THREADS, 0, st>>>(dB);
-  k_tile_sort_warp<<<P.tsort_blocks[0], 256, 0, st>>>(dB);
-  k_tile_sort_block<256, TSORT_K, 1><<<P.tsort_blocks[1], 256, tsort_smem(256), st>>>(dB);
-  k_tile_sort_block<512, TSORT_K, 2><<<P.tsort_blocks[2], 512, tsort_smem(512), st>>>(dB);
-  k_tile_sort_block<1024, TSORT_K, 3><<<P.tsort_blocks[3], 1024, tsort_smem(1024), st>>>(dB);
-  k_tile_sort_long<<<P.tsort_blocks[4], TSORT_L_THREADS, TSORT_L_SMEM, st>>>(dB);
+  k_tile_sort<<<P.tsort_blocks, TSORT_NT, 0, st>>>(dB);
   k_worklist_count<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
   k_worklist_scan<<<1, 17 * 32, 0, st>>>(dB, P.wl_blocks);
   k_worklist_place<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
-  return 12;
-}
-
-// Opt-in of the long-list sort to its dynamic shared memory (once per
-// process; a failure shows as the launch error of that kernel).
-static int binning_setup() {
-  static int rc = -1;
-  if (rc < 0)
-    rc = (cudaFuncSetAttribute(k_tile_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               TSORT_L_SMEM) == cudaSuccess &&
-          cudaFuncSetAttribute(k_tile_sort_block<1024, TSORT_K, 3>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               tsort_smem(1024)) == cudaSuccess) ? 0 : 1;
-  return rc;
+  return 8;
 }
 
 int launch_debug_keys(const HostPlan& P, const Batch* dB, cudaStream_t st) {
-  k_debug_keys<<<P.tsort_blocks[1], 256, 0, st>>>(dB);
+  k_debug_keys<<<P.tsort_blocks, 256, 0, st>>>(dB);
   return 1;
 }
 

@@ -945,6 +945,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
 // is summed over the views and pushed once through the world-space
 // n = g / |g| of the tet's affine SDF.
 // ---------------------------------------------------------------------------
+template <bool NRM>
 __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
@@ -953,7 +954,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
   float* __restrict__ gV = go.dV[s];
   float* __restrict__ gf = go.df[s];
   float* __restrict__ gc = go.drgb[s];
-  const bool nrm = (B->flags & TTS_FLAG_NORMALS) != 0;
+  constexpr bool nrm = NRM;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
     const int tet = B->surv[S.surv_off + k];
     TetIn in;
@@ -1045,7 +1046,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       }
       dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
     }
-    if (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f) {
+    if (NRM && (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f)) {
       if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
       TetGrad TG;
       tet_grad(in.v, in.f, TG);
@@ -1165,7 +1166,8 @@ int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, co
 
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st) {
   dim3 g(P.tet_bwd_blocks, P.n_scenes);
-  k_tet_bwd<<<g, 256, 0, st>>>(dB, go);
+  if (P.normals) k_tet_bwd<true><<<g, 256, 0, st>>>(dB, go);
+  else k_tet_bwd<false><<<g, 256, 0, st>>>(dB, go);
   return 1;
 }
 

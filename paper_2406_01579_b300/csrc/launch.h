@@ -10,7 +10,7 @@ namespace tts {
 struct HostPlan {
   int n_scenes, n_views;
   int max_pf_chunks, max_pp_chunks;
-  int tsort_blocks[TSORT_CLASSES];   // persistent grid of each depth-sort class
+  int tsort_blocks;         // persistent grid of the depth sort
   int wl_blocks;
   int total_tiles;
   int tile;

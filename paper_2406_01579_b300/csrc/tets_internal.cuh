@@ -15,13 +15,7 @@ constexpr int PF_THREADS = 256;
 constexpr int PP_CHUNK = 512;       // survivors per preprocess / key placement block
 constexpr int PP_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
-// Per-tile depth sort of the longest lists: a 1024-thread block with
-// TSORT_L_CAP keys of dynamic shared memory (lists longer than that: sorted
-// runs of TSORT_L_CAP keys merged in global memory).
-constexpr int TSORT_L_THREADS = 1024;
-constexpr int TSORT_CLASSES = 5;    // list lengths (0,256] (256,2K] (2K,4K] (4K,8K] (8K,...)
-constexpr int TSORT_L_CAP = 16384;
-constexpr int TSORT_L_SMEM = (TSORT_L_CAP + TSORT_L_CAP / 16) * 8;   // one pad key per 16
+constexpr int TSORT_CLASSES = 4;    // depth-sort list lengths (0,256] (256,2K] (2K,4K] (4K,...)
 
 // Counters at the start of the workspace (after the descriptor).
 struct Counters {
@@ -39,6 +33,7 @@ struct Counters {
   int n_units;              // blend work units (tile segments) of the last binning
   int seg_total;            // checkpoint slots handed out by the work-list builder
   int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
+  int sort_q[3];            // depth-sort queues: block, half-block and warp lists taken
 };
 
 struct SceneD {

@@ -286,11 +286,11 @@ def test_torus64_gradients(torus64):
 @pytest.mark.parametrize("res,tile,lo,hi", [(64, 32, 16385, None), (256, 32, 2049, 16384),
                                             (96, 8, 1, 2048)])
 def test_long_tile_lists(res, tile, lo, hi):
-    """Tile lists of every length class of the per-tile depth sort: up to
-    2,048 keys (256-thread on-chip sort), 2,049..16,384 (one 1024-thread
-    on-chip sort) and longer (sorted runs of 16,384 merged in global memory).
-    The 64^3 torus seen at a low resolution piles many tets into each tile.
-    Keys, values and ranges bit for bit against the oracle's sort."""
+    """Tile lists of every length class of the per-tile depth sort: up to 256
+    keys (a warp), 2,048 (half a block), 4,096 (a block) and longer (sorted
+    runs of 4,096 merged in global memory).  The 64^3 torus seen at a low
+    resolution piles many tets into each tile.  Keys, values and ranges bit
+    for bit against the oracle's sort."""
     sc = synth.scene_torus64(res=res)
     p = Params(s=60.0, tile=tile)
     cam = sc.cams[0]
@@ -301,7 +301,7 @@ def test_long_tile_lists(res, tile, lo, hi):
     r = gpu["lists"]["ranges"]
     lens = r[:, 1] - r[:, 0]
     assert ((lens >= lo) & (lens <= (hi or lens.max()))).sum() >= 1, lens.max()
-    assert (gpu["info"].long_lists > 0) == (lens.max() > 16384)
+    assert gpu["info"].long_lists == (lens > 4096).sum()
 
 
 @pytest.fixture(scope="module")
