@@ -336,50 +336,52 @@ __device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned act
 }
 
 // ---------------------------------------------------------------------------
-// K2: per-view preprocess.  grid (max_pp_chunks, n_views).  Writes each
-// slot's record, tile rect and depth bits, and counts the keys of every
-// tile the slot's rect overlaps.
+// K2: preprocess.  grid (max_pre_chunks, n_scenes), one thread per survivor
+// of a scene: the tet is loaded once, then for each of the scene's views the
+// thread writes the slot's record, tile rect and depth bits, and counts the
+// keys of every tile the slot's rect overlaps.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
-  const int v = blockIdx.y;
-  const ViewD& vw = B->vw[v];
-  const int chunk = blockIdx.x;
-  if (chunk >= vw.pp_chunks) return;
-  const SceneD& S = B->sc[vw.scene];
-  const int nsurv = B->ctr->n_surv[vw.scene];
+  const int sc = blockIdx.y;
+  const SceneD& S = B->sc[sc];
+  const int nsurv = B->ctr->n_surv[sc];
+  const int k0 = blockIdx.x * PRE_CHUNK;
+  if (k0 >= nsurv) return;
   const float s = B->s;
   const int tile = B->tile;
-  int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
   unsigned zmn = 0xffffffffu, zmx = 0u;
-  for (int q = threadIdx.x; q < PP_CHUNK; q += PP_THREADS) {
-    const int k = chunk * PP_CHUNK + q;
+  for (int q = threadIdx.x; q < PRE_CHUNK; q += PP_THREADS) {
+    const int k = k0 + q;
     if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
-    int tx0 = 0, ty0 = 0, ntx = 0, nt = 0;
-    if (k < nsurv) {
-      const long long slot = vw.rec_base + k;
-      const int tet = B->surv[S.surv_off + k];
-      TetIn in;
-      load_tet(S, tet, in);
-      Geo G;
-      tet_geometry(vw, s, in, G);
-      if (G.visible) {
-        tx0 = G.i0 / tile;
-        ty0 = G.j0 / tile;
-        const int tx1 = G.i1 / tile, ty1 = G.j1 / tile;
-        ntx = tx1 - tx0 + 1;
-        nt = ntx * (ty1 - ty0 + 1);
-        B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
-        write_record(vw, s, in, G, B->rec + slot * REC_Q);
-        zmn = min(zmn, G.zbits);
-        zmx = max(zmx, G.zbits);
+    TetIn in;
+    if (k < nsurv) load_tet(S, B->surv[S.surv_off + k], in);
+    for (int vi = 0; vi < S.view_cnt; ++vi) {
+      const ViewD& vw = B->vw[B->scene_views[S.view_off + vi]];
+      int tx0 = 0, ty0 = 0, ntx = 0, nt = 0;
+      if (k < nsurv) {
+        const long long slot = vw.rec_base + k;
+        Geo G;
+        tet_geometry(vw, s, in, G);
+        if (G.visible) {
+          tx0 = G.i0 / tile;
+          ty0 = G.j0 / tile;
+          const int tx1 = G.i1 / tile, ty1 = G.j1 / tile;
+          ntx = tx1 - tx0 + 1;
+          nt = ntx * (ty1 - ty0 + 1);
+          B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
+          write_record(vw, s, in, G, B->rec + slot * REC_Q);
+          zmn = min(zmn, G.zbits);
+          zmx = max(zmx, G.zbits);
+        }
+        B->rec_nt[slot] = nt;
+        B->rec_z[slot] = G.zbits;
       }
-      B->rec_nt[slot] = nt;
-      B->rec_z[slot] = G.zbits;
-    }
-    // key counts per tile, one atomic per (warp, tile) and round
-    for (int r = 0; __any_sync(0xffffffffu, r < nt); ++r) {
-      const unsigned act = __ballot_sync(0xffffffffu, r < nt);
-      if (r < nt) warp_bucket_add(cnt, (ty0 + r / ntx) * vw.tiles_x + tx0 + r % ntx, act, false);
+      // key counts per tile, one atomic per (warp, tile) and round
+      int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
+      for (int r = 0; __any_sync(0xffffffffu, r < nt); ++r) {
+        const unsigned act = __ballot_sync(0xffffffffu, r < nt);
+        if (r < nt) warp_bucket_add(cnt, (ty0 + r / ntx) * vw.tiles_x + tx0 + r % ntx, act, false);
+      }
     }
   }
   // block min/max of the depth bits
@@ -886,7 +888,7 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   k_fwd_reset<<<64, 256, 0, st>>>(dB);
   dim3 g(P.max_pp_chunks, P.n_views);
-  k_preprocess<<<g, PP_THREADS, 0, st>>>(dB);
+  k_preprocess<<<dim3(P.max_pre_chunks, P.n_scenes), PP_THREADS, 0, st>>>(dB);
   k_tile_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
   k_place<<<g, PP_THREADS, 0, st>>>(dB);
   k_tile_sort<<<P.tsort_blocks, TSORT_NT, 0, st>>>(dB);

@@ -9,7 +9,7 @@ namespace tts {
 
 struct HostPlan {
   int n_scenes, n_views;
-  int max_pf_chunks, max_pp_chunks;
+  int max_pf_chunks, max_pp_chunks, max_pre_chunks;
   int tsort_blocks;         // persistent grid of the depth sort
   int wl_blocks;
   int total_tiles;

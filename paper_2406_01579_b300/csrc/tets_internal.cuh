@@ -12,7 +12,8 @@ namespace tts {
 
 constexpr int PF_CHUNK = 4096;      // tets per pre-filter block
 constexpr int PF_THREADS = 256;
-constexpr int PP_CHUNK = 512;       // survivors per preprocess / key placement block
+constexpr int PP_CHUNK = 512;       // slots per key placement block
+constexpr int PRE_CHUNK = 256;      // survivors per preprocess block
 constexpr int PP_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
 constexpr int TSORT_CLASSES = 4;    // depth-sort list lengths (0,256] (256,2K] (2K,4K] (4K,...)
