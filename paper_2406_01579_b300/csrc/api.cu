@@ -194,6 +194,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_v = take(sizeof(unsigned) * cap);
   const size_t o_tc = take(sizeof(int) * tiles);
   const size_t o_tcl = take(sizeof(int) * TSORT_CLASSES * (size_t)tiles);
+  const size_t o_slb = take(sizeof(unsigned long long) * (size_t)((tiles + TS_TILES - 1) / TS_TILES));
   const size_t o_rng = take(sizeof(int2) * tiles);
   // split-tile segments: at most 2 * keys / seg_len (each split tile has more
   // than seg_len keys, so ceil(len / seg_len) <= 2 len / seg_len); one
@@ -237,6 +238,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.vals = reinterpret_cast<unsigned*>(base + o_v);
     B.tile_cnt = reinterpret_cast<int*>(base + o_tc);
     B.tile_class = reinterpret_cast<int*>(base + o_tcl);
+    B.scan_lb = reinterpret_cast<unsigned long long*>(base + o_slb);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
     B.worklist = reinterpret_cast<int2*>(base + o_wl);
     B.tseg = reinterpret_cast<int2*>(base + o_tseg);

@@ -73,7 +73,11 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->seg_total = 0;
     for (int q = 0; q < TSORT_CLASSES; ++q) c->class_n[q] = 0;
     for (int q = 0; q < 3; ++q) c->sort_q[q] = 0;
+    c->scan_ticket = 0u;
   }
+  const int nlb = (B->total_tiles + TS_TILES - 1) / TS_TILES;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nlb; t += gridDim.x * blockDim.x)
+    B->scan_lb[t] = 0ull;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
     B->tile_cnt[t] = 0;
 }
@@ -397,13 +401,18 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
 }
 
 // ---------------------------------------------------------------------------
-// K3: tile scan (one block).  Exclusive prefix of the per-tile key counts ->
-// each tile's [start, end) ((0, 0) when empty) and its placement cursor
-// (= start); the total is the key count.  Past the key capacity every range
-// is left empty and the overflow status is set.  Also fixes the key
-// encoding's depth bit count.
+// K3: tile scan.  Exclusive prefix of the per-tile key counts -> each tile's
+// [start, end) ((0, 0) when empty) and its placement cursor (= start); the
+// tiles listed by list-length class; the total is the key count.  Blocks of
+// TS_THREADS x TS_ITEMS tiles take tickets in order, publish their count
+// sum, and find the sum of all earlier blocks by decoupled look-back (the
+// waits are bounded: past the limit the scan sets TTS_STATUS_TIMEOUT and its
+// output is undefined).  Past the key capacity the key count is set, the
+// overflow status raised and no key is used (the work-list builder then
+// empties every range).  The last block also fixes the depth bit count.
 // ---------------------------------------------------------------------------
-constexpr int TS_ITEMS = 16;
+constexpr unsigned long long TS_AGG = 1ull << 62, TS_PREFIX = 2ull << 62;
+constexpr long long TS_SPIN_LIMIT = 1ll << 22;
 
 // List-length class of the per-tile depth sort (see K5): up to 256 keys,
 // 2,048, 4,096, more.
@@ -411,69 +420,95 @@ __device__ __forceinline__ int tsort_class(int n) {
   return n <= 256 ? 0 : n <= 2048 ? 1 : n <= 4096 ? 2 : 3;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_tile_scan(const Batch* __restrict__ B) {
+__global__ void __launch_bounds__(TS_THREADS) k_tile_scan(const Batch* __restrict__ B) {
+  __shared__ int s_b;
+  __shared__ long long s_excl;
+  Counters* c = B->ctr;
+  if (threadIdx.x == 0) s_b = (int)atomicAdd(&c->scan_ticket, 1u);
+  __syncthreads();
+  const int b = s_b;
   const int n = B->total_tiles;
   int* __restrict__ cnt = B->tile_cnt;
   int2* __restrict__ ranges = B->ranges;
-  long long carry = 0;
-  for (int base = 0; base < n; base += SCAN_THREADS * TS_ITEMS) {
-    const int i0 = base + threadIdx.x * TS_ITEMS;
-    int v[TS_ITEMS];
-    long long sum = 0;
-    if (i0 + TS_ITEMS <= n) {
-      const int4* p = reinterpret_cast<const int4*>(cnt + i0);
+  const int i0 = b * TS_TILES + threadIdx.x * TS_ITEMS;
+  int v[TS_ITEMS];
+  if (i0 + TS_ITEMS <= n) {
+    const int4* p = reinterpret_cast<const int4*>(cnt + i0);
 #pragma unroll
-      for (int j = 0; j < TS_ITEMS / 4; ++j) {
-        const int4 x = p[j];
-        v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < TS_ITEMS; ++j) v[j] = (i0 + j < n) ? cnt[i0 + j] : 0;
+    for (int j = 0; j < TS_ITEMS / 4; ++j) {
+      const int4 x = p[j];
+      v[4 * j] = x.x; v[4 * j + 1] = x.y; v[4 * j + 2] = x.z; v[4 * j + 3] = x.w;
     }
+  } else {
 #pragma unroll
-    for (int j = 0; j < TS_ITEMS; ++j) sum += v[j];
-    long long tot;
-    long long ex = carry + block_excl_scan<long long, SCAN_THREADS>(sum, &tot);
-    int cls[TS_ITEMS];
-#pragma unroll
-    for (int j = 0; j < TS_ITEMS; ++j) {
-      cls[j] = -1;
-      if (i0 + j < n) {
-        const bool keep = v[j] > 0 && ex + v[j] <= B->key_cap;
-        ranges[i0 + j] = keep ? make_int2((int)ex, (int)(ex + v[j])) : make_int2(0, 0);
-        cnt[i0 + j] = (int)min(ex, (long long)0x7fffffff);
-        if (keep) cls[j] = tsort_class(v[j]);
-      }
-      ex += v[j];
-    }
-    carry += tot;
-    // the non-empty tiles by list-length class (one atomic per warp and class)
-#pragma unroll
-    for (int q = 0; q < TSORT_CLASSES; ++q) {
-      int nq = 0;
-#pragma unroll
-      for (int j = 0; j < TS_ITEMS; ++j) nq += (cls[j] == q);
-      int wt;
-      const int wx = warp_excl_scan(nq, &wt);
-      int b0 = 0;
-      if ((threadIdx.x & 31) == 0 && wt > 0) b0 = atomicAdd(&B->ctr->class_n[q], wt);
-      int pos = __shfl_sync(0xffffffffu, b0, 0) + wx;
-      int* list = B->tile_class + (size_t)q * n;
-#pragma unroll
-      for (int j = 0; j < TS_ITEMS; ++j)
-        if (cls[j] == q) list[pos++] = i0 + j;
-    }
+    for (int j = 0; j < TS_ITEMS; ++j) v[j] = (i0 + j < n) ? cnt[i0 + j] : 0;
   }
-  const bool over = carry > B->key_cap;
-  if (over) {   // rare: no list at all
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += SCAN_THREADS) ranges[i] = make_int2(0, 0);
-  }
+  long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < TS_ITEMS; ++j) sum += v[j];
+  long long tot;
+  const long long tex = block_excl_scan<long long, TS_THREADS>(sum, &tot);
   if (threadIdx.x == 0) {
-    Counters* c = B->ctr;
-    c->n_keys = carry;
-    c->n_keys_used = over ? 0 : carry;
+    unsigned long long* lb = B->scan_lb;
+    long long excl = 0;
+    if (b > 0) {
+      atomicExch(lb + b, TS_AGG | (unsigned long long)tot);
+      bool timed_out = false;
+      for (int p = b - 1; p >= 0 && !timed_out;) {
+        unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(lb + p);
+        long long spins = 0;
+        while (w == 0ull) {
+          if (++spins > TS_SPIN_LIMIT) {
+            timed_out = true;
+            break;
+          }
+          w = *reinterpret_cast<volatile unsigned long long*>(lb + p);
+        }
+        if (timed_out) break;
+        excl += (long long)(w & (TS_AGG - 1));
+        if (w & TS_PREFIX) break;
+        --p;
+      }
+      if (timed_out) set_status(c, TTS_STATUS_TIMEOUT);
+    }
+    atomicExch(lb + b, TS_PREFIX | (unsigned long long)(excl + tot));
+    s_excl = excl;
+  }
+  __syncthreads();
+  long long ex = s_excl + tex;
+  int cls[TS_ITEMS];
+#pragma unroll
+  for (int j = 0; j < TS_ITEMS; ++j) {
+    cls[j] = -1;
+    if (i0 + j < n) {
+      const bool keep = v[j] > 0 && ex + v[j] <= B->key_cap;
+      ranges[i0 + j] = keep ? make_int2((int)ex, (int)(ex + v[j])) : make_int2(0, 0);
+      cnt[i0 + j] = (int)min(ex, (long long)0x7fffffff);
+      if (keep) cls[j] = tsort_class(v[j]);
+    }
+    ex += v[j];
+  }
+  // the non-empty tiles by list-length class (one atomic per warp and class)
+#pragma unroll
+  for (int q = 0; q < TSORT_CLASSES; ++q) {
+    int nq = 0;
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j) nq += (cls[j] == q);
+    int wt;
+    const int wx = warp_excl_scan(nq, &wt);
+    int b0 = 0;
+    if ((threadIdx.x & 31) == 0 && wt > 0) b0 = atomicAdd(&c->class_n[q], wt);
+    int pos = __shfl_sync(0xffffffffu, b0, 0) + wx;
+    int* list = B->tile_class + (size_t)q * n;
+#pragma unroll
+    for (int j = 0; j < TS_ITEMS; ++j)
+      if (cls[j] == q) list[pos++] = i0 + j;
+  }
+  if (threadIdx.x == 0 && b == gridDim.x - 1) {
+    const long long total = s_excl + tot;
+    const bool over = total > B->key_cap;
+    c->n_keys = total;
+    c->n_keys_used = over ? 0 : total;
     if (over) set_status(c, TTS_STATUS_KEY_OVERFLOW);
     unsigned span = (c->zmax_bits >= c->zmin_bits) ? (c->zmax_bits - c->zmin_bits) : 0u;
     if (c->zmin_bits == 0xffffffffu) span = 0;
@@ -790,7 +825,13 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
   const int L = B->seg_len;
   const int lane = threadIdx.x & 31;
   const bool in = t < nt;
-  const int2 r = in ? B->ranges[t] : make_int2(0, 0);
+  // no key used (capacity exceeded): every list is empty
+  const bool none = B->ctr->n_keys_used == 0;
+  int2 r = in ? B->ranges[t] : make_int2(0, 0);
+  if (in && none && (r.x | r.y)) {
+    r = make_int2(0, 0);
+    B->ranges[t] = r;
+  }
   const int len = r.y - r.x;
   int nseg = (in && L > 0 && len > L) ? (len + L - 1) / L : 1;
   // checkpoint slots, one atomic per warp
@@ -889,7 +930,7 @@ int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   k_fwd_reset<<<64, 256, 0, st>>>(dB);
   dim3 g(P.max_pp_chunks, P.n_views);
   k_preprocess<<<dim3(P.max_pre_chunks, P.n_scenes), PP_THREADS, 0, st>>>(dB);
-  k_tile_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
+  k_tile_scan<<<(P.total_tiles + TS_TILES - 1) / TS_TILES, TS_THREADS, 0, st>>>(dB);
   k_place<<<g, PP_THREADS, 0, st>>>(dB);
   k_tile_sort<<<P.tsort_blocks, TSORT_NT, 0, st>>>(dB);
   k_worklist_count<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);

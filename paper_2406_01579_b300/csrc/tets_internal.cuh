@@ -16,6 +16,9 @@ constexpr int PP_CHUNK = 512;       // slots per key placement block
 constexpr int PRE_CHUNK = 256;      // survivors per preprocess block
 constexpr int PP_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
+constexpr int TS_THREADS = 256;     // tile scan: threads per block
+constexpr int TS_ITEMS = 8;         // tiles per thread
+constexpr int TS_TILES = TS_THREADS * TS_ITEMS;
 constexpr int TSORT_CLASSES = 4;    // depth-sort list lengths (0,256] (256,2K] (2K,4K] (4K,...)
 
 // Counters at the start of the workspace (after the descriptor).
@@ -35,6 +38,7 @@ struct Counters {
   int seg_total;            // checkpoint slots handed out by the work-list builder
   int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
   int sort_q[3];            // depth-sort queues: block, half-block and warp lists taken
+  unsigned int scan_ticket; // tile-scan blocks started
 };
 
 struct SceneD {
@@ -92,6 +96,7 @@ struct Batch {
   unsigned int* vals;       // [key_cap] record slot of each key, sorted per tile
   int* tile_cnt;            // [total_tiles] keys per tile, then the placement cursor
   int* tile_class;          // [TSORT_CLASSES * total_tiles] non-empty tiles by list length
+  unsigned long long* scan_lb;   // [tile-scan blocks] look-back words (flag << 62 | sum)
   int2* ranges;             // [total_tiles]
   int2* worklist;           // [units] (tile, segment), longest first
   int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)
