@@ -85,9 +85,23 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
 // ---------------------------------------------------------------------------
 // K1: pre-filter.  alpha_max = Eq. 1 at (f_max, f_min) of the tet's vertices,
 // keep iff alpha_max >= T_f.  Flags, then a stable compaction.
-// grid (max_pf_chunks, n_scenes)
+// grid (max_pf_chunks, n_scenes).  A block first copies its chunk of tet
+// indices into shared memory with asynchronous 16-byte copies (all in flight
+// at once, evict-first in L2), then gathers the vertex SDF values.
 // ---------------------------------------------------------------------------
+// 16-byte asynchronous copy global -> shared that marks the L2 lines it
+// brings in evict-first: the tet indices stream through once and should not
+// push the vertex arrays (gathered right after) out of L2.
+__device__ __forceinline__ void cp_async16_stream(void* smem, const void* gmem,
+                                                  unsigned long long policy) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa),
+               "l"(gmem), "l"(policy)
+               : "memory");
+}
+
 __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __restrict__ B) {
+  __shared__ int4 sT[PF_CHUNK];
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int chunk = blockIdx.x;
@@ -101,11 +115,18 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __r
   const float fcut = (thr > 0.f && thr < 1.f) ? logf(1.f / thr - 1.f) / sv : __int_as_float(0x7f800000);
   const unsigned N = (unsigned)S.N;
   unsigned char* flags = B->pf_flags + S.flag_off;
+  const int nk = (int)(k1 - k0);
+  unsigned long long policy;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(policy));
+  for (int i = threadIdx.x; i < nk; i += PF_THREADS) cp_async16_stream(&sT[i], &S.T[k0 + i], policy);
+  asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
   int cnt = 0;
   bool bad = false;
 #pragma unroll 4
-  for (long long k = k0 + threadIdx.x; k < k1; k += PF_THREADS) {
-    const int4 t = __ldg(&S.T[k]);
+  for (int i = threadIdx.x; i < nk; i += PF_THREADS) {
+    const long long k = k0 + i;
+    const int4 t = sT[i];
     unsigned char keep = 0;
     if ((unsigned)t.x < N && (unsigned)t.y < N && (unsigned)t.z < N && (unsigned)t.w < N) {
       if (pure) {
@@ -165,15 +186,20 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* _
   const SceneD& S = B->sc[s];
   const int chunk = blockIdx.x;
   if (chunk >= S.pf_chunks) return;
-  constexpr int PER = PF_CHUNK / PF_THREADS;  // 16 consecutive flags per thread
+  constexpr int PER = PF_CHUNK / PF_THREADS;  // 8 consecutive flags per thread
+  static_assert(PER == 8, "one 8-byte load of flags per thread");
   const long long k0 = (long long)chunk * PF_CHUNK + (long long)threadIdx.x * PER;
-  const unsigned char* flags = B->pf_flags + S.flag_off;
+  // flag_off and k0 are multiples of 8 and the flag region is padded to 16
+  // bytes per scene, so a load that starts below K stays inside it; flags
+  // past K are masked
+  const uint2 w = (k0 < S.K) ? *reinterpret_cast<const uint2*>(B->pf_flags + S.flag_off + k0)
+                             : make_uint2(0u, 0u);
   unsigned char fl[PER];
   int cnt = 0;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
-    const long long k = k0 + q;
-    fl[q] = (k < S.K) ? flags[k] : 0;
+    const unsigned word = (q < 4) ? w.x : w.y;
+    fl[q] = (k0 + q < S.K) ? (unsigned char)((word >> (8 * (q & 3))) & 0xffu) : 0;
     cnt += fl[q];
   }
   int total;

@@ -10,7 +10,7 @@
 
 namespace tts {
 
-constexpr int PF_CHUNK = 4096;      // tets per pre-filter block
+constexpr int PF_CHUNK = 2048;      // tets per pre-filter block (32 KB of indices in shared memory)
 constexpr int PF_THREADS = 256;
 constexpr int PP_CHUNK = 512;       // slots per key placement block
 constexpr int PRE_CHUNK = 256;      // survivors per preprocess block
