@@ -469,6 +469,38 @@ def extras(a, st, sc, params, ups, dev, barrier):
                                        stream.cuda_stream))
     out["marching_tets_ms"] = timed(mt, 5)
     out["mesh"] = {"vertices": nv, "triangles": nt}
+    # Sec. 3.3's device radix sort on this step's (tile, depth) keys, in the
+    # order the binning emits them (slot-major, then tile), beside the
+    # binning's own per-tile on-chip ordering (part of the headline step) and
+    # a library sort (torch.sort, all 64 key bits) of the same keys
+    rk = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
+    rk.forward()
+    d = rk.debug_lists()
+    k = d["keys"].cpu().numpy().view(np.uint64)
+    v = d["vals"].cpu().numpy()
+    order = np.lexsort((k >> np.uint64(d["depth_bits"]), v))
+    kin = torch.from_numpy(k[order].view(np.int64).copy()).to(dev)
+    vin = torch.from_numpy(v[order].copy()).to(dev)
+    bits = int(d["info"].sort_bits)
+    need = ctypes.c_size_t(0)
+    _lib.check(L.tts_sort_pairs_scratch_size(kin.numel(), ctypes.byref(need)))
+    scratch = torch.empty(int(need.value), dtype=torch.uint8, device=dev)
+    kout, vout = torch.empty_like(kin), torch.empty_like(vin)
+
+    def radix():
+        _lib.check(L.tts_sort_pairs(kin.data_ptr(), vin.data_ptr(), kout.data_ptr(),
+                                    vout.data_ptr(), kin.numel(), bits, scratch.data_ptr(),
+                                    scratch.numel(), stream.cuda_stream))
+    out["radix_sort_ms"] = timed(radix, 5)
+    out["radix_sort_matches_binning"] = bool(torch.equal(kout, d["keys"]) and torch.equal(vout, d["vals"]))
+
+    def lib_sort():
+        sk, idx = torch.sort(kin, stable=True)
+        return sk, vin[idx]
+    out["torch_sort_ms"] = timed(lib_sort, 5)
+    out["sort_keys"] = int(kin.numel())
+    out["sort_bits"] = bits
+    del rk, kin, vin, kout, vout, scratch
     # coarse-to-fine pre-filter: bounds of the first round's survivors, refit
     rb = Rasterizer([st], [(sc.cams[0], 0)], params, device=dev)
     rb.prepare()

@@ -284,8 +284,24 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
  * notes) and to the per-slot survivor-relative tet index order. */
 int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
 
-/* Sorts n (key, value) pairs by the low key_bits bits of the key, stably
- * (an LSD radix sort), without allocating anything.
+/* Sorts n (key, value) pairs by the low key_bits bits of the key, stably: an
+ * LSD radix sort with 8-bit digits (per pass: per-block digit counts, a scan
+ * of the counts, a stable scatter), the device radix sort of Sec. 3.3's
+ * (tile, depth) keys.  The binning of tts_bin_views does not call it: it
+ * orders the same keys per tile on chip (see the design notes), with the
+ * same result.  keys_in/vals_in (device, n each) are read only;
+ * keys_out/vals_out receive the sorted pairs and must not alias the inputs.
+ * scratch: device, 256-byte aligned, at least tts_sort_pairs_scratch_size(n)
+ * bytes, owned by the caller, overwritten.  n <= 2^31 - 1.  Returns
+ * TTS_ERR_ARG (bad n, key_bits outside [1, 64], aliasing) or
+ * TTS_ERR_WORKSPACE (scratch missing, misaligned or too small) before
+ * anything is enqueued. */
+int tts_sort_pairs_scratch_size(int64_t n, size_t* bytes);
+int tts_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                   uint32_t* vals_out, int64_t n, int32_t key_bits, void* scratch,
+                   size_t scratch_bytes, tts_stream stream);
+
+/* The same sort without allocating anything.
  * The paper has no counterpart: this entry point exists for callers that must
  * not allocate device memory themselves (code inside a host callback or an
  * allocator hook, plugin hosts that own every device allocation, loops that

@@ -85,6 +85,7 @@ ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
                 "tts_blend_fwd", "tts_blend_bwd", "tts_blend_fwd_ex", "tts_blend_bwd_ex",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
                 "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
+                "tts_sort_pairs_scratch_size", "tts_sort_pairs",
                 "tts_tet_edges_workspace_size", "tts_tet_edges", "tts_regularizers_workspace_size",
                 "tts_regularizers", "tts_marching_tets_workspace_size", "tts_marching_tets",
                 "tts_geometry_status",
@@ -135,6 +136,8 @@ def load():
                                   ctypes.POINTER(ctypes.c_int32), P]
     L.tts_debug_records.argtypes = [B, ctypes.POINTER(P), P]
     L.tts_sort_pairs_noalloc.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int32, P]
+    L.tts_sort_pairs_scratch_size.argtypes = [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+    L.tts_sort_pairs.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int32, P, ctypes.c_size_t, P]
     i64 = ctypes.c_int64
     L.tts_tet_edges_workspace_size.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_size_t)]
     L.tts_tet_edges.argtypes = [P, i64, i64, P, i64, P, P, ctypes.c_size_t, P]

@@ -1,6 +1,10 @@
-// tts_sort_pairs_noalloc: the stable LSD radix sort of (uint64 key, uint32
-// value) pairs used for tile binning, in a variant that allocates nothing.
+// Stable LSD radix sort of (uint64 key, uint32 value) pairs, 8-bit digits,
+// three kernels per pass (per-block digit counts, a scan of each digit's row
+// over the blocks, a stable scatter ranked per warp by match_any).  Two entry
+// points: tts_sort_pairs sorts in caller-provided scratch;
+// tts_sort_pairs_noalloc sorts in a scratch array compiled into the library.
 //
+// tts_sort_pairs_noalloc:
 // Who needs it: callers that must not allocate device memory themselves, for
 // example code running inside a host callback or a custom allocator hook
 // (where calling cudaMalloc is forbidden or deadlocks), plugin hosts that own
@@ -21,11 +25,16 @@
 //    capture on that device.
 // Nothing in the scratch needs to start at zero: every pass rewrites the
 // histogram rows it reads.
+#include <cstdint>
 #include <mutex>
 
 #include <cuda_runtime.h>
 
 #include "tets.h"
+
+namespace tts {
+void count_launches(long long n);
+}
 
 namespace {
 
@@ -191,6 +200,28 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_scatter(
   }
 }
 
+// The passes over the low key_bits bits: ks/vs in, the final pass into
+// kout/vout, the others into tk/tv (ping-pong), hist: NA_RADIX x (NA_BLOCKS+1).
+void radix_sort_pairs(const unsigned long long* ks, const unsigned* vs, unsigned long long* kout,
+                      unsigned* vout, unsigned long long* tk, unsigned* tv, unsigned* hist,
+                      long long n, int key_bits, cudaStream_t st) {
+  const int passes = (key_bits + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    // the pass that writes the final result targets the caller's output
+    const bool to_out = ((passes - 1 - p) % 2) == 0;
+    unsigned long long* kd = to_out ? kout : tk;
+    unsigned* vd = to_out ? vout : tv;
+    k_na_hist<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, n, 8 * p, hist);
+    k_na_rowscan<<<NA_RADIX, NA_THREADS, 0, st>>>(hist);
+    k_na_scatter<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, vs, kd, vd, n, 8 * p, hist);
+    ks = kd;
+    vs = vd;
+  }
+  tts::count_launches(3ll * passes);
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
 // Per-device address of the scratch array, looked up once per device (with
 // that device current) and reused.
 constexpr int NA_MAX_DEVICES = 64;
@@ -224,20 +255,39 @@ extern "C" int tts_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* v
   NaScratch* S = nullptr;
   int rc = na_scratch(&S);
   if (rc != TTS_OK) return rc;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int passes = (key_bits + 7) / 8;
-  const unsigned long long* ks = reinterpret_cast<const unsigned long long*>(keys_in);
-  const unsigned* vs = vals_in;
-  for (int p = 0; p < passes; ++p) {
-    // the pass that writes the final result targets the caller's output
-    const bool to_out = ((passes - 1 - p) % 2) == 0;
-    unsigned long long* kd = to_out ? reinterpret_cast<unsigned long long*>(keys_out) : S->keys;
-    unsigned* vd = to_out ? vals_out : S->vals;
-    k_na_hist<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, n, 8 * p, S->hist);
-    k_na_rowscan<<<NA_RADIX, NA_THREADS, 0, st>>>(S->hist);
-    k_na_scatter<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, vs, kd, vd, n, 8 * p, S->hist);
-    ks = kd;
-    vs = vd;
-  }
+  radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
+                   reinterpret_cast<unsigned long long*>(keys_out), vals_out, S->keys, S->vals,
+                   S->hist, n, key_bits, reinterpret_cast<cudaStream_t>(stream));
+  return (cudaPeekAtLastError() == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
+}
+
+extern "C" int tts_sort_pairs_scratch_size(int64_t n, size_t* bytes) {
+  if (!bytes || n < 0 || n > 0x7fffffffLL) return TTS_ERR_ARG;
+  *bytes = align256(sizeof(unsigned long long) * (size_t)n) + align256(sizeof(unsigned) * (size_t)n) +
+           align256(sizeof(unsigned) * NA_RADIX * (NA_BLOCKS + 1));
+  return TTS_OK;
+}
+
+extern "C" int tts_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                              uint32_t* vals_out, int64_t n, int32_t key_bits, void* scratch,
+                              size_t scratch_bytes, tts_stream stream) {
+  size_t need = 0;
+  if (tts_sort_pairs_scratch_size(n, &need) != TTS_OK) return TTS_ERR_ARG;
+  if (key_bits < 1 || key_bits > 64) return TTS_ERR_ARG;
+  if (n == 0) return TTS_OK;
+  if (!keys_in || !vals_in || !keys_out || !vals_out) return TTS_ERR_ARG;
+  if ((const void*)keys_in == (void*)keys_out || (const void*)vals_in == (void*)vals_out)
+    return TTS_ERR_ARG;
+  if (!scratch || reinterpret_cast<uintptr_t>(scratch) % 256 != 0 || scratch_bytes < need)
+    return TTS_ERR_WORKSPACE;
+  char* base = static_cast<char*>(scratch);
+  unsigned long long* tk = reinterpret_cast<unsigned long long*>(base);
+  base += align256(sizeof(unsigned long long) * (size_t)n);
+  unsigned* tv = reinterpret_cast<unsigned*>(base);
+  base += align256(sizeof(unsigned) * (size_t)n);
+  unsigned* hist = reinterpret_cast<unsigned*>(base);
+  radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
+                   reinterpret_cast<unsigned long long*>(keys_out), vals_out, tk, tv, hist, n,
+                   key_bits, reinterpret_cast<cudaStream_t>(stream));
   return (cudaPeekAtLastError() == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
 }
