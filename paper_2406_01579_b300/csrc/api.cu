@@ -13,6 +13,8 @@ static_assert(sizeof(Batch) < 30000, "descriptor must fit in kernel parameters")
 // Copies the by-value descriptor into the workspace (kernel parameters are
 // captured by value in CUDA graphs, so this stays valid under capture).
 __global__ void k_upload(const Batch b, Batch* dst) {
+  pdl_wait();
+  pdl_launch_dependents();
   const unsigned* src = reinterpret_cast<const unsigned*>(&b);
   unsigned* d = reinterpret_cast<unsigned*>(dst);
   constexpr int n = (int)(sizeof(Batch) / 4);
@@ -20,13 +22,15 @@ __global__ void k_upload(const Batch b, Batch* dst) {
 }
 
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st) {
-  k_upload<<<1, 256, 0, st>>>(hb, dB);
+  launch_k(k_upload, dim3(1), dim3(256), 0, st, hb, dB);
   return 1;
 }
 
 static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_launch_err{0};
 
 void count_launches(long long n) { g_launches += n; }
+void note_launch_error(cudaError_t e) { g_launch_err.store((int)e); }
 
 namespace {
 
@@ -280,7 +284,8 @@ Batch* dev_desc(const tts_batch* b, const Plan& P) {
 
 int check_launch() {
   const cudaError_t e = cudaPeekAtLastError();
-  return (e == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
+  const int le = g_launch_err.exchange(0);
+  return (e == cudaSuccess && le == 0) ? TTS_OK : TTS_ERR_CUDA;
 }
 
 }  // namespace

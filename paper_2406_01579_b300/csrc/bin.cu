@@ -58,6 +58,8 @@ __device__ __forceinline__ int warp_excl_scan(int v, int* total) {
 // per-call resets
 // ---------------------------------------------------------------------------
 __global__ void k_fwd_reset(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   Counters* c = B->ctr;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     c->zmin_bits = 0xffffffffu;
@@ -101,6 +103,8 @@ __device__ __forceinline__ void cp_async16_stream(void* smem, const void* gmem,
 }
 
 __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int4 sT[PF_CHUNK];
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
@@ -156,6 +160,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_flags(const Batch* __r
 
 // Single block: per-scene exclusive scans of the pre-filter block counts.
 __global__ void __launch_bounds__(SCAN_THREADS) k_prefilter_scan(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   for (int s = 0; s < B->n_scenes; ++s) {
     const SceneD& S = B->sc[s];
     int* a = B->pf_blocksum + S.pf_chunk_base;
@@ -182,6 +188,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_prefilter_scan(const Batch* __
 
 // Stable compaction: survivors in original tet order.
 __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int chunk = blockIdx.x;
@@ -218,6 +226,8 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* _
 // per-tet normal, App. A.3), view independent and hoisted into the scene
 // preparation (App. B.1).  grid (blocks, n_scenes)
 __global__ void __launch_bounds__(256) k_tet_normals(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int nsurv = B->ctr->n_surv[s];
@@ -372,6 +382,8 @@ __device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned act
 // keys of every tile the slot's rect overlaps.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int sc = blockIdx.y;
   const SceneD& S = B->sc[sc];
   const int nsurv = B->ctr->n_surv[sc];
@@ -447,6 +459,8 @@ __device__ __forceinline__ int tsort_class(int n) {
 }
 
 __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int s_b;
   __shared__ long long s_excl;
   Counters* c = B->ctr;
@@ -552,6 +566,8 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(const Batch* __restric
 // removes.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int v = blockIdx.y;
   const ViewD& vw = B->vw[v];
   const int chunk = blockIdx.x;
@@ -757,6 +773,8 @@ __device__ void sort_long_list(const Batch* __restrict__ B, int2 r, unsigned lon
 }
 
 __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ unsigned long long s[spad_size<TSORT_BLOCK_CAP>()];
   __shared__ int s_item[2];
   Counters* c = B->ctr;
@@ -843,6 +861,8 @@ constexpr int WL_THREADS = 256;     // one tile per thread
 // Work-list step 1 (one tile per thread): segment count and checkpoint slots
 // of each tile, and per block the units of each length bucket.
 __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int cnt[WL_BUCKETS];
   if (threadIdx.x < WL_BUCKETS) cnt[threadIdx.x] = 0;
   __syncthreads();
@@ -890,6 +910,8 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
 // the exclusive prefix of the blocks' unit counts (in place) and, over the
 // buckets from the longest down, the first unit of each bucket.
 __global__ void __launch_bounds__(17 * 32) k_worklist_scan(const Batch* __restrict__ B, int nb) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int total[WL_BUCKETS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int j = w; j < WL_BUCKETS; j += 17) {
@@ -918,6 +940,8 @@ __global__ void __launch_bounds__(17 * 32) k_worklist_scan(const Batch* __restri
 // Work-list step 3 (one tile per thread): each tile's units go after all
 // units of longer buckets and after the earlier blocks' units of its bucket.
 __global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __restrict__ B) {
+  pdl_wait();
+  pdl_launch_dependents();
   __shared__ int off[WL_BUCKETS];
   if (threadIdx.x < WL_BUCKETS)
     off[threadIdx.x] = B->wl_base[threadIdx.x] + B->wl_blockcnt[blockIdx.x * WL_BUCKETS + threadIdx.x];
@@ -942,26 +966,26 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __re
 // ---------------------------------------------------------------------------
 int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   dim3 g(P.max_pf_chunks, P.n_scenes);
-  k_prefilter_flags<<<g, PF_THREADS, 0, st>>>(dB);
-  k_prefilter_scan<<<1, SCAN_THREADS, 0, st>>>(dB);
-  k_prefilter_compact<<<g, PF_THREADS, 0, st>>>(dB);
+  launch_k(k_prefilter_flags, dim3(g), dim3(PF_THREADS), 0, st, dB);
+  launch_k(k_prefilter_scan, dim3(1), dim3(SCAN_THREADS), 0, st, dB);
+  launch_k(k_prefilter_compact, dim3(g), dim3(PF_THREADS), 0, st, dB);
   if (P.normals) {
-    k_tet_normals<<<dim3(P.normal_blocks, P.n_scenes), 256, 0, st>>>(dB);
+    launch_k(k_tet_normals, dim3(P.normal_blocks, P.n_scenes), dim3(256), 0, st, dB);
     return 4;
   }
   return 3;
 }
 
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
-  k_fwd_reset<<<64, 256, 0, st>>>(dB);
+  launch_k(k_fwd_reset, dim3(64), dim3(256), 0, st, dB);
   dim3 g(P.max_pp_chunks, P.n_views);
-  k_preprocess<<<dim3(P.max_pre_chunks, P.n_scenes), PP_THREADS, 0, st>>>(dB);
-  k_tile_scan<<<(P.total_tiles + TS_TILES - 1) / TS_TILES, TS_THREADS, 0, st>>>(dB);
-  k_place<<<g, PP_THREADS, 0, st>>>(dB);
-  k_tile_sort<<<P.tsort_blocks, TSORT_NT, 0, st>>>(dB);
-  k_worklist_count<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
-  k_worklist_scan<<<1, 17 * 32, 0, st>>>(dB, P.wl_blocks);
-  k_worklist_place<<<P.wl_blocks, WL_THREADS, 0, st>>>(dB);
+  launch_k(k_preprocess, dim3(P.max_pre_chunks, P.n_scenes), dim3(PP_THREADS), 0, st, dB);
+  launch_k(k_tile_scan, dim3((P.total_tiles + TS_TILES - 1) / TS_TILES), dim3(TS_THREADS), 0, st, dB);
+  launch_k(k_place, dim3(g), dim3(PP_THREADS), 0, st, dB);
+  launch_k(k_tile_sort, dim3(P.tsort_blocks), dim3(TSORT_NT), 0, st, dB);
+  launch_k(k_worklist_count, dim3(P.wl_blocks), dim3(WL_THREADS), 0, st, dB);
+  launch_k(k_worklist_scan, dim3(1), dim3(17 * 32), 0, st, dB, P.wl_blocks);
+  launch_k(k_worklist_place, dim3(P.wl_blocks), dim3(WL_THREADS), 0, st, dB);
   return 8;
 }
 

@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
                                                        float* __restrict__ alpha,
                                                        float* __restrict__ depth,
                                                        float* __restrict__ normal) {
+  pdl_wait();
+  pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q + NRM][32];
   __shared__ int sidx[WPB][32];
@@ -452,6 +454,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
                                                            float* __restrict__ alpha,
                                                            float* __restrict__ depth,
                                                            float* __restrict__ normal) {
+  pdl_wait();
+  pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q][32];
   __shared__ unsigned sslot[WPB][32];
@@ -561,6 +565,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
                                                        const float* __restrict__ dalpha,
                                                        const float* __restrict__ ddepth,
                                                        const float* __restrict__ dnormal) {
+  pdl_wait();
+  pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
   constexpr int NF = NRM ? 23 : 20;          // gradient fields per fragment
   constexpr int RS = NRM ? 23 : 21;          // row stride (odd: no bank conflicts)
@@ -784,6 +790,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
                                                            const float* __restrict__ dalpha,
                                                            const float* __restrict__ ddepth,
                                                            const float* __restrict__ dnormal) {
+  pdl_wait();
+  pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[WPB][REC_Q][32];
   __shared__ unsigned sslot[WPB][32];
@@ -947,6 +955,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
 // ---------------------------------------------------------------------------
 template <bool NRM>
 __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
+  pdl_wait();
+  pdl_launch_dependents();
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int nsurv = B->ctr->n_surv[s];
@@ -1122,10 +1132,10 @@ static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha,
                  float* normal, cudaStream_t st) {
   const int g = P.blend_fwd_blocks;
   if (P.window > 0) {
-    k_blend_fwd_win<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+    launch_k(k_blend_fwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, image, alpha, depth, normal);
     return 1;
   }
-  k_blend_fwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, image, alpha, depth, normal);
+  launch_k(k_blend_fwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, image, alpha, depth, normal);
   return 1;
 }
 
@@ -1134,9 +1144,9 @@ static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const
                   const float* ddepth, const float* dnormal, cudaStream_t st) {
   const int g = P.blend_bwd_blocks;
   if (P.window > 0)
-    k_blend_bwd_win<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth, dnormal);
+    launch_k(k_blend_bwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth, dnormal);
   else
-    k_blend_bwd<TILE, NRM><<<g, WPB * 32, 0, st>>>(dB, dimage, dalpha, ddepth, dnormal);
+    launch_k(k_blend_bwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth, dnormal);
 }
 
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
@@ -1166,8 +1176,8 @@ int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, co
 
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st) {
   dim3 g(P.tet_bwd_blocks, P.n_scenes);
-  if (P.normals) k_tet_bwd<true><<<g, 256, 0, st>>>(dB, go);
-  else k_tet_bwd<false><<<g, 256, 0, st>>>(dB, go);
+  if (P.normals) launch_k(k_tet_bwd<true>, dim3(g), dim3(256), 0, st, dB, go);
+  else launch_k(k_tet_bwd<false>, dim3(g), dim3(256), 0, st, dB, go);
   return 1;
 }
 

@@ -28,6 +28,27 @@ struct GradOut {
   float* drgb[TTS_MAX_SCENES];
 };
 
+// Launch with programmatic stream serialization (see pdl_wait): the kernel's
+// blocks may be scheduled while the previous kernel in the stream finishes.
+// A launch error is kept for check_launch.
+void note_launch_error(cudaError_t e);
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  if (e != cudaSuccess) note_launch_error(e);
+}
+
 // Each launcher returns the number of kernels it launched.
 int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st);
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st);

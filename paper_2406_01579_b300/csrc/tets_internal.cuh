@@ -216,6 +216,16 @@ __device__ __forceinline__ Opacity opacity_eval(const float4& q4, const Chord& c
   return o;
 }
 
+// Programmatic dependent launch: a kernel of the step may be scheduled while
+// its predecessor in the stream finishes.  pdl_wait, its first statement,
+// blocks until the predecessor grid has completed and its writes are
+// visible; pdl_launch_dependents lets the successor be scheduled once every
+// block of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_status(Counters* c, unsigned int bit) {
   atomicOr(&c->status, bit);
 }
