@@ -438,15 +438,7 @@ int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, floa
     go.drgb[s] = drgb[s];
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!(b->params.flags & TTS_FLAG_ACCUM_GRAD)) {
-    for (int s = 0; s < b->n_scenes; ++s) {
-      const size_t N = (size_t)b->scenes[s].N;
-      if (cudaMemsetAsync(dV[s], 0, 12 * N, st) != cudaSuccess ||
-          cudaMemsetAsync(df[s], 0, 4 * N, st) != cudaSuccess ||
-          cudaMemsetAsync(drgb[s], 0, 12 * N, st) != cudaSuccess)
-        return TTS_ERR_CUDA;
-    }
-  }
+  if (!(b->params.flags & TTS_FLAG_ACCUM_GRAD)) g_launches += launch_zero_grads(P.hp, dev_desc(b, P), go, st);
   g_launches += launch_tet_bwd(P.hp, dev_desc(b, P), go, st);
   return check_launch();
 }

@@ -1083,6 +1083,31 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
   }
 }
 
+// Clears dV, df, drgb of every scene before the record -> vertex scatter
+// (16-byte stores where the arrays allow, grid-stride).  grid (blocks, n_scenes)
+__global__ void __launch_bounds__(256) k_zero_grads(const Batch* __restrict__ B, GradOut go) {
+  pdl_wait();
+  pdl_launch_dependents();
+  const int s = blockIdx.y;
+  const long long N = B->sc[s].N;
+  float* const arr[3] = {go.dV[s], go.df[s], go.drgb[s]};
+  const long long len[3] = {3 * N, N, 3 * N};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int a = 0; a < 3; ++a) {
+    float* p = arr[a];
+    const long long n = len[a];
+    // head up to 16-byte alignment, then float4 stores, then the tail
+    const long long head = min(n, (long long)((16 - (reinterpret_cast<uintptr_t>(p) & 15)) & 15) / 4);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < head; i += stride) p[i] = 0.f;
+    float4* q = reinterpret_cast<float4*>(p + head);
+    const long long n4 = (n - head) / 4;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride)
+      q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = head + 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+      p[i] = 0.f;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -1171,6 +1196,11 @@ int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, co
     case 64: bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
     default: bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
   }
+  return 1;
+}
+
+int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st) {
+  launch_k(k_zero_grads, dim3(P.tet_bwd_blocks * 4, P.n_scenes), dim3(256), 0, st, dB, go);
   return 1;
 }
 

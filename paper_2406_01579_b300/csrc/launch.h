@@ -61,6 +61,7 @@ int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* al
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                      const float* ddepth, const float* dnormal, cudaStream_t st);
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
+int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);
 // persistent grid sizes of the blend kernels for a tile size (occupancy based)
 void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, int* bwd_blocks);
