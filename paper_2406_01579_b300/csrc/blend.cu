@@ -1015,9 +1015,10 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
         const float3 dm = f3(gP * xr.x + gA * G.zr, gP * xr.y + gB * G.zr, gP * xr.z);
         const float e = G.e[fk];
         const float3 n = G.n[fk];
-        const float lam = dot3(n, dm) / (e * e);
+        const float ie = rcp_approx(e);
+        const float lam = dot3(n, dm) * (ie * ie);
         const float3 Xi = G.xm + G.y[i];
-        const float3 dn = (1.f / e) * dm - lam * Xi;
+        const float3 dn = ie * dm - lam * Xi;
         dX[i] = dX[i] - lam * n;
         const float3 dnr = G.sgn[fk] * dn;
         const float3 ea = G.y[j] - G.y[i], eb = G.y[l] - G.y[i];
@@ -1036,7 +1037,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
         dX[q] = dX[q] - (0.25f * dfr) * G.g;
       }
       // g = Y^-1 df with Y rows y_j - y_0 (j = 1..3)
-      const float idet = 1.f / G.det;
+      const float idet = rcp_approx(G.det);
       const float dd1 = dot3(G.cof[0], dg) * idet, dd2 = dot3(G.cof[1], dg) * idet,
                   dd3 = dot3(G.cof[2], dg) * idet;
       dff[1] += dd1; dff[2] += dd2; dff[3] += dd3;

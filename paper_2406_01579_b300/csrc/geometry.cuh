@@ -172,7 +172,7 @@ __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const Tet
     G.n[k] = n;
     G.e[k] = e;
     G.sgn[k] = sg;
-    const float inv = 1.f / e;
+    const float inv = rcp_approx(e);   // |e| is clamped away from 0 above
     Pf[k] = dot3(n, G.w - G.y[i]) * inv;
     Af[k] = G.zr * n.x * inv;
     Bf[k] = G.zr * n.y * inv;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const Tet
   }
   // affine SDF: gradient g from the edge system, value at the reference point
   const float d1 = in.f[1] - in.f[0], d2 = in.f[2] - in.f[0], d3 = in.f[3] - in.f[0];
-  const float idet = 1.f / G.det;
+  const float idet = rcp_approx(G.det);   // a flat tet was rejected above
   G.g = idet * (d1 * G.cof[0] + d2 * G.cof[1] + d3 * G.cof[2]);
   G.fm = 0.25f * ((in.f[0] + in.f[1]) + (in.f[2] + in.f[3]));
   G.fr = G.fm + dot3(G.g, G.w);
