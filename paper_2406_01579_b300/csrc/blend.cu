@@ -690,13 +690,14 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         if (contrib) {
           const float4 q5 = st[wid][5][k];
           const float om = __fsub_rn(1.f, a);
-          const float Ti = __fdiv_rn(T, om);
+          const float iom = rcp_approx(om);   // a <= cap < 1 (or a pure-mode alpha < 1)
+          const float Ti = T * iom;
           float wv = gC0 * q5.y + gC1 * q5.z + gC2 * q5.w + gD * q5.x;
           if constexpr (NRM) {
             const float4 n = st[wid][REC_Q][k];
             wv += gN0 * n.x + gN1 * n.y + gN2 * n.z;
           }
-          const float dLda = Ti * wv - (S - gOT) / om;
+          const float dLda = Ti * wv - (S - gOT) * iom;
           S += Ti * a * wv;
           T = Ti;
           const float wgt = Ti * a;
@@ -857,7 +858,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       }
       const float twa = T * a * wv;
       const float suffix = Wt - Pw - twa;
-      const float dLda = T * wv - (suffix - gOT) / __fsub_rn(1.f, a);
+      const float dLda = T * wv - (suffix - gOT) * rcp_approx(__fsub_rn(1.f, a));
       Pw += twa;
       const float wgt = T * a;
       float4* dst = rgrad + (size_t)slot * REC_Q;
