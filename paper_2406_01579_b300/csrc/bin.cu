@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   const int k0 = blockIdx.x * PRE_CHUNK;
   if (k0 >= nsurv) return;
   const float s = B->s;
-  const int tile = B->tile;
+  const int tsh = __ffs(B->tile) - 1;   // tile is 8, 16 or 32
   unsigned zmn = 0xffffffffu, zmx = 0u;
   for (int q = threadIdx.x; q < PRE_CHUNK; q += PP_THREADS) {
     const int k = k0 + q;
@@ -405,9 +405,9 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
         Geo G;
         tet_geometry(vw, s, in, G);
         if (G.visible) {
-          tx0 = G.i0 / tile;
-          ty0 = G.j0 / tile;
-          const int tx1 = G.i1 / tile, ty1 = G.j1 / tile;
+          tx0 = G.i0 >> tsh;     // pixel bounds are >= 0
+          ty0 = G.j0 >> tsh;
+          const int tx1 = G.i1 >> tsh, ty1 = G.j1 >> tsh;
           ntx = tx1 - tx0 + 1;
           nt = ntx * (ty1 - ty0 + 1);
           B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
@@ -420,9 +420,16 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
       }
       // key counts per tile, one atomic per (warp, tile) and round
       int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
+      int cx = 0, cy = 0;    // position of round r in the rect
       for (int r = 0; __any_sync(0xffffffffu, r < nt); ++r) {
         const unsigned act = __ballot_sync(0xffffffffu, r < nt);
-        if (r < nt) warp_bucket_add(cnt, (ty0 + r / ntx) * vw.tiles_x + tx0 + r % ntx, act, false);
+        if (r < nt) {
+          warp_bucket_add(cnt, (ty0 + cy) * vw.tiles_x + tx0 + cx, act, false);
+          if (++cx == ntx) {
+            cx = 0;
+            ++cy;
+          }
+        }
       }
     }
   }
@@ -593,11 +600,16 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
         comp = ((unsigned long long)B->rec_z[slot] << 32) | (unsigned)slot;
       }
     }
+    int cx = 0, cy = 0;    // position of round j in the rect
     for (int j = 0; __any_sync(0xffffffffu, j < nt); ++j) {
       const unsigned act = __ballot_sync(0xffffffffu, j < nt);
       if (j < nt) {
-        const int pos = warp_bucket_add(cur, (r.z + j / ntx) * vw.tiles_x + r.x + j % ntx, act, true);
+        const int pos = warp_bucket_add(cur, (r.z + cy) * vw.tiles_x + r.x + cx, act, true);
         if (pos < used) out[pos] = comp;
+        if (++cx == ntx) {
+          cx = 0;
+          ++cy;
+        }
       }
     }
   }
