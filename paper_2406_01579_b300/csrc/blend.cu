@@ -993,8 +993,10 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
       dnw = dnw + f3(g0.x, g0.y, g0.z);
       if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
+      // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
+      const float4 q0 = __ldg(B->rec + slot * REC_Q);
       Geo G;
-      tet_geometry(vw, sv, in, G);
+      tet_geometry_at(vw, in, (int)(fabsf(q0.x) - 0.5f), (int)(fabsf(q0.y) - 0.5f), G);
       if (!G.visible) continue;
       any = true;
       const float gPs[4] = {g1.x, g1.y, g1.z, g1.w};

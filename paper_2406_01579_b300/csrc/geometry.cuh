@@ -131,9 +131,28 @@ __device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& 
 // offset between the tet and the reference pixel ray carries no rounding at
 // the scale of the camera distance (which the Eq. 1 steepness s would
 // amplify).
+__device__ __forceinline__ void tet_geometry_rest(const ViewD& vw, const TetIn& in, Geo& G);
+
 __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const TetIn& in, Geo& G) {
+  (void)s;
   G.visible = key_path(vw, in, G);
   if (!G.visible) return;
+  tet_geometry_rest(vw, in, G);
+}
+
+// The same geometry for a tet whose key path already ran (in the forward): the
+// pixel bbox corner (i0, j0) comes from its record instead.  zbits, zbar and
+// (i1, j1) are not set.
+__device__ __forceinline__ void tet_geometry_at(const ViewD& vw, const TetIn& in, int i0, int j0,
+                                                Geo& G) {
+  G.visible = true;
+  G.i0 = i0;
+  G.j0 = j0;
+  tet_geometry_rest(vw, in, G);
+}
+
+// Everything after the key path: frame, reference point, faces, affine SDF.
+__device__ __forceinline__ void tet_geometry_rest(const ViewD& vw, const TetIn& in, Geo& G) {
   const float sx = vw.fx, sy = vw.fy;
   const float3 m = 0.25f * ((in.v[0] + in.v[1]) + (in.v[2] + in.v[3]));
 #pragma unroll
@@ -200,7 +219,6 @@ __device__ __forceinline__ void tet_geometry(const ViewD& vw, float s, const Tet
   G.g = idet * (d1 * G.cof[0] + d2 * G.cof[1] + d3 * G.cof[2]);
   G.fm = 0.25f * ((in.f[0] + in.f[1]) + (in.f[2] + in.f[3]));
   G.fr = G.fm + dot3(G.g, G.w);
-  (void)s;
 }
 
 __device__ __forceinline__ void write_record(const ViewD& vw, float s, const TetIn& in, const Geo& G,
