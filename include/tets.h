@@ -118,8 +118,8 @@ typedef struct {
                              more than N_w, the rest at the end.  0: per-tile sort order. */
   int32_t blend_segment;  /* list entries per backward work unit: 0 (library default, 256)
                              or a multiple of 32 in 32..65536.  The forward walks each tile
-                             list whole (a list longer than blend_segment as 4x4 blocks with
-                             two lanes per pixel) and records its state every blend_segment
+                             list whole (a list longer than blend_segment as 4x2 blocks with
+                             four lanes per pixel) and records its state every blend_segment
                              entries; the backward walks the segments of a longer list in
                              parallel from those states (equal to the unsplit walk up to
                              FP32 rounding).  Ignored with a resort window. */

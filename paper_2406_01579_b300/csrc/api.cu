@@ -205,8 +205,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   // checkpoint of 32 B per pixel and segment
   B.seg_cap = B.seg_len > 0 ? (int)std::min<long long>(2 * cap / B.seg_len + 1, 0x3fffffffLL) : 0;
   const long long tt = (long long)pr.tile * pr.tile;
-  // units: one per tile, one per later segment, one more per split tile
-  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + 2 * (size_t)B.seg_cap));
+  // units: one per tile, one per later segment, up to three more per split
+  // tile (each split tile has at least two segments)
+  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + 3 * (size_t)B.seg_cap));
   const size_t o_tseg = take(sizeof(int2) * tiles);
   const int wl_blocks = (tiles + 255) / 256;
   const size_t o_wlc = take(sizeof(int) * 34 * (size_t)wl_blocks);

@@ -859,9 +859,9 @@ __global__ void k_debug_keys(const Batch* __restrict__ B) {
 
 // Work list for the persistent blend kernels, units (tile, segment | part << 24).
 // A tile whose list is longer than seg_len entries is split into segments of
-// seg_len entries: the forward walks the whole list (the segment-0 units,
-// parts 0 and 1 covering its 4x4 blocks) and records its state at each
-// segment end, and the backward walks the segments in parallel from those
+// seg_len entries: the forward walks the whole list (the segment-0 units:
+// parts 0..3 covering its 4x2 blocks, see fwd_lanes) and records its state at
+// each segment end, and the backward walks the segments in parallel from those
 // states (one warp per 8x4 block walking a long list back to front would
 // otherwise bound its duration).  Units (tile, segment) are ordered by
 // decreasing work (bucketed by bit length), so the longest start first; the
@@ -911,7 +911,7 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
     // segment 0 carries the forward's walk of the whole list (two parts for
     // a split list): bucketed by the list length; the later segments
     // (backward only) by the segment length
-    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], nseg > 1 ? 2 : 1);
+    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], fwd_lanes(nseg));
     if (nseg > 1) atomicAdd(&cnt[32 - __clz(L)], nseg - 1);
   }
   __syncthreads();
@@ -964,10 +964,11 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __re
   const int2 r = B->ranges[t];
   const int2 ts = B->tseg[t];
   const int len = r.y - r.x;
-  const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], ts.y > 1 ? 2 : 1);
+  const int parts = fwd_lanes(ts.y);         // forward units of the list
+  const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], parts);
   B->worklist[pos0] = make_int2(t, 0);
+  for (int q = 1; q < parts; ++q) B->worklist[pos0 + q] = make_int2(t, q << 24);   // forward only
   if (ts.y > 1) {
-    B->worklist[pos0 + 1] = make_int2(t, 1 << 24);   // part 1: forward only
     const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
     for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
   }

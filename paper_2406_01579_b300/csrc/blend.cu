@@ -42,7 +42,7 @@ struct WarpBlock {
   int gt;
   int seg;                    // segment of a split tile list (0 otherwise)
   int sb;                     // 8x4 block within the tile
-  int part;                   // forward part of a long list (4x4 blocks part*SB ..)
+  int part;                   // forward part of a long list (4x2 blocks part*SB ..)
   int tpix;                   // the lane's pixel within the tile, row-major
   int px, py;
   bool inimg;
@@ -97,10 +97,10 @@ __device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B
   return vw;
 }
 
-// A 4x4 pixel block (b4 in tile-local row-major order of 4x4 blocks) with two
-// lanes per pixel: lane = 2 * (4 * row + column) + sub.
+// A 4x2 pixel block (b8 in tile-local row-major order of 4x2 blocks) with
+// four lanes per pixel: lane = 4 * (4 * row + column) + sub.
 template <int TILE>
-__device__ __forceinline__ const ViewD& decode_block4(const Batch* __restrict__ B, int gt, int b4,
+__device__ __forceinline__ const ViewD& decode_block8(const Batch* __restrict__ B, int gt, int b8,
                                                       WarpBlock& wb) {
   constexpr int BX = TILE / 4;
   wb.gt = gt;
@@ -110,8 +110,8 @@ __device__ __forceinline__ const ViewD& decode_block4(const Batch* __restrict__ 
   const ViewD& vw = B->vw[find_view(B, wb.gt)];
   const int lt = wb.gt - vw.tile_base;
   const int tyi = lt / vw.tiles_x, txi = lt - tyi * vw.tiles_x;
-  const int ox = (b4 % BX) * 4, oy = (b4 / BX) * 4;
-  const int pix = (threadIdx.x & 31) >> 1;
+  const int ox = (b8 % BX) * 4, oy = (b8 / BX) * 2;
+  const int pix = (threadIdx.x & 31) >> 2;
   wb.tpix = (oy + (pix >> 2)) * TILE + ox + (pix & 3);
   const int bx = txi * TILE + ox, by = tyi * TILE + oy;
   wb.px = bx + (pix & 3);
@@ -122,13 +122,13 @@ __device__ __forceinline__ const ViewD& decode_block4(const Batch* __restrict__ 
   wb.wx0 = (float)bx + 0.5f;
   wb.wx1 = wb.wx0 + 3.f;
   wb.wy0 = (float)by + 0.5f;
-  wb.wy1 = wb.wy0 + 3.f;
+  wb.wy1 = wb.wy0 + 1.f;
   return vw;
 }
 
 // Work item -> warp block: item / SB indexes the (tile, segment) unit list.
 // Units are (tile, segment | part << 24): segment > 0 units are backward
-// work only, part > 0 units forward work only (the further 4x4 blocks of a
+// work only, part > 0 units forward work only (the further 4x2 blocks of a
 // long list).
 template <int TILE>
 __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
@@ -237,13 +237,13 @@ __device__ __forceinline__ float fragment_code(const float4& q4, const Chord& ch
 // lanes that are not done: the entries whose bbox meets a live pixel are
 // staged (ballot) in the warp's shared-memory slice and blended in order
 // (Eq. 1 opacity, Eq. 2 compositing, 3DGS conventions); a pixel stops before
-// the fragment that would take T below eps (not in PURE mode).  Candidates
-// are taken in pairs.  LPP = 1 (an 8x4 block, one lane per pixel): each lane
-// evaluates both chords, then (when either meets a live lane) both
-// opacities, then composites the two in order.  LPP = 2 (a 4x4 block, two
-// lanes per pixel): each lane of a pixel evaluates one candidate of the
-// pair, the two exchange their fragment codes and both composite the pair
-// in order, which halves the chain a long list puts on one warp.  `last`
+// the fragment that would take T below eps (not in PURE mode).  LPP = 1 (an
+// 8x4 block, one lane per pixel): candidates in pairs; each lane evaluates
+// both chords, then (when either meets a live lane) both opacities, then
+// composites the two in order.  LPP = 4 (a 4x2 block, four lanes per pixel):
+// candidates in fours; each lane of a pixel evaluates one of them, the four
+// exchange their fragment codes and all composite the four in order, which
+// cuts the chain a long list puts on one warp by four.  `last`
 // counts list entries from lo.  When the list is split into segments for
 // the backward (ts.y > 1), the state at the end of each segment is stored as
 // the walk passes it.
@@ -255,7 +255,7 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
                                          int tt, bool pure, float cap, float skip, float eps,
                                          float4 (*st)[32], int* sidx, FwdState& S) {
   const int lane = threadIdx.x & 31;
-  const int sub = (LPP == 2) ? (lane & 1) : 0;
+  const int sub = lane & (LPP - 1);
   const unsigned ltm = (1u << lane) - 1u;
   const int L = B->seg_len;
   const bool split = ts.y > 1;
@@ -290,7 +290,8 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
       __syncwarp();
       const int cnt = __popc(m);
       const int base = g - lo;
-      for (int k0 = 0; k0 < cnt; k0 += 2) {
+      constexpr int STEP = (LPP == 4) ? 4 : 2;
+      for (int k0 = 0; k0 < cnt; k0 += STEP) {
         if constexpr (LPP == 1) {
           const int ka = k0, kb = min(k0 + 1, cnt - 1);   // past the end: evaluated again, masked
           const Chord cha = chord_eval(st[0][ka], st[1][ka], st[2][ka], st[3][ka], wb.fpx, wb.fpy);
@@ -307,9 +308,13 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           const bool h = ch.hit && (k0 + sub < cnt);
           if (!__any_sync(FULL, h && !S.done)) continue;
           const float mine = h ? fragment_code(st[4][k], ch, pure, cap, skip) : 0.f;
-          const float other = __shfl_xor_sync(FULL, mine, 1);
-          composite<NRM>(sub ? other : mine, k0, base, pure, eps, st, sidx, S);
-          composite<NRM>(sub ? mine : other, min(k0 + 1, cnt - 1), base, pure, eps, st, sidx, S);
+          const int l0 = lane & ~3;
+          const float c0 = __shfl_sync(FULL, mine, l0), c1 = __shfl_sync(FULL, mine, l0 + 1),
+                      c2 = __shfl_sync(FULL, mine, l0 + 2), c3 = __shfl_sync(FULL, mine, l0 + 3);
+          composite<NRM>(c0, k0, base, pure, eps, st, sidx, S);
+          composite<NRM>(c1, min(k0 + 1, cnt - 1), base, pure, eps, st, sidx, S);
+          composite<NRM>(c2, min(k0 + 2, cnt - 1), base, pure, eps, st, sidx, S);
+          composite<NRM>(c3, min(k0 + 3, cnt - 1), base, pure, eps, st, sidx, S);
         }
         if (__all_sync(FULL, S.done)) break;
       }
@@ -350,17 +355,18 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
     const ViewD* vwp = &decode_item<TILE>(B, item, wb);
     if (wb.seg > 0) continue;
     const int2 ts = B->tseg[wb.gt];
-    const bool two = ts.y > 1;   // a long list: 4x4 blocks with two lanes per pixel
-    if (two) vwp = &decode_block4<TILE>(B, wb.gt, wb.part * SB + wb.sb, wb);
+    const int2 rg = B->ranges[wb.gt];
+    // a long list: 4x2 blocks with four lanes per pixel (four forward units)
+    const bool four = fwd_lanes(ts.y) == 4;
+    if (four) vwp = &decode_block8<TILE>(B, wb.gt, wb.part * SB + wb.sb, wb);
     const ViewD& vw = *vwp;
     if (!__any_sync(FULL, wb.inimg)) continue;
-    const int2 rg = B->ranges[wb.gt];
     const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
     FwdState S = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, !wb.inimg};
-    if (two) {
-      fwd_walk<NRM, 2>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
+    if (four) {
+      fwd_walk<NRM, 4>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
                        st[wid], sidx[wid], S);
-      if (wb.inimg && (threadIdx.x & 1) == 0) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+      if (wb.inimg && (threadIdx.x & 3) == 0) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
     } else {
       fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
                        st[wid], sidx[wid], S);
