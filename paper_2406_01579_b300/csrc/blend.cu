@@ -562,8 +562,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
 // K7: backward blend.  Same warp blocks; each warp re-walks its tile's list
 // back to front from the last entry any of its pixels blended, recomputes
 // every fragment bit for bit, and accumulates the record-field gradients
-// (warp-reduced; one vector atomic per field group) into the per-slot record
-// gradient buffer.
+// (per contributing lane, one vector atomic per field group) into the
+// per-slot record gradient buffer.
 // ---------------------------------------------------------------------------
 template <int TILE, bool NRM>
 __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict__ B,
@@ -574,12 +574,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   pdl_wait();
   pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  constexpr int NF = NRM ? 23 : 20;          // gradient fields per fragment
-  constexpr int RS = NRM ? 23 : 21;          // row stride (odd: no bank conflicts)
   __shared__ float4 st[WPB][REC_Q + NRM][32];
   __shared__ int sidx[WPB][32];
   __shared__ unsigned sslot[WPB][32];
-  __shared__ float red[WPB][32][RS];         // per-lane gradient rows
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
@@ -736,47 +733,16 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
             gKy = (dy + dsGz) * ch.dy;
           }
         }
-        float4* dst = rgrad + (size_t)sslot[wid][k] * REC_Q;
-        if (__popc(mc) == 1) {
-          if (contrib) {
-            atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-            atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-            atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-            atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-            atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
-            if constexpr (NRM) atomicAdd(dst, make_float4(gn0, gn1, gn2, 0.f));
-          }
-        } else {
-          // transpose through shared memory: lane j < NF sums field j over the
-          // contributing lanes' rows and issues one atomic (fields 0..19 are
-          // record components 4..23, fields 20..22 the normal gradient at 0..2)
-          if (contrib) {
-            float* row = red[wid][lane];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              row[q] = gP[q];
-              row[4 + q] = gA[q];
-              row[8 + q] = gB[q];
-            }
-            row[12] = gF; row[13] = gK0; row[14] = gKx; row[15] = gKy;
-            row[16] = gz; row[17] = gc0; row[18] = gc1; row[19] = gc2;
-            if constexpr (NRM) {
-              row[20] = gn0; row[21] = gn1; row[22] = gn2;
-            }
-          }
-          __syncwarp();
-          if (lane < NF) {
-            float acc = 0.f;
-            unsigned mm = mc;
-            while (mm) {
-              const int r = __ffs(mm) - 1;
-              mm &= mm - 1u;
-              acc += red[wid][r][lane];
-            }
-            if (acc != 0.f)
-              atomicAdd(reinterpret_cast<float*>(dst) + (lane < 20 ? 4 + lane : lane - 20), acc);
-          }
-          __syncwarp();
+        // each contributing lane adds its record-field gradients with vector
+        // atomics (the few lanes of one candidate meet in L2)
+        if (contrib) {
+          float4* dst = rgrad + (size_t)sslot[wid][k] * REC_Q;
+          atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
+          atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
+          atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
+          atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
+          atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
+          if constexpr (NRM) atomicAdd(dst, make_float4(gn0, gn1, gn2, 0.f));
         }
       }
       __syncwarp();
