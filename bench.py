@@ -202,25 +202,33 @@ def run_ours(a, rank, world):
     b = r.batch()
     bp = ctypes.byref(b)
     stages = ["prefilter", "bin", "blend_fwd", "blend_bwd", "scatter_bwd"]
+    outs = _lib.tts_outputs()
+    outs.image, outs.alpha, outs.depth, outs.normal = (img.data_ptr(), alpha.data_ptr(),
+                                                        depth.data_ptr(), None)
+    ups_c = _lib.tts_upstream()
+    ups_c.dimage, ups_c.dalpha, ups_c.ddepth, ups_c.dnormal = (gi.data_ptr(), ga.data_ptr(),
+                                                               gd.data_ptr(), None)
 
     def step(ev=None):
-        if ev is not None:
-            ev[0].record(stream)
+        """One training step through the public entry points (pre-filter,
+        render forward, render backward); with ev, the same work through the
+        per-stage entry points with an event between stages (stage timing)."""
+        if ev is None:
+            _lib.check(L.tts_prepare_scene(bp, sp))
+            _lib.check(L.tts_render_fwd_ex(bp, ctypes.byref(outs), sp))
+            _lib.check(L.tts_render_bwd_ex(bp, ctypes.byref(ups_c), dV, df, dc, sp))
+            return
+        ev[0].record(stream)
         _lib.check(L.tts_prepare_scene(bp, sp))
-        if ev is not None:
-            ev[1].record(stream)
+        ev[1].record(stream)
         _lib.check(L.tts_bin_views(bp, sp))
-        if ev is not None:
-            ev[2].record(stream)
+        ev[2].record(stream)
         _lib.check(L.tts_blend_fwd(bp, img.data_ptr(), alpha.data_ptr(), depth.data_ptr(), sp))
-        if ev is not None:
-            ev[3].record(stream)
+        ev[3].record(stream)
         _lib.check(L.tts_blend_bwd(bp, gi.data_ptr(), ga.data_ptr(), gd.data_ptr(), sp))
-        if ev is not None:
-            ev[4].record(stream)
+        ev[4].record(stream)
         _lib.check(L.tts_scatter_bwd(bp, dV, df, dc, sp))
-        if ev is not None:
-            ev[5].record(stream)
+        ev[5].record(stream)
 
     def barrier():
         torch.cuda.synchronize(dev)
@@ -242,7 +250,7 @@ def run_ours(a, rank, world):
     clk.mark(0)
     t_start.record(stream)
     for k in range(a.steps):
-        step(evs[k])
+        step()
     t_end.record(stream)
     barrier()
     clk.mark(1)
@@ -250,6 +258,10 @@ def run_ours(a, rank, world):
     clocks = clk.stop()
     launches = L.tts_launch_count() - n0
     elapsed = t_start.elapsed_time(t_end) / 1e3
+    # stage breakdown: the same steps again, with events between the stages
+    for k in range(a.steps):
+        step(evs[k])
+    barrier()
     stage_ms = {s: statistics.mean(evs[k][i].elapsed_time(evs[k][i + 1]) for k in range(a.steps))
                 for i, s in enumerate(stages)}
     info = r.info()

@@ -407,15 +407,23 @@ int tts_render_fwd(const tts_batch* b, float* image, float* alpha, float* depth,
   return tts_render_fwd_ex(b, &o, stream);
 }
 
-int tts_blend_bwd_ex(const tts_batch* b, const tts_upstream* up, tts_stream stream) {
+// The blend backward; with zero, its warps also clear those vertex-gradient
+// arrays once their work is done (for a record -> vertex scatter that
+// follows without clearing).
+static int blend_bwd_impl(const tts_batch* b, const tts_upstream* up, const GradOut* zero,
+                          tts_stream stream) {
   if (!upstream_ok(b, up)) return TTS_ERR_ARG;
   Plan P;
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   g_launches += launch_blend_bwd(P.hp, dev_desc(b, P), up->dimage, up->dalpha, up->ddepth,
-                                 up->dnormal, st);
+                                 up->dnormal, zero, st);
   return check_launch();
+}
+
+int tts_blend_bwd_ex(const tts_batch* b, const tts_upstream* up, tts_stream stream) {
+  return blend_bwd_impl(b, up, nullptr, stream);
 }
 
 int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,
@@ -424,32 +432,52 @@ int tts_blend_bwd(const tts_batch* b, const float* dimage, const float* dalpha, 
   return tts_blend_bwd_ex(b, &u, stream);
 }
 
-int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
-                    tts_stream stream) {
+static int grad_out(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
+                    GradOut* go) {
   if (!dV || !df || !drgb || !b || (b->params.flags & TTS_FLAG_FORWARD_ONLY)) return TTS_ERR_ARG;
+  if (b->n_scenes < 1 || b->n_scenes > TTS_MAX_SCENES) return TTS_ERR_ARG;
+  std::memset(go, 0, sizeof(*go));
+  for (int s = 0; s < b->n_scenes; ++s) {
+    if (!dV[s] || !df[s] || !drgb[s]) return TTS_ERR_ARG;
+    go->dV[s] = dV[s];
+    go->df[s] = df[s];
+    go->drgb[s] = drgb[s];
+  }
+  return TTS_OK;
+}
+
+// The record -> vertex scatter; `cleared`: the gradient arrays were already
+// cleared (by the blend backward) and must not be cleared again.
+static int scatter_bwd_impl(const tts_batch* b, const GradOut& go, bool cleared, tts_stream stream) {
   Plan P;
   int rc = make_plan(b, &P, true);
   if (rc != TTS_OK) return rc;
-  GradOut go;
-  std::memset(&go, 0, sizeof(go));
-  for (int s = 0; s < b->n_scenes; ++s) {
-    if (!dV[s] || !df[s] || !drgb[s]) return TTS_ERR_ARG;
-    go.dV[s] = dV[s];
-    go.df[s] = df[s];
-    go.drgb[s] = drgb[s];
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!(b->params.flags & TTS_FLAG_ACCUM_GRAD)) g_launches += launch_zero_grads(P.hp, dev_desc(b, P), go, st);
+  if (!cleared && !(b->params.flags & TTS_FLAG_ACCUM_GRAD))
+    g_launches += launch_zero_grads(P.hp, dev_desc(b, P), go, st);
   g_launches += launch_tet_bwd(P.hp, dev_desc(b, P), go, st);
   return check_launch();
 }
 
+int tts_scatter_bwd(const tts_batch* b, float* const* dV, float* const* df, float* const* drgb,
+                    tts_stream stream) {
+  GradOut go;
+  int rc = grad_out(b, dV, df, drgb, &go);
+  if (rc != TTS_OK) return rc;
+  return scatter_bwd_impl(b, go, false, stream);
+}
+
 int tts_render_bwd_ex(const tts_batch* b, const tts_upstream* up, float* const* dV,
                       float* const* df, float* const* drgb, tts_stream stream) {
-  if (!upstream_ok(b, up) || !dV || !df || !drgb) return TTS_ERR_ARG;
-  int rc = tts_blend_bwd_ex(b, up, stream);
+  if (!upstream_ok(b, up)) return TTS_ERR_ARG;
+  GradOut go;
+  int rc = grad_out(b, dV, df, drgb, &go);
   if (rc != TTS_OK) return rc;
-  return tts_scatter_bwd(b, dV, df, drgb, stream);
+  // the blend backward clears the gradients as its warps run out of work
+  const bool clear = !(b->params.flags & TTS_FLAG_ACCUM_GRAD);
+  rc = blend_bwd_impl(b, up, clear ? &go : nullptr, stream);
+  if (rc != TTS_OK) return rc;
+  return scatter_bwd_impl(b, go, clear, stream);
 }
 
 int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha, const float* ddepth,

@@ -24,16 +24,53 @@ __device__ __forceinline__ int next_item(unsigned* counter) {
   return __shfl_sync(FULL, it, 0);
 }
 
-// The last warp to leave resets the queue so the next launch starts at 0.
-__device__ __forceinline__ void queue_done(unsigned* counter, unsigned* done) {
+// The last warp to leave resets the queue (and the optional second queue
+// `extra`) so the next launch starts at 0.
+__device__ __forceinline__ void queue_done(unsigned* counter, unsigned* done,
+                                           unsigned* extra = nullptr) {
   if ((threadIdx.x & 31) == 0) {
     __threadfence();
     const unsigned total = gridDim.x * (blockDim.x >> 5);
     if (atomicAdd(done, 1u) == total - 1u) {
       *counter = 0u;
+      if (extra) *extra = 0u;
       *done = 0u;
       __threadfence();
     }
+  }
+}
+
+// The vertex-gradient arrays of a following record -> vertex scatter, cleared
+// by the backward's warps once its work queue is empty (chunks of ZCH floats
+// from the device queue q), so the clearing overlaps the longest walks.
+// zg.dV[0] == nullptr: nothing to clear.
+constexpr int ZCH = 4096;
+
+__device__ __forceinline__ void zero_tail(const Batch* __restrict__ B, const GradOut& zg,
+                                          unsigned* q) {
+  if (zg.dV[0] == nullptr) return;
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    long long ch = next_item(q);
+    float* p = nullptr;
+    long long len = 0;
+    for (int s = 0; s < B->n_scenes && !p; ++s) {
+      const long long N = B->sc[s].N;
+      float* const arr[3] = {zg.dV[s], zg.df[s], zg.drgb[s]};
+      const long long n[3] = {3 * N, N, 3 * N};
+      for (int a = 0; a < 3; ++a) {
+        const long long nch = (n[a] + ZCH - 1) / ZCH;
+        if (ch < nch) {
+          p = arr[a];
+          len = n[a];
+          break;
+        }
+        ch -= nch;
+      }
+    }
+    if (!p) break;
+    const long long i1 = min((ch + 1) * ZCH, len);
+    for (long long i = ch * ZCH + lane; i < i1; i += 32) p[i] = 0.f;
   }
 }
 
@@ -570,7 +607,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
                                                        const float* __restrict__ dimage,
                                                        const float* __restrict__ dalpha,
                                                        const float* __restrict__ ddepth,
-                                                       const float* __restrict__ dnormal) {
+                                                       const float* __restrict__ dnormal,
+                                                        GradOut zg) {
   pdl_wait();
   pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
@@ -748,7 +786,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
       __syncwarp();
     }
   }
-  queue_done(&c->work_bwd, &c->done_bwd);
+  zero_tail(B, zg, &c->zero_q);
+  queue_done(&c->work_bwd, &c->done_bwd, &c->zero_q);
 }
 
 // Backward with the resort window: replays the forward (same walk, same
@@ -762,7 +801,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
                                                            const float* __restrict__ dimage,
                                                            const float* __restrict__ dalpha,
                                                            const float* __restrict__ ddepth,
-                                                           const float* __restrict__ dnormal) {
+                                                           const float* __restrict__ dnormal,
+                                                            GradOut zg) {
   pdl_wait();
   pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
@@ -912,7 +952,8 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       emit(s0, a0);
     }
   }
-  queue_done(&c->work_bwd, &c->done_bwd);
+  zero_tail(B, zg, &c->zero_q);
+  queue_done(&c->work_bwd, &c->done_bwd, &c->zero_q);
 }
 
 // ---------------------------------------------------------------------------
@@ -1142,12 +1183,14 @@ static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha,
 
 template <int TILE, bool NRM>
 static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                  const float* ddepth, const float* dnormal, cudaStream_t st) {
+                  const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
   const int g = P.blend_bwd_blocks;
   if (P.window > 0)
-    launch_k(k_blend_bwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth, dnormal);
+    launch_k(k_blend_bwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth,
+             dnormal, zg);
   else
-    launch_k(k_blend_bwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth, dnormal);
+    launch_k(k_blend_bwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth,
+             dnormal, zg);
 }
 
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
@@ -1163,14 +1206,18 @@ int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* al
 }
 
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                     const float* ddepth, const float* dnormal, cudaStream_t st) {
+                     const float* ddepth, const float* dnormal, const GradOut* zero,
+                     cudaStream_t st) {
+  GradOut zg;
+  if (zero) zg = *zero;
+  else zg.dV[0] = nullptr;
   switch (P.tile * 2 + (P.normals ? 1 : 0)) {
-    case 16: bwd_t<8, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
-    case 17: bwd_t<8, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
-    case 32: bwd_t<16, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
-    case 33: bwd_t<16, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
-    case 64: bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
-    default: bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, st); break;
+    case 16: bwd_t<8, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 17: bwd_t<8, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 32: bwd_t<16, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 33: bwd_t<16, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 64: bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    default: bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
   }
   return 1;
 }

@@ -59,7 +59,8 @@ int launch_fit_grid(const float* V_in, long long N, const float lo[3], const flo
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      float* normal, cudaStream_t st);
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                     const float* ddepth, const float* dnormal, cudaStream_t st);
+                     const float* ddepth, const float* dnormal, const GradOut* zero,
+                     cudaStream_t st);
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);

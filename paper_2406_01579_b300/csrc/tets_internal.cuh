@@ -39,6 +39,7 @@ struct Counters {
   int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
   int sort_q[3];            // depth-sort queues: block, half-block and warp lists taken
   unsigned int scan_ticket; // tile-scan blocks started
+  unsigned int zero_q;      // gradient-clearing chunks taken by the backward
 };
 
 struct SceneD {
