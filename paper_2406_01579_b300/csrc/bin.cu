@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
     if (k < nsurv) load_tet(S, B->surv[S.surv_off + k], in);
     for (int vi = 0; vi < S.view_cnt; ++vi) {
       const ViewD& vw = B->vw[B->scene_views[S.view_off + vi]];
-      int tx0 = 0, ty0 = 0, ntx = 0, nt = 0;
+      int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0, ntx = 0, nt = 0;
       if (k < nsurv) {
         const long long slot = vw.rec_base + k;
         Geo G;
@@ -407,14 +407,17 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
         if (G.visible) {
           tx0 = G.i0 >> tsh;     // pixel bounds are >= 0
           ty0 = G.j0 >> tsh;
-          const int tx1 = G.i1 >> tsh, ty1 = G.j1 >> tsh;
+          tx1 = G.i1 >> tsh;
+          ty1 = G.j1 >> tsh;
           ntx = tx1 - tx0 + 1;
           nt = ntx * (ty1 - ty0 + 1);
-          B->rec_rect[slot] = make_int4(tx0, tx1, ty0, ty1);
           write_record(vw, s, in, G, B->rec + slot * REC_Q);
           zmn = min(zmn, G.zbits);
           zmx = max(zmx, G.zbits);
         }
+        // the rect of a culled slot is empty (x1 < x0): the placement reads
+        // the rect and the depth bits only
+        B->rec_rect[slot] = nt > 0 ? make_int4(tx0, tx1, ty0, ty1) : make_int4(1, 0, 0, 0);
         B->rec_nt[slot] = nt;
         B->rec_z[slot] = G.zbits;
       }
@@ -593,11 +596,12 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
     unsigned long long comp = 0;
     if (k < nsurv) {
       const long long slot = vw.rec_base + k;
-      nt = B->rec_nt[slot];
-      if (nt > 0) {
-        r = B->rec_rect[slot];
+      r = B->rec_rect[slot];            // empty (x1 < x0) for a culled slot
+      const unsigned zb = B->rec_z[slot];
+      if (r.y >= r.x) {
         ntx = r.y - r.x + 1;
-        comp = ((unsigned long long)B->rec_z[slot] << 32) | (unsigned)slot;
+        nt = ntx * (r.w - r.z + 1);
+        comp = ((unsigned long long)zb << 32) | (unsigned)slot;
       }
     }
     int cx = 0, cy = 0;    // position of round j in the rect
