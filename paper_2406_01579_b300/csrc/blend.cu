@@ -992,7 +992,8 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       const int v = B->scene_views[S.view_off + vi];
       const ViewD& vw = B->vw[v];
       const long long slot = vw.rec_base + k;
-      if (B->rec_nt[slot] == 0) continue;
+      // a culled slot's gradient is zero (never accumulated): the magnitude
+      // test below skips it without reading its tile count first
       float4* gq = B->rec_grad + slot * REC_Q;
       const float4 g0 = nrm ? gq[0] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4], g5 = gq[5];
