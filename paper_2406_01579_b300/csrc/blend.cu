@@ -982,7 +982,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
     const int tet = B->surv[S.surv_off + k];
     TetIn in;
-    bool loaded = false;
+    load_tet<false>(S, tet, in);   // in flight while the first view's gradient loads
     float3 dv[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
     float dfv[4] = {0.f, 0.f, 0.f, 0.f};
     float3 dcol = f3(0, 0, 0);
@@ -997,6 +997,8 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       float4* gq = B->rec_grad + slot * REC_Q;
       const float4 g0 = nrm ? gq[0] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4], g5 = gq[5];
+      // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
+      const float4 q0 = __ldg(B->rec + slot * REC_Q);
       const float mag = fabsf(g0.x) + fabsf(g0.y) + fabsf(g0.z) + fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
                         fabsf(g2.y) + fabsf(g2.z) + fabsf(g2.w) + fabsf(g3.x) + fabsf(g3.y) +
                         fabsf(g3.z) + fabsf(g3.w) + fabsf(g4.x) + fabsf(g4.y) + fabsf(g4.z) +
@@ -1006,9 +1008,6 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       if (nrm) gq[0] = z4;
       gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
       dnw = dnw + f3(g0.x, g0.y, g0.z);
-      if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
-      // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
-      const float4 q0 = __ldg(B->rec + slot * REC_Q);
       Geo G;
       tet_geometry_at(vw, in, (int)(fabsf(q0.x) - 0.5f), (int)(fabsf(q0.y) - 0.5f), G);
       if (!G.visible) continue;
@@ -1075,7 +1074,6 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
     }
     if (NRM && (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f)) {
-      if (!loaded) { load_tet<false>(S, tet, in); loaded = true; }
       TetGrad TG;
       tet_grad(in.v, in.f, TG);
       float ih, sg;
