@@ -186,6 +186,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_pff = take((size_t)flag_total);
   const size_t o_bnd = take(sizeof(unsigned) * 6 * b->n_scenes);
   const size_t o_surv = take(sizeof(int) * surv_total);
+  const size_t o_survT = take(sizeof(int4) * surv_total);
   const size_t o_rz = take(sizeof(unsigned) * slots);
   const size_t o_rnt = take(sizeof(int) * slots);
   const size_t o_rr = take(sizeof(int4) * slots);
@@ -233,6 +234,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.pf_flags = reinterpret_cast<unsigned char*>(base + o_pff);
     B.bounds = reinterpret_cast<unsigned*>(base + o_bnd);
     B.surv = reinterpret_cast<int*>(base + o_surv);
+    B.surv_T = reinterpret_cast<int4*>(base + o_survT);
     B.rec_z = reinterpret_cast<unsigned*>(base + o_rz);
     B.rec_nt = reinterpret_cast<int*>(base + o_rnt);
     B.rec_rect = reinterpret_cast<int4*>(base + o_rr);

@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_prefilter_scan(const Batch* __
   }
 }
 
-// Stable compaction: survivors in original tet order.
+// Stable compaction: survivors (tet ids and their vertex ids) in original
+// tet order.
 __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
@@ -213,10 +214,14 @@ __global__ void __launch_bounds__(PF_THREADS) k_prefilter_compact(const Batch* _
   int total;
   int off = block_excl_scan<int, PF_THREADS>(cnt, &total) + B->pf_blocksum[S.pf_chunk_base + chunk];
   int* out = B->surv + S.surv_off;
+  int4* outT = B->surv_T + S.surv_off;
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     if (fl[q]) {
-      if (off < S.surv_cap) out[off] = (int)(k0 + q);
+      if (off < S.surv_cap) {
+        out[off] = (int)(k0 + q);
+        outT[off] = __ldg(&S.T[k0 + q]);
+      }
       ++off;
     }
   }
@@ -232,7 +237,7 @@ __global__ void __launch_bounds__(256) k_tet_normals(const Batch* __restrict__ B
   const SceneD& S = B->sc[s];
   const int nsurv = B->ctr->n_surv[s];
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
-    const int4 t = __ldg(&S.T[B->surv[S.surv_off + k]]);
+    const int4 t = B->surv_T[S.surv_off + k];
     const int id[4] = {t.x, t.y, t.z, t.w};
     float3 v[4];
     float f[4];
@@ -276,7 +281,7 @@ __global__ void __launch_bounds__(256) k_bounds(const Batch* __restrict__ B) {
   const int nsurv = B->ctr->n_surv[s];
   unsigned mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
-    const int4 t = __ldg(&S.T[B->surv[S.surv_off + k]]);
+    const int4 t = B->surv_T[S.surv_off + k];
     const int id[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -396,7 +401,7 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
     const int k = k0 + q;
     if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
     TetIn in;
-    if (k < nsurv) load_tet(S, B->surv[S.surv_off + k], in);
+    if (k < nsurv) load_tet_ids(S, B->surv_T[S.surv_off + k], in);
     for (int vi = 0; vi < S.view_cnt; ++vi) {
       const ViewD& vw = B->vw[B->scene_views[S.view_off + vi]];
       int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0, ntx = 0, nt = 0;

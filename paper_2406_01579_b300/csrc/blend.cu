@@ -980,9 +980,9 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
   float* __restrict__ gc = go.drgb[s];
   constexpr bool nrm = NRM;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
-    const int tet = B->surv[S.surv_off + k];
+    const int4 t = B->surv_T[S.surv_off + k];
     TetIn in;
-    load_tet<false>(S, tet, in);   // in flight while the first view's gradient loads
+    load_tet_ids<false>(S, t, in);   // in flight while the first view's gradient loads
     float3 dv[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
     float dfv[4] = {0.f, 0.f, 0.f, 0.f};
     float3 dcol = f3(0, 0, 0);
@@ -1084,7 +1084,6 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       }
     }
     if (!any) continue;
-    const int4 t = __ldg(&S.T[tet]);
     const int id[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {

@@ -304,10 +304,10 @@ __device__ __forceinline__ float3 tet_normal_adjoint(float3 n, float inv_h, floa
   return (sg * inv_h) * (dn - dot3(n, dn) * n);
 }
 
-// The tet's vertices, SDF values and (when COLOURS) vertex colours.
+// The vertices, SDF values and (when COLOURS) vertex colours of the tet with
+// vertex ids t.
 template <bool COLOURS = true>
-__device__ __forceinline__ void load_tet(const SceneD& S, int tet, TetIn& in) {
-  const int4 t = __ldg(&S.T[tet]);
+__device__ __forceinline__ void load_tet_ids(const SceneD& S, int4 t, TetIn& in) {
   const int id[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
   for (int j = 0; j < 4; ++j) {

@@ -87,6 +87,7 @@ struct Batch {
   unsigned char* pf_flags;  // [sum K]
   unsigned int* bounds;     // [6 * n_scenes] survivor AABB as order-preserving float keys
   int* surv;                // [sum surv_cap]
+  int4* surv_T;             // [sum surv_cap] vertex ids of each survivor
   unsigned int* rec_z;      // [slots] FP32 mean depth bits
   int* rec_nt;              // [slots] tiles overlapped (0: culled)
   int4* rec_rect;           // [slots] tile rect (tx0, tx1, ty0, ty1)
