@@ -1,5 +1,6 @@
 // C ABI of libtets: argument checks, workspace layout, launch sequences.
 #include <atomic>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -11,14 +12,25 @@ namespace tts {
 static_assert(sizeof(Batch) < 30000, "descriptor must fit in kernel parameters");
 
 // Copies the by-value descriptor into the workspace (kernel parameters are
-// captured by value in CUDA graphs, so this stays valid under capture).
+// captured by value in CUDA graphs, so this stays valid under capture): the
+// header and the batch's scene and view entries only.
+static_assert(offsetof(Batch, sc) % 4 == 0 && sizeof(SceneD) % 4 == 0 && sizeof(ViewD) % 4 == 0,
+              "word copies");
+
 __global__ void k_upload(const Batch b, Batch* dst) {
   pdl_wait();
   pdl_launch_dependents();
   const unsigned* src = reinterpret_cast<const unsigned*>(&b);
   unsigned* d = reinterpret_cast<unsigned*>(dst);
-  constexpr int n = (int)(sizeof(Batch) / 4);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = src[i];
+  constexpr int oS = (int)(offsetof(Batch, sc) / 4), oV = (int)(offsetof(Batch, vw) / 4),
+                oSV = (int)(offsetof(Batch, scene_views) / 4);
+  const int nS = b.n_scenes * (int)(sizeof(SceneD) / 4), nV = b.n_views * (int)(sizeof(ViewD) / 4);
+  const int n = oS + nS + nV + b.n_views;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int w = (i < oS) ? i : (i < oS + nS) ? i : (i < oS + nS + nV) ? oV + (i - oS - nS)
+                                                                        : oSV + (i - oS - nS - nV);
+    d[w] = src[w];
+  }
 }
 
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st) {
