@@ -161,6 +161,7 @@ def run_ours(a, rank, world):
 
     import synth
     from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors, _lib
+    from paper_2406_01579_b300.multirank import job_mpix_s, max_over_ranks, rank_cameras
     from paper_2406_01579_b300.pipeline import HostStepPipeline
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -170,9 +171,8 @@ def run_ours(a, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     sc = synth.scene_spheres128(res=a.res, n_views=a.views)
-    if rank > 0:  # weak scaling: each rank renders its own views of the scene
-        rng = np.random.default_rng(1000 + rank)
-        sc.cams = [synth.random_camera(rng, a.res, a.res) for _ in range(a.views)]
+    # weak scaling: each rank renders its own views of the scene
+    sc.cams = rank_cameras(sc.cams, rank, a.res, a.res)
     st = SceneTensors(*(torch.from_numpy(x).to(dev) for x in (sc.V, sc.T, sc.f, sc.rgb)))
     tune = None
     if a.tile == 0:
@@ -266,12 +266,9 @@ def run_ours(a, rank, world):
                 for i, s in enumerate(stages)}
     info = r.info()
     assert info.status == 0, f"status {info.status}"
-    if dist is not None:
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
     pixels_per_step = sum(c.width * c.height for c in sc.cams)
-    value = world * pixels_per_step * a.steps / elapsed / 1e6
+    value = job_mpix_s(pixels_per_step, a.steps, elapsed, dist, dev)
+    elapsed = max_over_ranks(elapsed, dist, dev)
     # fragments met by the forward (per-pixel counters of the last step)
     Tp, Lp, Np = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
     _lib.check(L.tts_debug_pixels(bp, ctypes.byref(Tp), ctypes.byref(Lp), ctypes.byref(Np), sp))
@@ -299,7 +296,7 @@ def run_ours(a, rank, world):
         e1.record(stream)
         barrier()
         tg = e0.elapsed_time(e1) / 1e3
-        res["graph"] = world * pixels_per_step * a.steps / tg / 1e6
+        res["graph"] = job_mpix_s(pixels_per_step, a.steps, tg, dist, dev)
         del gstep
     except Exception as exc:  # capture unsupported: report eager only
         res["graph_error"] = repr(exc)[:200]
@@ -394,11 +391,7 @@ def run_ours(a, rank, world):
         e1.record(stream)
         barrier()
         te = e0.elapsed_time(e1) / 1e3
-        if dist is not None:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        res["e2e"] = {"value": world * pixels_per_step * a.steps / te / 1e6, "unit": UNIT,
+        res["e2e"] = {"value": job_mpix_s(pixels_per_step, a.steps, te, dist, dev), "unit": UNIT,
                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                       "overlap": "copies of neighbouring steps overlap compute (two buffer sets)"}
         r.set_scenes([st])
