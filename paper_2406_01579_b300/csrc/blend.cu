@@ -685,20 +685,23 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
     if (maxlast <= lo - rg.x) continue;
     const float gOT = gO * Tfin;
     const int top = rg.x + maxlast;
+    // one group of lookahead on (slot, bbox), as in the forward: the group
+    // [max(lo, ge - 32), ge) is tested while the next one's bboxes load
+    int idx = max(lo, top - 32) + lane;
+    unsigned slot = (idx < top) ? vals[idx] : 0u;
+    float4 q0 = (idx < top) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
+    int idn = max(lo, top - 64) + lane;
+    unsigned slot_n = (idn < top - 32) ? vals[idn] : 0u;
     for (int ge = top; ge > lo; ge -= 32) {
       const int g0 = max(lo, ge - 32);
-      if (!wb.cull_to(last > g0 - rg.x)) continue;
-      const int idx = g0 + lane;
-      bool ov = false;
-      unsigned slot = 0u;
-      float4 q0;
-      if (idx < ge) {
-        slot = vals[idx];
-        q0 = __ldg(rec + (size_t)slot * REC_Q);
-        ov = !wb.misses(q0);
-      }
+      const int idnn = max(lo, ge - 96) + lane;
+      const float4 q0_n = (idn < ge - 32) ? __ldg(rec + (size_t)slot_n * REC_Q)
+                                          : make_float4(0.f, 0.f, -1.f, -1.f);
+      const unsigned slot_nn = (idnn < ge - 64) ? vals[idnn] : 0u;
+      const bool live = wb.cull_to(last > g0 - rg.x);
+      const bool ov = live && (idx < ge) && !wb.misses(q0);
       const unsigned m = __ballot_sync(FULL, ov);
-      if (m == 0u) continue;
+      if (m != 0u) {
       if (ov) {
         const int pos = __popc(m & ltm);
         const float4* r = rec + (size_t)slot * REC_Q;
@@ -784,6 +787,12 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         }
       }
       __syncwarp();
+      }
+      idx = idn;
+      slot = slot_n;
+      q0 = q0_n;
+      idn = idnn;
+      slot_n = slot_nn;
     }
   }
   zero_tail(B, zg, &c->zero_q);
