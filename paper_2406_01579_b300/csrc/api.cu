@@ -200,7 +200,6 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_surv = take(sizeof(int) * surv_total);
   const size_t o_survT = take(sizeof(int4) * surv_total);
   const size_t o_rz = take(sizeof(unsigned) * slots);
-  const size_t o_rnt = take(sizeof(int) * slots);
   const size_t o_rr = take(sizeof(int4) * slots);
   const size_t o_rec = take(sizeof(float4) * REC_Q * slots);
   const bool fwd_only = (pr.flags & TTS_FLAG_FORWARD_ONLY) != 0;
@@ -248,7 +247,6 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.surv = reinterpret_cast<int*>(base + o_surv);
     B.surv_T = reinterpret_cast<int4*>(base + o_survT);
     B.rec_z = reinterpret_cast<unsigned*>(base + o_rz);
-    B.rec_nt = reinterpret_cast<int*>(base + o_rnt);
     B.rec_rect = reinterpret_cast<int4*>(base + o_rr);
     B.rec = reinterpret_cast<float4*>(base + o_rec);
     B.rec_grad = reinterpret_cast<float4*>(base + P->off_rec_grad);

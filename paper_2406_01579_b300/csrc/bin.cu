@@ -423,7 +423,6 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
         // the rect of a culled slot is empty (x1 < x0): the placement reads
         // the rect and the depth bits only
         B->rec_rect[slot] = nt > 0 ? make_int4(tx0, tx1, ty0, ty1) : make_int4(1, 0, 0, 0);
-        B->rec_nt[slot] = nt;
         B->rec_z[slot] = G.zbits;
       }
       // key counts per tile, one atomic per (warp, tile) and round

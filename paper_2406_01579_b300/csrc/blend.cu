@@ -85,16 +85,21 @@ struct WarpBlock {
   bool inimg;
   float fpx, fpy;
   float wx0, wx1, wy0, wy1;   // the block's pixel-centre rectangle
+  unsigned lmask;             // the lanes the rectangle was taken over
   __device__ __forceinline__ bool misses(const float4& q0) const {
     return (fabsf(q0.x) > wx1) | (q0.z < wx0) | (fabsf(q0.y) > wy1) | (q0.w < wy0);
   }
   // Shrink the test rectangle to the pixels of the lanes in `live`: an entry
   // whose bbox misses all of them cannot produce a fragment for any lane that
-  // still needs one.  Returns false when no lane is live.
+  // still needs one.  Returns false when no lane is live.  The rectangle is
+  // taken again only when the set of live lanes has changed.
   __device__ __forceinline__ bool cull_to(bool live) {
+    const unsigned lm = __ballot_sync(FULL, live);
+    if (lm == lmask) return lm != 0u;
+    lmask = lm;
+    if (lm == 0u) return false;
     const unsigned big = 0x7fffffffu;
     const unsigned x0 = __reduce_min_sync(FULL, live ? (unsigned)px : big);
-    if (x0 == big) return false;
     const unsigned x1 = __reduce_max_sync(FULL, live ? (unsigned)px : 0u);
     const unsigned y0 = __reduce_min_sync(FULL, live ? (unsigned)py : big);
     const unsigned y1 = __reduce_max_sync(FULL, live ? (unsigned)py : 0u);
@@ -127,6 +132,7 @@ __device__ __forceinline__ const ViewD& decode_block(const Batch* __restrict__ B
   wb.inimg = (wb.px < vw.W) & (wb.py < vw.H);
   wb.fpx = (float)wb.px + 0.5f;
   wb.fpy = (float)wb.py + 0.5f;
+  wb.lmask = FULL;             // the whole block
   wb.wx0 = (float)bx + 0.5f;
   wb.wx1 = wb.wx0 + 7.f;
   wb.wy0 = (float)by + 0.5f;
@@ -156,6 +162,7 @@ __device__ __forceinline__ const ViewD& decode_block8(const Batch* __restrict__ 
   wb.inimg = (wb.px < vw.W) & (wb.py < vw.H);
   wb.fpx = (float)wb.px + 0.5f;
   wb.fpy = (float)wb.py + 0.5f;
+  wb.lmask = FULL;             // the whole block
   wb.wx0 = (float)bx + 0.5f;
   wb.wx1 = wb.wx0 + 3.f;
   wb.wy0 = (float)by + 0.5f;

@@ -89,7 +89,6 @@ struct Batch {
   int* surv;                // [sum surv_cap]
   int4* surv_T;             // [sum surv_cap] vertex ids of each survivor
   unsigned int* rec_z;      // [slots] FP32 mean depth bits
-  int* rec_nt;              // [slots] tiles overlapped (0: culled)
   int4* rec_rect;           // [slots] tile rect (tx0, tx1, ty0, ty1)
   float4* rec;              // [slots * 6]
   float4* rec_grad;         // [slots * 6]
