@@ -308,11 +308,16 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
   unsigned slot = (idx < hi) ? vals[idx] : 0u;
   float4 q0 = (idx < hi) ? __ldg(rec + (size_t)slot * REC_Q) : make_float4(0.f, 0.f, -1.f, -1.f);
   unsigned slot_n = (idx + 32 < hi) ? vals[idx + 32] : 0u;
+  int gck = split ? lo + L : hi;   // the next segment end (L is a multiple of 32)
+  long long pck = (long long)ts.x * tt + wb.tpix;
   for (int g = lo; g < hi; g += 32) {
-    if (split && g > lo && (g - lo) % L == 0 && sub == 0) {
-      const long long pi = ((long long)ts.x + (g - lo) / L - 1) * tt + wb.tpix;
-      B->pseg_a[pi] = make_float4(S.T, S.C0, S.C1, S.C2);
-      B->pseg_b[pi] = make_float4(S.D, S.N0, S.N1, S.N2);
+    if (g == gck) {
+      if (sub == 0) {
+        B->pseg_a[pck] = make_float4(S.T, S.C0, S.C1, S.C2);
+        B->pseg_b[pck] = make_float4(S.D, S.N0, S.N1, S.N2);
+      }
+      gck += L;
+      pck += tt;
     }
     if (!wb.cull_to(!S.done)) break;
     const int idn = g + 32 + lane;
