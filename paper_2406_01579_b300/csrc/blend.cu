@@ -277,6 +277,79 @@ __device__ __forceinline__ float fragment_code(const float4& q4, const Chord& ch
   return use ? (a > 0.f ? a : FRAG_ZERO) : FRAG_SKIP;
 }
 
+// LPP = 4: the four lanes of a pixel hold the fragment codes v of four
+// consecutive candidates (lane sub has the sub-th).  The pixel's compositing
+// of the four in order (as composite() one after the other): the
+// transmittance in front of each is T times a product over the lanes before
+// it (a scan over the four lanes), the first lane whose fragment would take
+// T below eps stops the pixel, and each lane before it adds its own
+// fragment to its partial colour / depth / normal sums (a pixel's sums are
+// those of its four lanes).  T, done agree over the four lanes.
+template <bool NRM>
+__device__ __forceinline__ void composite4(float v, int k, int base, bool pure, float eps,
+                                           float4 (*st)[32], const int* sidx, FwdState& S) {
+  const int lane = threadIdx.x & 31, sub = lane & 3, g0 = lane & ~3;
+  const bool bl = (v != 0.f) & (v != FRAG_SKIP);
+  const float a = bl ? fmaxf(v, 0.f) : 0.f;
+  float P = bl ? __fsub_rn(1.f, a) : 1.f;        // inclusive product of (1 - a)
+  float t = __shfl_up_sync(FULL, P, 1, 4);
+  if (sub >= 1) P = __fmul_rn(t, P);
+  t = __shfl_up_sync(FULL, P, 2, 4);
+  if (sub >= 2) P = __fmul_rn(t, P);
+  float Pex = __shfl_up_sync(FULL, P, 1, 4);      // exclusive
+  if (sub == 0) Pex = 1.f;
+  const float Tn = __fmul_rn(S.T, P);
+  const bool stop = bl && !pure && (Tn < eps);
+  const unsigned sbits = (__ballot_sync(FULL, stop) >> g0) & 0xfu;
+  const int f = sbits ? __ffs(sbits) - 1 : 4;     // the first stopping lane (4: none)
+  const float Tl = __shfl_sync(FULL, Tn, g0 + max(f - 1, 0));
+  if (S.done) return;
+  S.nfrag += (v != 0.f) && sub <= f;
+  if (bl && sub < f) {
+    const float4 q5 = st[5][k];
+    const float wgt = __fmul_rn(__fmul_rn(S.T, Pex), a);
+    S.C0 = __fmaf_rn(wgt, q5.y, S.C0);
+    S.C1 = __fmaf_rn(wgt, q5.z, S.C1);
+    S.C2 = __fmaf_rn(wgt, q5.w, S.C2);
+    S.D = __fmaf_rn(wgt, q5.x, S.D);
+    if constexpr (NRM) {
+      const float4 n = st[REC_Q][k];
+      S.N0 = __fmaf_rn(wgt, n.x, S.N0);
+      S.N1 = __fmaf_rn(wgt, n.y, S.N1);
+      S.N2 = __fmaf_rn(wgt, n.z, S.N2);
+    }
+    S.last = base + sidx[k] + 1;
+  }
+  if (f >= 1) S.T = Tl;
+  S.done = f < 4;
+}
+
+// Sum (max) of a value over the LPP lanes of a pixel.
+template <int LPP>
+__device__ __forceinline__ float pix_sum(float x) {
+  if constexpr (LPP == 4) {
+    x += __shfl_xor_sync(FULL, x, 1);
+    x += __shfl_xor_sync(FULL, x, 2);
+  }
+  return x;
+}
+template <int LPP>
+__device__ __forceinline__ int pix_sum_i(int x) {
+  if constexpr (LPP == 4) {
+    x += __shfl_xor_sync(FULL, x, 1);
+    x += __shfl_xor_sync(FULL, x, 2);
+  }
+  return x;
+}
+template <int LPP>
+__device__ __forceinline__ int pix_max_i(int x) {
+  if constexpr (LPP == 4) {
+    x = max(x, __shfl_xor_sync(FULL, x, 1));
+    x = max(x, __shfl_xor_sync(FULL, x, 2));
+  }
+  return x;
+}
+
 // Walks the list entries [lo, hi) of the warp's tile front to back for the
 // lanes that are not done: the entries whose bbox meets a live pixel are
 // staged (ballot) in the warp's shared-memory slice and blended in order
@@ -312,9 +385,17 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
   long long pck = (long long)ts.x * tt + wb.tpix;
   for (int g = lo; g < hi; g += 32) {
     if (g == gck) {
+      const float c0 = pix_sum<LPP>(S.C0), c1 = pix_sum<LPP>(S.C1), c2 = pix_sum<LPP>(S.C2);
+      const float d = pix_sum<LPP>(S.D);
+      float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+      if constexpr (NRM) {
+        n0 = pix_sum<LPP>(S.N0);
+        n1 = pix_sum<LPP>(S.N1);
+        n2 = pix_sum<LPP>(S.N2);
+      }
       if (sub == 0) {
-        B->pseg_a[pck] = make_float4(S.T, S.C0, S.C1, S.C2);
-        B->pseg_b[pck] = make_float4(S.D, S.N0, S.N1, S.N2);
+        B->pseg_a[pck] = make_float4(S.T, c0, c1, c2);
+        B->pseg_b[pck] = make_float4(d, n0, n1, n2);
       }
       gck += L;
       pck += tt;
@@ -357,13 +438,7 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           const bool h = ch.hit && (k0 + sub < cnt);
           if (!__any_sync(FULL, h && !S.done)) continue;
           const float mine = h ? fragment_code(st[4][k], ch, pure, cap, skip) : 0.f;
-          const int l0 = lane & ~3;
-          const float c0 = __shfl_sync(FULL, mine, l0), c1 = __shfl_sync(FULL, mine, l0 + 1),
-                      c2 = __shfl_sync(FULL, mine, l0 + 2), c3 = __shfl_sync(FULL, mine, l0 + 3);
-          composite<NRM>(c0, k0, base, pure, eps, st, sidx, S);
-          composite<NRM>(c1, min(k0 + 1, cnt - 1), base, pure, eps, st, sidx, S);
-          composite<NRM>(c2, min(k0 + 2, cnt - 1), base, pure, eps, st, sidx, S);
-          composite<NRM>(c3, min(k0 + 3, cnt - 1), base, pure, eps, st, sidx, S);
+          composite4<NRM>(mine, k, base, pure, eps, st, sidx, S);
         }
         if (__all_sync(FULL, S.done)) break;
       }
@@ -415,6 +490,18 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
     if (four) {
       fwd_walk<NRM, 4>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
                        st[wid], sidx[wid], S);
+      // the pixel's sums over its four lanes
+      S.C0 = pix_sum<4>(S.C0);
+      S.C1 = pix_sum<4>(S.C1);
+      S.C2 = pix_sum<4>(S.C2);
+      S.D = pix_sum<4>(S.D);
+      if constexpr (NRM) {
+        S.N0 = pix_sum<4>(S.N0);
+        S.N1 = pix_sum<4>(S.N1);
+        S.N2 = pix_sum<4>(S.N2);
+      }
+      S.nfrag = pix_sum_i<4>(S.nfrag);
+      S.last = pix_max_i<4>(S.last);
       if (wb.inimg && (threadIdx.x & 3) == 0) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
     } else {
       fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
