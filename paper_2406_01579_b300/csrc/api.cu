@@ -217,13 +217,14 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   // checkpoint of 32 B per pixel and segment
   B.seg_cap = B.seg_len > 0 ? (int)std::min<long long>(2 * cap / B.seg_len + 1, 0x3fffffffLL) : 0;
   const long long tt = (long long)pr.tile * pr.tile;
-  // units: one per tile, one per later segment, up to three more per split
-  // tile (each split tile has at least two segments)
-  const size_t o_wl = take(sizeof(int2) * ((size_t)tiles + 3 * (size_t)B.seg_cap));
+  // forward units: one per tile, four per split tile; backward units: one
+  // per tile, one per segment of a split tile
+  const size_t o_wl = take(sizeof(int2) * 4 * (size_t)tiles);
+  const size_t o_wlbk = take(sizeof(int2) * ((size_t)tiles + (size_t)B.seg_cap));
   const size_t o_tseg = take(sizeof(int2) * tiles);
   const int wl_blocks = (tiles + 255) / 256;
-  const size_t o_wlc = take(sizeof(int) * 34 * (size_t)wl_blocks);
-  const size_t o_wlb = take(sizeof(int) * 34);
+  const size_t o_wlc = take(sizeof(int) * 68 * (size_t)wl_blocks);
+  const size_t o_wlb = take(sizeof(int) * 68);
   const size_t o_psa = take(sizeof(float4) * B.seg_cap * tt);
   const size_t o_psb = take(sizeof(float4) * B.seg_cap * tt);
 
@@ -258,6 +259,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.scan_lb = reinterpret_cast<unsigned long long*>(base + o_slb);
     B.ranges = reinterpret_cast<int2*>(base + o_rng);
     B.worklist = reinterpret_cast<int2*>(base + o_wl);
+    B.worklist_b = reinterpret_cast<int2*>(base + o_wlbk);
     B.tseg = reinterpret_cast<int2*>(base + o_tseg);
     B.wl_blockcnt = reinterpret_cast<int*>(base + o_wlc);
     B.wl_base = reinterpret_cast<int*>(base + o_wlb);
@@ -529,7 +531,7 @@ int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream) {
   for (int s = 0; s < b->n_scenes; ++s) info->n_surv[s] = c.n_surv[s];
   info->sort_bits = c.total_bits;
   info->long_lists = c.long_lists;
-  info->blend_units = c.n_units;
+  info->blend_units = c.n_units_b;
   return TTS_OK;
 }
 

@@ -865,26 +865,30 @@ __global__ void k_debug_keys(const Batch* __restrict__ B) {
   }
 }
 
-// Work list for the persistent blend kernels, units (tile, segment | part << 24).
-// A tile whose list is longer than seg_len entries is split into segments of
-// seg_len entries: the forward walks the whole list (the segment-0 units:
-// parts 0..3 covering its 4x2 blocks, see fwd_lanes) and records its state at
-// each segment end, and the backward walks the segments in parallel from those
-// states (one warp per 8x4 block walking a long list back to front would
-// otherwise bound its duration).  Units (tile, segment) are ordered by
-// decreasing work (bucketed by bit length), so the longest start first; the
-// order inside a bucket is arbitrary.
+// Work lists for the persistent blend kernels.  A tile whose list is longer
+// than seg_len entries is split into segments of seg_len entries: the forward
+// walks the whole list as 4x2 blocks, in four units (tile, part << 24) of two
+// blocks each (see fwd_lanes), and records its state at each segment end; the
+// backward walks the segments in parallel from those states, one unit (tile,
+// segment) each (one warp walking a long list back to front would otherwise
+// bound its duration).  Another tile is one unit (tile, 0) of each list.
+// Each list is ordered by decreasing work (bucketed by bit length: the
+// forward's by list length, the backward's by list or segment length), so
+// the longest start first; the order inside a bucket is arbitrary.
 
 constexpr int WL_BUCKETS = 34;      // bit length of a work amount (0..32), 33: unused
+constexpr int WL_COLS = 2 * WL_BUCKETS;   // forward buckets, then backward buckets
 constexpr int WL_THREADS = 256;     // one tile per thread
 
+__device__ __forceinline__ int wl_bucket(int n) { return n > 0 ? 32 - __clz(n) : 0; }
+
 // Work-list step 1 (one tile per thread): segment count and checkpoint slots
-// of each tile, and per block the units of each length bucket.
+// of each tile, and per block the units of each list and length bucket.
 __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
-  __shared__ int cnt[WL_BUCKETS];
-  if (threadIdx.x < WL_BUCKETS) cnt[threadIdx.x] = 0;
+  __shared__ int cnt[WL_COLS];
+  if (threadIdx.x < WL_COLS) cnt[threadIdx.x] = 0;
   __syncthreads();
   const int t = blockIdx.x * WL_THREADS + threadIdx.x;
   const int nt = B->total_tiles;
@@ -916,44 +920,43 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
   }
   if (in) {
     B->tseg[t] = make_int2(base, nseg);
-    // segment 0 carries the forward's walk of the whole list (two parts for
-    // a split list): bucketed by the list length; the later segments
-    // (backward only) by the segment length
-    atomicAdd(&cnt[len > 0 ? 32 - __clz(len) : 0], fwd_lanes(nseg));
-    if (nseg > 1) atomicAdd(&cnt[32 - __clz(L)], nseg - 1);
+    atomicAdd(&cnt[wl_bucket(len)], fwd_lanes(nseg));
+    atomicAdd(&cnt[WL_BUCKETS + wl_bucket(nseg > 1 ? L : len)], nseg);
   }
   __syncthreads();
-  if (threadIdx.x < WL_BUCKETS) B->wl_blockcnt[blockIdx.x * WL_BUCKETS + threadIdx.x] = cnt[threadIdx.x];
+  if (threadIdx.x < WL_COLS) B->wl_blockcnt[blockIdx.x * WL_COLS + threadIdx.x] = cnt[threadIdx.x];
 }
 
-// Work-list step 2 (one block of 17 warps, two buckets each): per bucket,
-// the exclusive prefix of the blocks' unit counts (in place) and, over the
-// buckets from the longest down, the first unit of each bucket.
+// Work-list step 2 (one block of 17 warps, four bucket columns each): per
+// column, the exclusive prefix of the blocks' unit counts (in place) and, per
+// list over its buckets from the longest down, the first unit of each bucket.
 __global__ void __launch_bounds__(17 * 32) k_worklist_scan(const Batch* __restrict__ B, int nb) {
   pdl_wait();
   pdl_launch_dependents();
-  __shared__ int total[WL_BUCKETS];
+  __shared__ int total[WL_COLS];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int j = w; j < WL_BUCKETS; j += 17) {
+  for (int j = w; j < WL_COLS; j += 17) {
     int carry = 0;
     for (int b0 = 0; b0 < nb; b0 += 32) {
       const int b = b0 + lane;
-      const int v = (b < nb) ? B->wl_blockcnt[b * WL_BUCKETS + j] : 0;
+      const int v = (b < nb) ? B->wl_blockcnt[b * WL_COLS + j] : 0;
       int tot;
       const int ex = warp_excl_scan(v, &tot);
-      if (b < nb) B->wl_blockcnt[b * WL_BUCKETS + j] = carry + ex;
+      if (b < nb) B->wl_blockcnt[b * WL_COLS + j] = carry + ex;
       carry += tot;
     }
     if (lane == 0) total[j] = carry;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
+    const int l = threadIdx.x;
     int run = 0;
     for (int j = WL_BUCKETS - 1; j >= 0; --j) {
-      B->wl_base[j] = run;
-      run += total[j];
+      B->wl_base[l * WL_BUCKETS + j] = run;
+      run += total[l * WL_BUCKETS + j];
     }
-    B->ctr->n_units = run;
+    if (l == 0) B->ctr->n_units = run;
+    else B->ctr->n_units_b = run;
   }
 }
 
@@ -962,9 +965,9 @@ __global__ void __launch_bounds__(17 * 32) k_worklist_scan(const Batch* __restri
 __global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
-  __shared__ int off[WL_BUCKETS];
-  if (threadIdx.x < WL_BUCKETS)
-    off[threadIdx.x] = B->wl_base[threadIdx.x] + B->wl_blockcnt[blockIdx.x * WL_BUCKETS + threadIdx.x];
+  __shared__ int off[WL_COLS];
+  if (threadIdx.x < WL_COLS)
+    off[threadIdx.x] = B->wl_base[threadIdx.x] + B->wl_blockcnt[blockIdx.x * WL_COLS + threadIdx.x];
   __syncthreads();
   const int t = blockIdx.x * WL_THREADS + threadIdx.x;
   if (t >= B->total_tiles) return;
@@ -973,13 +976,10 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_place(const Batch* __re
   const int2 ts = B->tseg[t];
   const int len = r.y - r.x;
   const int parts = fwd_lanes(ts.y);         // forward units of the list
-  const int pos0 = atomicAdd(&off[len > 0 ? 32 - __clz(len) : 0], parts);
-  B->worklist[pos0] = make_int2(t, 0);
-  for (int q = 1; q < parts; ++q) B->worklist[pos0 + q] = make_int2(t, q << 24);   // forward only
-  if (ts.y > 1) {
-    const int pos = atomicAdd(&off[32 - __clz(L)], ts.y - 1);
-    for (int j = 1; j < ts.y; ++j) B->worklist[pos + j - 1] = make_int2(t, j);
-  }
+  const int pf = atomicAdd(&off[wl_bucket(len)], parts);
+  for (int q = 0; q < parts; ++q) B->worklist[pf + q] = make_int2(t, q << 24);
+  const int pb = atomicAdd(&off[WL_BUCKETS + wl_bucket(ts.y > 1 ? L : len)], ts.y);
+  for (int j = 0; j < ts.y; ++j) B->worklist_b[pb + j] = make_int2(t, j);
 }
 
 // ---------------------------------------------------------------------------

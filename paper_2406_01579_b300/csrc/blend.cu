@@ -170,15 +170,15 @@ __device__ __forceinline__ const ViewD& decode_block8(const Batch* __restrict__ 
   return vw;
 }
 
-// Work item -> warp block: item / SB indexes the (tile, segment) unit list.
-// Units are (tile, segment | part << 24): segment > 0 units are backward
-// work only, part > 0 units forward work only (the further 4x2 blocks of a
-// long list).
+// Work item -> warp block: item / SB indexes a work list of units (tile,
+// segment | part << 24): the forward's (tile, part << 24), the parts of a long
+// list covering its 4x2 blocks, or the backward's (tile, segment).
 template <int TILE>
-__device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B, int item,
+__device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B,
+                                                    const int2* __restrict__ list, int item,
                                                     WarpBlock& wb) {
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  const int2 u = B->worklist[item / SB];
+  const int2 u = list[item / SB];
   const ViewD& vw = decode_block<TILE>(B, u.x, u.y & 0xffffff, item - (item / SB) * SB, wb);
   wb.part = u.y >> 24;
   return vw;
@@ -476,8 +476,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
   const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
-    const ViewD* vwp = &decode_item<TILE>(B, item, wb);
-    if (wb.seg > 0) continue;
+    const ViewD* vwp = &decode_item<TILE>(B, B->worklist, item, wb);
     const int2 ts = B->tseg[wb.gt];
     const int2 rg = B->ranges[wb.gt];
     // a long list: 4x2 blocks with four lanes per pixel (four forward units)
@@ -612,7 +611,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
   const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
-    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    const ViewD& vw = decode_item<TILE>(B, B->worklist, item, wb);
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
     const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
@@ -722,11 +721,10 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   float4* __restrict__ rgrad = B->rec_grad;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip;
-  const int total = c->n_units * SB;
+  const int total = c->n_units_b * SB;
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
-    const ViewD& vw = decode_item<TILE>(B, item, wb);
-    if (wb.part > 0) continue;                 // forward-only unit
+    const ViewD& vw = decode_item<TILE>(B, B->worklist_b, item, wb);
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;
     const long long p = (long long)wb.py * vw.W + wb.px;
@@ -925,10 +923,10 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
   const int nw = B->resort_window;
-  const int total = c->n_units * SB;
+  const int total = c->n_units_b * SB;
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
-    const ViewD& vw = decode_item<TILE>(B, item, wb);
+    const ViewD& vw = decode_item<TILE>(B, B->worklist_b, item, wb);
     if (!__any_sync(FULL, wb.inimg)) continue;
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;

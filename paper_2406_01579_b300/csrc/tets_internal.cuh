@@ -34,7 +34,8 @@ struct Counters {
   int n_surv[TTS_MAX_SCENES];
   unsigned int work_fwd, work_bwd;      // persistent blend work queues
   unsigned int done_fwd, done_bwd;      // warps finished (last one resets)
-  int n_units;              // blend work units (tile segments) of the last binning
+  int n_units;              // forward work units (tile lists, 4x2-block parts) of the last binning
+  int n_units_b;            // backward work units (tile lists and list segments)
   int seg_total;            // checkpoint slots handed out by the work-list builder
   int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
   int sort_q[3];            // depth-sort queues: block, half-block and warp lists taken
@@ -99,10 +100,11 @@ struct Batch {
   int* tile_class;          // [TSORT_CLASSES * total_tiles] non-empty tiles by list length
   unsigned long long* scan_lb;   // [tile-scan blocks] look-back words (flag << 62 | sum)
   int2* ranges;             // [total_tiles]
-  int2* worklist;           // [units] (tile, segment), longest first
+  int2* worklist;           // [forward units] (tile, part << 24), longest first
+  int2* worklist_b;         // [backward units] (tile, segment), longest first
   int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)
-  int* wl_blockcnt;         // [work-list blocks * 34] units per length bucket and block
-  int* wl_base;             // [34] first unit of each length bucket
+  int* wl_blockcnt;         // [work-list blocks * 68] units per list, length bucket and block
+  int* wl_base;             // [68] first unit of each list's length buckets
   float4* pseg_a;           // [seg_cap * tile^2] forward state at each segment end: (T, C0, C1, C2)
   float4* pseg_b;           // [seg_cap * tile^2] (D, N0, N1, N2)
   float* pix_T;             // [total_pixels]
