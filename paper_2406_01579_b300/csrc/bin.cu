@@ -394,6 +394,14 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   const int nsurv = B->ctr->n_surv[sc];
   const int k0 = blockIdx.x * PRE_CHUNK;
   if (k0 >= nsurv) return;
+  __shared__ unsigned s_zmn, s_zmx;
+  __shared__ int s_left;
+  if (threadIdx.x == 0) {
+    s_zmn = 0xffffffffu;
+    s_zmx = 0u;
+    s_left = PP_THREADS / 32;
+  }
+  __syncthreads();
   const float s = B->s;
   const int tsh = __ffs(B->tile) - 1;   // tile is 8, 16 or 32
   unsigned zmn = 0xffffffffu, zmx = 0u;
@@ -440,15 +448,23 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
       }
     }
   }
-  // block min/max of the depth bits
-  __shared__ unsigned smn, smx;
-  if (threadIdx.x == 0) { smn = 0xffffffffu; smx = 0u; }
-  __syncthreads();
-  if (zmn != 0xffffffffu) { atomicMin(&smn, zmn); atomicMax(&smx, zmx); }
-  __syncthreads();
-  if (threadIdx.x == 0 && smn != 0xffffffffu) {
-    atomicMin(&B->ctr->zmin_bits, smn);
-    atomicMax(&B->ctr->zmax_bits, smx);
+  // block min/max of the depth bits without a block barrier: each warp adds
+  // its own to shared memory, the block's last warp to do so adds the block's
+  zmn = __reduce_min_sync(0xffffffffu, zmn);
+  zmx = __reduce_max_sync(0xffffffffu, zmx);
+  if ((threadIdx.x & 31) == 0) {
+    if (zmn != 0xffffffffu) {
+      atomicMin(&s_zmn, zmn);
+      atomicMax(&s_zmx, zmx);
+    }
+    __threadfence_block();
+    if (atomicAdd(&s_left, -1) == 1) {
+      const unsigned mn = atomicOr(&s_zmn, 0u), mx = atomicOr(&s_zmx, 0u);
+      if (mn != 0xffffffffu) {
+        atomicMin(&B->ctr->zmin_bits, mn);
+        atomicMax(&B->ctr->zmax_bits, mx);
+      }
+    }
   }
 }
 
