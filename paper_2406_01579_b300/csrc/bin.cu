@@ -74,7 +74,7 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->done_fwd = c->done_bwd = 0u;
     c->seg_total = 0;
     for (int q = 0; q < TSORT_CLASSES; ++q) c->class_n[q] = 0;
-    for (int q = 0; q < 3; ++q) c->sort_q[q] = 0;
+    for (int q = 0; q < 5; ++q) c->sort_q[q] = 0;
     c->scan_ticket = 0u;
   }
   const int nlb = (B->total_tiles + TS_TILES - 1) / TS_TILES;
@@ -483,9 +483,9 @@ constexpr unsigned long long TS_AGG = 1ull << 62, TS_PREFIX = 2ull << 62;
 constexpr long long TS_SPIN_LIMIT = 1ll << 22;
 
 // List-length class of the per-tile depth sort (see K5): up to 256 keys,
-// 2,048, 4,096, more.
+// 512, 1,024, 2,048, 4,096, more.
 __device__ __forceinline__ int tsort_class(int n) {
-  return n <= 256 ? 0 : n <= 2048 ? 1 : n <= 4096 ? 2 : 3;
+  return n <= 256 ? 0 : n <= 512 ? 1 : n <= 1024 ? 2 : n <= 2048 ? 3 : n <= 4096 ? 4 : 5;
 }
 
 __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(const Batch* __restrict__ B) {
@@ -654,24 +654,32 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
 // One persistent kernel of 512-thread blocks sorts every list, longest
 // first: the tile scan lists the tiles by length class, and the blocks take
 // (1) lists of more than 2,048 keys, one per block (more than 4,096: sorted
-// runs of 4,096 merged in global memory), then (2) lists of 257..2,048
-// keys, one per half block, then (3) lists of up to 256 keys, one per warp,
-// each from its own device queue.
+// runs of 4,096 merged in global memory), then lists of (2) 1,025..2,048
+// keys, one per half block, (3) 513..1,024, one per quarter block, (4)
+// 257..512, one per eighth of a block, and (5) up to 256 keys, one per warp,
+// each from its own device queue.  A group sorts its list padded to 8 keys
+// per thread, so the finer classes bound the padding by the list length.
 // ---------------------------------------------------------------------------
 constexpr int TSORT_NT = 512;
 
-// Barrier of a group of NT threads: the warp, the whole block, or (NT = 256)
-// the named barrier bar (1 or 2) of a half block.
+// Barrier of a group of NT threads: the warp, the whole block, or the named
+// barrier bar of a half block (1, 2), a quarter (3..6) or an eighth (7..14).
+// Named barriers take immediate ids.
 template <int NT>
 __device__ __forceinline__ void group_sync(int bar) {
   if constexpr (NT == 32) {
     __syncwarp();
   } else if constexpr (NT == TSORT_NT) {
     __syncthreads();
-  } else if (bar == 1) {
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
   } else {
-    asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+    switch (bar) {
+#define TSORT_BAR(i) case i: asm volatile("bar.sync " #i ", %0;" ::"n"(NT) : "memory"); break;
+      TSORT_BAR(1) TSORT_BAR(2) TSORT_BAR(3) TSORT_BAR(4) TSORT_BAR(5) TSORT_BAR(6) TSORT_BAR(7)
+      TSORT_BAR(8) TSORT_BAR(9) TSORT_BAR(10) TSORT_BAR(11) TSORT_BAR(12) TSORT_BAR(13)
+      TSORT_BAR(14)
+#undef TSORT_BAR
+      default: break;
+    }
   }
 }
 
@@ -757,7 +765,6 @@ __device__ __forceinline__ void group_sort_list(const unsigned long long* in, in
 
 constexpr int TSORT_K = 8;
 constexpr int TSORT_BLOCK_CAP = TSORT_NT * TSORT_K;        // 4,096
-constexpr int TSORT_HALF_CAP = TSORT_NT / 2 * TSORT_K;     // 2,048
 constexpr int TSORT_WARP_CAP = 32 * TSORT_K;               // 256
 
 // Merge of the sorted runs a[0, la) and b[0, lb) into o[0, la + lb) by all
@@ -808,16 +815,38 @@ __device__ void sort_long_list(const Batch* __restrict__ B, int2 r, unsigned lon
   __syncthreads();
 }
 
+// Lists of one class, one per group of NT threads (group g of the block,
+// named barrier bar), from device queue q; s: the group's shared memory.
+template <int NT>
+__device__ __forceinline__ void sort_group_lists(const Batch* __restrict__ B, int cls, int q,
+                                                 int g, int bar, unsigned long long* s,
+                                                 int* s_item) {
+  Counters* c = B->ctr;
+  const int n = c->class_n[cls];
+  const int* list = B->tile_class + (size_t)cls * B->total_tiles;
+  const unsigned long long* in = B->keys[1];
+  const int tid = threadIdx.x & (NT - 1);
+  for (;;) {
+    if (tid == 0) s_item[g] = atomicAdd(&c->sort_q[q], 1);
+    group_sync<NT>(bar);
+    const int it = s_item[g];
+    group_sync<NT>(bar);
+    if (it >= n) break;
+    const int2 r = B->ranges[list[it]];
+    group_sort_list<NT, TSORT_K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, s, tid, bar);
+  }
+}
+
 __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
   __shared__ unsigned long long s[spad_size<TSORT_BLOCK_CAP>()];
-  __shared__ int s_item[2];
+  __shared__ int s_item[16];
   Counters* c = B->ctr;
   if (c->n_keys_used == 0) return;
   const int nt = B->total_tiles;
   const int* list = B->tile_class;
-  const int n3 = c->class_n[3], n2 = c->class_n[2], n1 = c->class_n[1], n0 = c->class_n[0];
+  const int n5 = c->class_n[5], n4 = c->class_n[4], n0 = c->class_n[0];
   const unsigned long long* in = B->keys[1];
   // (1) lists of more than 2,048 keys (the longest class first), a block each
   for (;;) {
@@ -825,8 +854,8 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
     __syncthreads();
     const int it = s_item[0];
     __syncthreads();
-    if (it >= n3 + n2) break;
-    const int t = (it < n3) ? list[3 * nt + it] : list[2 * nt + it - n3];
+    if (it >= n5 + n4) break;
+    const int t = (it < n5) ? list[5 * nt + it] : list[4 * nt + it - n5];
     const int2 r = B->ranges[t];
     if (r.y - r.x > TSORT_BLOCK_CAP) {
       if (threadIdx.x == 0) atomicAdd(&c->long_lists, 1);
@@ -836,24 +865,18 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
                                          threadIdx.x, 0);
     }
   }
-  // (2) lists of 257..2,048 keys, a half block each (named barriers 1, 2)
-  const int h = threadIdx.x >> 8, htid = threadIdx.x & 255;
-  unsigned long long* sh = s + h * spad_size<TSORT_HALF_CAP>();
-  for (;;) {
-    if (htid == 0) s_item[h] = atomicAdd(&c->sort_q[1], 1);
-    group_sync<256>(1 + h);
-    const int it = s_item[h];
-    group_sync<256>(1 + h);
-    if (it >= n1) break;
-    const int2 r = B->ranges[list[nt + it]];
-    group_sort_list<256, TSORT_K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, sh, htid, 1 + h);
-  }
-  // (3) lists of up to 256 keys, a warp each, inside the warp's half
-  const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
-  unsigned long long* sw = sh + w * spad_size<TSORT_WARP_CAP>();
+  // (2) .. (4): halves, quarters, eighths, each inside the shared memory of
+  // the group it came from
+  const int h = threadIdx.x >> 8, qd = threadIdx.x >> 7, e = threadIdx.x >> 6;
+  sort_group_lists<256>(B, 3, 1, h, 1 + h, s + h * spad_size<2048>(), s_item);
+  sort_group_lists<128>(B, 2, 2, 2 + qd, 3 + qd, s + qd * spad_size<1024>(), s_item);
+  sort_group_lists<64>(B, 1, 3, 6 + e, 7 + e, s + e * spad_size<512>(), s_item);
+  // (5) lists of up to 256 keys, a warp each, inside the warp's eighth
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long* sw = s + w * spad_size<TSORT_WARP_CAP>();
   for (;;) {
     int it = 0;
-    if (lane == 0) it = atomicAdd(&c->sort_q[2], 1);
+    if (lane == 0) it = atomicAdd(&c->sort_q[4], 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n0) break;
     const int2 r = B->ranges[list[it]];

@@ -19,7 +19,7 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int TS_THREADS = 256;     // tile scan: threads per block
 constexpr int TS_ITEMS = 8;         // tiles per thread
 constexpr int TS_TILES = TS_THREADS * TS_ITEMS;
-constexpr int TSORT_CLASSES = 4;    // depth-sort list lengths (0,256] (256,2K] (2K,4K] (4K,...)
+constexpr int TSORT_CLASSES = 6;    // depth-sort list lengths (0,256] (256,512] (512,1K] (1K,2K] (2K,4K] (4K,...)
 
 // Counters at the start of the workspace (after the descriptor).
 struct Counters {
@@ -38,7 +38,7 @@ struct Counters {
   int n_units_b;            // backward work units (tile lists and list segments)
   int seg_total;            // checkpoint slots handed out by the work-list builder
   int class_n[TSORT_CLASSES];   // tiles in each list-length class of the depth sort
-  int sort_q[3];            // depth-sort queues: block, half-block and warp lists taken
+  int sort_q[5];            // depth-sort queues: block, half, quarter, eighth and warp lists taken
   unsigned int scan_ticket; // tile-scan blocks started
   unsigned int zero_q;      // gradient-clearing chunks taken by the backward
 };
