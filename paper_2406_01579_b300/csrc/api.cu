@@ -203,8 +203,10 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_rr = take(sizeof(int4) * slots);
   const size_t o_rec = take(sizeof(float4) * REC_Q * slots);
   const bool fwd_only = (pr.flags & TTS_FLAG_FORWARD_ONLY) != 0;
-  P->off_rec_grad = take(fwd_only ? 0 : sizeof(float4) * REC_Q * slots);
-  P->bytes_rec_grad = fwd_only ? 0 : sizeof(float4) * REC_Q * slots;
+  // record gradients and their touched flags, cleared together at init
+  const size_t rg_bytes = sizeof(float4) * REC_Q * slots;
+  P->bytes_rec_grad = fwd_only ? 0 : rg_bytes + (((size_t)slots + 15) & ~(size_t)15);
+  P->off_rec_grad = take(P->bytes_rec_grad);
   const size_t o_k0 = take(sizeof(unsigned long long) * cap);
   const size_t o_k1 = take(sizeof(unsigned long long) * cap);
   const size_t o_v = take(sizeof(unsigned) * cap);
@@ -251,6 +253,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.rec_rect = reinterpret_cast<int4*>(base + o_rr);
     B.rec = reinterpret_cast<float4*>(base + o_rec);
     B.rec_grad = reinterpret_cast<float4*>(base + P->off_rec_grad);
+    B.rec_touched = fwd_only ? nullptr : reinterpret_cast<unsigned char*>(base + P->off_rec_grad + rg_bytes);
     B.keys[0] = reinterpret_cast<unsigned long long*>(base + o_k0);
     B.keys[1] = reinterpret_cast<unsigned long long*>(base + o_k1);
     B.vals = reinterpret_cast<unsigned*>(base + o_v);

@@ -719,6 +719,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   float4* __restrict__ rgrad = B->rec_grad;
+  unsigned char* __restrict__ touched = B->rec_touched;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip;
   const int total = c->n_units_b * SB;
@@ -874,7 +875,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
         // each contributing lane adds its record-field gradients with vector
         // atomics (the few lanes of one candidate meet in L2)
         if (contrib) {
-          float4* dst = rgrad + (size_t)sslot[wid][k] * REC_Q;
+          const unsigned sl = sslot[wid][k];
+          touched[sl] = 1;   // the same byte from every contributing lane
+          float4* dst = rgrad + (size_t)sl * REC_Q;
           atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
           atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
           atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
@@ -980,6 +983,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       Pw += twa;
       const float wgt = T * a;
       float4* dst = rgrad + (size_t)slot * REC_Q;
+      B->rec_touched[slot] = 1;
       const bool clamped = !pure && (o.alpha > cap);
       if (!clamped) {
         const float dx = dLda * o.e1 * o.B;
@@ -1098,8 +1102,10 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       const int v = B->scene_views[S.view_off + vi];
       const ViewD& vw = B->vw[v];
       const long long slot = vw.rec_base + k;
-      // a culled slot's gradient is zero (never accumulated): the magnitude
-      // test below skips it without reading its tile count first
+      // a slot the blend backward never added to has a zero gradient: only
+      // the touched ones are read (and cleared, with their flag)
+      if (!B->rec_touched[slot]) continue;
+      B->rec_touched[slot] = 0;
       float4* gq = B->rec_grad + slot * REC_Q;
       const float4 g0 = nrm ? gq[0] : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4], g5 = gq[5];

@@ -92,7 +92,8 @@ struct Batch {
   unsigned int* rec_z;      // [slots] FP32 mean depth bits
   int4* rec_rect;           // [slots] tile rect (tx0, tx1, ty0, ty1)
   float4* rec;              // [slots * 6]
-  float4* rec_grad;         // [slots * 6]
+  float4* rec_grad;         // [slots * 6] record gradient (self-clearing)
+  unsigned char* rec_touched;    // [slots] 1 once the slot's gradient was added to (self-clearing)
   unsigned long long* keys[2];   // [key_cap] each: [1] (zbits << 32 | slot) bucketed by
                                  // tile; [0] merge scratch, debug keys on request
   unsigned int* vals;       // [key_cap] record slot of each key, sorted per tile
