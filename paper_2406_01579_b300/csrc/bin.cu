@@ -386,6 +386,8 @@ __device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned act
 // thread writes the slot's record, tile rect and depth bits, and counts the
 // keys of every tile the slot's rect overlaps.
 // ---------------------------------------------------------------------------
+constexpr int PP_SMEM_VIEWS = 16;
+
 __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
@@ -396,10 +398,22 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   if (k0 >= nsurv) return;
   __shared__ unsigned s_zmn, s_zmx;
   __shared__ int s_left;
+  // the scene's view constants in shared memory (up to PP_SMEM_VIEWS views)
+  __shared__ ViewD s_vw[PP_SMEM_VIEWS];
+  const int nv = S.view_cnt;
+  const bool vs = nv <= PP_SMEM_VIEWS;
   if (threadIdx.x == 0) {
     s_zmn = 0xffffffffu;
     s_zmx = 0u;
     s_left = PP_THREADS / 32;
+  }
+  if (vs) {
+    constexpr int VW = sizeof(ViewD) / 4;
+    for (int w = threadIdx.x; w < nv * VW; w += PP_THREADS) {
+      const int vi = w / VW;
+      reinterpret_cast<int*>(s_vw)[w] =
+          reinterpret_cast<const int*>(&B->vw[B->scene_views[S.view_off + vi]])[w - vi * VW];
+    }
   }
   __syncthreads();
   const float s = B->s;
@@ -410,8 +424,8 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
     if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
     TetIn in;
     if (k < nsurv) load_tet_ids(S, B->surv_T[S.surv_off + k], in);
-    for (int vi = 0; vi < S.view_cnt; ++vi) {
-      const ViewD& vw = B->vw[B->scene_views[S.view_off + vi]];
+    // one view of the survivor: record, pixel rect, depth bits, tile counts
+    auto view = [&](const ViewD& vw) {
       int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0, ntx = 0, nt = 0;
       if (k < nsurv) {
         const long long slot = vw.rec_base + k;
@@ -446,6 +460,11 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
           }
         }
       }
+    };
+    if (vs) {
+      for (int vi = 0; vi < nv; ++vi) view(s_vw[vi]);
+    } else {
+      for (int vi = 0; vi < nv; ++vi) view(B->vw[B->scene_views[S.view_off + vi]]);
     }
   }
   // block min/max of the depth bits without a block barrier: each warp adds
