@@ -203,6 +203,33 @@ def test_batch_of_views_and_scenes_matches_single_views(sphere16):
             assert err < GRAD_TOL, f"scene{si}: rel err {err:.3e}"
 
 
+@pytest.mark.parametrize("nv", [14, 18])
+def test_many_views_of_one_scene(sphere16, nv):
+    """Up to and more views of one scene than the preprocess stages in shared
+    memory (16): past that it reads the view constants from the descriptor.
+    Image sizes are even: with an odd width the look-at cameras put a column of
+    pixel centres exactly on the image of the world z axis, where grid tets have
+    edges, and a ray through an edge meets two faces at one point (a kink of the
+    chord where adjoint, dual-number and finite-difference derivatives differ)."""
+    rng = np.random.default_rng(11)
+    cams = [synth.random_camera(rng, 40 + 4 * i, 36 + 2 * (i % 5)) for i in range(nv)]
+    views = [(c, 0) for c in cams]
+    p = Params(s=60.0, tile=8)
+    ups = synth.upstream_grads(13, cams)
+    orcs = [oracle_run(sphere16, c, p) for c in cams]
+    ups = [masked_upstream(u, o["amb"]) for u, o in zip(ups, orcs)]
+    gpu = gpu_run([sphere16], views, p, upstream=ups)
+    for i, o in enumerate(orcs):
+        _check_view(gpu["views"][i], o, f"view{i}")
+    acc = [np.zeros((sphere16.N, 3)), np.zeros(sphere16.N), np.zeros((sphere16.N, 3))]
+    for c, u in zip(cams, ups):
+        o = oracle_run(sphere16, c, p, upstream=u)
+        acc[0] += o["dV"]; acc[1] += o["df"]; acc[2] += o["drgb"]
+    for g, o in zip(gpu["grads"][0], acc):
+        err = grad_rel_err(g, o)
+        assert err < GRAD_TOL, f"{nv} views: rel err {err:.3e}"
+
+
 def test_empty_and_degenerate_inputs(sphere16):
     p = Params(s=175.0, tile=16)
     # all tets pre-filtered away: transparent image
