@@ -726,9 +726,12 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
     }
   }
   for (int run = K; run < NT * K; run <<= 1) {
+    // merges of runs within one warp's 32 K keys need only the warp's barrier
+    const bool in_warp = 2 * run <= 32 * K;
 #pragma unroll
     for (int i = 0; i < K; ++i) s[spad(tid * K + i)] = k[i];
-    group_sync<NT>(bar);
+    if (in_warp) __syncwarp();
+    else group_sync<NT>(bar);
     const int d0 = tid * K;
     const int start = d0 & ~(2 * run - 1);
     const int d = d0 - start;
@@ -754,7 +757,8 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
         vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
       }
     }
-    group_sync<NT>(bar);
+    if (in_warp) __syncwarp();
+    else group_sync<NT>(bar);
   }
 }
 
