@@ -812,8 +812,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
       }
       __syncwarp();
       for (int k = __popc(m) - 1; k >= 0; --k) {
+        // some lane is active for every staged entry (they all lie below the
+        // largest `last` of the warp)
         const bool active = (g0 + sidx[wid][k] - rg.x) < last;
-        if (!__any_sync(FULL, active)) continue;
         const Chord ch = chord_eval(st[wid][0][k], st[wid][1][k], st[wid][2][k], st[wid][3][k],
                                     wb.fpx, wb.fpy);
         bool contrib = active & ch.hit;
