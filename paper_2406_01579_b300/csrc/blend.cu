@@ -439,7 +439,9 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           const float mine = h ? fragment_code(st[4][k], ch, pure, cap, skip) : 0.f;
           composite4<NRM>(mine, k, base, pure, eps, st, sidx, S);
         }
-        if (__all_sync(FULL, S.done)) break;
+        // with four lanes per pixel a group is short: the walk checks for an
+        // all-stopped block once per group of 32 entries only
+        if (LPP == 1 && __all_sync(FULL, S.done)) break;
       }
       __syncwarp();
     }
