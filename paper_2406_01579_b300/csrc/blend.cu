@@ -826,8 +826,6 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
           a = pure ? o.alpha : fminf(o.alpha, cap);
           contrib = pure ? (a > 0.f) : (a >= skip);
         }
-        const unsigned mc = __ballot_sync(FULL, contrib);
-        if (mc == 0u) continue;
         float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
         float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
         float gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
