@@ -436,7 +436,10 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           const int k = min(k0 + sub, cnt - 1);
           const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
           const bool h = ch.hit && (k0 + sub < cnt);
-          const float mine = h ? fragment_code(st[4][k], ch, pure, cap, skip) : 0.f;
+          // every lane evaluates its candidate's code (no divergence before the
+          // pixel's exchange); a miss codes 0
+          const float code = fragment_code(st[4][k], ch, pure, cap, skip);
+          const float mine = h ? code : 0.f;
           composite4<NRM>(mine, k, base, pure, eps, st, sidx, S);
         }
         // with four lanes per pixel a group is short: the walk checks for an
