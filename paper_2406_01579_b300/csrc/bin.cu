@@ -388,7 +388,7 @@ __device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned act
 // ---------------------------------------------------------------------------
 constexpr int PP_SMEM_VIEWS = 16;
 
-__global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __restrict__ B) {
+__global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
   const int sc = blockIdx.y;
@@ -405,11 +405,11 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   if (threadIdx.x == 0) {
     s_zmn = 0xffffffffu;
     s_zmx = 0u;
-    s_left = PP_THREADS / 32;
+    s_left = PRE_THREADS / 32;
   }
   if (vs) {
     constexpr int VW = sizeof(ViewD) / 4;
-    for (int w = threadIdx.x; w < nv * VW; w += PP_THREADS) {
+    for (int w = threadIdx.x; w < nv * VW; w += PRE_THREADS) {
       const int vi = w / VW;
       reinterpret_cast<int*>(s_vw)[w] =
           reinterpret_cast<const int*>(&B->vw[B->scene_views[S.view_off + vi]])[w - vi * VW];
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(PP_THREADS, 3) k_preprocess(const Batch* __res
   const float s = B->s;
   const int tsh = __ffs(B->tile) - 1;   // tile is 8, 16 or 32
   unsigned zmn = 0xffffffffu, zmx = 0u;
-  for (int q = threadIdx.x; q < PRE_CHUNK; q += PP_THREADS) {
+  for (int q = threadIdx.x; q < PRE_CHUNK; q += PRE_THREADS) {
     const int k = k0 + q;
     if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
     TetIn in;
@@ -1062,7 +1062,7 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   launch_k(k_fwd_reset, dim3(64), dim3(256), 0, st, dB);
   dim3 g(P.max_pp_chunks, P.n_views);
-  launch_k(k_preprocess, dim3(P.max_pre_chunks, P.n_scenes), dim3(PP_THREADS), 0, st, dB);
+  launch_k(k_preprocess, dim3(P.max_pre_chunks, P.n_scenes), dim3(PRE_THREADS), 0, st, dB);
   launch_k(k_tile_scan, dim3((P.total_tiles + TS_TILES - 1) / TS_TILES), dim3(TS_THREADS), 0, st, dB);
   launch_k(k_place, dim3(g), dim3(PP_THREADS), 0, st, dB);
   launch_k(k_tile_sort, dim3(P.tsort_blocks), dim3(TSORT_NT), 0, st, dB);

@@ -13,7 +13,8 @@ namespace tts {
 constexpr int PF_CHUNK = 2048;      // tets per pre-filter block (32 KB of indices in shared memory)
 constexpr int PF_THREADS = 256;
 constexpr int PP_CHUNK = 512;       // slots per key placement block
-constexpr int PRE_CHUNK = 256;      // survivors per preprocess block
+constexpr int PRE_THREADS = 128;    // preprocess block
+constexpr int PRE_CHUNK = 128;      // survivors per preprocess block
 constexpr int PP_THREADS = 256;
 constexpr int SCAN_THREADS = 1024;
 constexpr int TS_THREADS = 256;     // tile scan: threads per block
