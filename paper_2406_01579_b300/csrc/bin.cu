@@ -715,15 +715,17 @@ __host__ __device__ constexpr int spad_size() { return N + N / 16; }
 template <int NT, int K>
 __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], unsigned long long* s,
                                                  int tid, int bar) {
+  static_assert(K == 8, "the register network sorts 8 keys");
+  // Batcher's odd-even merge network for 8 keys (19 compare-exchanges)
+  constexpr int NET[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6},
+                              {5, 7}, {1, 2}, {5, 6}, {0, 4}, {1, 5}, {2, 6}, {3, 7},
+                              {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
 #pragma unroll
-  for (int r = 0; r < K; ++r) {       // odd-even transposition network
-#pragma unroll
-    for (int i = r & 1; i + 1 < K; i += 2) {
-      const unsigned long long x = k[i], y = k[i + 1];
-      const bool sw = y < x;
-      k[i] = sw ? y : x;
-      k[i + 1] = sw ? x : y;
-    }
+  for (int c = 0; c < 19; ++c) {
+    const unsigned long long x = k[NET[c][0]], y = k[NET[c][1]];
+    const bool sw = y < x;
+    k[NET[c][0]] = sw ? y : x;
+    k[NET[c][1]] = sw ? x : y;
   }
   for (int run = K; run < NT * K; run <<= 1) {
     // merges of runs within one warp's 32 K keys need only the warp's barrier
