@@ -224,6 +224,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const size_t o_wl = take(sizeof(int2) * 4 * (size_t)tiles);
   const size_t o_wlbk = take(sizeof(int2) * ((size_t)tiles + (size_t)B.seg_cap));
   const size_t o_tseg = take(sizeof(int2) * tiles);
+  const size_t o_tlast = take(sizeof(int) * tiles);
   const int wl_blocks = (tiles + 255) / 256;
   const size_t o_wlc = take(sizeof(int) * 68 * (size_t)wl_blocks);
   const size_t o_wlb = take(sizeof(int) * 68);
@@ -264,6 +265,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.worklist = reinterpret_cast<int2*>(base + o_wl);
     B.worklist_b = reinterpret_cast<int2*>(base + o_wlbk);
     B.tseg = reinterpret_cast<int2*>(base + o_tseg);
+    B.tile_last = reinterpret_cast<int*>(base + o_tlast);
     B.wl_blockcnt = reinterpret_cast<int*>(base + o_wlc);
     B.wl_base = reinterpret_cast<int*>(base + o_wlb);
     B.pseg_a = reinterpret_cast<float4*>(base + o_psa);

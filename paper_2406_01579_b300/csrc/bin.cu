@@ -984,6 +984,7 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
   }
   if (in) {
     B->tseg[t] = make_int2(base, nseg);
+    B->tile_last[t] = 0;
     atomicAdd(&cnt[wl_bucket(len)], fwd_lanes(nseg));
     atomicAdd(&cnt[WL_BUCKETS + wl_bucket(nseg > 1 ? L : len)], nseg);
   }

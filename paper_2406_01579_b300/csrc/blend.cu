@@ -506,6 +506,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict_
       S.nfrag = pix_sum_i<4>(S.nfrag);
       S.last = pix_max_i<4>(S.last);
       if (wb.inimg && (threadIdx.x & 3) == 0) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+      // the tile's largest blended index: the backward skips the segments past it
+      const unsigned ml = __reduce_max_sync(FULL, (unsigned)S.last);
+      if ((threadIdx.x & 31) == 0 && ml > 0u) atomicMax(B->tile_last + wb.gt, (int)ml);
     } else {
       fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
                        st[wid], sidx[wid], S);
@@ -730,6 +733,9 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
   for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, B->worklist_b, item, wb);
+    // a segment past every entry the tile's pixels blended has no work
+    const int2 ts = B->tseg[wb.gt];
+    if (ts.y > 1 && wb.seg * B->seg_len >= B->tile_last[wb.gt]) continue;
     const int2 rg = B->ranges[wb.gt];
     const long long HW = (long long)vw.W * vw.H;
     const long long p = (long long)wb.py * vw.W + wb.px;
@@ -753,7 +759,6 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict_
     }
     // the list range of this item: the whole list, or one segment of a split
     // one; T and the suffix S start at the range's end
-    const int2 ts = B->tseg[wb.gt];
     int lo = rg.x, hi = rg.y;
     float T = Tfin, S = 0.f;
     if (ts.y > 1) {

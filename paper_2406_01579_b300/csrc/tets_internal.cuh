@@ -105,6 +105,7 @@ struct Batch {
   int2* worklist;           // [forward units] (tile, part << 24), longest first
   int2* worklist_b;         // [backward units] (tile, segment), longest first
   int2* tseg;               // [total_tiles] (first segment slot or -1, segment count)
+  int* tile_last;           // [total_tiles] largest blended entry + 1 of a split list's pixels
   int* wl_blockcnt;         // [work-list blocks * 68] units per list, length bucket and block
   int* wl_base;             // [68] first unit of each list's length buckets
   float4* pseg_a;           // [seg_cap * tile^2] forward state at each segment end: (T, C0, C1, C2)
