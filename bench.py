@@ -41,7 +41,7 @@ BWD_FLOP_PER_FRAG = 150
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "eca117681ee39541": {8: {"blend_fwd": 121316864, "blend_bwd": 227427072}},
+    "f3ecb4a47dfa0e76": {8: {"blend_fwd": 121882112, "blend_bwd": 227429632}},
 }
 
 
