@@ -1,11 +1,13 @@
 """Weak scaling over ranks, one GPU per rank.
 
 The views of a training step are independent (each view's lists, blend and
-record gradients are its own), so ranks do not exchange data: each rank
-renders its own views of the scene.  The only collectives are the barrier
-around the timed region and two reductions of the timing: the slowest rank's
-time (max) and the pixels all ranks rendered (sum).  The job's throughput is
-then the pixels of all ranks over the slowest rank's time.
+record gradients are its own): each rank renders its own views of the scene.
+The one exchange of the step is the sum of the scene's vertex gradients over
+the ranks (dV, df, drgb: each rank's views give part of them), one
+all-reduce per tensor after the backward.  The other collectives are the
+barrier around the timed region and two reductions of the timing: the
+slowest rank's time (max) and the pixels all ranks rendered (sum).  The job's
+throughput is then the pixels of all ranks over the slowest rank's time.
 """
 
 from __future__ import annotations
@@ -48,3 +50,13 @@ def max_over_ranks(x: float, dist=None, device=None) -> float:
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def allreduce_grads(grads, dist=None) -> None:
+    """Sum each scene's vertex gradients (dV, df, drgb) over the ranks, in
+    place: afterwards every rank holds the gradient of all ranks' views."""
+    if dist is None:
+        return
+    for g in grads:
+        for t in g:
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)

@@ -28,8 +28,12 @@ class HostStepPipeline:
     tensors of ``rast`` provide the tet indices; the vertex arrays of every
     step come from the host."""
 
-    def __init__(self, rast: Rasterizer):
+    def __init__(self, rast: Rasterizer, reduce_grads=None):
+        """``reduce_grads``: called with each step's device gradients (per
+        scene (dV, df, drgb)) on the compute stream after the backward and
+        before they are copied out, e.g. a sum over ranks."""
         self.r = rast
+        self.reduce_grads = reduce_grads
         dev = rast.device
         P = rast.total_pixels
         n_up = 4 if rast.params.normals else 3
@@ -87,6 +91,8 @@ class HostStepPipeline:
             cs.wait_event(self.ev_out[b])            # step i-2's gradients have left set b
         self.r.set_scenes(scenes)
         self.r.step(self.out, up, grads)
+        if self.reduce_grads is not None:
+            self.reduce_grads(grads)
         self.ev_comp[b].record(cs)
         self.d2h.wait_event(self.ev_comp[b])
         with torch.cuda.stream(self.d2h):
