@@ -594,6 +594,10 @@ def cpu_baseline(a, sc=None, min_seconds=10.0, max_steps=6):
 
 def run_reference(a):
     import synth
+    if a.tile == 0:
+        # the autotuner (a GPU measurement) is not run on this arm: the tile it
+        # picks on this workload
+        a.tile = 8
     sc = synth.scene_spheres128(res=a.res, n_views=a.views)
     ups = synth.upstream_grads(2, sc.cams)
     for k in range(a.warmup):
