@@ -234,7 +234,7 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 
 // Lanes per pixel of the forward walk of a tile list split into nseg
 // backward segments: 1 (8x4 blocks) for an unsplit list, 4 (4x2 blocks) for a
-// split one.  The work list holds as many forward units (parts, TILE^2 / 32
+// split one.  The forward work list holds as many units (parts, TILE^2 / 32
 // blocks each) for the list as it has lanes per pixel.
 __device__ __forceinline__ int fwd_lanes(int nseg) { return (nseg <= 1) ? 1 : 4; }
 
