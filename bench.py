@@ -19,6 +19,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -91,7 +92,9 @@ class ClockSampler:
 
     def __init__(self, gpu_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples; the JSON line carries their summary
+        self.path = os.path.join(os.environ.get("TTS_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"tts_clocks_rank{gpu_index}.csv")
         self.gpu = gpu_index
 
     def start(self):
