@@ -1,16 +1,18 @@
 // Stable LSD radix sort of (uint64 key, uint32 value) pairs, 8-bit digits,
 // three kernels per pass (per-block digit counts, a scan of each digit's row
-// over the blocks, a stable scatter ranked per warp by match_any).  Two entry
-// points: tts_sort_pairs sorts in caller-provided scratch;
-// tts_sort_pairs_noalloc sorts in a scratch array compiled into the library.
+// over the blocks, a stable scatter ranked per warp by match_any).  Only the
+// low key_bits bits of a key take part in the order: the last pass reads a
+// digit of key_bits - 8 (passes - 1) bits.  Two entry points: tts_sort_pairs
+// sorts in caller-provided scratch; tts_sort_pairs_noalloc sorts in a scratch
+// array compiled into the library.
 //
 // tts_sort_pairs_noalloc:
 // Who needs it: callers that must not allocate device memory themselves, for
-// example code running inside a host callback or a custom allocator hook
-// (where calling cudaMalloc is forbidden or deadlocks), plugin hosts that own
-// every device allocation, or latency-critical loops that cannot afford
-// cudaMalloc's implicit device synchronisation.  They pass inputs and outputs;
-// the temporary storage lives in a fixed-size array compiled into this file.
+// example a custom allocator hook (which cannot call back into cudaMalloc),
+// plugin hosts that own every device allocation, or latency-critical loops
+// that cannot afford cudaMalloc's implicit device synchronisation.  They pass
+// inputs and outputs; the temporary storage lives in a fixed-size array
+// compiled into this file.
 //
 // Limits and sharing rules:
 //  * at most TTS_SORT_NOALLOC_MAX_KEYS pairs per call; larger calls return
@@ -25,6 +27,10 @@
 //    capture on that device.
 // Nothing in the scratch needs to start at zero: every pass rewrites the
 // histogram rows it reads.
+//
+// Errors: each kernel is launched with cudaLaunchKernelEx and its own return
+// code is checked, so an error left pending by unrelated earlier CUDA calls
+// is neither reported as this call's nor cleared.
 #include <cstdint>
 #include <mutex>
 
@@ -89,7 +95,7 @@ __device__ __forceinline__ T na_block_excl_scan(T v, T* total) {
 }
 
 __global__ void __launch_bounds__(NA_THREADS) k_na_hist(const unsigned long long* __restrict__ src,
-                                                        long long n, int shift,
+                                                        long long n, int shift, unsigned mask,
                                                         unsigned* __restrict__ hist) {
   long long lo, hi;
   na_chunk(n, &lo, &hi);
@@ -98,7 +104,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_hist(const unsigned long long
   __syncthreads();
   const int wid = threadIdx.x >> 5;
   for (long long i = lo + threadIdx.x; i < hi; i += NA_THREADS)
-    atomicAdd(&h[wid][(unsigned)(src[i] >> shift) & (NA_RADIX - 1)], 1u);
+    atomicAdd(&h[wid][(unsigned)(src[i] >> shift) & mask], 1u);
   __syncthreads();
   for (int d = threadIdx.x; d < NA_RADIX; d += NA_THREADS) {
     unsigned t = 0;
@@ -126,7 +132,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_rowscan(unsigned* __restrict_
 __global__ void __launch_bounds__(NA_THREADS) k_na_scatter(
     const unsigned long long* __restrict__ ksrc, const unsigned* __restrict__ vsrc,
     unsigned long long* __restrict__ kdst, unsigned* __restrict__ vdst, long long n, int shift,
-    const unsigned* __restrict__ hist) {
+    unsigned mask, const unsigned* __restrict__ hist) {
   long long lo, hi;
   na_chunk(n, &lo, &hi);
   constexpr int NW = NA_THREADS / 32;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_scatter(
       if (i < hi) {
         k[j] = ksrc[i];
         val[j] = vsrc[i];
-        dg[j] = (unsigned)(k[j] >> shift) & (NA_RADIX - 1);
+        dg[j] = (unsigned)(k[j] >> shift) & mask;
       } else {
         dg[j] = NA_RADIX;
       }
@@ -200,24 +206,46 @@ __global__ void __launch_bounds__(NA_THREADS) k_na_scatter(
   }
 }
 
+// Launches one kernel of the sort and returns its own launch status.
+template <typename... KArgs, typename... Args>
+cudaError_t na_launch(void (*kernel)(KArgs...), int grid, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(NA_THREADS);
+  cfg.stream = st;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // The passes over the low key_bits bits: ks/vs in, the final pass into
 // kout/vout, the others into tk/tv (ping-pong), hist: NA_RADIX x (NA_BLOCKS+1).
-void radix_sort_pairs(const unsigned long long* ks, const unsigned* vs, unsigned long long* kout,
-                      unsigned* vout, unsigned long long* tk, unsigned* tv, unsigned* hist,
-                      long long n, int key_bits, cudaStream_t st) {
+// Pass p sorts by bits [8p, 8p + 8) masked to key_bits.  Returns TTS_OK or
+// TTS_ERR_CUDA when one of its launches failed (nothing after it is enqueued).
+int radix_sort_pairs(const unsigned long long* ks, const unsigned* vs, unsigned long long* kout,
+                     unsigned* vout, unsigned long long* tk, unsigned* tv, unsigned* hist,
+                     long long n, int key_bits, cudaStream_t st) {
   const int passes = (key_bits + 7) / 8;
-  for (int p = 0; p < passes; ++p) {
+  long long launched = 0;
+  int rc = TTS_OK;
+  for (int p = 0; p < passes && rc == TTS_OK; ++p) {
     // the pass that writes the final result targets the caller's output
     const bool to_out = ((passes - 1 - p) % 2) == 0;
     unsigned long long* kd = to_out ? kout : tk;
     unsigned* vd = to_out ? vout : tv;
-    k_na_hist<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, n, 8 * p, hist);
-    k_na_rowscan<<<NA_RADIX, NA_THREADS, 0, st>>>(hist);
-    k_na_scatter<<<NA_BLOCKS, NA_THREADS, 0, st>>>(ks, vs, kd, vd, n, 8 * p, hist);
+    const int bits = key_bits - 8 * p < 8 ? key_bits - 8 * p : 8;
+    const unsigned mask = (1u << bits) - 1u;
+    cudaError_t e = na_launch(k_na_hist, NA_BLOCKS, st, ks, n, 8 * p, mask, hist);
+    if (e == cudaSuccess) { ++launched; e = na_launch(k_na_rowscan, NA_RADIX, st, hist); }
+    if (e == cudaSuccess) {
+      ++launched;
+      e = na_launch(k_na_scatter, NA_BLOCKS, st, ks, vs, kd, vd, n, 8 * p, mask,
+                    (const unsigned*)hist);
+    }
+    if (e == cudaSuccess) ++launched; else rc = TTS_ERR_CUDA;
     ks = kd;
     vs = vd;
   }
-  tts::count_launches(3ll * passes);
+  tts::count_launches(launched);
+  return rc;
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -255,10 +283,9 @@ extern "C" int tts_sort_pairs_noalloc(const uint64_t* keys_in, const uint32_t* v
   NaScratch* S = nullptr;
   int rc = na_scratch(&S);
   if (rc != TTS_OK) return rc;
-  radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
-                   reinterpret_cast<unsigned long long*>(keys_out), vals_out, S->keys, S->vals,
-                   S->hist, n, key_bits, reinterpret_cast<cudaStream_t>(stream));
-  return (cudaPeekAtLastError() == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
+  return radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
+                          reinterpret_cast<unsigned long long*>(keys_out), vals_out, S->keys,
+                          S->vals, S->hist, n, key_bits, reinterpret_cast<cudaStream_t>(stream));
 }
 
 extern "C" int tts_sort_pairs_scratch_size(int64_t n, size_t* bytes) {
@@ -286,8 +313,7 @@ extern "C" int tts_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, 
   unsigned* tv = reinterpret_cast<unsigned*>(base);
   base += align256(sizeof(unsigned) * (size_t)n);
   unsigned* hist = reinterpret_cast<unsigned*>(base);
-  radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
-                   reinterpret_cast<unsigned long long*>(keys_out), vals_out, tk, tv, hist, n,
-                   key_bits, reinterpret_cast<cudaStream_t>(stream));
-  return (cudaPeekAtLastError() == cudaSuccess) ? TTS_OK : TTS_ERR_CUDA;
+  return radix_sort_pairs(reinterpret_cast<const unsigned long long*>(keys_in), vals_in,
+                          reinterpret_cast<unsigned long long*>(keys_out), vals_out, tk, tv, hist,
+                          n, key_bits, reinterpret_cast<cudaStream_t>(stream));
 }
