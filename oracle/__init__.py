@@ -90,7 +90,7 @@ def lib():
         L.orc_fragment_grad.restype = ctypes.c_int
         L.orc_render.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P,
                                  P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int,
-                                 P, P, P, P, P, P]
+                                 P, P, P, P, P, P, P, P, P, P, P, P, P]
         L.orc_render.restype = ctypes.c_int
         L.orc_render_dirderiv.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P, P, P, P,
                                           P, P, P, P, P, P, P, P]
@@ -190,12 +190,22 @@ def bin_view(surv, T, V, cam, tile: int):
 
 
 def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=None,
-           nthreads: int = 0, V64=None, f64=None, rgb64=None, normals: bool = False):
+           nthreads: int = 0, V64=None, f64=None, rgb64=None, normals: bool = False,
+           branch=None, abs_terms: bool = False):
     """Render one view; returns a dict with image (3,H,W), alpha, depth, amb,
     alt_*, nfrag, the binning lists and (if ``upstream`` = (dimg, dalpha,
     ddepth) is given) the FP64 gradients dV, df, drgb.  ``V64``/``f64``/``rgb64``
     override the FP64 values used after binning (the lists come from the FP32
-    inputs)."""
+    inputs).  ``branch`` (H,W int8, optional): where 1, the gradient is that of
+    the pixel's alternative branch (first ambiguous decision inverted).
+    ``abs_terms``: also return dV_abs, df_abs, drgb_abs, the sums of the
+    absolute values of the per-fragment terms of each gradient entry, and
+    dV_kink, df_kink, drgb_kink (zero): per entry the sum over fragments whose
+    ray passes within rounding of an edge of its entry or exit face of the
+    change of the fragment's term under the other one-sided derivative, and
+    dV_graze (df_graze, drgb_graze zero): per entry the sum over fragments of
+    |the term through the opacity| / c^2, c the smaller |cos| between the
+    pixel ray and the chord's entry and exit face normals."""
     V = _c(V, np.float32)
     T = _c(T, np.int32)
     f = _c(f, np.float32)
@@ -227,18 +237,30 @@ def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=
         dV = np.zeros((N, 3))
         df = np.zeros(N)
         drgb = np.zeros((N, 3))
+    aV = af = argb = kV = kf = gzV = None
+    if upstream is not None and abs_terms:
+        aV, af, argb = np.zeros((N, 3)), np.zeros(N), np.zeros((N, 3))
+        kV, kf, gzV = np.zeros((N, 3)), np.zeros(N), np.zeros((N, 3))
+    br = None if branch is None else _c(branch, np.int8)
+    if br is not None:
+        assert br.shape == (H, W)
     surv = _c(surv, np.int32)
     rc = lib().orc_render(N, _p(V), _p(f), _p(rgb), _p(T), len(surv), _p(surv),
                           _p(bins["rect"]), ctypes.byref(c), ctypes.byref(params),
                           _p(bins["key_val"]), _p(bins["ranges"]), _p(img), _p(alpha), _p(depth),
                           _p(amb), _p(aimg), _p(aalpha), _p(adepth), _p(nfrag), _p(gi), _p(ga),
                           _p(gd), _p(dV), _p(df), _p(drgb), nthreads, _p(V64), _p(f64),
-                          _p(rgb64), _p(nrm), _p(anrm), _p(gn))
+                          _p(rgb64), _p(nrm), _p(anrm), _p(gn), _p(br), _p(aV), _p(af),
+                          _p(argb), _p(kV), _p(kf), _p(gzV))
     assert rc == 0
     out = dict(image=img, alpha=alpha, depth=depth, amb=amb, alt_image=aimg, alt_alpha=aalpha,
                alt_depth=adepth, nfrag=nfrag, surv=surv, bins=bins, normal=nrm, alt_normal=anrm)
     if upstream is not None:
         out.update(dV=dV, df=df, drgb=drgb)
+        if abs_terms:
+            out.update(dV_abs=aV, df_abs=af, drgb_abs=argb, dV_kink=kV, df_kink=kf,
+                       drgb_kink=np.zeros_like(argb), dV_graze=gzV, df_graze=np.zeros_like(af),
+                       drgb_graze=np.zeros_like(argb))
     return out
 
 

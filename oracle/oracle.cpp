@@ -86,22 +86,34 @@ static S opacity_eq1(const S& fp, const S& fn, double s) {
 template <class S>
 struct FragOut {
   S f_prev, f_next, z_in, z_out;
+  int k_in, k_out;    // faces giving the entry and the exit point
 };
 
+// One face of a tet against the ray of pixel centre (px, py): App. A.1's 2D
+// barycentrics of the projected triangle (Cramer) and App. A.2's perspective
+// correction of the depth z_p and the SDF f_p at the point where the ray meets
+// the face's plane.  ok: the projected triangle is not edge-on; minb: the
+// smallest of the three barycentrics (>= 0 inside the triangle).
 template <class S>
-static bool eval_fragment(const S X[4][3], const S F[4], double px, double py,
-                          double fx, double fy, double cx, double cy,
-                          FragOut<S>* out) {
+struct FaceEval {
+  bool ok;
+  double minb;
+  S z, f;
+};
+
+static const int kFaces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+template <class S>
+static void eval_faces(const S X[4][3], const S F[4], double px, double py, double fx, double fy,
+                       double cx, double cy, FaceEval<S> out[4]) {
   S u[4], v[4];
   for (int j = 0; j < 4; ++j) {
     u[j] = fx * (X[j][0] / X[j][2]) + cx;
     v[j] = fy * (X[j][1] / X[j][2]) + cy;
   }
-  static const int faces[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
-  int nhit = 0;
-  S hz[4], hf[4];
   for (int k = 0; k < 4; ++k) {
-    const int a = faces[k][0], b = faces[k][1], c = faces[k][2];
+    const int a = kFaces[k][0], b = kFaces[k][1], c = kFaces[k][2];
+    out[k].ok = false;
     // [v_a' v_b' v_c'; 1 1 1] [1-u'-v', u', v']^T = [p; 1]  (App. A.1), Cramer
     S ub = u[b] - u[a], vb = v[b] - v[a], uc = u[c] - u[a], vc = v[c] - v[a];
     S det = ub * vc - uc * vb;
@@ -111,30 +123,68 @@ static bool eval_fragment(const S X[4][3], const S F[4], double px, double py,
     S bu = (qx * vc - uc * qy) / det;   // u'
     S bv = (ub * qy - qx * vb) / det;   // v'
     S b0 = 1.0 - bu - bv;               // 1 - u' - v'
-    const double tol = -1e-12;
-    if (val(b0) < tol || val(bu) < tol || val(bv) < tol) continue;
     // App. A.2: perspective-correct barycentrics and the interpolated SDF/depth
     S sig = b0 / X[a][2] + bu / X[b][2] + bv / X[c][2];
     S uu = (bu / X[b][2]) / sig;
     S vv = (bv / X[c][2]) / sig;
-    S fp = (1.0 - uu - vv) * F[a] + uu * F[b] + vv * F[c];
-    S zp = 1.0 / sig;
-    hz[nhit] = zp;
-    hf[nhit] = fp;
+    out[k].f = (1.0 - uu - vv) * F[a] + uu * F[b] + vv * F[c];
+    out[k].z = 1.0 / sig;
+    out[k].minb = std::min(val(b0), std::min(val(bu), val(bv)));
+    out[k].ok = true;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one fragment: ray through pixel centre (px, py) against tet with camera-space
+// vertices X[4][3] and vertex SDF F[4].  The faces the ray hits (closed inside
+// test); the nearest hit gives f_prev, the farthest f_next.  Returns false
+// when the ray meets the tet in fewer than two distinct points.
+// ---------------------------------------------------------------------------
+template <class S>
+static bool eval_fragment(const S X[4][3], const S F[4], double px, double py,
+                          double fx, double fy, double cx, double cy,
+                          FragOut<S>* out) {
+  FaceEval<S> fe[4];
+  eval_faces<S>(X, F, px, py, fx, fy, cx, cy, fe);
+  const double tol = -1e-12;
+  int imin = -1, imax = -1, nhit = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (!fe[k].ok || fe[k].minb < tol) continue;
     ++nhit;
+    if (imin < 0 || val(fe[k].z) < val(fe[imin].z)) imin = k;
+    if (imax < 0 || val(fe[k].z) > val(fe[imax].z)) imax = k;
   }
   if (nhit < 2) return false;
-  int imin = 0, imax = 0;
-  for (int h = 1; h < nhit; ++h) {
-    if (val(hz[h]) < val(hz[imin])) imin = h;
-    if (val(hz[h]) > val(hz[imax])) imax = h;
-  }
-  if (!(val(hz[imax]) - val(hz[imin]) > 1e-12 * val(hz[imax]))) return false;
-  out->f_prev = hf[imin];
-  out->f_next = hf[imax];
-  out->z_in = hz[imin];
-  out->z_out = hz[imax];
+  if (!(val(fe[imax].z) - val(fe[imin].z) > 1e-12 * val(fe[imax].z))) return false;
+  out->f_prev = fe[imin].f;
+  out->f_next = fe[imax].f;
+  out->z_in = fe[imin].z;
+  out->z_out = fe[imax].z;
+  out->k_in = imin;
+  out->k_out = imax;
   return true;
+}
+
+// Faces other than the chosen entry (exit) face whose plane the ray meets
+// within rel_z of the entry (exit) depth, at a point within rel_b of their
+// triangle: the ray passes that close to the edge they share with the chosen
+// face, where the chord's entry (exit) point has a kink (its derivative with
+// respect to the vertex positions depends on the face).  A computation in
+// another precision may take either face.  Returns the candidates for the
+// entry in alt_in[0..n_in) and for the exit in alt_out[0..n_out).
+template <class S>
+static void near_kink_faces(const S X[4][3], const S F[4], double px, double py, double fx,
+                            double fy, double cx, double cy, const FragOut<S>& o, double rel_z,
+                            double rel_b, int alt_in[4], int* n_in, int alt_out[4], int* n_out) {
+  FaceEval<S> fe[4];
+  eval_faces<S>(X, F, px, py, fx, fy, cx, cy, fe);
+  *n_in = *n_out = 0;
+  for (int k = 0; k < 4; ++k) {
+    if (!fe[k].ok || fe[k].minb < -rel_b) continue;
+    const double z = val(fe[k].z);
+    if (k != o.k_in && std::fabs(z - val(o.z_in)) <= rel_z * val(o.z_in)) alt_in[(*n_in)++] = k;
+    if (k != o.k_out && std::fabs(z - val(o.z_out)) <= rel_z * val(o.z_out)) alt_out[(*n_out)++] = k;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -379,7 +429,8 @@ struct PixelResult {
 };
 
 // Walk the fragment list.  Decision indices count every threshold test in
-// evaluation order; flip = index of the decision to invert (-1: none).
+// the order a walk meets them (none past the stop); flip = index of the
+// decision to invert (-1: none).
 // Resort window (Sec. 3.3): fragments that pass the cap and skip tests enter
 // a window kept sorted by the entry depth z_in (ties: earlier first); when it
 // holds more than N_w fragments the nearest one leaves it and is blended; at
@@ -389,7 +440,25 @@ struct Staged {
   Frag f;
   double a;
   bool clamped;
+  bool cap_exact;   // clamped by an unambiguous cap decision: alpha' is the FP32 cap exactly
 };
+
+// The stop test of a fragment whose alpha' is the cap, after blended
+// fragments that all were (n_capped of them): T (1 - alpha') is then a product
+// of FP32 factors (1 - cap) and 1, which the kernel forms in FP32 (3DGS
+// evaluates this test in FP32 too).  For up to three factors every order of
+// the products rounds to the same FP32 value, so the decision is taken here
+// in FP32 exactly, as the kernel takes it, and is not ambiguous.  With the
+// 3DGS constants two capped fragments land on the threshold in real
+// arithmetic: (1 - 0.99)^2 = 1e-4.
+// Applies when cap and t_eps are FP32 values (the thresholds a kernel call
+// receives); with other values the FP64 decision and its band stand.
+static bool fp32_thresholds(const OrcParams& p) {
+  return (double)(float)p.alpha_cap == p.alpha_cap && (double)(float)p.t_eps == p.t_eps;
+}
+static bool capped_stop_exact(int n_capped, const Staged& st, const OrcParams& p) {
+  return st.cap_exact && n_capped >= 0 && n_capped <= 2 && fp32_thresholds(p);
+}
 
 static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip, bool record,
                       PixelResult* r) {
@@ -407,57 +476,82 @@ static void composite(const std::vector<Frag>& fr, const OrcParams& p, int flip,
     }
     return (id == flip) ? !outcome : outcome;
   };
-  // cap and skip in list order, then the window's emission order
-  std::vector<Staged> in;
-  for (const Frag& f : fr) {
-    double a = f.alpha;
-    bool clamped = false;
-    if (!pure) {
-      if (decide(a > p.alpha_cap, a, p.alpha_cap)) { a = p.alpha_cap; clamped = true; }
-      if (decide(a < p.alpha_skip, a, p.alpha_skip)) continue;
-    } else if (!(a > 0.0)) {
-      continue;
-    }
-    in.push_back({f, a, clamped});
-  }
-  std::vector<Staged> order;
-  if (p.window == 0) {
-    order = in;
-  } else {
-    const size_t cap = (p.window < 0) ? in.size() + 1 : (size_t)p.window;
-    std::vector<Staged> win;
-    auto near_tie = [&](double x, double y) {
-      return std::fabs(x - y) <= 1e-5 * std::max(std::fabs(x), std::fabs(y));
-    };
-    for (const Staged& st : in) {
-      size_t pos = 0;
-      while (pos < win.size() && win[pos].f.zin <= st.f.zin) ++pos;
-      for (const Staged& w : win)
-        if (near_tie(w.f.zin, st.f.zin)) r->amb += 2;  // order not decidable in FP32
-      win.insert(win.begin() + pos, st);
-      if (win.size() > cap) {
-        order.push_back(win.front());
-        win.erase(win.begin());
-      }
-    }
-    for (const Staged& w : win) order.push_back(w);
-  }
-  for (const Staged& st : order) {
+  float T32 = 1.0f;   // T as the kernel holds it, while n_capped >= 0
+  int n_capped = 0;   // blended fragments so far, all exactly at the cap (-1: not so)
+  // Blends one fragment (Eq. 2) unless the stop test ends the pixel first;
+  // returns true when the pixel stops.
+  auto emit = [&](const Staged& st) {
     const Frag& f = st.f;
     const double a = st.a;
-    const bool clamped = st.clamped;
-    double Tn = T * (1.0 - a);
+    const double Tn = T * (1.0 - a);
     if (!pure) {
-      if (decide(Tn < p.t_eps, Tn, p.t_eps)) break;
+      if (capped_stop_exact(n_capped, st, p)) {
+        const float Tn32 = T32 * (1.0f - (float)p.alpha_cap);
+        const int id = dec++;
+        const bool stop = Tn32 < (float)p.t_eps;
+        if ((id == flip) ? !stop : stop) return true;
+      } else if (decide(Tn < p.t_eps, Tn, p.t_eps)) {
+        return true;
+      }
+    }
+    if (st.cap_exact && n_capped >= 0) {
+      T32 = T32 * (1.0f - (float)p.alpha_cap);
+      ++n_capped;
+    } else {
+      n_capped = -1;
     }
     for (int q = 0; q < 3; ++q) C[q] += T * a * f.c[q];
     for (int q = 0; q < 3; ++q) Nn[q] += T * a * f.n[q];
     D += T * a * f.zbar;
     if (record)
       r->blended.push_back({f.s, a, T, f.zbar, {f.c[0], f.c[1], f.c[2]}, {f.n[0], f.n[1], f.n[2]},
-                            clamped});
+                            st.clamped});
     T = Tn;
+    return false;
+  };
+  auto near_tie = [&](double x, double y) {
+    return std::fabs(x - y) <= 1e-5 * std::max(std::fabs(x), std::fabs(y));
+  };
+  // One pass in list order, as a walk that stops meets the fragments: the cap
+  // and skip decisions of each fragment, its way through the window (if any)
+  // and the stop test of each fragment leaving it.  Decisions past the stop
+  // are never taken.
+  const size_t wcap = (p.window < 0) ? fr.size() + 1 : (size_t)p.window;
+  std::vector<Staged> win;
+  bool stopped = false;
+  for (const Frag& f : fr) {
+    double a = f.alpha;
+    bool clamped = false, cap_exact = false;
+    if (!pure) {
+      const int amb0 = r->amb;
+      if (decide(a > p.alpha_cap, a, p.alpha_cap)) {
+        a = p.alpha_cap;
+        clamped = true;
+        cap_exact = r->amb == amb0;
+      }
+      if (decide(a < p.alpha_skip, a, p.alpha_skip)) continue;
+    } else if (!(a > 0.0)) {
+      continue;
+    }
+    const Staged st = {f, a, clamped, cap_exact};
+    if (p.window == 0) {
+      if (emit(st)) { stopped = true; break; }
+      continue;
+    }
+    size_t pos = 0;
+    while (pos < win.size() && win[pos].f.zin <= st.f.zin) ++pos;
+    for (const Staged& w : win)
+      if (near_tie(w.f.zin, st.f.zin)) r->amb += 2;  // order not decidable in FP32
+    win.insert(win.begin() + pos, st);
+    if (win.size() > wcap) {
+      const Staged w = win.front();
+      win.erase(win.begin());
+      if (emit(w)) { stopped = true; break; }
+    }
   }
+  if (!stopped)
+    for (const Staged& w : win)
+      if (emit(w)) break;
   for (int q = 0; q < 3; ++q) r->C[q] = C[q];
   for (int q = 0; q < 3; ++q) r->N[q] = Nn[q];
   r->D = D;
@@ -479,6 +573,22 @@ extern "C" {
 // When dimg != nullptr, also accumulates the gradient of
 //   L = sum(dimg * img) + sum(dalpha * alpha) + sum(ddepth * depth)
 // into dV (3N), df (N), drgb (3N) (FP64, added to what is there).
+// branch (HW, nullable): 1 differentiates the pixel's alternative branch (its
+// first ambiguous decision inverted) instead of the primary one.
+// dV_abs, df_abs, drgb_abs (nullable): the sums of the absolute values of the
+// per-fragment terms added into each gradient entry (the scale of the
+// rounding a sum of those terms in another order can show).
+// dV_kink, df_kink (nullable): per entry, the sum over fragments whose ray
+// passes within 1e-4 (relative depth) of an edge of its entry or exit face of
+// the largest change of that fragment's term when another face nearly as
+// near gives the entry or exit point (the other one-sided derivative at the
+// chord's kink, which a computation in another precision may take).
+// dV_graze (nullable): per entry, the sum over fragments of |the fragment's
+// term through its opacity| / c^2, c the smaller of |cos| of the angles
+// between the pixel ray and the normals of the chord's entry and exit faces
+// (a face seen at grazing incidence makes the entry or exit point, and most
+// of all its derivative, ill-conditioned: the relative rounding error of the
+// term in a precision with unit roundoff u grows as about u / c^2).
 // ---------------------------------------------------------------------------
 int orc_render(int64_t N, const float* V, const float* f, const float* rgb, const int32_t* T,
                int64_t ns, const int32_t* surv, const int32_t* rect, const OrcCam* cam,
@@ -488,7 +598,9 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
                const float* dimg, const float* dalpha, const float* ddepth,
                double* dV, double* df, double* drgb, int nthreads,
                const double* V64, const double* f64, const double* rgb64,
-               double* nrm, double* alt_nrm, const float* dnrm) {
+               double* nrm, double* alt_nrm, const float* dnrm, const int8_t* branch,
+               double* dV_abs, double* df_abs, double* drgb_abs, double* dV_kink,
+               double* df_kink, double* dV_graze) {
   const OrcCam& c = *cam;
   const Fields fld(N, V, f, rgb, V64, f64, rgb64);
   const int W = c.width, H = c.height, B = p->tile;
@@ -545,8 +657,9 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
       depth[pix] = pr.D;
       amb[pix] = pr.amb;
       nfrag[pix] = hits;
+      const bool use_alt = want_grad && branch && branch[(int64_t)j * W + i] && pr.first_amb >= 0;
       if (pr.first_amb >= 0) {
-        composite(fr, *p, pr.first_amb, false, &alt);
+        composite(fr, *p, pr.first_amb, use_alt, &alt);
         for (int q = 0; q < 3; ++q) alt_img[q * HW + pix] = alt.C[q];
         if (alt_nrm)
           for (int q = 0; q < 3; ++q) alt_nrm[q * HW + pix] = alt.N[q];
@@ -559,16 +672,17 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
         alt_alpha[pix] = pr.O;
         alt_depth[pix] = pr.D;
       }
-      if (!want_grad || pr.blended.empty()) continue;
-      // ---- adjoint of the composite (primary branch) ----
+      // ---- adjoint of the composite (the primary branch, or the alternative) ----
+      const PixelResult& ad = use_alt ? alt : pr;
+      if (!want_grad || ad.blended.empty()) continue;
       const double gC[3] = {dimg[pix], dimg[HW + pix], dimg[2 * HW + pix]};
       const double gO = dalpha[pix], gD = ddepth[pix];
       const double gN[3] = {dnrm ? (double)dnrm[pix] : 0.0, dnrm ? (double)dnrm[HW + pix] : 0.0,
                             dnrm ? (double)dnrm[2 * HW + pix] : 0.0};
-      const double Tfin = 1.0 - pr.O;
+      const double Tfin = 1.0 - ad.O;
       double Ssuf = 0.0;
-      for (int b = (int)pr.blended.size() - 1; b >= 0; --b) {
-        const Blended& bl = pr.blended[b];
+      for (int b = (int)ad.blended.size() - 1; b >= 0; --b) {
+        const Blended& bl = ad.blended[b];
         const double w = gC[0] * bl.c[0] + gC[1] * bl.c[1] + gC[2] * bl.c[2] + gD * bl.zbar +
                          gN[0] * bl.n[0] + gN[1] * bl.n[1] + gN[2] * bl.n[2];
         const double dLda = bl.T * w - (Ssuf - gO * Tfin) / (1.0 - bl.a);
@@ -579,6 +693,10 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
           for (int ch = 0; ch < 3; ++ch) {
 #pragma omp atomic
             drgb[3 * (size_t)t[q] + ch] += 0.25 * bl.T * bl.a * gC[ch];
+            if (drgb_abs) {
+#pragma omp atomic
+              drgb_abs[3 * (size_t)t[q] + ch] += std::fabs(0.25 * bl.T * bl.a * gC[ch]);
+            }
           }
         // depth term: zbar = mean camera z -> world via R^T (third row)
         double dX[4][3] = {{0}};
@@ -601,6 +719,65 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
             for (int q = 0; q < 4; ++q) {
               for (int r = 0; r < 3; ++r) dX[q][r] += dLda * a.d[3 * q + r];
               dF[q] += dLda * a.d[12 + q];
+            }
+            if (dV_graze) {
+              // grazing cosines of the entry and exit faces for this ray
+              const double ray[3] = {(px - c.cx) / c.fx, (py - c.cy) / c.fy, 1.0};
+              const double rl = std::sqrt(ray[0] * ray[0] + ray[1] * ray[1] + 1.0);
+              double cmin = 1.0;
+              for (const int k : {o.k_in, o.k_out}) {
+                const int ia = kFaces[k][0], ib = kFaces[k][1], ic = kFaces[k][2];
+                double e1[3], e2[3];
+                for (int r = 0; r < 3; ++r) {
+                  e1[r] = val(X[ib][r]) - val(X[ia][r]);
+                  e2[r] = val(X[ic][r]) - val(X[ia][r]);
+                }
+                const double nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2],
+                             nz = e1[0] * e2[1] - e1[1] * e2[0];
+                const double nl = std::sqrt(nx * nx + ny * ny + nz * nz);
+                if (nl > 0.0)
+                  cmin = std::min(cmin, std::fabs(nx * ray[0] + ny * ray[1] + nz * ray[2]) / (nl * rl));
+              }
+              const double wgt = 1.0 / std::max(cmin * cmin, 1e-12);
+              for (int q = 0; q < 4; ++q)
+                for (int r = 0; r < 3; ++r) {
+                  double g = 0.0;
+                  for (int k = 0; k < 3; ++k) g += std::fabs(c.R[3 * k + r]) * std::fabs(dLda * a.d[3 * q + k]);
+#pragma omp atomic
+                  dV_graze[3 * (size_t)t[q] + r] += wgt * g;
+                }
+            }
+            if (dV_kink && df_kink) {
+              int ai[4], ao[4], ni = 0, no = 0;
+              near_kink_faces<D16>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, o, 1e-4, 1e-4, ai, &ni,
+                                   ao, &no);
+              if (ni + no > 0) {
+                FaceEval<D16> fe[4];
+                eval_faces<D16>(X, F, px, py, c.fx, c.fy, c.cx, c.cy, fe);
+                int cin[5] = {o.k_in}, cout_[5] = {o.k_out};
+                for (int k = 0; k < ni; ++k) cin[k + 1] = ai[k];
+                for (int k = 0; k < no; ++k) cout_[k + 1] = ao[k];
+                double dmax[16] = {0};
+                for (int x = 0; x <= ni; ++x)
+                  for (int y = 0; y <= no; ++y) {
+                    if ((x == 0 && y == 0) || cin[x] == cout_[y]) continue;
+                    const D16 a2 = opacity_eq1<D16>(fe[cin[x]].f, fe[cout_[y]].f, p->s);
+                    for (int k = 0; k < 16; ++k)
+                      dmax[k] = std::max(dmax[k], std::fabs(dLda * (a2.d[k] - a.d[k])));
+                  }
+                for (int q = 0; q < 4; ++q) {
+                  for (int r = 0; r < 3; ++r) {
+                    // |R^T d| <= sum_k |R_kr| |d_k| per world component
+                    const double b = std::fabs(c.R[r]) * dmax[3 * q] +
+                                     std::fabs(c.R[3 + r]) * dmax[3 * q + 1] +
+                                     std::fabs(c.R[6 + r]) * dmax[3 * q + 2];
+#pragma omp atomic
+                    dV_kink[3 * (size_t)t[q] + r] += b;
+                  }
+#pragma omp atomic
+                  df_kink[t[q]] += dmax[12 + q];
+                }
+              }
             }
           }
         }
@@ -632,9 +809,17 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
             double g = c.R[r] * dX[q][0] + c.R[3 + r] * dX[q][1] + c.R[6 + r] * dX[q][2];
 #pragma omp atomic
             dV[3 * (size_t)t[q] + r] += g;
+            if (dV_abs) {
+#pragma omp atomic
+              dV_abs[3 * (size_t)t[q] + r] += std::fabs(g);
+            }
           }
 #pragma omp atomic
           df[t[q]] += dF[q];
+          if (df_abs) {
+#pragma omp atomic
+            df_abs[t[q]] += std::fabs(dF[q]);
+          }
         }
       }
     }
@@ -724,9 +909,26 @@ int orc_render_dirderiv(int64_t N, const float* V, const float* f, const float* 
         }
         for (const FD& w : win) order.push_back(w);
       }
+      float T32 = 1.0f;
+      int n_capped = 0;
       for (const FD& fd : order) {
         D1 Tn = Tr * (1.0 - fd.a);
-        if (!pure && Tn.v < p->t_eps) break;
+        if (!pure) {
+          // the stop test as in composite(): exact in FP32 after capped fragments
+          const bool capped = fd.a.v == p->alpha_cap;
+          if (capped && n_capped >= 0 && n_capped <= 2 && fp32_thresholds(*p)) {
+            const float Tn32 = T32 * (1.0f - (float)p->alpha_cap);
+            if (Tn32 < (float)p->t_eps) break;
+          } else if (Tn.v < p->t_eps) {
+            break;
+          }
+          if (capped && n_capped >= 0) {
+            T32 = T32 * (1.0f - (float)p->alpha_cap);
+            ++n_capped;
+          } else {
+            n_capped = -1;
+          }
+        }
         for (int q = 0; q < 3; ++q) C[q] = C[q] + Tr * fd.a * fd.cc[q];
         for (int q = 0; q < 3; ++q) Nn[q] = Nn[q] + Tr * fd.a * fd.nn[q];
         Dp = Dp + Tr * fd.a * fd.zb;

@@ -66,3 +66,56 @@ def test_even_width_derivatives_agree(width):
     res = _dual_vs_fd(width)
     assert res and not any(on_axis for on_axis, _ in res)
     assert max(err for _, err in res) < 1e-4
+
+
+def _kink_allowance(width):
+    """(adjoint dL/dV[VERT, 0], its kink allowance, central FD) per covered
+    pixel, L = alpha at that pixel."""
+    sph = synth.scene_sphere16()
+    p = Params(s=60.0, tile=8)
+    op = oracle_params(p)
+    V0 = sph.V.astype(np.float64)
+    T = sph.T[[TET]]
+    surv, _, _ = oracle.prefilter(T, sph.f, op)
+    rng = np.random.default_rng(11)
+    synth.random_camera(rng, 40, 36)
+    cam = synth.random_camera(rng, width, 38)
+    H, W = 38, width
+    bins = oracle.bin_view(surv, T, V0, cam, p.tile)
+    r0 = oracle.render(V0, T, sph.f, sph.rgb, cam, op, surv=surv, bins=bins)
+    h = 1e-6
+    Vp, Vm = V0.copy(), V0.copy()
+    Vp[VERT, 0] += h
+    Vm[VERT, 0] -= h
+    rp = oracle.render(Vp, T, sph.f, sph.rgb, cam, op, surv=surv,
+                       bins=oracle.bin_view(surv, T, Vp, cam, p.tile))
+    rm = oracle.render(Vm, T, sph.f, sph.rgb, cam, op, surv=surv,
+                       bins=oracle.bin_view(surv, T, Vm, cam, p.tile))
+    out = []
+    for y, x in zip(*np.nonzero(r0["alpha"] > 0)):
+        ga = np.zeros((H, W), np.float32)
+        ga[y, x] = 1
+        u = (np.zeros((3, H, W), np.float32), ga, np.zeros((H, W), np.float32))
+        r = oracle.render(V0, T, sph.f, sph.rgb, cam, op, surv=surv, bins=bins, upstream=u,
+                          abs_terms=True)
+        fd = (rp["alpha"][y, x] - rm["alpha"][y, x]) / (2 * h)
+        out.append((r["dV"][VERT, 0], r["dV_kink"][VERT, 0], fd))
+    return out
+
+
+@pytest.mark.parametrize("width", [43, 45])
+def test_kink_allowance_covers_the_other_one_sided_derivative(width):
+    """On the kink the adjoint takes one face's derivative and finite
+    differences their mean: the oracle's kink allowance (the change under
+    the other face) is nonzero there and the gap is half of it."""
+    res = _kink_allowance(width)
+    assert res
+    for adj, kink, fd in res:
+        assert kink > 0
+        assert 0.49 * kink <= abs(adj - fd) <= 0.51 * kink
+
+
+@pytest.mark.parametrize("width", [42, 44])
+def test_no_kink_allowance_away_from_edges(width):
+    res = _kink_allowance(width)
+    assert res and all(kink == 0.0 for _, kink, _ in res)

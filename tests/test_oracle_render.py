@@ -177,6 +177,45 @@ def test_large_s_limit_matches_level_set():
     assert n_in > 100 and n_out > 100
 
 
+def test_capped_stop_tie_is_decided_in_fp32():
+    """With the 3DGS constants two fragments at the cap leave T = (1 - 0.99)^2,
+    which equals t_eps = 1e-4 in real arithmetic.  With the FP32 thresholds a
+    kernel receives, the oracle takes that stop decision exactly as FP32 does:
+    1 - 0.99f = 0.0099999905 (exact), its square rounds to 9.99998e-5 <
+    1e-4f, so a ray whose first two fragments are capped stops before the
+    second (alpha = 0.99f exactly) and the decision is not ambiguous.  With
+    the FP64 constants 0.99 and 1e-4 the square is 1.0000000000000018e-4 >=
+    1e-4: the FP64 decision blends the second fragment and stays a band
+    decision."""
+    cap32, eps32 = float(np.float32(0.99)), float(np.float32(1e-4))
+    x = np.float32(1.0) - np.float32(cap32)
+    assert float(x) == 1.0 - cap32                       # Sterbenz: exact
+    assert np.float32(x * x) < np.float32(eps32)         # FP32: stop
+    assert (1.0 - 0.99) ** 2 >= 1e-4                     # FP64 constants: blend
+    V, T, f, rgb = small_grid(16, lambda X: np.linalg.norm(X, axis=1) - 0.5)
+    cam = synth.orbit_camera(30.0, 20.0, 64, 64)
+    R, t, C0, Ri = cam_world(cam)
+    p32 = oracle.make_params(s=3000.0, tile=16, alpha_cap=cap32, t_eps=eps32,
+                             alpha_skip=float(np.float32(1 / 255)),
+                             prefilter_thresh=float(np.float32(1 / 255)))
+    p64 = oracle.make_params(s=3000.0, tile=16)
+    r32 = oracle.render(V, T, f, rgb, cam, p32)
+    r64 = oracle.render(V, T, f, rgb, cam, p64)
+    # rays stopped before their second fragment, the first one at the cap
+    stopped = r32["alpha"] == cap32
+    assert stopped.sum() > 100
+    assert np.all(r32["amb"][stopped] == 0)
+    # with the FP64 constants nearly all of them blend that second fragment,
+    # as a band decision
+    blended = (r64["alpha"][stopped] > 0.99) & (r64["amb"][stopped] > 0)
+    assert blended.mean() > 0.95
+    # they are the rays through the sphere's interior
+    for j, i in zip(*np.nonzero(stopped)):
+        dw = Ri @ ray_dir(cam, i, j)
+        dw /= np.linalg.norm(dw)
+        assert np.linalg.norm(C0 - (C0 @ dw) * dw) < 0.52
+
+
 # ---------------------------------------------------------------------------
 # invariants
 # ---------------------------------------------------------------------------
