@@ -5,8 +5,8 @@ requires the built libtets.so."""
 
 from . import camera  # noqa: F401
 from ._lib import TetsError, load  # noqa: F401
-from .rasterizer import (Params, Rasterizer, SceneTensors, TetRender, fit_grid,  # noqa: F401
-                         make_camera, render)
+from .rasterizer import (Params, Rasterizer, SceneTensors, TetRender, TetRenderBatch,  # noqa: F401
+                         fit_grid, make_camera, render)
 
-__all__ = ["Params", "Rasterizer", "SceneTensors", "TetRender", "render", "make_camera", "load",
-           "TetsError", "camera", "fit_grid"]
+__all__ = ["Params", "Rasterizer", "SceneTensors", "TetRender", "TetRenderBatch", "render",
+           "make_camera", "load", "TetsError", "camera", "fit_grid"]

@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import math
+import weakref
 from typing import Sequence
 
 import torch
@@ -117,6 +118,11 @@ class Rasterizer:
         byte count, instead of allocating one."""
         self.lib = _lib.load()
         self._ext_ws = workspace
+        # forwards enqueued on this workspace so far: a backward uses the
+        # state of the latest one (TetRender checks it has not moved on)
+        self.generation = 0
+        # a TetRender output of this rasterizer still awaits its backward
+        self.awaiting_backward = False
         self.params = params
         self.device = torch.device(device) if device is not None else scenes[0].V.device
         self.views = [(c, int(s)) for c, s in views]
@@ -187,6 +193,32 @@ class Rasterizer:
         b = self.batch()
         check(self.lib.tts_workspace_init(ctypes.byref(b), _stream_ptr()), "tts_workspace_init")
 
+    def rebind(self, scenes: Sequence[SceneTensors] | None = None, cams: Sequence | None = None):
+        """Points the batch at other scenes (each with the N and K of the one
+        it replaces) and other cameras (the same image sizes): the workspace
+        layout is unchanged, so nothing is reallocated."""
+        if scenes is not None:
+            old = [(int(s.V.shape[0]), int(s.T.shape[0])) for s in self.scenes]
+            new = [(int(s.V.shape[0]), int(s.T.shape[0])) for s in scenes]
+            if old != new:
+                raise TetsError("rebind: the scenes must keep their vertex and tet counts")
+            self.set_scenes(scenes)
+        if cams is not None:
+            if len(cams) != len(self.views):
+                raise TetsError("rebind: one camera per view")
+            for i, c in enumerate(cams):
+                w, h = int(c.width), int(c.height)
+                if (w, h) != (int(self.views[i][0].width), int(self.views[i][0].height)):
+                    raise TetsError("rebind: the views must keep their image sizes")
+                self._c_views[i].cam = make_camera(c)
+            self.views = [(c, s) for c, (_, s) in zip(cams, self.views)]
+
+    def reinit(self):
+        """Clears the workspace's persistent state (status word, gradient
+        accumulators), as after allocation."""
+        b = self.batch()
+        check(self.lib.tts_workspace_init(ctypes.byref(b), _stream_ptr()), "tts_workspace_init")
+
     # -- calls ------------------------------------------------------------
     def prepare(self):
         b = self.batch()
@@ -234,6 +266,7 @@ class Rasterizer:
         out = tuple(out) if out is not None else self._outputs()
         b = self.batch()
         o = self._c_outputs(out)
+        self.generation += 1
         check(self.lib.tts_render_fwd_ex(ctypes.byref(b), ctypes.byref(o), _stream_ptr()),
               "tts_render_fwd_ex")
         return out
@@ -309,6 +342,7 @@ class Rasterizer:
         o = self._c_outputs(out)
         u = self._c_upstream(upstream)
         check(L.tts_prepare_scene(ctypes.byref(b), sp), "tts_prepare_scene")
+        self.generation += 1
         check(L.tts_render_fwd_ex(ctypes.byref(b), ctypes.byref(o), sp), "tts_render_fwd_ex")
         check(L.tts_render_bwd_ex(ctypes.byref(b), ctypes.byref(u), dV, df, dc, sp),
               "tts_render_bwd_ex")
@@ -364,6 +398,19 @@ class Rasterizer:
         return dict(keys=keys, vals=vals, ranges=ranges, surv=surv, zmin_bits=int(zmin.value),
                     depth_bits=int(db.value), n_keys=n, info=info)
 
+    def debug_pixels(self):
+        """Per-pixel state of the last forward (flat, view-major like alpha):
+        final transmittance (float32), list entries walked up to the last
+        blended one and fragments met (int32)."""
+        P = ctypes.c_void_p
+        t, last, nf = P(), P(), P()
+        b = self.batch()
+        check(self.lib.tts_debug_pixels(ctypes.byref(b), ctypes.byref(t), ctypes.byref(last),
+                                        ctypes.byref(nf), _stream_ptr()), "tts_debug_pixels")
+        n = 4 * self.total_pixels
+        return (self._ws_slice(t.value, n, torch.float32), self._ws_slice(last.value, n, torch.int32),
+                self._ws_slice(nf.value, n, torch.int32))
+
     def view_outputs(self, img, alpha, depth, normal=None):
         """Split flat outputs into per-view (3,H,W), (H,W), (H,W) tensors
         (and a (3,H,W) normal map when given)."""
@@ -393,47 +440,138 @@ def fit_grid(V: torch.Tensor, grid_lo, grid_hi, aabb: torch.Tensor, pad: float =
     return out
 
 
+def _check_autograd_params(raster: Rasterizer):
+    if raster.params.accum_grad or raster.params.forward_only:
+        raise TetsError("TetRender needs a rasterizer without accum_grad and forward_only")
+
+
+def _mark_pending(raster: Rasterizer, outputs, ctx) -> None:
+    """Records that a backward through these outputs may follow; the mark is
+    dropped by that backward or once the outputs are freed."""
+    if not any(ctx.needs_input_grad):
+        return
+    raster.awaiting_backward = True
+    gen = raster.generation
+
+    def release(r=raster, g=gen):
+        if r.generation == g:
+            r.awaiting_backward = False
+    weakref.finalize(outputs[0], release)
+
+
+def _stale(raster: Rasterizer, gen: int):
+    if raster.generation != gen:
+        raise TetsError(
+            "backward of a TetRender output after another forward ran on the same rasterizer: "
+            "the workspace holds the later forward's lists and per-pixel state.  Call backward "
+            "before the next forward on that rasterizer, or render with separate rasterizers "
+            "(render() keeps one per output that awaits its backward).")
+
+
 class TetRender(torch.autograd.Function):
     """(V, f, rgb) -> (image, alpha, depth[, normal]) for the views of a
     single-scene ``Rasterizer``; outputs are flat view-major planar tensors
-    (the normal map when the rasterizer's params ask for it)."""
+    (the normal map when the rasterizer's params ask for it).
+
+    The backward re-walks the tile lists of the forward, which live in the
+    rasterizer's workspace: it raises if another forward ran on that
+    rasterizer in between (per-pixel transmittance is recomputed in the
+    backward, never stored per fragment)."""
 
     @staticmethod
     def forward(ctx, V, f, rgb, raster: Rasterizer, check_status: bool = True):
+        _check_autograd_params(raster)
         sc = raster.scenes[0]
         if V.data_ptr() != sc.V.data_ptr() or f.data_ptr() != sc.f.data_ptr() or \
                 rgb.data_ptr() != sc.rgb.data_ptr():
             raster.set_scenes([SceneTensors(V.detach(), sc.T, f.detach(), rgb.detach())])
         out = raster.forward(prepare=True, check_status=check_status)
         ctx.raster = raster
+        ctx.gen = raster.generation
+        _mark_pending(raster, out, ctx)
         return tuple(out)
 
     @staticmethod
     def backward(ctx, gimg, galpha, gdepth, gnormal=None):
         raster = ctx.raster
+        _stale(raster, ctx.gen)
         gimg = gimg if gimg is not None else torch.zeros(3 * raster.total_pixels, device=raster.device)
         (dV, df, drgb), = raster.backward(gimg, galpha, gdepth, dnormal=gnormal)
+        raster.awaiting_backward = False
         return dV, df, drgb, None, None
 
 
-_cache: dict = {}
+class TetRenderBatch(torch.autograd.Function):
+    """The batched form: ``raster`` over any number of scenes (and views of
+    them), inputs ``V_0, f_0, rgb_0, V_1, f_1, rgb_1, ...`` in scene order;
+    outputs as ``TetRender`` (flat over all views of the batch)."""
+
+    @staticmethod
+    def forward(ctx, raster: Rasterizer, check_status: bool, *vfr):
+        _check_autograd_params(raster)
+        n = len(raster.scenes)
+        if len(vfr) != 3 * n:
+            raise TetsError(f"expected 3 tensors per scene ({3 * n}), got {len(vfr)}")
+        scenes = []
+        for i, sc in enumerate(raster.scenes):
+            V, f, rgb = vfr[3 * i:3 * i + 3]
+            scenes.append(SceneTensors(V.detach(), sc.T, f.detach(), rgb.detach()))
+        raster.set_scenes(scenes)
+        out = raster.forward(prepare=True, check_status=check_status)
+        ctx.raster = raster
+        ctx.gen = raster.generation
+        _mark_pending(raster, out, ctx)
+        return tuple(out)
+
+    @staticmethod
+    def backward(ctx, gimg, galpha, gdepth, gnormal=None):
+        raster = ctx.raster
+        _stale(raster, ctx.gen)
+        gimg = gimg if gimg is not None else torch.zeros(3 * raster.total_pixels, device=raster.device)
+        grads = raster.backward(gimg, galpha, gdepth, dnormal=gnormal)
+        raster.awaiting_backward = False
+        flat = [g for trio in grads for g in trio]
+        return (None, None, *flat)
+
+
+# render(): rasterizers per batch shape, at most _POOL_MAX per shape; one
+# whose output still awaits its backward is not handed out again while
+# another can be (a reused one makes that pending backward raise).
+_POOL_MAX = 4
+_pools: dict = {}
+
+
+def _pooled(key, make):
+    pool = _pools.setdefault(key, [])
+    for r in pool:
+        if not r.awaiting_backward:
+            pool.remove(r)
+            pool.append(r)      # most recently used last
+            return r
+    if len(pool) < _POOL_MAX:
+        r = make()
+        pool.append(r)
+        return r
+    r = pool.pop(0)             # all busy: the least recently used
+    pool.append(r)
+    return r
 
 
 def render(V, T, f, rgb, cams, params: Params | None = None, check_status: bool = True):
     """Renders the views ``cams`` of one scene and returns a list of
     (image (3,H,W), alpha (H,W), depth (H,W)[, normal (3,H,W)]) per view;
-    differentiable with respect to V, f and rgb."""
+    differentiable with respect to V, f and rgb.  Each call's backward gets
+    its own forward's gradient: outputs that still await their backward keep
+    their rasterizer (up to four per batch shape; past that the oldest one is
+    reused and its backward raises)."""
     params = params or Params()
-    key = (tuple(V.shape), tuple(T.shape), T.data_ptr(), len(cams),
+    key = (tuple(V.shape), tuple(T.shape), T.data_ptr(), V.device.index, len(cams),
            tuple((int(c.width), int(c.height)) for c in cams), dataclasses.astuple(params))
-    raster = _cache.get(key)
-    if raster is None:
-        raster = Rasterizer([SceneTensors(V.detach(), T, f.detach(), rgb.detach())],
-                            [(c, 0) for c in cams], params)
-        _cache.clear()
-        _cache[key] = raster
-    else:
-        for i, c in enumerate(cams):
-            raster._c_views[i].cam = make_camera(c)
+    raster = _pooled(key, lambda: Rasterizer([SceneTensors(V.detach(), T, f.detach(),
+                                                           rgb.detach())],
+                                             [(c, 0) for c in cams], params))
+    for i, c in enumerate(cams):
+        raster._c_views[i].cam = make_camera(c)
+    raster.views = [(c, 0) for c in cams]
     out = TetRender.apply(V, f, rgb, raster, check_status)
     return raster.view_outputs(*out)

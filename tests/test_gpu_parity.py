@@ -12,8 +12,8 @@ import torch
 import oracle
 import synth
 from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors
-from parity import (GRAD_TOL, IMG_TOL, compare_images, compare_keys, gpu_run, grad_rel_err,
-                    masked_upstream, oracle_params, oracle_run, to_dev)
+from parity import (BAND_MAX, IMG_TOL, check_gradients, compare_images, compare_keys, gpu_run,
+                    oracle_params, oracle_run, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def _check_view(gpu, orc, name=""):
     npx = orc["alpha"].size
     assert bad == 0, f"{name}: {bad} pixels off by > {IMG_TOL} (max unambiguous err {emax})"
     assert multi <= max(2, 1e-4 * npx), f"{name}: {multi} multi-band pixels unmatched"
-    assert namb <= 0.1 * npx, f"{name}: {namb} band pixels"
+    assert namb <= BAND_MAX * npx, f"{name}: {namb} band pixels"
     return emax
 
 
@@ -54,19 +54,15 @@ def test_sphere16_pure_mode(sphere16):
     _check_view(gpu["views"][0], orc, "pure")
 
 
-@pytest.mark.parametrize("s", [20.0, 175.0])
+@pytest.mark.parametrize("s", [20.0, 175.0, 620.0])
 def test_sphere16_gradients(sphere16, s):
+    """Per-element gradient parity; band pixels are differentiated on the
+    branch the GPU took (at s = 620 most covered pixels stop after two
+    fragments at the cap, a decision both sides take exactly in FP32)."""
     p = Params(s=s, tile=16)
     cam = sphere16.cams[0]
-    up0 = synth.upstream_grads(0, [cam])[0]
-    orc0 = oracle_run(sphere16, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(sphere16, cam, p, upstream=up)
-    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
-    dV, df, drgb = gpu["grads"][0]
-    for name, g, o in (("dV", dV, orc["dV"]), ("df", df, orc["df"]), ("drgb", drgb, orc["drgb"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
+    check_gradients([sphere16], [(cam, 0)], p, [synth.upstream_grads(0, [cam])[0]],
+                    name=f"sphere16 s{s}")
 
 
 @pytest.mark.parametrize("nw", [1, 5])
@@ -75,15 +71,14 @@ def test_resort_window_parity(sphere16, nw):
     window of the same size."""
     p = Params(s=60.0, tile=16, resort_window=nw)
     cam = sphere16.cams[0]
-    up0 = synth.upstream_grads(6, [cam])[0]
-    orc0 = oracle_run(sphere16, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(sphere16, cam, p, upstream=up)
-    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
-    _check_view(gpu["views"][0], orc0, f"window{nw}")
-    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"window{nw} {name}: rel err {err:.3e}"
+    check_gradients([sphere16], [(cam, 0)], p, [synth.upstream_grads(6, [cam])[0]],
+                    name=f"window{nw}")
+
+
+def _with_normal_upstream(seed_up, seed_n, cam):
+    up = tuple(synth.upstream_grads(seed_up, [cam])[0])
+    return up + (np.random.default_rng(seed_n).normal(size=(3, cam.height, cam.width))
+                 .astype(np.float32),)
 
 
 @pytest.mark.parametrize("tile,nw,pure", [(8, 0, False), (16, 0, False), (16, 0, True),
@@ -93,19 +88,10 @@ def test_normal_map_and_gradients(sphere16, tile, nw, pure):
     normal map and the gradients of all four upstream channels."""
     p = Params(s=60.0, tile=tile, resort_window=nw, pure=pure, normals=True)
     cam = sphere16.cams[0]
-    up0 = tuple(synth.upstream_grads(11, [cam])[0])
-    up0 = up0 + (np.random.default_rng(12).normal(size=(3, cam.height, cam.width))
-                 .astype(np.float32),)
     orc0 = oracle_run(sphere16, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(sphere16, cam, p, upstream=up)
-    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
-    assert len(gpu["views"][0]) == 4
     assert np.abs(orc0["normal"]).max() > 0.5
-    _check_view(gpu["views"][0], orc0, f"normals tile{tile} nw{nw}")
-    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"normals {name}: rel err {err:.3e}"
+    check_gradients([sphere16], [(cam, 0)], p, [_with_normal_upstream(11, 12, cam)],
+                    name=f"normals tile{tile} nw{nw} pure{pure}")
 
 
 def test_normal_gradient_alone(sphere16):
@@ -115,16 +101,10 @@ def test_normal_gradient_alone(sphere16):
     cam = sphere16.cams[0]
     H, W = cam.height, cam.width
     rng = np.random.default_rng(13)
-    up0 = (np.zeros((3, H, W), np.float32), np.zeros((H, W), np.float32),
-           np.zeros((H, W), np.float32), rng.normal(size=(3, H, W)).astype(np.float32))
-    orc0 = oracle_run(sphere16, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(sphere16, cam, p, upstream=up)
-    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
-    assert np.abs(orc["drgb"]).max() == 0.0
-    for name, g, o in zip(("dV", "df"), gpu["grads"][0][:2], (orc["dV"], orc["df"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"normal-only {name}: rel err {err:.3e}"
+    up = (np.zeros((3, H, W), np.float32), np.zeros((H, W), np.float32),
+          np.zeros((H, W), np.float32), rng.normal(size=(3, H, W)).astype(np.float32))
+    rep = check_gradients([sphere16], [(cam, 0)], p, [up], name="normal-only")
+    assert rep["tensors"]["s0.drgb"]["maxnorm"] == 0.0
 
 
 @pytest.mark.parametrize("seg", [32, 96])
@@ -136,18 +116,10 @@ def test_split_tile_lists(sphere16, seg, s, pure):
     oracle."""
     p = Params(s=s, tile=16, pure=pure, normals=True, blend_segment=seg)
     cam = sphere16.cams[0]
-    up0 = tuple(synth.upstream_grads(21, [cam])[0])
-    up0 = up0 + (np.random.default_rng(22).normal(size=(3, cam.height, cam.width))
-                 .astype(np.float32),)
-    orc0 = oracle_run(sphere16, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(sphere16, cam, p, upstream=up)
-    gpu = gpu_run([sphere16], [(cam, 0)], p, upstream=[up], lists=True)
+    gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
     assert int(np.diff(gpu["lists"]["ranges"], axis=1).max()) > 4 * seg
-    _check_view(gpu["views"][0], orc0, f"split{seg} s{s}")
-    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"split{seg} {name}: rel err {err:.3e}"
+    check_gradients([sphere16], [(cam, 0)], p, [_with_normal_upstream(21, 22, cam)],
+                    name=f"split{seg} s{s} pure{pure}")
 
 
 def test_resort_window_torus64(torus64):
@@ -166,41 +138,21 @@ def test_gradients_pure_small_grids():
         rgb = np.random.default_rng(n).uniform(size=(len(V), 3)).astype(np.float32)
         cam = synth.orbit_camera(33.0, 21.0, 40, 40)
         p = Params(s=s, tile=8, pure=True)
-        up = synth.upstream_grads(30 + n, [cam])[0]
-        orc = oracle_run((V, T, f, rgb), cam, p, upstream=up)
-        gpu = gpu_run([(V, T, f, rgb)], [(cam, 0)], p, upstream=[up])
-        _check_view(gpu["views"][0], orc, f"pure{n}")
-        for g, o in zip(gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
-            err = grad_rel_err(g, o)
-            assert err < GRAD_TOL, f"pure{n}: rel err {err:.3e}"
+        rep = check_gradients([(V, T, f, rgb)], [(cam, 0)], p,
+                              [synth.upstream_grads(30 + n, [cam])[0]], name=f"pure{n}")
+        assert rep["views"][0]["band"] == 0
 
 
 def test_batch_of_views_and_scenes_matches_single_views(sphere16):
-    """Several scenes and views of uneven sizes (ragged tiles) in one call."""
+    """Several scenes and views of uneven sizes (ragged tiles) in one call;
+    each scene's gradient sums over its views."""
     rng = np.random.default_rng(5)
     sc2 = synth.Scene(8, *synth.random_scene(rng, 8, "torus")[:4], [], "torus8")
     cams = [synth.orbit_camera(30.0, 20.0, 128, 128), synth.random_camera(rng, 77, 53),
             synth.random_camera(rng, 200, 96), synth.random_camera(rng, 33, 130)]
     views = [(cams[0], 0), (cams[1], 1), (cams[2], 0), (cams[3], 1)]
-    p = Params(s=60.0, tile=16)
-    scenes = [sphere16, sc2]
-    ups = synth.upstream_grads(9, cams)
-    orcs = [oracle_run(scenes[si], c, p) for c, si in views]
-    ups = [masked_upstream(u, o["amb"]) for u, o in zip(ups, orcs)]
-    gpu = gpu_run(scenes, views, p, upstream=ups)
-    for i, ((c, si), o) in enumerate(zip(views, orcs)):
-        _check_view(gpu["views"][i], o, f"view{i}")
-    # gradients: sum over each scene's views
-    for si, sc in enumerate(scenes):
-        acc = [np.zeros((sc.N, 3)), np.zeros(sc.N), np.zeros((sc.N, 3))]
-        for (c, sj), u in zip(views, ups):
-            if sj != si:
-                continue
-            o = oracle_run(sc, c, p, upstream=u)
-            acc[0] += o["dV"]; acc[1] += o["df"]; acc[2] += o["drgb"]
-        for g, o in zip(gpu["grads"][si], acc):
-            err = grad_rel_err(g, o)
-            assert err < GRAD_TOL, f"scene{si}: rel err {err:.3e}"
+    check_gradients([sphere16, sc2], views, Params(s=60.0, tile=16),
+                    synth.upstream_grads(9, cams), name="ragged batch")
 
 
 @pytest.mark.parametrize("nv", [14, 18])
@@ -213,21 +165,8 @@ def test_many_views_of_one_scene(sphere16, nv):
     chord where adjoint, dual-number and finite-difference derivatives differ)."""
     rng = np.random.default_rng(11)
     cams = [synth.random_camera(rng, 40 + 4 * i, 36 + 2 * (i % 5)) for i in range(nv)]
-    views = [(c, 0) for c in cams]
-    p = Params(s=60.0, tile=8)
-    ups = synth.upstream_grads(13, cams)
-    orcs = [oracle_run(sphere16, c, p) for c in cams]
-    ups = [masked_upstream(u, o["amb"]) for u, o in zip(ups, orcs)]
-    gpu = gpu_run([sphere16], views, p, upstream=ups)
-    for i, o in enumerate(orcs):
-        _check_view(gpu["views"][i], o, f"view{i}")
-    acc = [np.zeros((sphere16.N, 3)), np.zeros(sphere16.N), np.zeros((sphere16.N, 3))]
-    for c, u in zip(cams, ups):
-        o = oracle_run(sphere16, c, p, upstream=u)
-        acc[0] += o["dV"]; acc[1] += o["df"]; acc[2] += o["drgb"]
-    for g, o in zip(gpu["grads"][0], acc):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"{nv} views: rel err {err:.3e}"
+    check_gradients([sphere16], [(c, 0) for c in cams], Params(s=60.0, tile=8),
+                    synth.upstream_grads(13, cams), name=f"{nv} views")
 
 
 def test_empty_and_degenerate_inputs(sphere16):
@@ -300,14 +239,8 @@ def test_torus64_full_size(torus64):
 def test_torus64_gradients(torus64):
     p = Params(s=175.0, tile=16)
     cam = torus64.cams[0]
-    up0 = synth.upstream_grads(1, [cam])[0]
-    orc0 = oracle_run(torus64, cam, p)
-    up = masked_upstream(up0, orc0["amb"])
-    orc = oracle_run(torus64, cam, p, upstream=up)
-    gpu = gpu_run([torus64], [(cam, 0)], p, upstream=[up])
-    for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0], (orc["dV"], orc["df"], orc["drgb"])):
-        err = grad_rel_err(g, o)
-        assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
+    check_gradients([torus64], [(cam, 0)], p, [synth.upstream_grads(1, [cam])[0]],
+                    name="torus64")
 
 
 @pytest.mark.parametrize("res,tile,lo,hi", [(64, 32, 16385, None), (256, 32, 2049, 16384),
@@ -372,20 +305,24 @@ def test_spheres128_bench_workload(spheres128, tile):
 
 
 def test_spheres128_subgrid_gradients(spheres128):
-    """Gradients on the 4^3 sub-grid (cubes [62,66)^3) against the oracle and
-    against central finite differences of the oracle."""
+    """Gradients on the 4^3 sub-grid (cubes [62,66)^3) against the oracle."""
     sub = synth.subgrid(spheres128, 62, 66)
     p = Params(s=175.0, tile=16)
-    for cam in sub.cams:
-        up0 = synth.upstream_grads(2, [cam])[0]
-        orc0 = oracle_run(sub, cam, p)
-        if orc0["alpha"].max() == 0:
+    for k, cam in enumerate(sub.cams):
+        if oracle_run(sub, cam, p)["alpha"].max() == 0:
             continue
-        up = masked_upstream(up0, orc0["amb"])
-        orc = oracle_run(sub, cam, p, upstream=up)
-        gpu = gpu_run([sub], [(cam, 0)], p, upstream=[up])
-        _check_view(gpu["views"][0], orc0, "sub")
-        for name, g, o in zip(("dV", "df", "drgb"), gpu["grads"][0],
-                              (orc["dV"], orc["df"], orc["drgb"])):
-            err = grad_rel_err(g, o)
-            assert err < GRAD_TOL, f"{name}: rel err {err:.3e}"
+        check_gradients([sub], [(cam, 0)], p, [synth.upstream_grads(2, [cam])[0]],
+                        name=f"sub view{k}")
+
+
+def test_spheres128_full_gradients(spheres128):
+    """The benchmark's own step at full size: 128^3 grid (12.6 M tets), 4
+    views at 512^2, s = 175, tile 8, the default backward segment (split
+    lists walked by four lanes per pixel in the forward and in parallel
+    segments in the backward): every entry of dV, df and drgb against the
+    oracle, per element."""
+    sc = spheres128
+    p = Params(s=175.0, tile=8)
+    rep = check_gradients([sc], [(c, 0) for c in sc.cams], p, synth.upstream_grads(2, sc.cams),
+                          name="spheres128 4x512 tile8")
+    assert sum(v["band"] for v in rep["views"]) <= BAND_MAX * 4 * 512 * 512
