@@ -276,12 +276,24 @@ def upstream_grads(seed: int, cams) -> list:
     return out
 
 
+_TOPOLOGY: dict = {}
+
+
+def shared_grid(n: int) -> tuple:
+    """(V, T) of the n^3 grid, built once per n and shared by every caller
+    (the batched and served workloads hold many scenes of a few
+    resolutions).  The arrays must not be modified."""
+    if n not in _TOPOLOGY:
+        _TOPOLOGY[n] = (grid_vertices(n), grid_tets(n))
+    return _TOPOLOGY[n]
+
+
 def random_scene(rng: np.random.Generator, n: int, kind: str = "sphere",
                  noise: float = 0.01) -> tuple:
     """Vertex fields for a batched/served scene: a random sphere or torus SDF
-    plus N(0, noise^2); rgb U[0,1]."""
-    V = grid_vertices(n)
-    T = grid_tets(n)
+    plus N(0, noise^2); rgb U[0,1].  V and T are the shared grid of
+    ``shared_grid(n)`` (do not modify them)."""
+    V, T = shared_grid(n)
     if kind == "sphere":
         c = rng.uniform(-0.2, 0.2, size=3)
         r = rng.uniform(0.3, 0.6)

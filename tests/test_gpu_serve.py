@@ -67,3 +67,72 @@ def test_batches_overlap_and_budget(server):
                    streams=3, ref_res=256)
     res2, stats2 = small.run(reqs[:10])
     assert len(res2) == 10 and stats2["max_inflight"] == 1   # budget admits one batch at a time
+
+
+def test_cancelled_requests_neither_return_nor_block(server):
+    """Requests cancelled before the run (cancel), by a deadline before
+    their arrival, or from another thread while the loop runs: none returns
+    a result, the others all complete, and a request's result is the same
+    as without the cancellations."""
+    import threading
+
+    reqs = poisson_requests(np.random.default_rng(21), 40, 2000.0, 3, sizes=(128, 192),
+                            grad_fraction=0.3)
+    probe = reqs[7]
+    alone, _ = server.run([Request(probe.rid, probe.scene, probe.camera, probe.want_grad, 0.0,
+                                   probe.upstream)])
+    gone = {3, 11, 25}
+    for rid in gone:
+        server.cancel(rid)
+    reqs[30].deadline = reqs[30].arrival - 1e-3        # expired when it arrives
+    late = max(reqs, key=lambda q: q.arrival)
+    late.arrival += 0.2                                 # cancelled by a thread before it arrives
+    t = threading.Timer(0.05, server.cancel, args=(late.rid,))
+    t.start()
+    res, stats = server.run(reqs)
+    t.join()
+    dropped = gone | {reqs[30].rid, late.rid}
+    assert set(res) == {q.rid for q in reqs} - dropped
+    assert stats["cancelled"] == len(dropped)
+    a, b = alone[probe.rid], res[probe.rid]
+    for u, v in ((a.image, b.image), (a.alpha, b.alpha), (a.depth, b.depth)):
+        assert (u - v).abs().max().item() <= 1e-4
+
+
+def test_bad_scene_fails_alone():
+    """A resident scene with a tet index outside [0, N): batches holding its
+    requests are split per scene, its requests fail with an error once they
+    fail alone, and the other scenes' requests batched with them complete
+    normally."""
+    good = synth.scene_sphere16()
+    bad = to_dev(good)
+    srv = Server([to_dev(good), bad], Params(s=120.0, tile=16), hbm_budget=4e9, max_views=8,
+                 streams=2, ref_res=128)
+    bad.T[5, 2] = good.N + 7        # goes bad after registration: found in its batches
+    reqs = poisson_requests(np.random.default_rng(4), 24, 5000.0, 2, sizes=(128,),
+                            grad_fraction=0.3)
+    res, stats = srv.run(reqs)
+    assert set(res) == {q.rid for q in reqs}
+    for q in reqs:
+        r = res[q.rid]
+        if q.scene == 1:
+            assert r.error is not None and r.image is None
+        else:
+            assert r.error is None and r.alpha.max().item() > 0.5
+    assert stats["failed"] == sum(q.scene == 1 for q in reqs) and 1 in srv.bad_scenes
+
+
+def test_layout_reuse_matches_fresh_rasterizer(server):
+    """Batches whose workspace layout repeats reuse the slot's rasterizer
+    (rebound to other scenes of the same size and other cameras): the result
+    equals a fresh render of the same request."""
+    rng = np.random.default_rng(31)
+    q0 = Request(0, 0, on_sphere(rng, 160, 160), False, 0.0)
+    q1 = Request(1, 0, on_sphere(rng, 160, 160), False, 0.0)   # same layout, other camera
+    r0, _ = server.run([q0])
+    r1, _ = server.run([q1])
+    fresh = Server(server.scenes, Params(s=120.0, tile=16), hbm_budget=4e9, max_views=8,
+                   streams=1, ref_res=256)
+    f1, _ = fresh.run([Request(1, 0, q1.camera, False, 0.0)])
+    assert (r1[1].image - f1[1].image).abs().max().item() <= 1e-6
+    assert (r0[0].alpha - r1[1].alpha).abs().max().item() > 0.0   # different cameras
