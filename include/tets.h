@@ -258,6 +258,32 @@ int tts_blend_bwd_ex(const tts_batch* b, const tts_upstream* up, tts_stream stre
  * (host-side counter, all threads). */
 int64_t tts_launch_count(void);
 
+/* Kernel-event hook, for timing the kernels of a call one by one: after
+ * tts_debug_kernel_events(events, n) (events: n caller-created cudaEvent_t,
+ * n <= 256), each kernel the library launches through its calls records the
+ * next event on the call's stream right after the launch, until n have been
+ * used.  tts_debug_kernel_events_used(names, max) returns how many were
+ * recorded since the hook was set and fills names[i] (up to max) with the
+ * name of the kernel the i-th event follows (strings owned by the CUDA
+ * runtime).  n = 0 turns the hook off.  Process-wide, not thread safe,
+ * returns TTS_ERR_ARG for n outside [0, 256] or missing events.  For
+ * profiling: the events keep each kernel from overlapping the next. */
+int tts_debug_kernel_events(void* const* events, int32_t n);
+int32_t tts_debug_kernel_events_used(const char** names, int32_t max_names);
+
+/* Test hook for the bounded waits of the binning's tile scan (a scan over
+ * blocks of 2,048 tiles in which each block waits for the running sum of
+ * the blocks before it).  spin_limit: polls of a predecessor's word before a
+ * block gives up (0: the default, 2^22); unset_block: the index of a scan
+ * block (in ticket order) whose wait polls a word that no block ever
+ * publishes, so that it gives up after spin_limit polls (-1: none).  A wait
+ * that gives up sets TTS_STATUS_TIMEOUT; that forward then uses no key (its
+ * outputs are those of an empty scene) and the next forward clears the bit.
+ * Process-wide, read when a call plans its launches; tts_debug_scan_wait(0,
+ * -1) restores the defaults.  Returns TTS_ERR_ARG for spin_limit < 0 or
+ * unset_block < -1.  Not for production use. */
+int tts_debug_scan_wait(int64_t spin_limit, int32_t unset_block);
+
 /* Device pointers to the per-pixel forward state (view-major, like alpha):
  * final transmittance (fp32), number of list entries walked up to the last
  * blended one (int32) and number of fragments met (int32: list entries whose
@@ -284,7 +310,8 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
  * notes) and to the per-slot survivor-relative tet index order. */
 int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
 
-/* Sorts n (key, value) pairs by the low key_bits bits of the key, stably: an
+/* Sorts n (key, value) pairs by the low key_bits bits of the key, stably
+ * (bits above key_bits are carried along and take no part in the order): an
  * LSD radix sort with 8-bit digits (per pass: per-block digit counts, a scan
  * of the counts, a stable scatter), the device radix sort of Sec. 3.3's
  * (tile, depth) keys.  The binning of tts_bin_views does not call it: it
@@ -295,7 +322,9 @@ int tts_debug_records(const tts_batch* b, const void** records, tts_stream strea
  * bytes, owned by the caller, overwritten.  n <= 2^31 - 1.  Returns
  * TTS_ERR_ARG (bad n, key_bits outside [1, 64], aliasing) or
  * TTS_ERR_WORKSPACE (scratch missing, misaligned or too small) before
- * anything is enqueued. */
+ * anything is enqueued, TTS_ERR_CUDA when one of its own kernel launches
+ * failed (an error left pending by earlier unrelated CUDA calls is neither
+ * reported nor cleared). */
 int tts_sort_pairs_scratch_size(int64_t n, size_t* bytes);
 int tts_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                    uint32_t* vals_out, int64_t n, int32_t key_bits, void* scratch,
@@ -303,9 +332,9 @@ int tts_sort_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* k
 
 /* The same sort without allocating anything.
  * The paper has no counterpart: this entry point exists for callers that must
- * not allocate device memory themselves (code inside a host callback or an
- * allocator hook, plugin hosts that own every device allocation, loops that
- * cannot take cudaMalloc's implicit synchronisation).  keys_in/vals_in are
+ * not allocate device memory themselves (a custom allocator hook, which cannot
+ * call back into cudaMalloc; plugin hosts that own every device allocation;
+ * loops that cannot take cudaMalloc's implicit synchronisation).  keys_in/vals_in are
  * read only; keys_out/vals_out (device, n each) receive the sorted pairs and
  * must not alias the inputs.  Temporary storage is a fixed array of about
  * 12.3 MiB compiled into the library, present on every device that loads it

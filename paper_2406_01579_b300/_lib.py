@@ -88,7 +88,8 @@ ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
                 "tts_sort_pairs_scratch_size", "tts_sort_pairs",
                 "tts_tet_edges_workspace_size", "tts_tet_edges", "tts_regularizers_workspace_size",
                 "tts_regularizers", "tts_marching_tets_workspace_size", "tts_marching_tets",
-                "tts_geometry_status",
+                "tts_geometry_status", "tts_debug_scan_wait", "tts_debug_kernel_events",
+                "tts_debug_kernel_events_used",
                 "tts_error_string", "tts_version")
 
 _lib = None
@@ -148,6 +149,9 @@ def load():
     L.tts_marching_tets.argtypes = [P, P, P, i64, i64, P, i64, P, P, i64, P, i64, P, P,
                                     ctypes.c_size_t, P]
     L.tts_geometry_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint32), P]
+    L.tts_debug_scan_wait.argtypes = [ctypes.c_int64, ctypes.c_int32]
+    L.tts_debug_kernel_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]
+    L.tts_debug_kernel_events_used.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.c_int32]
     L.tts_error_string.argtypes = [ctypes.c_int]
     L.tts_error_string.restype = ctypes.c_char_p
     L.tts_version.argtypes = []
@@ -156,6 +160,7 @@ def load():
         if name not in ("tts_error_string", "tts_version"):
             getattr(L, name).restype = ctypes.c_int
     L.tts_launch_count.restype = ctypes.c_int64
+    L.tts_debug_kernel_events_used.restype = ctypes.c_int32
     _lib = L
     return L
 

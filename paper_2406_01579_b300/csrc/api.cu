@@ -1,4 +1,5 @@
 // C ABI of libtets: argument checks, workspace layout, launch sequences.
+#include <algorithm>
 #include <atomic>
 #include <cstddef>
 #include <cmath>
@@ -41,8 +42,30 @@ int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st) {
 static std::atomic<long long> g_launches{0};
 static std::atomic<int> g_launch_err{0};
 
+// Tile-scan look-back waits (tts_debug_scan_wait): polls before giving up,
+// and the scan block made to poll a word that is never published (-1: none).
+constexpr long long kScanSpinLimit = 1ll << 22;
+static std::atomic<long long> g_scan_spin_limit{kScanSpinLimit};
+static std::atomic<int> g_scan_unset_block{-1};
+
 void count_launches(long long n) { g_launches += n; }
 void note_launch_error(cudaError_t e) { g_launch_err.store((int)e); }
+
+// Kernel-event hook (tts_debug_kernel_events): events recorded after each
+// launch_k launch, with the kernels' names.  Off (n == 0) by default.
+static std::atomic<int> g_kev_n{0}, g_kev_i{0};
+static cudaEvent_t g_kev[256];
+static const char* g_kev_name[256];
+
+void note_kernel_launched(const void* kernel, cudaStream_t st) {
+  if (g_kev_n.load(std::memory_order_relaxed) == 0) return;
+  const int i = g_kev_i.fetch_add(1);
+  if (i >= g_kev_n.load()) return;
+  const char* name = nullptr;
+  if (cudaFuncGetName(&name, kernel) != cudaSuccess) name = "?";
+  g_kev_name[i] = name;
+  if (cudaEventRecord(g_kev[i], st) != cudaSuccess) note_launch_error(cudaErrorInvalidValue);
+}
 
 namespace {
 
@@ -108,6 +131,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   B.resort_window = pr.resort_window;
   B.seg_len = (pr.resort_window > 0) ? 0 : (pr.blend_segment > 0 ? pr.blend_segment : kBlendSegment);
   B.key_cap = b->key_capacity;
+  B.ts_spin_limit = g_scan_spin_limit.load();
+  B.ts_unset_block = g_scan_unset_block.load();
   // scenes
   long long surv_total = 0, flag_total = 0, max_surv = 1;
   int pf_chunks = 0, max_pf = 1;
@@ -506,6 +531,28 @@ int tts_render_bwd(const tts_batch* b, const float* dimage, const float* dalpha,
 }
 
 int64_t tts_launch_count(void) { return g_launches.load(); }
+
+int tts_debug_kernel_events(void* const* events, int32_t n) {
+  if (n < 0 || n > 256 || (n > 0 && !events)) return TTS_ERR_ARG;
+  g_kev_n.store(0);
+  for (int i = 0; i < n; ++i) g_kev[i] = static_cast<cudaEvent_t>(events[i]);
+  g_kev_i.store(0);
+  g_kev_n.store(n);
+  return TTS_OK;
+}
+
+int32_t tts_debug_kernel_events_used(const char** names, int32_t max_names) {
+  const int used = std::min(g_kev_i.load(), g_kev_n.load());
+  for (int i = 0; names && i < std::min(used, (int)max_names); ++i) names[i] = g_kev_name[i];
+  return used;
+}
+
+int tts_debug_scan_wait(int64_t spin_limit, int32_t unset_block) {
+  if (spin_limit < 0 || unset_block < -1) return TTS_ERR_ARG;
+  g_scan_spin_limit.store(spin_limit == 0 ? kScanSpinLimit : spin_limit);
+  g_scan_unset_block.store(unset_block);
+  return TTS_OK;
+}
 
 int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last,
                      const void** n_frag, tts_stream stream) {

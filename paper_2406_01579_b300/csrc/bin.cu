@@ -69,7 +69,7 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
     c->long_lists = 0;
     c->n_keys = 0;
     c->n_keys_used = 0;
-    c->status &= ~(unsigned)TTS_STATUS_KEY_OVERFLOW;
+    c->status &= ~(unsigned)(TTS_STATUS_KEY_OVERFLOW | TTS_STATUS_TIMEOUT);
     c->work_fwd = c->work_bwd = 0u;
     c->done_fwd = c->done_bwd = 0u;
     c->seg_total = 0;
@@ -493,13 +493,19 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
 // tiles listed by list-length class; the total is the key count.  Blocks of
 // TS_THREADS x TS_ITEMS tiles take tickets in order, publish their count
 // sum, and find the sum of all earlier blocks by decoupled look-back (the
-// waits are bounded: past the limit the scan sets TTS_STATUS_TIMEOUT and its
-// output is undefined).  Past the key capacity the key count is set, the
-// overflow status raised and no key is used (the work-list builder then
-// empties every range).  The last block also fixes the depth bit count.
+// waits are bounded: past B->ts_spin_limit polls the scan sets
+// TTS_STATUS_TIMEOUT, and the kernels after it use no key, as on overflow).
+// Past the key capacity the key count is set, the overflow status raised and
+// no key is used (the work-list builder then empties every range).  The last
+// block also fixes the depth bit count.
 // ---------------------------------------------------------------------------
 constexpr unsigned long long TS_AGG = 1ull << 62, TS_PREFIX = 2ull << 62;
-constexpr long long TS_SPIN_LIMIT = 1ll << 22;
+
+// No key is used: the scan exceeded the key capacity or one of its waits gave
+// up (both leave ranges and cursors that do not describe placed keys).
+__device__ __forceinline__ bool keys_unusable(const Counters* c) {
+  return c->n_keys_used == 0 || (c->status & TTS_STATUS_TIMEOUT) != 0u;
+}
 
 // List-length class of the per-tile depth sort (see K5): up to 256 keys,
 // 512, 1,024, 2,048, 4,096, more.
@@ -543,15 +549,18 @@ __global__ void __launch_bounds__(TS_THREADS) k_tile_scan(const Batch* __restric
     if (b > 0) {
       atomicExch(lb + b, TS_AGG | (unsigned long long)tot);
       bool timed_out = false;
+      const long long limit = B->ts_spin_limit;
       for (int p = b - 1; p >= 0 && !timed_out;) {
-        unsigned long long w = *reinterpret_cast<volatile unsigned long long*>(lb + p);
+        // the test hook: this block polls a word no block publishes
+        const unsigned long long* src = (b == B->ts_unset_block) ? &c->scan_unset : lb + p;
+        unsigned long long w = *reinterpret_cast<const volatile unsigned long long*>(src);
         long long spins = 0;
         while (w == 0ull) {
-          if (++spins > TS_SPIN_LIMIT) {
+          if (++spins > limit) {
             timed_out = true;
             break;
           }
-          w = *reinterpret_cast<volatile unsigned long long*>(lb + p);
+          w = *reinterpret_cast<const volatile unsigned long long*>(src);
         }
         if (timed_out) break;
         excl += (long long)(w & (TS_AGG - 1));
@@ -623,7 +632,7 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
   if (chunk >= vw.pp_chunks) return;
   const Counters* c = B->ctr;
   const long long used = c->n_keys_used;
-  if (used == 0) return;
+  if (keys_unusable(c)) return;
   const int nsurv = c->n_surv[vw.scene];
   int* __restrict__ cur = B->tile_cnt + vw.tile_base;
   unsigned long long* __restrict__ out = B->keys[1];
@@ -868,7 +877,7 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
   __shared__ unsigned long long s[spad_size<TSORT_BLOCK_CAP>()];
   __shared__ int s_item[16];
   Counters* c = B->ctr;
-  if (c->n_keys_used == 0) return;
+  if (keys_unusable(c)) return;
   const int nt = B->total_tiles;
   const int* list = B->tile_class;
   const int n5 = c->class_n[5], n4 = c->class_n[4], n0 = c->class_n[0];
@@ -919,7 +928,7 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
 // depth bits.  Not part of a render.
 __global__ void k_debug_keys(const Batch* __restrict__ B) {
   const Counters* c = B->ctr;
-  if (c->n_keys_used == 0) return;
+  if (keys_unusable(c)) return;
   const int db = c->depth_bits;
   const unsigned zmin = c->zmin_bits;
   for (int t = blockIdx.x; t < B->total_tiles; t += gridDim.x) {
@@ -960,7 +969,7 @@ __global__ void __launch_bounds__(WL_THREADS) k_worklist_count(const Batch* __re
   const int lane = threadIdx.x & 31;
   const bool in = t < nt;
   // no key used (capacity exceeded): every list is empty
-  const bool none = B->ctr->n_keys_used == 0;
+  const bool none = keys_unusable(B->ctr);
   int2 r = in ? B->ranges[t] : make_int2(0, 0);
   if (in && none && (r.x | r.y)) {
     r = make_int2(0, 0);

@@ -30,8 +30,10 @@ struct GradOut {
 
 // Launch with programmatic stream serialization (see pdl_wait): the kernel's
 // blocks may be scheduled while the previous kernel in the stream finishes.
-// A launch error is kept for check_launch.
+// A launch error is kept for check_launch.  With the kernel-event hook on
+// (tts_debug_kernel_events), an event is recorded after the launch.
 void note_launch_error(cudaError_t e);
+void note_kernel_launched(const void* kernel, cudaStream_t st);
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                      Args... args) {
@@ -47,6 +49,7 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
   if (e != cudaSuccess) note_launch_error(e);
+  note_kernel_launched(reinterpret_cast<const void*>(kernel), st);
 }
 
 // Each launcher returns the number of kernels it launched.

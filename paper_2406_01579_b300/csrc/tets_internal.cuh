@@ -42,6 +42,7 @@ struct Counters {
   int sort_q[5];            // depth-sort queues: block, half, quarter, eighth and warp lists taken
   unsigned int scan_ticket; // tile-scan blocks started
   unsigned int zero_q;      // gradient-clearing chunks taken by the backward
+  unsigned long long scan_unset; // a look-back word no kernel writes (the scan-wait test hook)
 };
 
 struct SceneD {
@@ -80,6 +81,8 @@ struct Batch {
   int resort_window;
   int seg_len;              // list entries per blend work unit (0: no splitting)
   int seg_cap;              // segment slots of the split-tile checkpoints
+  int ts_unset_block;       // tile-scan block whose look-back reads Counters::scan_unset (-1: none)
+  long long ts_spin_limit;  // polls of a tile-scan look-back word before it gives up
   long long key_cap;
   long long total_pixels;
   long long total_slots;

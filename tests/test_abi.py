@@ -77,3 +77,13 @@ def test_workspace_size_and_argument_checks():
     b6, k6 = _batch()
     assert L.tts_prepare_scene(ctypes.byref(b6), None) == _lib.TTS_ERR_WORKSPACE
     assert L.tts_error_string(3) == b"key or survivor capacity exceeded"
+
+
+def test_scan_wait_hook_arguments():
+    """The tile-scan wait hook checks its arguments on the host and leaves the
+    defaults in place afterwards (no device call)."""
+    L = _lib.load()
+    assert L.tts_debug_scan_wait(-1, -1) == _lib.TTS_ERR_ARG
+    assert L.tts_debug_scan_wait(100, -2) == _lib.TTS_ERR_ARG
+    assert L.tts_debug_scan_wait(100, 1) == _lib.TTS_OK
+    assert L.tts_debug_scan_wait(0, -1) == _lib.TTS_OK
