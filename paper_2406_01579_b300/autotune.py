@@ -17,8 +17,8 @@ import torch
 
 from .rasterizer import Params, Rasterizer
 
-DEFAULT_CACHE = os.environ.get("TTS_AUTOTUNE_CACHE",
-                               os.path.join(os.path.expanduser("~"), ".cache", "tets_autotune.json"))
+# No cache file unless the caller names one (here or in TTS_AUTOTUNE_CACHE).
+DEFAULT_CACHE = os.environ.get("TTS_AUTOTUNE_CACHE") or None
 
 
 def _round2(x: int) -> int:

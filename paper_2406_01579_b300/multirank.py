@@ -20,9 +20,9 @@ def rank_cameras(base_cams, rank: int, width: int, height: int, seed: int = 1000
     same number of random cameras (seeded by the rank) for the others."""
     if rank == 0:
         return list(base_cams)
-    import synth
+    from .camera import on_sphere
     rng = np.random.default_rng(seed + rank)
-    return [synth.random_camera(rng, width, height) for _ in range(len(base_cams))]
+    return [on_sphere(rng, width, height) for _ in range(len(base_cams))]
 
 
 def job_mpix_s(local_pixels_per_step: int, steps: int, local_elapsed_s: float, dist=None,
