@@ -90,7 +90,12 @@ enum {
   TTS_FLAG_PURE = 1,        /* no cap / skip / early stop / pre-filter */
   TTS_FLAG_ACCUM_GRAD = 2,  /* backward adds into dV/df/drgb instead of overwriting */
   TTS_FLAG_FORWARD_ONLY = 4, /* workspace without backward state; backward calls fail */
-  TTS_FLAG_NORMALS = 8       /* also render the normal map: use the _ex calls */
+  TTS_FLAG_NORMALS = 8,      /* also render the normal map: use the _ex calls */
+  TTS_FLAG_HULL = 16         /* tile test against the projected tet (Sec. 3.3 culling): a tile
+                                of a tet's bbox rect gets no key when, for some edge of the
+                                convex hull of the four projected vertices, the corner pixel
+                                centres of (tile x bbox) all lie strictly outside it (an exact
+                                FP32 edge function, see the design notes) */
 };
 
 #define TTS_MAX_SCENES 64

@@ -80,9 +80,9 @@ def lib():
         i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
         L.orc_prefilter.argtypes = [i64, P, i64, P, P, P, P, P]
         L.orc_prefilter.restype = i64
-        L.orc_bin_prepare.argtypes = [i64, P, P, P, P, i32, P, P, P]
+        L.orc_bin_prepare.argtypes = [i64, P, P, P, P, i32, P, P, P, i32, P]
         L.orc_bin_prepare.restype = i64
-        L.orc_bin_sort.argtypes = [i64, P, P, P, i32, P, P, P, P]
+        L.orc_bin_sort.argtypes = [i64, P, P, P, i32, P, P, P, P, P]
         L.orc_bin_sort.restype = i64
         L.orc_fragment.argtypes = [P, P, f64, f64, f64, f64, f64, f64, f64, P]
         L.orc_fragment.restype = ctypes.c_int
@@ -165,7 +165,10 @@ def prefilter(T, f, params: OrcParams):
     return surv, amb.astype(bool), amax
 
 
-def bin_view(surv, T, V, cam, tile: int):
+def bin_view(surv, T, V, cam, tile: int, hull: bool = False):
+    """Sec. 3.3 binning of one view; ``hull``: the tile test against the
+    projected tet (only tiles whose (tile x bbox) corner pixel centres are not
+    all outside one hull edge keep their key)."""
     surv = _c(surv, np.int32)
     T = _c(T, np.int32)
     V = _c(V, np.float32)
@@ -174,8 +177,9 @@ def bin_view(surv, T, V, cam, tile: int):
     rect = np.zeros((ns, 4), np.int32)
     zbits = np.zeros(ns, np.uint32)
     ntl = np.zeros(ns, np.int32)
+    keep = np.zeros(ns, np.uint32)
     total = lib().orc_bin_prepare(ns, _p(surv), _p(T), _p(V), ctypes.byref(c), tile, _p(rect),
-                                  _p(zbits), _p(ntl))
+                                  _p(zbits), _p(ntl), 1 if hull else 0, _p(keep))
     tx = (cam.width + tile - 1) // tile
     ty = (cam.height + tile - 1) // tile
     ktile = np.zeros(total, np.int32)
@@ -183,7 +187,7 @@ def bin_view(surv, T, V, cam, tile: int):
     kval = np.zeros(total, np.int32)
     ranges = np.zeros((tx * ty, 2), np.int32)
     n = lib().orc_bin_sort(ns, _p(rect), _p(zbits), ctypes.byref(c), tile, _p(ktile), _p(kz),
-                           _p(kval), _p(ranges))
+                           _p(kval), _p(ranges), _p(keep) if hull else None)
     assert n == total
     return dict(rect=rect, zbits=zbits, ntiles=ntl, key_tile=ktile, key_z=kz, key_val=kval,
                 ranges=ranges, tiles_x=tx, tiles_y=ty)

@@ -294,10 +294,62 @@ int64_t orc_prefilter(int64_t K, const int32_t* T, int64_t N, const float* f,
 //   tile rect = [i0 / B, i1 / B] x [j0 / B, j1 / B]
 // rect[4s] = (i0, i1, j0, j1) or (-1,-1,-1,-1) when culled; zbits[s] = bits of
 // zbar; ntl[s] = tiles overlapped.  Returns the total number of keys.
+//
+// With hull != 0 (the tile test against the projected tet, Sec. 3.3
+// culling): the projection of a tet is the convex hull of its projected
+// vertices, so a pixel centre outside it meets no chord.  A tile of the rect
+// keeps its key unless, for some edge of that hull, the four corner pixel
+// centres of (tile x bbox) all lie strictly outside it.  FP32, in this order:
+// for the edge (a, b) and a point p,
+//   ex = bu - au, ey = bv - av,
+//   E = fma(ex, pv - av, -(ey * (pu - au))),
+// (a, b) is a hull edge iff E has the same nonzero sign at the other two
+// vertices, and a corner is outside iff its E has the opposite strict sign.
+// One-tile rects and rects wider or taller than 2 tiles keep every tile.  keep[s] (nullable)
+// receives the kept cells as bits cy * ntx + cx (all ones when not tested).
 // ---------------------------------------------------------------------------
+static float hull_edge_fn(float au, float av, float ex, float ey, float px, float py) {
+  return std::fma(ex, py - av, -(ey * (px - au)));
+}
+
+static uint32_t hull_keep_mask(const float pu[4], const float pv[4], int i0, int i1, int j0, int j1,
+                               int tile) {
+  const int tx0 = i0 / tile, tx1 = i1 / tile, ty0 = j0 / tile, ty1 = j1 / tile;
+  const int ntx = tx1 - tx0 + 1, nty = ty1 - ty0 + 1, nt = ntx * nty;
+  // one-tile rects and rects wider or taller than 2 tiles are not tested
+  if (nt == 1 || ntx > 2 || nty > 2) return 0xffffffffu;
+  uint32_t keep = (nt == 32) ? 0xffffffffu : ((1u << nt) - 1u);
+  static const int pairs[6][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2},
+                                  {1, 2, 0, 3}, {1, 3, 0, 2}, {2, 3, 0, 1}};
+  for (const auto& pr : pairs) {
+    const int a = pr[0], b = pr[1], c = pr[2], d = pr[3];
+    const float ex = pu[b] - pu[a], ey = pv[b] - pv[a];
+    const float ec = hull_edge_fn(pu[a], pv[a], ex, ey, pu[c], pv[c]);
+    const float ed = hull_edge_fn(pu[a], pv[a], ex, ey, pu[d], pv[d]);
+    if (!((ec > 0.f && ed > 0.f) || (ec < 0.f && ed < 0.f))) continue;   // not a hull edge
+    const bool pos = ec > 0.f;
+    for (int cell = 0; cell < nt; ++cell) {
+      if (!((keep >> cell) & 1u)) continue;
+      const int tx = tx0 + cell % ntx, ty = ty0 + cell / ntx;
+      const float x0 = (float)std::max(tx * tile, i0) + 0.5f;
+      const float x1 = (float)std::min(tx * tile + tile - 1, i1) + 0.5f;
+      const float y0 = (float)std::max(ty * tile, j0) + 0.5f;
+      const float y1 = (float)std::min(ty * tile + tile - 1, j1) + 0.5f;
+      const float cs[4] = {hull_edge_fn(pu[a], pv[a], ex, ey, x0, y0),
+                           hull_edge_fn(pu[a], pv[a], ex, ey, x1, y0),
+                           hull_edge_fn(pu[a], pv[a], ex, ey, x0, y1),
+                           hull_edge_fn(pu[a], pv[a], ex, ey, x1, y1)};
+      bool out = true;
+      for (const float e : cs) out = out && (pos ? (e < 0.f) : (e > 0.f));
+      if (out) keep &= ~(1u << cell);
+    }
+  }
+  return keep;
+}
+
 int64_t orc_bin_prepare(int64_t ns, const int32_t* surv, const int32_t* T, const float* V,
                         const OrcCam* cam, int32_t tile, int32_t* rect, uint32_t* zbits,
-                        int32_t* ntl) {
+                        int32_t* ntl, int32_t hull, uint32_t* keep) {
   const OrcCam& c = *cam;
   int64_t total = 0;
   const float W1 = (float)(c.width - 1), H1 = (float)(c.height - 1);
@@ -320,9 +372,12 @@ int64_t orc_bin_prepare(int64_t ns, const int32_t* surv, const int32_t* T, const
     ntl[s] = 0;
     if (cull) continue;
     float umin = INFINITY, umax = -INFINITY, vmin = INFINITY, vmax = -INFINITY;
+    float pu[4], pv[4];
     for (int j = 0; j < 4; ++j) {
       float u = std::fma(c.fx, x[j] / z[j], c.cx);
       float v = std::fma(c.fy, y[j] / z[j], c.cy);
+      pu[j] = u;
+      pv[j] = v;
       umin = std::fmin(umin, u); umax = std::fmax(umax, u);
       vmin = std::fmin(vmin, v); vmax = std::fmax(vmax, v);
     }
@@ -332,8 +387,15 @@ int64_t orc_bin_prepare(int64_t ns, const int32_t* surv, const int32_t* T, const
     float j1 = std::fmin(std::floor(vmax - 0.5f), H1);
     if (!(i0 <= i1) || !(j0 <= j1)) continue;
     int ii0 = (int)i0, ii1 = (int)i1, jj0 = (int)j0, jj1 = (int)j1;
-    rect[4 * s + 0] = ii0; rect[4 * s + 1] = ii1; rect[4 * s + 2] = jj0; rect[4 * s + 3] = jj1;
     int nt = (ii1 / tile - ii0 / tile + 1) * (jj1 / tile - jj0 / tile + 1);
+    uint32_t km = 0xffffffffu;
+    if (hull) {
+      km = hull_keep_mask(pu, pv, ii0, ii1, jj0, jj1, tile);
+      if (km != 0xffffffffu) nt = __builtin_popcount(km);   // a tested rect
+      if (nt == 0) continue;      // no pixel centre of the bbox inside the hull
+    }
+    if (keep) keep[s] = km;
+    rect[4 * s + 0] = ii0; rect[4 * s + 1] = ii1; rect[4 * s + 2] = jj0; rect[4 * s + 3] = jj1;
     ntl[s] = nt;
     total += nt;
   }
@@ -345,15 +407,21 @@ int64_t orc_bin_prepare(int64_t ns, const int32_t* surv, const int32_t* T, const
 // order).  ranges[2*tile] = [start, end).
 int64_t orc_bin_sort(int64_t ns, const int32_t* rect, const uint32_t* zbits, const OrcCam* cam,
                      int32_t tile, int32_t* out_tile, uint32_t* out_z, int32_t* out_val,
-                     int32_t* ranges) {
+                     int32_t* ranges, const uint32_t* keep) {
   const int tx = (cam->width + tile - 1) / tile, ty = (cam->height + tile - 1) / tile;
   struct E { int32_t tile; uint32_t z; int32_t val; };
   std::vector<E> ent;
   for (int64_t s = 0; s < ns; ++s) {
     if (rect[4 * s] < 0) continue;
-    for (int b = rect[4 * s + 2] / tile; b <= rect[4 * s + 3] / tile; ++b)
-      for (int a = rect[4 * s] / tile; a <= rect[4 * s + 1] / tile; ++a)
+    const int a0 = rect[4 * s] / tile, a1 = rect[4 * s + 1] / tile;
+    const int b0 = rect[4 * s + 2] / tile, b1 = rect[4 * s + 3] / tile;
+    const int ncell = (a1 - a0 + 1) * (b1 - b0 + 1);
+    for (int b = b0; b <= b1; ++b)
+      for (int a = a0; a <= a1; ++a) {
+        const int cell = (b - b0) * (a1 - a0 + 1) + (a - a0);
+        if (keep && keep[s] != 0xffffffffu && !((keep[s] >> cell) & 1u)) continue;   // hull test
         ent.push_back({b * tx + a, zbits[s], (int32_t)s});
+      }
   }
   std::stable_sort(ent.begin(), ent.end(), [](const E& p, const E& q) {
     if (p.tile != q.tile) return p.tile < q.tile;
@@ -583,12 +651,14 @@ extern "C" {
 // the largest change of that fragment's term when another face nearly as
 // near gives the entry or exit point (the other one-sided derivative at the
 // chord's kink, which a computation in another precision may take).
-// dV_graze (nullable): per entry, the sum over fragments of |the fragment's
-// term through its opacity| / c^2, c the smaller of |cos| of the angles
-// between the pixel ray and the normals of the chord's entry and exit faces
-// (a face seen at grazing incidence makes the entry or exit point, and most
-// of all its derivative, ill-conditioned: the relative rounding error of the
-// term in a precision with unit roundoff u grows as about u / c^2).
+// dV_graze (nullable): per entry, the sum over the fragments of its tet of
+// (the largest of the fragment's terms through its opacity over the tet's
+// four vertices) / c^2, c the smaller of |cos| of the angles between the
+// pixel ray and the normals of the chord's entry and exit faces (a face seen
+// at grazing incidence makes the entry or exit point, and most of all its
+// derivative, ill-conditioned: in a precision with unit roundoff u the
+// rounding error of the terms grows as about u / c^2 times their largest,
+// and it reaches every vertex through the face planes they share).
 // ---------------------------------------------------------------------------
 int orc_render(int64_t N, const float* V, const float* f, const float* rgb, const int32_t* T,
                int64_t ns, const int32_t* surv, const int32_t* rect, const OrcCam* cam,
@@ -738,13 +808,21 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
                 if (nl > 0.0)
                   cmin = std::min(cmin, std::fabs(nx * ray[0] + ny * ray[1] + nz * ray[2]) / (nl * rl));
               }
+              // the fragment's largest term (world components bounded through
+              // |R^T|): rounding of the shared record-field gradients reaches
+              // every vertex of the tet at that scale
               const double wgt = 1.0 / std::max(cmin * cmin, 1e-12);
+              double gmax = 0.0;
               for (int q = 0; q < 4; ++q)
                 for (int r = 0; r < 3; ++r) {
                   double g = 0.0;
                   for (int k = 0; k < 3; ++k) g += std::fabs(c.R[3 * k + r]) * std::fabs(dLda * a.d[3 * q + k]);
+                  gmax = std::max(gmax, g);
+                }
+              for (int q = 0; q < 4; ++q)
+                for (int r = 0; r < 3; ++r) {
 #pragma omp atomic
-                  dV_graze[3 * (size_t)t[q] + r] += wgt * g;
+                  dV_graze[3 * (size_t)t[q] + r] += wgt * gmax;
                 }
             }
             if (dV_kink && df_kink) {

@@ -26,6 +26,7 @@ TTS_FLAG_PURE = 1
 TTS_FLAG_ACCUM_GRAD = 2
 TTS_FLAG_FORWARD_ONLY = 4
 TTS_FLAG_NORMALS = 8
+TTS_FLAG_HULL = 16
 
 TTS_MAX_SCENES = 64
 TTS_MAX_VIEWS = 128

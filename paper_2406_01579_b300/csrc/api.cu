@@ -115,7 +115,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   if (pr.blend_segment != 0 &&
       (pr.blend_segment < 32 || pr.blend_segment > 65536 || pr.blend_segment % 32 != 0))
     return TTS_ERR_ARG;
-  if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS))
+  if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS |
+                   TTS_FLAG_HULL))
     return TTS_ERR_ARG;
   std::memset(&P->hb, 0, sizeof(Batch));
   Batch& B = P->hb;

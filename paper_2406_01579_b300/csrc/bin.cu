@@ -418,19 +418,27 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
   __syncthreads();
   const float s = B->s;
   const int tsh = __ffs(B->tile) - 1;   // tile is 8, 16 or 32
+  const bool hull = (B->flags & TTS_FLAG_HULL) != 0;
   unsigned zmn = 0xffffffffu, zmx = 0u;
   for (int q = threadIdx.x; q < PRE_CHUNK; q += PRE_THREADS) {
     const int k = k0 + q;
     if (!__any_sync(0xffffffffu, k < nsurv)) break;   // warps stay converged
     TetIn in;
-    if (k < nsurv) load_tet_ids(S, B->surv_T[S.surv_off + k], in);
+    float3 colour = f3(0.f, 0.f, 0.f);
+    if (k < nsurv) {
+      load_tet_ids(S, B->surv_T[S.surv_off + k], in);
+      colour = tet_colour(in.c);     // view independent: the vertex colours die here
+    }
     // one view of the survivor: record, pixel rect, depth bits, tile counts
     auto view = [&](const ViewD& vw) {
       int tx0 = 0, ty0 = 0, tx1 = 0, ty1 = 0, ntx = 0, nt = 0;
+      unsigned mask = 0xffffffffu;
       if (k < nsurv) {
         const long long slot = vw.rec_base + k;
         Geo G;
-        tet_geometry(vw, s, in, G);
+        float pu[4], pv[4];
+        G.visible = key_path(vw, in, G, pu, pv);
+        if (G.visible) tet_geometry_rest(vw, in, G);   // may find a flat tet (not visible)
         if (G.visible) {
           tx0 = G.i0 >> tsh;     // pixel bounds are >= 0
           ty0 = G.j0 >> tsh;
@@ -438,26 +446,36 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
           ty1 = G.j1 >> tsh;
           ntx = tx1 - tx0 + 1;
           nt = ntx * (ty1 - ty0 + 1);
-          write_record(vw, s, in, G, B->rec + slot * REC_Q);
-          zmn = min(zmn, G.zbits);
-          zmx = max(zmx, G.zbits);
+          write_record(vw, s, in, G, colour, B->rec + slot * REC_Q);
+          // the hull test after the record (most of the geometry is dead by then)
+          if (hull) {
+            mask = hull_tile_mask(pu, pv, G, tsh, tx0, ty0, ntx, ty1 - ty0 + 1);
+            if (mask == 0u) nt = 0;   // no pixel centre of the bbox inside the hull
+          }
+          if (nt > 0) {
+            zmn = min(zmn, G.zbits);
+            zmx = max(zmx, G.zbits);
+          }
         }
         // the rect of a culled slot is empty (x1 < x0): the placement reads
-        // the rect and the depth bits only
-        B->rec_rect[slot] = nt > 0 ? make_int4(tx0, tx1, ty0, ty1) : make_int4(1, 0, 0, 0);
+        // the rect (the hull's kept cells in the high halves of x and y) and
+        // the depth bits only
+        B->rec_rect[slot] = nt > 0 ? make_int4(tx0 | (int)((mask & 0xffffu) << 16),
+                                               tx1 | (int)((mask >> 16) << 16), ty0, ty1)
+                                   : make_int4(1, 0, 0, 0);
         B->rec_z[slot] = G.zbits;
       }
-      // key counts per tile, one atomic per (warp, tile) and round
+      // key counts per kept tile, one atomic per (warp, tile) and round
       int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
       int cx = 0, cy = 0;    // position of round r in the rect
+      const bool masked = nt <= 32;
       for (int r = 0; __any_sync(0xffffffffu, r < nt); ++r) {
-        const unsigned act = __ballot_sync(0xffffffffu, r < nt);
-        if (r < nt) {
-          warp_bucket_add(cnt, (ty0 + cy) * vw.tiles_x + tx0 + cx, act, false);
-          if (++cx == ntx) {
-            cx = 0;
-            ++cy;
-          }
+        const bool kept = r < nt && (!masked || ((mask >> r) & 1u));
+        const unsigned act = __ballot_sync(0xffffffffu, kept);
+        if (kept) warp_bucket_add(cnt, (ty0 + cy) * vw.tiles_x + tx0 + cx, act, false);
+        if (r < nt && ++cx == ntx) {
+          cx = 0;
+          ++cy;
         }
       }
     };
@@ -641,10 +659,14 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
     if (!__any_sync(0xffffffffu, k < nsurv)) break;
     int nt = 0, ntx = 1;
     int4 r = make_int4(0, 0, 0, 0);
+    unsigned mask = 0xffffffffu;
     unsigned long long comp = 0;
     if (k < nsurv) {
       const long long slot = vw.rec_base + k;
       r = B->rec_rect[slot];            // empty (x1 < x0) for a culled slot
+      mask = ((unsigned)r.x >> 16) | ((unsigned)r.y & 0xffff0000u);   // kept cells (hull test)
+      r.x &= 0xffff;
+      r.y &= 0xffff;
       const unsigned zb = B->rec_z[slot];
       if (r.y >= r.x) {
         ntx = r.y - r.x + 1;
@@ -652,16 +674,18 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
         comp = ((unsigned long long)zb << 32) | (unsigned)slot;
       }
     }
+    const bool masked = nt <= 32;
     int cx = 0, cy = 0;    // position of round j in the rect
     for (int j = 0; __any_sync(0xffffffffu, j < nt); ++j) {
-      const unsigned act = __ballot_sync(0xffffffffu, j < nt);
-      if (j < nt) {
+      const bool kept = j < nt && (!masked || ((mask >> j) & 1u));
+      const unsigned act = __ballot_sync(0xffffffffu, kept);
+      if (kept) {
         const int pos = warp_bucket_add(cur, (r.z + cy) * vw.tiles_x + r.x + cx, act, true);
         if (pos < used) out[pos] = comp;
-        if (++cx == ntx) {
-          cx = 0;
-          ++cy;
-        }
+      }
+      if (j < nt && ++cx == ntx) {
+        cx = 0;
+        ++cy;
       }
     }
   }

@@ -94,7 +94,8 @@ __constant__ static const int kFaceVerts[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3
 // The binning key path: an exact FP32 op sequence (the CPU checker replays
 // it bit for bit).  Returns false when the tet is culled (near plane or an
 // empty pixel bbox).
-__device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& G) {
+__device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& G,
+                                         float* pu = nullptr, float* pv = nullptr) {
   float x[4], y[4], z[4];
   bool cull = false;
 #pragma unroll
@@ -113,6 +114,8 @@ __device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& 
   for (int j = 0; j < 4; ++j) {
     const float u = __fmaf_rn(vw.fx, __fdiv_rn(x[j], z[j]), vw.cx);
     const float v = __fmaf_rn(vw.fy, __fdiv_rn(y[j], z[j]), vw.cy);
+    if (pu) pu[j] = u;
+    if (pv) pv[j] = v;
     umin = fminf(umin, u); umax = fmaxf(umax, u);
     vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
   }
@@ -123,6 +126,73 @@ __device__ __forceinline__ bool key_path(const ViewD& vw, const TetIn& in, Geo& 
   if (!(i0 <= i1) || !(j0 <= j1)) return false;
   G.i0 = (int)i0; G.i1 = (int)i1; G.j0 = (int)j0; G.j1 = (int)j1;
   return true;
+}
+
+// Hull test of the tile rect (TTS_FLAG_HULL): the tet's projection is the
+// convex hull of its four projected vertices; a tile of the rect is kept
+// unless, for some hull edge, all four corner pixel centres of (tile x pixel
+// bbox) lie strictly outside it.  An exact FP32 op sequence (the CPU checker
+// replays it bit for bit): for the edge (a, b) and a point p,
+//   E = fma(bu - au, pv - av, -((bv - av) * (pu - au)))
+// and (a, b) is a hull edge when E has the same nonzero sign at the other two
+// vertices.  Rects of two to HULL_MAX x HULL_MAX tiles are tested (one-tile
+// rects and wider or taller ones keep every tile); the kept cells come back
+// as a mask, bit cy * ntx + cx.  Per hull edge the factors (pv - av) of each row's two
+// corner heights and (bv - av) * (pu - au) of each column's two corner
+// abscissae are formed once and each corner costs one fma.
+constexpr int HULL_MAX = 2;
+
+__device__ __forceinline__ unsigned hull_tile_mask(const float pu[4], const float pv[4], const Geo& G,
+                                                   int tsh, int tx0, int ty0, int ntx, int nty) {
+  const int nt = ntx * nty;
+  const unsigned all = (nt >= 32) ? 0xffffffffu : ((1u << nt) - 1u);
+  // one-tile rects are not tested (only a sliver whose hull holds no pixel
+  // centre of its bbox could lose its key), nor rects of more than
+  // HULL_MAX tiles in a direction
+  if (nt == 1 || ntx > HULL_MAX || nty > HULL_MAX) return all;
+  const int T = 1 << tsh;
+  float xl[HULL_MAX], xr[HULL_MAX], yl[HULL_MAX], yr[HULL_MAX];
+#pragma unroll
+  for (int c = 0; c < HULL_MAX; ++c) {
+    const int tx = (tx0 + c) << tsh, ty = (ty0 + c) << tsh;
+    xl[c] = (float)max(tx, G.i0) + 0.5f;
+    xr[c] = (float)min(tx + T - 1, G.i1) + 0.5f;
+    yl[c] = (float)max(ty, G.j0) + 0.5f;
+    yr[c] = (float)min(ty + T - 1, G.j1) + 0.5f;
+  }
+  unsigned keep = all;
+  constexpr int PA[6] = {0, 0, 0, 1, 1, 2}, PB[6] = {1, 2, 3, 2, 3, 3};
+  constexpr int PC[6] = {2, 1, 1, 0, 0, 0}, PD[6] = {3, 3, 2, 3, 2, 1};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const float au = pu[PA[e]], av = pv[PA[e]];
+    const float ex = __fsub_rn(pu[PB[e]], au), ey = __fsub_rn(pv[PB[e]], av);
+    const float ec = __fmaf_rn(ex, __fsub_rn(pv[PC[e]], av), -__fmul_rn(ey, __fsub_rn(pu[PC[e]], au)));
+    const float ed = __fmaf_rn(ex, __fsub_rn(pv[PD[e]], av), -__fmul_rn(ey, __fsub_rn(pu[PD[e]], au)));
+    if (!((ec > 0.f && ed > 0.f) || (ec < 0.f && ed < 0.f))) continue;   // not a hull edge
+    const float sg = (ec > 0.f) ? 1.f : -1.f;   // the hull's side of the edge
+    float Al[HULL_MAX], Ar[HULL_MAX], Bl[HULL_MAX], Br[HULL_MAX];
+#pragma unroll
+    for (int c = 0; c < HULL_MAX; ++c) {
+      Al[c] = __fmul_rn(ey, __fsub_rn(xl[c], au));
+      Ar[c] = __fmul_rn(ey, __fsub_rn(xr[c], au));
+      Bl[c] = __fsub_rn(yl[c], av);
+      Br[c] = __fsub_rn(yr[c], av);
+    }
+#pragma unroll
+    for (int r = 0; r < HULL_MAX; ++r) {
+#pragma unroll
+      for (int c = 0; c < HULL_MAX; ++c) {
+        if (r < nty && c < ntx) {
+          // strictly outside at all four corners: sg * E < 0 (sg * E is exact)
+          const float m = fmaxf(fmaxf(sg * __fmaf_rn(ex, Bl[r], -Al[c]), sg * __fmaf_rn(ex, Bl[r], -Ar[c])),
+                                fmaxf(sg * __fmaf_rn(ex, Br[r], -Al[c]), sg * __fmaf_rn(ex, Br[r], -Ar[c])));
+          if (m < 0.f) keep &= ~(1u << (r * ntx + c));
+        }
+      }
+    }
+  }
+  return keep;
 }
 
 // Full per-(view, tet) geometry, in the pixel-scaled camera frame.  The chord
@@ -221,8 +291,13 @@ __device__ __forceinline__ void tet_geometry_rest(const ViewD& vw, const TetIn& 
   G.fr = G.fm + dot3(G.g, G.w);
 }
 
+// The tet's colour (R6): the mean of its vertex colours, in this sum order.
+__device__ __forceinline__ float3 tet_colour(const float3 c[4]) {
+  return 0.25f * ((c[0] + c[1]) + (c[2] + c[3]));
+}
+
 __device__ __forceinline__ void write_record(const ViewD& vw, float s, const TetIn& in, const Geo& G,
-                                             float4* __restrict__ out) {
+                                             float3 colour, float4* __restrict__ out) {
   (void)vw;
   const float bx = (float)G.i0 + 0.5f, by = (float)G.j0 + 0.5f;
   out[0] = make_float4((G.nf >= 2) ? -bx : bx, (G.nf >= 3) ? -by : by, (float)G.i1 + 0.5f,
@@ -234,8 +309,7 @@ __device__ __forceinline__ void write_record(const ViewD& vw, float s, const Tet
   const float F = s * G.fr;
   const float K0 = sz * dot3(G.g, G.dr);
   out[4] = make_float4(F, K0, sz * G.g.x, sz * G.g.y);
-  const float3 c = 0.25f * ((in.c[0] + in.c[1]) + (in.c[2] + in.c[3]));
-  out[5] = make_float4(G.zbar, c.x, c.y, c.z);
+  out[5] = make_float4(G.zbar, colour.x, colour.y, colour.z);
 }
 
 // World-space SDF gradient of a tet (App. A.3).  With edge rows

@@ -39,6 +39,7 @@ class Params:
     resort_window: int = 0      # N_w of Sec. 3.3 (0..7)
     normals: bool = False       # also render the Eq. 2 normal map
     blend_segment: int = 0      # list entries per backward work unit (0: library default)
+    hull: bool = False          # tile test against the projected tet (fewer keys, same image)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -50,7 +51,8 @@ class Params:
         p.tile = self.tile
         p.flags = ((TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
                    | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0)
-                   | (TTS_FLAG_NORMALS if self.normals else 0))
+                   | (TTS_FLAG_NORMALS if self.normals else 0)
+                   | (_lib.TTS_FLAG_HULL if self.hull else 0))
         p.resort_window = int(self.resort_window)
         p.blend_segment = int(self.blend_segment)
         return p

@@ -38,11 +38,12 @@ KAPPA = 1e-4
 FLOOR = 1e-6
 # grazing incidence: a fragment whose chord enters or leaves through a face
 # seen at a small angle c between the face normal and the ray has an
-# ill-conditioned entry or exit point; its term through the opacity carries
-# an FP32 rounding error of about u / c^2 relative (the record's face
-# coefficients scale with 1 / e, e the face plane's distance from the camera
-# centre, which is proportional to c, and the derivative takes two of them).
-# The bound adds C_GRAZE u sum(|term| / c^2) per dV entry.
+# ill-conditioned entry or exit point; its terms through the opacity carry an
+# FP32 rounding error of about u / c^2 times the largest of them (the
+# record's face coefficients scale with 1 / e, e the face plane's distance
+# from the camera centre, which is proportional to c, the derivative takes
+# two of them, and the record-field gradients are shared by the tet's four
+# vertices).  The bound adds C_GRAZE u sum(max |term| / c^2) per dV entry.
 C_GRAZE = 32.0
 U32 = 2.0 ** -24
 # band pixels whose branches' final transmittances differ by less than this
@@ -113,7 +114,7 @@ def oracle_run(scene, cam, params: Params, upstream=None, branch=None, abs_terms
     op = oracle_params(params)
     if pre is None:
         surv, amb_t, _ = oracle.prefilter(T, f, op)
-        bins = oracle.bin_view(surv, T, V, cam, params.tile)
+        bins = oracle.bin_view(surv, T, V, cam, params.tile, hull=params.hull)
     else:
         surv, amb_t, bins = pre
     V64, f64, rgb64 = fp64 if fp64 is not None else (None, None, None)

@@ -32,10 +32,13 @@ def _check_view(gpu, orc, name=""):
     return emax
 
 
+@pytest.mark.parametrize("hull", [True, False])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 @pytest.mark.parametrize("s", [20.0, 175.0, 620.0])
-def test_sphere16_keys_and_image(sphere16, tile, s):
-    p = Params(s=s, tile=tile)
+def test_sphere16_keys_and_image(sphere16, tile, s, hull):
+    """Keys bit for bit and images, with the tile test against the projected
+    tet (hull) and with bbox rects only."""
+    p = Params(s=s, tile=tile, hull=hull)
     cam = sphere16.cams[0]
     gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
     orc = oracle_run(sphere16, cam, p)
@@ -256,7 +259,8 @@ def test_long_tile_lists(res, tile, lo, hi):
     cam = sc.cams[0]
     gpu = gpu_run([sc], [(cam, 0)], p, lists=True)
     surv, amb_t, _ = oracle.prefilter(sc.T, sc.f, oracle_params(p))
-    orc = {"surv": surv, "amb_tets": amb_t, "bins": oracle.bin_view(surv, sc.T, sc.V, cam, tile)}
+    orc = {"surv": surv, "amb_tets": amb_t,
+           "bins": oracle.bin_view(surv, sc.T, sc.V, cam, tile, hull=p.hull)}
     compare_keys(gpu, orc)
     r = gpu["lists"]["ranges"]
     lens = r[:, 1] - r[:, 0]
@@ -269,12 +273,12 @@ def spheres128():
     return synth.scene_spheres128()
 
 
-@pytest.mark.parametrize("tile", [8, 16])
-def test_spheres128_bench_workload(spheres128, tile):
+@pytest.mark.parametrize("tile,hull", [(8, True), (8, False), (16, True)])
+def test_spheres128_bench_workload(spheres128, tile, hull):
     """The benchmark's configuration: 128^3 grid, 4 views at 512^2, s = 175,
     one batched call (tile 8 is the size the benchmark's autotuner picks).
     Keys are compared bit for bit per view; images pixel by pixel."""
-    p = Params(s=175.0, tile=tile)
+    p = Params(s=175.0, tile=tile, hull=hull)
     sc = spheres128
     views = [(c, 0) for c in sc.cams]
     gpu = gpu_run([sc], views, p, lists=True)

@@ -31,7 +31,10 @@ def _sort(L, kin, vin, bits):
                                               ("spheres128", 16, 2)])
 def test_radix_sort_matches_binning(scene, tile, nview):
     sc = synth.scene_sphere16() if scene == "sphere16" else synth.scene_spheres128(n_views=nview)
-    r = Rasterizer([to_dev(sc)], [(c, 0) for c in sc.cams[:nview]], Params(s=175.0, tile=tile))
+    # bbox rects (no hull test): one 128^3 view then holds more keys than the
+    # allocation-free sort takes
+    r = Rasterizer([to_dev(sc)], [(c, 0) for c in sc.cams[:nview]],
+                   Params(s=175.0, tile=tile, hull=False))
     r.forward()
     d = r.debug_lists()
     ref_k, ref_v = d["keys"].clone(), d["vals"].clone()
