@@ -31,11 +31,16 @@ METRIC = ("fwd+bwd Mpixel/s (128³ grid, 4×512² views) vs plain path; "
           "serve p50/p99 latency")
 UNIT = "Mpixel/s"
 
-# FP32 work per fragment of the forward blend (chord test 18, opacity and
-# compositing 30: see the design notes), and the FP32 peak of 148 SMs x 128
-# lanes x 2 flops (FMA) at the maximum SM clock.
+# FP32 work per fragment of the blend kernels: the forward's chord test (18
+# flop) and opacity and compositing (30 flop, of which 4 are special-function
+# operations: two exponentials and two reciprocals); the backward's ~150 flop
+# of which 5 are special-function operations (the recomputed opacity and
+# 1 / (1 - alpha)).  FMA-pipe flop and MUFU operations are set against the
+# peaks the build measures with its own microbenchmarks (libtets_peaks.so).
 FWD_FLOP_PER_FRAG = 48
 BWD_FLOP_PER_FRAG = 150
+FWD_MUFU_PER_FRAG = 4
+BWD_MUFU_PER_FRAG = 5
 
 # DRAM bytes (read + write) per launch of the blend kernels on this workload,
 # from one ncu capture (profiles/blend_spheres128_4x512.md), keyed by the
@@ -63,6 +68,8 @@ def parse():
                     help="tile edge 8, 16 or 32; 0: picked by the library's autotuner on this batch")
     ap.add_argument("--blend-segment", type=int, default=0,
                     help="list entries per backward segment (0: library default)")
+    ap.add_argument("--hull", type=int, default=0, choices=[0, 1],
+                    help="tile test against the projected tet (1) or bbox rects only (0)")
     ap.add_argument("--res", type=int, default=512)
     ap.add_argument("--views", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,12 +81,17 @@ def parse():
     ap.add_argument("--workload", default="spheres128", choices=["spheres128", "batched", "serve"])
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rates", default="200,500,1000,2000")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the batched-uneven and serving summaries of the default line")
+    ap.add_argument("--line-serve-requests", type=int, default=1000,
+                    help="requests per rate of the serving summary in the default line")
     return ap.parse_args()
 
 
 def workload_name(a):
     return (f"spheres128: 128^3 grid x6 tets (12,582,912 tets, 2,146,689 vertices), "
-            f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}")
+            f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}"
+            f"{', hull test' if a.hull else ', bbox rects'}")
 
 
 # ---------------------------------------------------------------------------
@@ -182,10 +194,11 @@ def run_ours(a, rank, world):
     if a.tile == 0:
         from paper_2406_01579_b300.autotune import autotune_tile
         best, times = autotune_tile([st], [(c, 0) for c in sc.cams],
-                                    Params(s=a.s, blend_segment=a.blend_segment), cache_path=None)
+                                    Params(s=a.s, blend_segment=a.blend_segment, hull=bool(a.hull)),
+                                    cache_path=None)
         a.tile = best
         tune = {str(k): round(v, 4) for k, v in times.items()}
-    params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment)
+    params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment, hull=bool(a.hull))
     r = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
     r.forward()
     r.shrink_to_fit(1.15)
@@ -280,7 +293,18 @@ def run_ours(a, rank, world):
     _lib.check(L.tts_debug_pixels(bp, ctypes.byref(Tp), ctypes.byref(Lp), ctypes.byref(Np), sp))
     nfrag = int(r._ws_slice(Np.value, 4 * r.total_pixels, torch.int32).sum().item())
     lasts = int(r._ws_slice(Lp.value, 4 * r.total_pixels, torch.int32).sum().item())
+    # per-kernel times (events after each launch) and the step's counts
+    kt = kernel_times(L, step, dev)
+    d = r.debug_lists()
+    surv_ids = d["surv"][0].long()
+    counts = {"K": int(st.T.shape[0]), "N": int(st.V.shape[0]), "surv": int(info.n_surv[0]),
+              "views": len(sc.cams), "keys": int(info.n_keys),
+              "tiles": int(d["ranges"].shape[0]), "fragments": nfrag,
+              "surv_vertices": int(torch.unique(st.T[surv_ids].reshape(-1)).numel()),
+              "visible_slots": int(torch.unique(d["vals"]).numel())}
+    del d
     res = {
+        "kernel_ms": kt, "counts": counts,
         "autotune_ms": tune,
         "elapsed": elapsed, "value": value, "stage_ms": stage_ms, "launches": launches,
         "clocks": clocks, "nfrag": nfrag, "entries_walked": lasts, "n_keys": int(info.n_keys),
@@ -404,12 +428,181 @@ def run_ours(a, rank, world):
                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                       "overlap": "copies of neighbouring steps overlap compute (two buffer sets)"}
         r.set_scenes([st])
-    if not a.no_serve and rank == 0:
+    # the quick serve (a small mix with the benchmark scene) when the full
+    # serving summary does not run
+    if not a.no_serve and rank == 0 and (a.no_workloads or world > 1):
         res["serve"] = quick_serve(a, st, dev)
     res["sc"] = sc
     if dist is not None:
         dist.barrier()
     return res
+
+
+# ---------------------------------------------------------------------------
+# ALU peaks (own microbenchmarks) and per-kernel times
+# ---------------------------------------------------------------------------
+def measure_alu_peaks(dev, target_ms=25.0):
+    """FP32 FMA TFLOP/s and ex2 / rcp MUFU Gop/s of this GPU, each the best of
+    three launches of register-resident dependency chains (libtets_peaks.so)
+    sized to about target_ms, timed with CUDA events; the SM clock is sampled
+    meanwhile."""
+    import ctypes
+
+    import torch
+    path = os.path.join(ROOT, "paper_2406_01579_b300", "libtets_peaks.so")
+    L = ctypes.CDLL(path)
+    L.tts_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                               ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    L.tts_peak_mufu.argtypes = [ctypes.c_int] + L.tts_peak_fma.argtypes
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    out = torch.empty(blocks * threads, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ops = ctypes.c_double()
+
+    def launch(which, iters):
+        if which == "fma":
+            rc = L.tts_peak_fma(blocks, threads, iters, out.data_ptr(), ctypes.byref(ops),
+                                stream.cuda_stream)
+        else:
+            rc = L.tts_peak_mufu(0 if which == "ex2" else 1, blocks, threads, iters,
+                                 out.data_ptr(), ctypes.byref(ops), stream.cuda_stream)
+        assert rc == 0, f"peak kernel {which} failed"
+        return ops.value
+
+    def timed(which, iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = launch(which, iters)
+        e1.record(stream)
+        e1.synchronize()
+        return n, e0.elapsed_time(e1)
+
+    clk = ClockSampler(dev.index)
+    clk.start()
+    clk.mark(0)
+    res = {}
+    for which in ("fma", "ex2", "rcp"):
+        timed(which, 16)                           # warm-up
+        _, ms = timed(which, 64)
+        iters = max(64, int(64 * target_ms / max(ms, 1e-3)))
+        runs = [timed(which, iters) for _ in range(3)]
+        res[which] = runs[0][0] / (min(t for _, t in runs) / 1e3)
+    clk.mark(1)
+    clocks = clk.stop()
+    # sanity: the chains' results are finite and no rate exceeds twice its
+    # nominal bound at the maximum clock (FMA: 128 lanes x 2 flop per SM and
+    # clock; MUFU: 32 lanes per SM and clock)
+    assert bool(torch.isfinite(out).all()), "peak kernels produced non-finite values"
+    nominal = {"fma": sms * 128 * 2 * 2.032e9, "ex2": sms * 32 * 2.032e9, "rcp": sms * 32 * 2.032e9}
+    for k, v in res.items():
+        assert v < 2.0 * nominal[k], f"{k} peak {v:.3e}/s is above twice its nominal bound"
+    return {"fma_tflops": res["fma"] / 1e12, "ex2_gops": res["ex2"] / 1e9,
+            "rcp_gops": res["rcp"] / 1e9, "mufu_gops": min(res["ex2"], res["rcp"]) / 1e9,
+            "launch": f"{blocks} blocks x {threads} threads, 8 independent chains per thread",
+            "clocks": clocks}
+
+
+def kernel_times(L, step, dev, n_steps=10):
+    """Per-kernel times of one step: the library records an event after each
+    of its kernel launches (tts_debug_kernel_events); the time of kernel i is
+    the gap between events i-1 and i (the events keep the kernels from
+    overlapping, so the sum exceeds the pipelined step a little).  Mean over
+    n_steps steps; names from the runtime."""
+    import ctypes
+    import re
+
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    nmax = 64
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nmax + 1)]
+    for e in evs:
+        e.record(stream)            # creates the CUDA events
+    torch.cuda.synchronize(dev)
+    handles = (ctypes.c_void_p * nmax)(*[e.cuda_event for e in evs[1:]])
+    tot, names = None, None
+    for _ in range(n_steps):
+        _lib_check(L.tts_debug_kernel_events(handles, nmax))
+        evs[0].record(stream)
+        step()
+        torch.cuda.synchronize(dev)
+        buf = (ctypes.c_char_p * nmax)()
+        n = L.tts_debug_kernel_events_used(buf, nmax)
+        ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(n)]
+        nm = []
+        for i in range(n):
+            raw = (buf[i] or b"?").decode(errors="replace")
+            m = re.search(r"k_[a-z0-9_]+", raw)     # the name inside a mangled symbol
+            nm.append(m.group(0) if m else raw)
+        if tot is None:
+            tot, names = ms, nm
+        else:
+            tot = [x + y for x, y in zip(tot, ms)]
+    _lib_check(L.tts_debug_kernel_events(None, 0))
+    out = {}
+    for name, t in zip(names, tot):
+        out[name] = out.get(name, 0.0) + t / n_steps
+    return out
+
+
+def _lib_check(rc):
+    assert rc == 0, f"library call failed ({rc})"
+
+
+def kernel_rooflines(kt, counts, peaks, hbm_gbs):
+    """Per kernel: algorithmic bytes (HBM-bound kernels) or FMA-pipe flop and
+    MUFU operations (blend kernels) per launch over its event-timed duration,
+    against the measured peaks.  The byte counts are the data each kernel must
+    move at least (unique reads and writes), from the step's counts."""
+    K, N, S, NV = counts["K"], counts["N"], counts["surv"], counts["views"]
+    U, keys, tiles = counts["surv_vertices"], counts["keys"], counts["tiles"]
+    slots, vis, frag = NV * S, counts["visible_slots"], counts["fragments"]
+    chunks = (K + 2047) // 2048
+    model = {
+        # K1: tet indices + vertex SDF (unique) + flag per tet
+        "k_prefilter_flags": ("hbm", 16 * K + 4 * N + K),
+        "k_prefilter_scan": ("hbm", 8 * chunks),
+        # flags + survivor ids and their vertex ids (read and written)
+        "k_prefilter_compact": ("hbm", K + 16 * S + 20 * S),
+        # K2: survivor ids + vertex ids + the survivors' vertices (28 B) once;
+        # per (view, survivor) the record (96 B), depth bits and tile rect
+        "k_preprocess": ("hbm", 20 * S + 28 * U + slots * (96 + 4 + 16)),
+        # K3: per tile a count read, a range, a cursor and a class entry written
+        "k_tile_scan": ("hbm", 20 * tiles),
+        # K4: per slot its rect and depth bits; per key 8 B written
+        "k_place": ("hbm", 20 * slots + 8 * keys),
+        # K5: per key 8 B read, 4 B written
+        "k_tile_sort": ("hbm", 12 * keys),
+        "k_worklist_count": ("hbm", 24 * tiles),
+        "k_worklist_place": ("hbm", 24 * tiles),
+        # K8: touched flags of all slots; for each visible slot its record
+        # gradient (80 B used) and bbox corner (16 B); the survivors' vertices
+        # read and their gradients written (28 B each way)
+        "k_tet_bwd": ("hbm", slots + 96 * vis + 56 * U),
+        "k_blend_fwd": ("alu", (frag * (FWD_FLOP_PER_FRAG - FWD_MUFU_PER_FRAG),
+                                frag * FWD_MUFU_PER_FRAG)),
+        "k_blend_bwd": ("alu", (frag * (BWD_FLOP_PER_FRAG - BWD_MUFU_PER_FRAG),
+                                frag * BWD_MUFU_PER_FRAG)),
+    }
+    out = []
+    for name, ms in sorted(kt.items(), key=lambda x: -x[1]):
+        rec = {"kernel": name, "ms": round(ms, 5)}
+        if name in model and ms > 0:
+            bound, work = model[name]
+            if bound == "hbm":
+                ach = work / (ms / 1e3) / 1e9
+                rec.update(bound="hbm", bytes=int(work), achieved=ach, peak=hbm_gbs, unit="GB/s",
+                           frac=ach / hbm_gbs)
+            else:
+                flop, mufu = work
+                af = flop / (ms / 1e3) / 1e12
+                am = mufu / (ms / 1e3) / 1e9
+                ff, fm = af / peaks["fma_tflops"], am / peaks["mufu_gops"]
+                rec.update(bound="alu", fma_flop=int(flop), mufu_ops=int(mufu),
+                           achieved=af, peak=peaks["fma_tflops"], unit="TFLOP/s", frac=max(ff, fm),
+                           fma_frac=ff, mufu_frac=fm, mufu_gops=am)
+        out.append(rec)
+    return out
 
 
 def extras(a, st, sc, params, ups, dev, barrier):
@@ -526,14 +719,20 @@ def extras(a, st, sc, params, ups, dev, barrier):
 
 
 def resident_scenes(rng, n_list, dev):
+    """Scenes of the given grid resolutions (sphere or torus SDF + noise); the
+    grid's vertex positions and tet indices are shared on the device by the
+    scenes of one resolution."""
     import torch
 
     import synth
     from paper_2406_01579_b300 import SceneTensors
-    out = []
+    out, grid = [], {}
     for n in n_list:
         V, T, f, rgb = synth.random_scene(rng, int(n), "sphere" if rng.uniform() < 0.5 else "torus")
-        out.append(SceneTensors(*(torch.from_numpy(x).to(dev) for x in (V, T, f, rgb))))
+        if int(n) not in grid:
+            grid[int(n)] = (torch.from_numpy(V).to(dev), torch.from_numpy(T).to(dev))
+        Vd, Td = grid[int(n)]
+        out.append(SceneTensors(Vd, Td, torch.from_numpy(f).to(dev), torch.from_numpy(rgb).to(dev)))
     return out
 
 
@@ -546,10 +745,12 @@ def quick_serve(a, big_scene, dev, n_requests=300, rate=200.0):
     rng = np.random.default_rng(44)
     scenes = [big_scene] + resident_scenes(rng, [32, 48, 64, 96, 32, 48, 64], dev)
     srv = Server(scenes, Params(s=a.s, tile=a.tile), hbm_budget=120e9, max_views=16, streams=3)
-    srv.run(poisson_requests(np.random.default_rng(1), 48, rate, len(scenes)))   # warm-up
-    srv.run(poisson_requests(np.random.default_rng(3), 100, 4 * rate, len(scenes)))
-    reqs = poisson_requests(np.random.default_rng(2), n_requests, rate, len(scenes))
-    _, stats = srv.run(reqs)
+    srv.run(poisson_requests(np.random.default_rng(1), 48, rate, len(scenes), pinned=True),
+            on_result=lambda r: None)   # warm-up
+    srv.run(poisson_requests(np.random.default_rng(3), 100, 4 * rate, len(scenes), pinned=True),
+            on_result=lambda r: None)
+    reqs = poisson_requests(np.random.default_rng(2), n_requests, rate, len(scenes), pinned=True)
+    _, stats = srv.run(reqs, on_result=lambda r: None)
     stats.update({"rate_req_s": rate, "scenes": len(scenes),
                   "mix": "views 256..1024 px, 30% fwd+bwd, 128^3 + 7 scenes of 32..96^3"})
     return stats
@@ -568,7 +769,7 @@ def oracle_step(sc, view_ids, a, upstream):
     px = 0
     for v in view_ids:
         cam = sc.cams[v]
-        bins = oracle.bin_view(surv, sc.T, sc.V, cam, a.tile)
+        bins = oracle.bin_view(surv, sc.T, sc.V, cam, a.tile, hull=bool(a.hull))
         oracle.render(sc.V, sc.T, sc.f, sc.rgb, cam, op, surv=surv, bins=bins, upstream=upstream[v])
         px += cam.width * cam.height
     return px
@@ -624,11 +825,11 @@ def run_reference(a):
     print(json.dumps(out))
 
 
-def run_batched(a):
+def run_batched(a, emit=True, steps=None):
     """16 scenes of uneven resolution (32..128)^3, 1-8 views each at
     256^2..1024^2, tile size autotuned, one CUDA graph per step (pre-filter +
     forward + backward of all views); compared with the plain single-view
-    path on the same views."""
+    path on the same views.  Prints its JSON line (emit) or returns it."""
     import torch
 
     import synth
@@ -659,8 +860,9 @@ def run_batched(a):
         g.replay()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nsteps = steps or a.steps
     e0.record()
-    for _ in range(a.steps):
+    for _ in range(nsteps):
         g.replay()
     e1.record()
     torch.cuda.synchronize()
@@ -686,26 +888,33 @@ def run_batched(a):
     plain_step()
     torch.cuda.synchronize()
     e0.record()
-    for _ in range(max(2, a.steps // 4)):
+    nplain = max(2, nsteps // 4)
+    for _ in range(nplain):
         plain_step()
     e1.record()
     torch.cuda.synchronize()
-    tp = e0.elapsed_time(e1) / 1e3 / max(2, a.steps // 4)
+    tp = e0.elapsed_time(e1) / 1e3 / nplain
     info = r.info()
-    print(json.dumps({
-        "metric": METRIC, "value": px * a.steps / t / 1e6, "unit": UNIT, "n_gpus": 1,
-        "steps": a.steps, "ms_per_step": t / a.steps * 1e3, "higher_is_better": True,
+    rec = {
+        "metric": METRIC, "value": px * nsteps / t / 1e6, "unit": UNIT, "n_gpus": 1,
+        "steps": nsteps, "ms_per_step": t / nsteps * 1e3, "higher_is_better": True,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched uneven: 16 scenes n={ns}, {len(views)} views "
                                f"256..1024 px, s={a.s:g}, one CUDA graph per step",
                    "tile": best, "autotune_ms": times},
-        "plain_path_mpix_s": px / tp / 1e6, "status": int(info.status),
-        "keys": int(info.n_keys)}))
+        "plain_path_mpix_s": px / tp / 1e6, "batched_vs_plain": (px * nsteps / t) / (px / tp),
+        "status": int(info.status), "keys": int(info.n_keys)}
+    del g, r, plains, scenes
+    torch.cuda.empty_cache()
+    if emit:
+        print(json.dumps(rec))
+    return rec
 
 
-def run_serve(a):
+def run_serve(a, emit=True, requests=None):
     """Serving: 64 resident scenes (32..128)^3, Poisson arrivals, 30%
-    forward+backward, views 256^2..1024^2, HBM budget 120 GB."""
+    forward+backward, views 256^2..1024^2, HBM budget 120 GB.  Prints its
+    JSON line (emit) or returns it."""
     import torch
 
     from paper_2406_01579_b300 import Params
@@ -719,19 +928,30 @@ def run_serve(a):
     srv = Server(scenes, Params(s=a.s, tile=tile), hbm_budget=120e9, max_views=16, streams=3)
     # warm-up: batches as large as the highest rate makes them, so the slots'
     # buffers have grown before the timed runs
-    srv.run(poisson_requests(np.random.default_rng(1), 64, 500.0, len(scenes)))
-    srv.run(poisson_requests(np.random.default_rng(3), 300, 4000.0, len(scenes)))
+    srv.run(poisson_requests(np.random.default_rng(1), 64, 500.0, len(scenes), pinned=True),
+            on_result=lambda r: None)
+    srv.run(poisson_requests(np.random.default_rng(3), 300, 4000.0, len(scenes), pinned=True),
+            on_result=lambda r: None)
     out = []
+    nreq = requests or a.serve_requests
     for rate in [float(x) for x in a.serve_rates.split(",")]:
-        reqs = poisson_requests(np.random.default_rng(int(rate)), a.serve_requests, rate, len(scenes))
-        _, st = srv.run(reqs)
+        reqs = poisson_requests(np.random.default_rng(int(rate)), nreq, rate, len(scenes),
+                                pinned=True)
+        _, st = srv.run(reqs, on_result=lambda r: None)
         st["rate_req_s"] = rate
         out.append(st)
-    print(json.dumps({"metric": "serve p50/p99 latency (ms) and Mpixel/s", "unit": "ms",
-                      "config": {"workload": f"serve: 64 resident scenes n={sorted(set(ns))}, "
-                                             "views 256..1024 px, 30% fwd+bwd, budget 120 GB",
-                                 "requests_per_rate": a.serve_requests, "tile": tile},
-                      "rates": out}))
+        del reqs
+    rec = {"metric": "serve p50/p99 latency (ms) and Mpixel/s", "unit": "ms",
+           "config": {"workload": f"serve: 64 resident scenes n={sorted(set(ns))}, "
+                                  "views 256..1024 px, 30% fwd+bwd, budget 120 GB, "
+                                  "upstream gradients from pinned host tensors",
+                      "requests_per_rate": nreq, "tile": tile},
+           "rates": out}
+    del srv, scenes
+    torch.cuda.empty_cache()
+    if emit:
+        print(json.dumps(rec))
+    return rec
 
 
 def main():
@@ -756,19 +976,39 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
-    alu_peak = 148 * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s FP32
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else \
+        "fallback 6.4 TB/s (of fallback)"
+    import torch
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    alu = measure_alu_peaks(dev)
+    roof = kernel_rooflines(res["kernel_ms"], res["counts"], alu, hbm)
     st = res["stage_ms"]
     dom = max(st, key=st.get)
-    launch_s = {"blend_fwd": st["blend_fwd"], "blend_bwd": st["blend_bwd"]}
-    flops = {"blend_fwd": res["nfrag"] * FWD_FLOP_PER_FRAG,
-             "blend_bwd": res["nfrag"] * BWD_FLOP_PER_FRAG}
-    rk = dom if dom in flops else "blend_bwd"
-    achieved = flops[rk] / (launch_s[rk] / 1e3) / 1e12
-    traffic = KERNEL_TRAFFIC.get(kernel_source_hash(), {}).get(a.tile, {}).get(rk)
-    roofline = {"kernel": rk, "bound": "alu", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": traffic,
-                "peak_source": f"148 SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz (max SM clock)"}
+    # the dominant kernel of the step (by its event-timed duration)
+    top = max((x for x in roof if "frac" in x), key=lambda x: x["ms"])
+    rk = top["kernel"]
+    traffic = KERNEL_TRAFFIC.get(kernel_source_hash(), {}).get(a.tile, {}).get(
+        rk.replace("k_", "", 1))
+    if top["bound"] == "alu":
+        roofline = {"kernel": rk, "bound": "alu", "achieved": top["achieved"],
+                    "peak": alu["fma_tflops"], "unit": "TFLOP/s", "frac": top["frac"],
+                    "traffic": traffic,
+                    "fma": {"achieved_tflops": top["achieved"], "peak_tflops": alu["fma_tflops"],
+                            "frac": top["fma_frac"]},
+                    "mufu": {"achieved_gops": top["mufu_gops"], "peak_gops": alu["mufu_gops"],
+                             "frac": top["mufu_frac"]},
+                    "peak_source": "measured by this benchmark (FMA and ex2/rcp chains, "
+                                   "libtets_peaks.so), of measured",
+                    "ms_per_launch": top["ms"]}
+    else:
+        roofline = {"kernel": rk, "bound": "hbm", "achieved": top["achieved"], "peak": hbm,
+                    "unit": "GB/s", "frac": top["frac"], "traffic": traffic,
+                    "peak_source": hbm_src, "ms_per_launch": top["ms"]}
+    workloads = None
+    if not a.no_workloads and world == 1:
+        workloads = {"batched_uneven": run_batched(a, emit=False, steps=max(5, a.steps // 4)),
+                     "serve": run_serve(a, emit=False, requests=a.line_serve_requests)}
     out = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup,
@@ -780,6 +1020,10 @@ def main():
                    "parallelism": f"dp{world} (own views per GPU; vertex gradients all-reduced)",
                    "tile_autotune_ms_per_step": res.get("autotune_ms")},
         "roofline": roofline,
+        "rooflines": roof,
+        "alu_peaks": alu,
+        "hbm_peak_source": hbm_src,
+        "step_counts": res["counts"],
         "stage_ms": st, "dominant_stage": dom,
         "plain_path_mpix_s": res.get("plain"),
         "graph_mpix_s": res.get("graph"),
@@ -791,6 +1035,8 @@ def main():
         "mtet_per_s": 12582912 * a.steps / res["elapsed"] / 1e6,
         "clocks": res["clocks"],
     }
+    if workloads is not None:
+        out["workloads"] = workloads
     if "extras" in res:
         out["extras"] = res["extras"]
     if "e2e" in res:

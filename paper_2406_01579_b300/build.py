@@ -13,6 +13,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libtets.so")
 SOURCES = ["bin.cu", "blend.cu", "api.cu", "sort_noalloc.cu", "regularize.cu", "marching.cu"]
+# ALU peak microbenchmarks for the roofline (a library of their own)
+PEAKS_LIB = os.path.join(HERE, "libtets_peaks.so")
+PEAKS_SOURCE = "peaks.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 
@@ -25,9 +28,9 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PEAKS_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
@@ -37,6 +40,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objdir = os.path.join(ROOT, "_build")
     os.makedirs(objdir, exist_ok=True)
     procs, objs = [], []
+    ptmp = PEAKS_LIB + ".tmp"
+    procs.append(subprocess.Popen(["nvcc", *ARCH, *FLAGS, "-shared", "-o", ptmp,
+                                   os.path.join(CSRC, PEAKS_SOURCE), "-lcudart"]))
     for src in SOURCES:
         obj = os.path.join(objdir, src.replace(".cu", ".o"))
         objs.append(obj)
@@ -50,6 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp"
     subprocess.check_call(["nvcc", *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
     os.replace(tmp, LIB)
+    os.replace(ptmp, PEAKS_LIB)
     return LIB
 
 
