@@ -67,7 +67,11 @@ def parse():
     ap.add_argument("--tile", type=int, default=0,
                     help="tile edge 8, 16 or 32; 0: picked by the library's autotuner on this batch")
     ap.add_argument("--blend-segment", type=int, default=0,
-                    help="list entries per backward segment (0: library default)")
+                    help="list entries per backward segment (0: autotuned, or the library "
+                         "default with --tile)")
+    ap.add_argument("--blend-warps", type=int, default=0,
+                    help="warps per block of the blend kernels (0: autotuned, or the library "
+                         "default with --tile)")
     ap.add_argument("--hull", type=int, default=0, choices=[0, 1],
                     help="tile test against the projected tet (1) or bbox rects only (0)")
     ap.add_argument("--res", type=int, default=512)
@@ -90,7 +94,8 @@ def parse():
 
 def workload_name(a):
     return (f"spheres128: 128^3 grid x6 tets (12,582,912 tets, 2,146,689 vertices), "
-            f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}"
+            f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}, "
+            f"backward segment {a.blend_segment or 256}, {a.blend_warps or 4} warps per blend block"
             f"{', hull test' if a.hull else ', bbox rects'}")
 
 
@@ -192,13 +197,20 @@ def run_ours(a, rank, world):
     st = SceneTensors(*(torch.from_numpy(x).to(dev) for x in (sc.V, sc.T, sc.f, sc.rgb)))
     tune = None
     if a.tile == 0:
-        from paper_2406_01579_b300.autotune import autotune_tile
-        best, times = autotune_tile([st], [(c, 0) for c in sc.cams],
-                                    Params(s=a.s, blend_segment=a.blend_segment, hull=bool(a.hull)),
-                                    cache_path=None)
-        a.tile = best
-        tune = {str(k): round(v, 4) for k, v in times.items()}
-    params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment, hull=bool(a.hull))
+        # the library's autotuner: tile, then backward segment, then warps per block
+        from paper_2406_01579_b300.autotune import autotune
+        best, times = autotune([st], [(c, 0) for c in sc.cams],
+                               Params(s=a.s, hull=bool(a.hull)), cache_path=None)
+        a.tile = best["tile"]
+        if a.blend_segment == 0:
+            a.blend_segment = best["blend_segment"]
+        if a.blend_warps == 0:
+            a.blend_warps = best["blend_warps"]
+        tune = {"picked": best,
+                "ms_per_step": {k: {str(c): round(t, 4) for c, t in v.items()}
+                                for k, v in times.items()}}
+    params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment, hull=bool(a.hull),
+                    blend_warps=a.blend_warps)
     r = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
     r.forward()
     r.shrink_to_fit(1.15)
@@ -834,7 +846,7 @@ def run_batched(a, emit=True, steps=None):
 
     import synth
     from paper_2406_01579_b300 import Params, Rasterizer
-    from paper_2406_01579_b300.autotune import autotune_tile
+    from paper_2406_01579_b300.autotune import autotune
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(3)
     ns = [int(rng.choice([32, 48, 64, 96, 128])) for _ in range(16)]
@@ -845,8 +857,8 @@ def run_batched(a, emit=True, steps=None):
             res = int(rng.choice([256, 512, 768, 1024]))
             views.append((synth.random_camera(rng, res, res), si))
     params = Params(s=a.s)
-    best, times = autotune_tile(scenes, views, params, reps=2, cache_path=None)
-    params = Params(s=a.s, tile=best)
+    best, times = autotune(scenes, views, params, reps=2, cache_path=None)
+    params = Params(s=a.s, **best)
     r = Rasterizer(scenes, views, params)
     r.forward()
     r.shrink_to_fit(1.15)
@@ -901,7 +913,9 @@ def run_batched(a, emit=True, steps=None):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batched uneven: 16 scenes n={ns}, {len(views)} views "
                                f"256..1024 px, s={a.s:g}, one CUDA graph per step",
-                   "tile": best, "autotune_ms": times},
+                   "autotune": {"picked": best,
+                                "ms_per_step": {k: {str(c): round(t, 3) for c, t in v.items()}
+                                                for k, v in times.items()}}},
         "plain_path_mpix_s": px / tp / 1e6, "batched_vs_plain": (px * nsteps / t) / (px / tp),
         "status": int(info.status), "keys": int(info.n_keys)}
     del g, r, plains, scenes
@@ -1018,7 +1032,7 @@ def main():
                    "l2": "inputs larger than L2 (tet indices 201 MB, per-step records "
                          f"{res['n_surv'] * a.views * 96 / 1e6:.0f} MB)",
                    "parallelism": f"dp{world} (own views per GPU; vertex gradients all-reduced)",
-                   "tile_autotune_ms_per_step": res.get("autotune_ms")},
+                   "autotune": res.get("autotune_ms")},
         "roofline": roofline,
         "rooflines": roof,
         "alu_peaks": alu,

@@ -128,6 +128,9 @@ typedef struct {
                              entries; the backward walks the segments of a longer list in
                              parallel from those states (equal to the unsplit walk up to
                              FP32 rounding).  Ignored with a resort window. */
+  int32_t blend_warps;    /* warps per block of the persistent blend kernels: 0 (library
+                             default, 4), 2, 4 or 8 (the resort-window kernels always use 4).
+                             Changes the scheduling only, not the result. */
 } tts_params;
 
 /* One scene: caller-owned device arrays (must outlive every call using them). */

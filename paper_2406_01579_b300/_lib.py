@@ -43,7 +43,8 @@ class tts_params(ctypes.Structure):
     _fields_ = [("s", ctypes.c_float), ("prefilter_thresh", ctypes.c_float),
                 ("alpha_skip", ctypes.c_float), ("alpha_cap", ctypes.c_float),
                 ("t_eps", ctypes.c_float), ("tile", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("resort_window", ctypes.c_int32), ("blend_segment", ctypes.c_int32)]
+                ("resort_window", ctypes.c_int32), ("blend_segment", ctypes.c_int32),
+                ("blend_warps", ctypes.c_int32)]
 
 
 class tts_scene(ctypes.Structure):

@@ -1,9 +1,18 @@
-"""Tile-size autotuner.
+"""Autotuner of the launch configuration.
 
 Times a whole step (pre-filter + forward + backward, or forward only) of the
-actual batch for each candidate tile size and keeps the fastest.  Decisions
-are cached in a JSON file keyed by the batch shape: the sorted view sizes,
-the survivor count (two significant digits) and s.
+actual batch for each candidate and keeps the fastest:
+
+  autotune_tile  the tile size (8, 16, 32);
+  autotune       a coordinate search over the tile size (library defaults
+                 otherwise), then the backward's list-segment length for the
+                 best tile, then the warps per block of the blend kernels for
+                 both (the knobs that change the scheduling, not the result).
+
+The hot path's per-tile depth sort is a comparison (merge) sort, so it has
+no digit-width knob.  Decisions are cached in a JSON file (when a path is
+given) keyed by the batch shape: the sorted view sizes, the survivor count
+(two significant digits), s and the searched knobs.
 """
 
 from __future__ import annotations
@@ -92,3 +101,69 @@ def autotune_tile(scenes, views, params: Params, candidates=(8, 16, 32), with_ba
             json.dump(cache, fh, indent=1)
         os.replace(tmp, cache_path)
     return best, times
+
+
+def _load_cache(path):
+    if path and os.path.exists(path):
+        try:
+            return json.load(open(path))
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store_cache(path, cache):
+    if not path:
+        return
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1)
+    os.replace(tmp, path)
+
+
+def autotune(scenes, views, params: Params, tiles=(8, 16, 32), segments=(128, 256, 512),
+             warps=(2, 4, 8), with_backward=True, reps: int = 5,
+             cache_path: str | None = DEFAULT_CACHE):
+    """Coordinate search of (tile, blend_segment, blend_warps): the tile with
+    the library defaults for the others, then the segment length at that
+    tile, then the warps per block at both.  Returns ({"tile", "blend_segment",
+    "blend_warps"}, {knob: {candidate: ms per step}}).  Uses and updates the
+    cache."""
+    probe = Rasterizer(scenes, views, dataclasses.replace(params, tile=16))
+    probe.forward()
+    n_surv = int(sum(probe.info().n_surv[i] for i in range(len(scenes))))
+    del probe
+    key = json.dumps({"shape": shape_key(views, n_surv, params, with_backward),
+                      "tiles": list(tiles), "segments": list(segments), "warps": list(warps)},
+                     sort_keys=True)
+    cache = _load_cache(cache_path)
+    if key in cache:
+        c = cache[key]
+        return dict(c["best"]), {k: {int(a): b for a, b in v.items()} for k, v in c["ms"].items()}
+
+    def time_cfg(**kw):
+        p = dataclasses.replace(params, forward_only=not with_backward, **kw)
+        r = Rasterizer(scenes, views, p)
+        r.forward()
+        r.shrink_to_fit(1.25)
+        r.forward()
+        t = _time_step(r, with_backward, reps)
+        del r
+        return t
+
+    best = {"tile": int(params.tile), "blend_segment": 0, "blend_warps": 0}
+    ms = {"tile": {}, "blend_segment": {}, "blend_warps": {}}
+    for t in tiles:
+        ms["tile"][t] = time_cfg(tile=t, blend_segment=0, blend_warps=0)
+    best["tile"] = min(ms["tile"], key=ms["tile"].get)
+    for g in segments:
+        ms["blend_segment"][g] = time_cfg(tile=best["tile"], blend_segment=g, blend_warps=0)
+    best["blend_segment"] = min(ms["blend_segment"], key=ms["blend_segment"].get)
+    for w in warps:
+        ms["blend_warps"][w] = time_cfg(tile=best["tile"], blend_segment=best["blend_segment"],
+                                        blend_warps=w)
+    best["blend_warps"] = min(ms["blend_warps"], key=ms["blend_warps"].get)
+    cache[key] = {"best": best, "ms": {k: {str(a): b for a, b in v.items()} for k, v in ms.items()}}
+    _store_cache(cache_path, cache)
+    return best, ms

@@ -115,6 +115,8 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   if (pr.blend_segment != 0 &&
       (pr.blend_segment < 32 || pr.blend_segment > 65536 || pr.blend_segment % 32 != 0))
     return TTS_ERR_ARG;
+  if (!(pr.blend_warps == 0 || pr.blend_warps == 2 || pr.blend_warps == 4 || pr.blend_warps == 8))
+    return TTS_ERR_ARG;
   if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS |
                    TTS_FLAG_HULL))
     return TTS_ERR_ARG;
@@ -316,9 +318,11 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.tile = pr.tile;
   H.window = pr.resort_window;
   H.normals = normals;
+  H.hull = (pr.flags & TTS_FLAG_HULL) != 0;
   H.normal_blocks = (int)std::min<long long>((max_surv + 255) / 256, 8LL * sm_count());
   H.tet_bwd_blocks = 2 * sm_count();
-  blend_grid(pr.tile, normals, pr.resort_window, sm_count(), &H.blend_fwd_blocks,
+  H.blend_warps = pr.blend_warps > 0 ? pr.blend_warps : 4;
+  blend_grid(pr.tile, normals, pr.resort_window, H.blend_warps, sm_count(), &H.blend_fwd_blocks,
              &H.blend_bwd_blocks);
   H.total_pixels = pix;
   return TTS_OK;

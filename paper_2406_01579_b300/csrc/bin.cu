@@ -388,6 +388,7 @@ __device__ __forceinline__ int warp_bucket_add(int* bucket, int gt, unsigned act
 // ---------------------------------------------------------------------------
 constexpr int PP_SMEM_VIEWS = 16;
 
+template <bool HULL>
 __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
@@ -418,7 +419,6 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
   __syncthreads();
   const float s = B->s;
   const int tsh = __ffs(B->tile) - 1;   // tile is 8, 16 or 32
-  const bool hull = (B->flags & TTS_FLAG_HULL) != 0;
   unsigned zmn = 0xffffffffu, zmx = 0u;
   for (int q = threadIdx.x; q < PRE_CHUNK; q += PRE_THREADS) {
     const int k = k0 + q;
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
         const long long slot = vw.rec_base + k;
         Geo G;
         float pu[4], pv[4];
-        G.visible = key_path(vw, in, G, pu, pv);
+        G.visible = HULL ? key_path(vw, in, G, pu, pv) : key_path(vw, in, G);
         if (G.visible) tet_geometry_rest(vw, in, G);   // may find a flat tet (not visible)
         if (G.visible) {
           tx0 = G.i0 >> tsh;     // pixel bounds are >= 0
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
           nt = ntx * (ty1 - ty0 + 1);
           write_record(vw, s, in, G, colour, B->rec + slot * REC_Q);
           // the hull test after the record (most of the geometry is dead by then)
-          if (hull) {
+          if constexpr (HULL) {
             mask = hull_tile_mask(pu, pv, G, tsh, tx0, ty0, ntx, ty1 - ty0 + 1);
             if (mask == 0u) nt = 0;   // no pixel centre of the bbox inside the hull
           }
@@ -1098,7 +1098,10 @@ int launch_prefilter(const HostPlan& P, const Batch* dB, cudaStream_t st) {
 int launch_binning(const HostPlan& P, const Batch* dB, cudaStream_t st) {
   launch_k(k_fwd_reset, dim3(64), dim3(256), 0, st, dB);
   dim3 g(P.max_pp_chunks, P.n_views);
-  launch_k(k_preprocess, dim3(P.max_pre_chunks, P.n_scenes), dim3(PRE_THREADS), 0, st, dB);
+  if (P.hull)
+    launch_k(k_preprocess<true>, dim3(P.max_pre_chunks, P.n_scenes), dim3(PRE_THREADS), 0, st, dB);
+  else
+    launch_k(k_preprocess<false>, dim3(P.max_pre_chunks, P.n_scenes), dim3(PRE_THREADS), 0, st, dB);
   launch_k(k_tile_scan, dim3((P.total_tiles + TS_TILES - 1) / TS_TILES), dim3(TS_THREADS), 0, st, dB);
   launch_k(k_place, dim3(g), dim3(PP_THREADS), 0, st, dB);
   launch_k(k_tile_sort, dim3(P.tsort_blocks), dim3(TSORT_NT), 0, st, dB);

@@ -5,7 +5,8 @@
 
 namespace tts {
 
-constexpr int WPB = 4;              // warps per block of the persistent blend kernels
+constexpr int WPB = 4;              // warps per block of the resort-window blend kernels and the
+                                    // default of the others (tts_params.blend_warps: 2, 4 or 8)
 constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ int find_view(const Batch* __restrict__ B, int gt) {
@@ -460,17 +461,17 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
 // front to back (fwd_walk).  Units of the backward's later list segments
 // (segment index > 0) have no forward work.
 // ---------------------------------------------------------------------------
-template <int TILE, bool NRM>
-__global__ void __launch_bounds__(WPB * 32) k_blend_fwd(const Batch* __restrict__ B,
-                                                       float* __restrict__ image,
-                                                       float* __restrict__ alpha,
-                                                       float* __restrict__ depth,
-                                                       float* __restrict__ normal) {
+template <int TILE, bool NRM, int NW>
+__global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__ B,
+                                                      float* __restrict__ image,
+                                                      float* __restrict__ alpha,
+                                                      float* __restrict__ depth,
+                                                      float* __restrict__ normal) {
   pdl_wait();
   pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  __shared__ float4 st[WPB][REC_Q + NRM][32];
-  __shared__ int sidx[WPB][32];
+  __shared__ float4 st[NW][REC_Q + NRM][32];
+  __shared__ int sidx[NW][32];
   const int wid = threadIdx.x >> 5;
   Counters* c = B->ctr;
   const unsigned* __restrict__ vals = B->vals;
@@ -707,19 +708,19 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
 // (per contributing lane, one vector atomic per field group) into the
 // per-slot record gradient buffer.
 // ---------------------------------------------------------------------------
-template <int TILE, bool NRM>
-__global__ void __launch_bounds__(WPB * 32) k_blend_bwd(const Batch* __restrict__ B,
-                                                       const float* __restrict__ dimage,
-                                                       const float* __restrict__ dalpha,
-                                                       const float* __restrict__ ddepth,
-                                                       const float* __restrict__ dnormal,
-                                                        GradOut zg) {
+template <int TILE, bool NRM, int NW>
+__global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__ B,
+                                                      const float* __restrict__ dimage,
+                                                      const float* __restrict__ dalpha,
+                                                      const float* __restrict__ ddepth,
+                                                      const float* __restrict__ dnormal,
+                                                       GradOut zg) {
   pdl_wait();
   pdl_launch_dependents();
   constexpr int SB = (TILE / 8) * (TILE / 4);
-  __shared__ float4 st[WPB][REC_Q + NRM][32];
-  __shared__ int sidx[WPB][32];
-  __shared__ unsigned sslot[WPB][32];
+  __shared__ float4 st[NW][REC_Q + NRM][32];
+  __shared__ int sidx[NW][32];
+  __shared__ unsigned sslot[NW][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned ltm = (1u << lane) - 1u;
   Counters* c = B->ctr;
@@ -1247,44 +1248,64 @@ __global__ void __launch_bounds__(256) k_zero_grads(const Batch* __restrict__ B,
 // launchers
 // ---------------------------------------------------------------------------
 template <typename K>
-static int occ_blocks(K kern, int sms) {
+static int occ_blocks(K kern, int threads, int sms) {
   int per = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, WPB * 32, 0) != cudaSuccess || per < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0) != cudaSuccess || per < 1)
     per = 4;
   return per * sms;
 }
 
-template <int TILE, bool NRM>
+template <int TILE, bool NRM, int NW>
 static void blend_grid_t(int sms, int window, int* fwd_blocks, int* bwd_blocks) {
   if (window > 0) {
-    *fwd_blocks = occ_blocks(k_blend_fwd_win<TILE, NRM>, sms);
-    *bwd_blocks = occ_blocks(k_blend_bwd_win<TILE, NRM>, sms);
+    *fwd_blocks = occ_blocks(k_blend_fwd_win<TILE, NRM>, WPB * 32, sms);
+    *bwd_blocks = occ_blocks(k_blend_bwd_win<TILE, NRM>, WPB * 32, sms);
   } else {
-    *fwd_blocks = occ_blocks(k_blend_fwd<TILE, NRM>, sms);
-    *bwd_blocks = occ_blocks(k_blend_bwd<TILE, NRM>, sms);
+    *fwd_blocks = occ_blocks(k_blend_fwd<TILE, NRM, NW>, NW * 32, sms);
+    *bwd_blocks = occ_blocks(k_blend_bwd<TILE, NRM, NW>, NW * 32, sms);
   }
 }
 
-void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, int* bwd_blocks) {
-  static int cache[3][2][2][2] = {};
+// warps per block of the main blend kernels: 2, 4 or 8
+static int warps_index(int warps) { return warps == 2 ? 0 : warps == 8 ? 2 : 1; }
+
+template <int TILE, bool NRM>
+static void blend_grid_w(int warps, int sms, int window, int* f, int* b) {
+  switch (warps_index(warps)) {
+    case 0: blend_grid_t<TILE, NRM, 2>(sms, window, f, b); break;
+    case 2: blend_grid_t<TILE, NRM, 8>(sms, window, f, b); break;
+    default: blend_grid_t<TILE, NRM, 4>(sms, window, f, b); break;
+  }
+}
+
+void blend_grid(int tile, bool normals, int window, int warps, int sms, int* fwd_blocks,
+                int* bwd_blocks) {
+  static int cache[3][2][2][3][2] = {};
   const int ti = (tile == 8) ? 0 : (tile == 16) ? 1 : 2;
   const int ni = normals ? 1 : 0, wi = (window > 0) ? 1 : 0;
-  int* c = cache[ti][ni][wi];
+  int* c = cache[ti][ni][wi][warps_index(warps)];
   if (c[0] > 0) {
     *fwd_blocks = c[0];
     *bwd_blocks = c[1];
     return;
   }
   switch (tile * 2 + ni) {
-    case 16: blend_grid_t<8, false>(sms, window, fwd_blocks, bwd_blocks); break;
-    case 17: blend_grid_t<8, true>(sms, window, fwd_blocks, bwd_blocks); break;
-    case 32: blend_grid_t<16, false>(sms, window, fwd_blocks, bwd_blocks); break;
-    case 33: blend_grid_t<16, true>(sms, window, fwd_blocks, bwd_blocks); break;
-    case 64: blend_grid_t<32, false>(sms, window, fwd_blocks, bwd_blocks); break;
-    default: blend_grid_t<32, true>(sms, window, fwd_blocks, bwd_blocks); break;
+    case 16: blend_grid_w<8, false>(warps, sms, window, fwd_blocks, bwd_blocks); break;
+    case 17: blend_grid_w<8, true>(warps, sms, window, fwd_blocks, bwd_blocks); break;
+    case 32: blend_grid_w<16, false>(warps, sms, window, fwd_blocks, bwd_blocks); break;
+    case 33: blend_grid_w<16, true>(warps, sms, window, fwd_blocks, bwd_blocks); break;
+    case 64: blend_grid_w<32, false>(warps, sms, window, fwd_blocks, bwd_blocks); break;
+    default: blend_grid_w<32, true>(warps, sms, window, fwd_blocks, bwd_blocks); break;
   }
   c[0] = *fwd_blocks;
   c[1] = *bwd_blocks;
+}
+
+template <int TILE, bool NRM, int NW>
+static void fwd_nw(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
+                   float* normal, cudaStream_t st) {
+  launch_k(k_blend_fwd<TILE, NRM, NW>, dim3(P.blend_fwd_blocks), dim3(NW * 32), 0, st, dB, image,
+           alpha, depth, normal);
 }
 
 template <int TILE, bool NRM>
@@ -1295,20 +1316,35 @@ static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha,
     launch_k(k_blend_fwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, image, alpha, depth, normal);
     return 1;
   }
-  launch_k(k_blend_fwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, image, alpha, depth, normal);
+  switch (warps_index(P.blend_warps)) {
+    case 0: fwd_nw<TILE, NRM, 2>(P, dB, image, alpha, depth, normal, st); break;
+    case 2: fwd_nw<TILE, NRM, 8>(P, dB, image, alpha, depth, normal, st); break;
+    default: fwd_nw<TILE, NRM, 4>(P, dB, image, alpha, depth, normal, st); break;
+  }
   return 1;
+}
+
+template <int TILE, bool NRM, int NW>
+static void bwd_nw(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
+                   const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
+  launch_k(k_blend_bwd<TILE, NRM, NW>, dim3(P.blend_bwd_blocks), dim3(NW * 32), 0, st, dB, dimage,
+           dalpha, ddepth, dnormal, zg);
 }
 
 template <int TILE, bool NRM>
 static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                   const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
   const int g = P.blend_bwd_blocks;
-  if (P.window > 0)
+  if (P.window > 0) {
     launch_k(k_blend_bwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth,
              dnormal, zg);
-  else
-    launch_k(k_blend_bwd<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth,
-             dnormal, zg);
+    return;
+  }
+  switch (warps_index(P.blend_warps)) {
+    case 0: bwd_nw<TILE, NRM, 2>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 2: bwd_nw<TILE, NRM, 8>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    default: bwd_nw<TILE, NRM, 4>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+  }
 }
 
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,

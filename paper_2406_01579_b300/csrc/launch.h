@@ -16,9 +16,11 @@ struct HostPlan {
   int tile;
   int window;
   bool normals;
+  bool hull;                // tile test against the projected tet (TTS_FLAG_HULL)
   int normal_blocks;
   int tet_bwd_blocks;
   int blend_fwd_blocks, blend_bwd_blocks;
+  int blend_warps;          // warps per block of the main blend kernels (2, 4 or 8)
   long long total_pixels;
 };
 
@@ -68,6 +70,7 @@ int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaSt
 int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st);
 int launch_upload(const Batch& hb, Batch* dB, cudaStream_t st);
 // persistent grid sizes of the blend kernels for a tile size (occupancy based)
-void blend_grid(int tile, bool normals, int window, int sms, int* fwd_blocks, int* bwd_blocks);
+void blend_grid(int tile, bool normals, int window, int warps, int sms, int* fwd_blocks,
+                int* bwd_blocks);
 
 }  // namespace tts

@@ -40,6 +40,7 @@ class Params:
     normals: bool = False       # also render the Eq. 2 normal map
     blend_segment: int = 0      # list entries per backward work unit (0: library default)
     hull: bool = False          # tile test against the projected tet (fewer keys, same image)
+    blend_warps: int = 0        # warps per block of the blend kernels (0: library default, 4)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -55,6 +56,7 @@ class Params:
                    | (_lib.TTS_FLAG_HULL if self.hull else 0))
         p.resort_window = int(self.resort_window)
         p.blend_segment = int(self.blend_segment)
+        p.blend_warps = int(self.blend_warps)
         return p
 
 

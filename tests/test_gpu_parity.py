@@ -330,3 +330,18 @@ def test_spheres128_full_gradients(spheres128):
     rep = check_gradients([sc], [(c, 0) for c in sc.cams], p, synth.upstream_grads(2, sc.cams),
                           name="spheres128 4x512 tile8")
     assert sum(v["band"] for v in rep["views"]) <= BAND_MAX * 4 * 512 * 512
+
+
+@pytest.mark.parametrize("warps", [2, 8])
+def test_blend_warps_per_block(sphere16, warps):
+    """The blend kernels at 2 and 8 warps per block (the autotuner's other
+    candidates): keys, images and per-element gradients against the oracle,
+    split lists included (segments of 64 entries)."""
+    p = Params(s=175.0, tile=8, blend_warps=warps, blend_segment=64)
+    cam = sphere16.cams[0]
+    gpu = gpu_run([sphere16], [(cam, 0)], p, lists=True)
+    orc = oracle_run(sphere16, cam, p)
+    compare_keys(gpu, orc)
+    assert int(np.diff(gpu["lists"]["ranges"], axis=1).max()) > 64
+    check_gradients([sphere16], [(cam, 0)], p, [synth.upstream_grads(3, [cam])[0]],
+                    name=f"warps{warps}")
