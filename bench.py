@@ -47,7 +47,19 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "f3ecb4a47dfa0e76": {8: {"blend_fwd": 121882112, "blend_bwd": 227429632}},
+    "41e0a04c0da6fa10": {8: {"blend_fwd": 123441536, "blend_bwd": 221243648}},
+}
+
+
+# Issue rate and occupancy of the blend kernels from one `ncu --set full`
+# capture each on the one-view case of this workload (tile 8,
+# profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
+KERNEL_NCU_ONE_VIEW = {
+    "41e0a04c0da6fa10": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.241,
+                      "warp_instructions": 45720375, "ms": 0.1235},
+        "blend_bwd": {"issued_warps_per_scheduler": 0.56, "achieved_occupancy": 0.284,
+                      "warp_instructions": 58891116, "ms": 0.1093}}},
 }
 
 
@@ -771,9 +783,10 @@ def quick_serve(a, big_scene, dev, n_requests=300, rate=200.0):
 # ---------------------------------------------------------------------------
 # the oracle (CPU) on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
-def oracle_step(sc, view_ids, a, upstream):
+def oracle_step(sc, view_ids, a, upstream, nthreads=0, tile=None):
     import oracle
-    op = oracle.make_params(s=float(np.float32(a.s)), tile=a.tile,
+    tile = a.tile if tile is None else tile
+    op = oracle.make_params(s=float(np.float32(a.s)), tile=tile,
                             prefilter_thresh=float(np.float32(1 / 255)),
                             alpha_skip=float(np.float32(1 / 255)),
                             alpha_cap=float(np.float32(0.99)), t_eps=float(np.float32(1e-4)))
@@ -781,8 +794,9 @@ def oracle_step(sc, view_ids, a, upstream):
     px = 0
     for v in view_ids:
         cam = sc.cams[v]
-        bins = oracle.bin_view(surv, sc.T, sc.V, cam, a.tile, hull=bool(a.hull))
-        oracle.render(sc.V, sc.T, sc.f, sc.rgb, cam, op, surv=surv, bins=bins, upstream=upstream[v])
+        bins = oracle.bin_view(surv, sc.T, sc.V, cam, tile, hull=bool(a.hull))
+        oracle.render(sc.V, sc.T, sc.f, sc.rgb, cam, op, surv=surv, bins=bins,
+                      upstream=upstream[v], nthreads=nthreads)
         px += cam.width * cam.height
     return px
 
@@ -806,6 +820,79 @@ def cpu_baseline(a, sc=None, min_seconds=10.0, max_steps=6):
             "kind": "oracle",
             "sample": f"{steps} whole steps of the same workload (pre-filter of the full grid + "
                       f"all {len(views)} views: bin, FP64 render, adjoint); {dt:.1f} s"}
+
+
+def cpu_configs(a, sc3):
+    """The oracle on the three single-GPU configurations, on all host cores
+    and on one thread (the render and its adjoint are the OpenMP part; the
+    pre-filter and the binning run on one thread in both): 16^3 sphere at
+    128^2, 64^3 torus at 512^2, and one of the 4 views of the 128^3 scene
+    (with the pre-filter of the whole grid).  Each entry repeats whole steps
+    until about `budget` seconds; about 25 s in all on 16 cores."""
+    import synth
+    tile = a.tile if a.tile else 8
+    out = {}
+    cases = (("sphere16_128", synth.scene_sphere16(), 16, (1.0, 1.0)),
+             ("torus64_512", synth.scene_torus64(), tile, (2.0, 0.1)),
+             ("spheres128_512_one_view", sc3, tile, (0.1, 0.1)))
+    for name, sc, t, (b_all, b_one) in cases:
+        ups = synth.upstream_grads(2, sc.cams[:1])
+        rec = {}
+        for label, nth, budget in (("all_cores", 0, b_all), ("one_thread", 1, b_one)):
+            t0 = time.perf_counter()
+            px, steps = 0, 0
+            while steps == 0 or (steps < 20 and time.perf_counter() - t0 < budget):
+                px += oracle_step(sc, [0], a, ups, nthreads=nth, tile=t)
+                steps += 1
+            dt = time.perf_counter() - t0
+            rec[label] = {"value": px / dt / 1e6, "unit": UNIT, "ms_per_step": dt / steps * 1e3,
+                          "steps": steps,
+                          "cores": len(os.sched_getaffinity(0)) if nth == 0 else 1}
+        rec["tile"] = t
+        out[name] = rec
+    return out
+
+
+def run_single_views(a, dev):
+    """The two single-view configurations on the GPU (16^3 sphere at 128^2,
+    64^3 torus at 512^2): one view per call, pre-filter + forward + backward,
+    the tile picked by the autotuner.  Each step is timed alone with CUDA
+    events, after a write of 256 MB (more than L2) that evicts the previous
+    step's data."""
+    import torch
+
+    import synth
+    from paper_2406_01579_b300 import Params, Rasterizer, SceneTensors
+    from paper_2406_01579_b300.autotune import autotune_tile
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = {}
+    for name, sc in (("sphere16_128", synth.scene_sphere16()),
+                     ("torus64_512", synth.scene_torus64())):
+        st = SceneTensors(*(torch.from_numpy(x).to(dev) for x in (sc.V, sc.T, sc.f, sc.rgb)))
+        views = [(sc.cams[0], 0)]
+        tile, _ = autotune_tile([st], views, Params(s=a.s), reps=3, cache_path=None)
+        r = Rasterizer([st], views, Params(s=a.s, tile=tile), device=dev)
+        r.forward()
+        r.shrink_to_fit(1.15)
+        o = r._outputs()
+        up = tuple(torch.randn(n, device=dev) for n in (3 * r.total_pixels, r.total_pixels,
+                                                           r.total_pixels))
+        g = [(torch.empty_like(st.V), torch.empty_like(st.f), torch.empty_like(st.rgb))]
+        for _ in range(3):
+            r.step(o, up, g)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.steps)]
+        for e0, e1 in ev:
+            flush.fill_(1.0)
+            e0.record()
+            r.step(o, up, g)
+            e1.record()
+        torch.cuda.synchronize(dev)
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+        out[name] = {"value": r.total_pixels / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                     "steps": len(ev), "tile": tile, "l2": "flushed before every step"}
+        del r, o, g
+    return out
 
 
 def run_reference(a):
@@ -1021,7 +1108,8 @@ def main():
                     "peak_source": hbm_src, "ms_per_launch": top["ms"]}
     workloads = None
     if not a.no_workloads and world == 1:
-        workloads = {"batched_uneven": run_batched(a, emit=False, steps=max(5, a.steps // 4)),
+        workloads = {"single_view": run_single_views(a, torch.device("cuda", 0)),
+                     "batched_uneven": run_batched(a, emit=False, steps=max(5, a.steps // 4)),
                      "serve": run_serve(a, emit=False, requests=a.line_serve_requests)}
     out = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
@@ -1035,6 +1123,7 @@ def main():
                    "autotune": res.get("autotune_ms")},
         "roofline": roofline,
         "rooflines": roof,
+        "ncu_one_view": KERNEL_NCU_ONE_VIEW.get(kernel_source_hash(), {}).get(a.tile),
         "alu_peaks": alu,
         "hbm_peak_source": hbm_src,
         "step_counts": res["counts"],
@@ -1057,6 +1146,7 @@ def main():
         out["e2e"] = res["e2e"]
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, res["sc"])
+        out["cpu_baseline"]["configs"] = cpu_configs(a, res["sc"])
     print(json.dumps(out))
 
 

@@ -677,16 +677,15 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
   const int tx = (W + B - 1) / B;
   const bool want_grad = dimg != nullptr;
   const int64_t HW = (int64_t)H * W;
+  // nthreads > 0 caps this call's team only (no process-wide setting)
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
   const int nth = (nthreads > 0) ? nthreads : omp_get_max_threads();
 #else
   const int nth = 1;
-  (void)nthreads;
 #endif
   (void)nth;
 
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nth)
   for (int j = 0; j < H; ++j) {
     std::vector<Frag> fr;
     PixelResult pr, alt;
