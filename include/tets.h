@@ -94,8 +94,10 @@ enum {
   TTS_FLAG_HULL = 16         /* tile test against the projected tet (Sec. 3.3 culling): a tile
                                 of a tet's bbox rect gets no key when, for some edge of the
                                 convex hull of the four projected vertices, the corner pixel
-                                centres of (tile x bbox) all lie strictly outside it (an exact
-                                FP32 edge function, see the design notes) */
+                                centres of (tile x bbox) all lie strictly outside it (the exact
+                                FP32 edge function fma(bu - au, pv - av, -((bv - av) * (pu - au)))
+                                of hull edge (a, b) at corner p; rects of 2 to 2 x 2 tiles are
+                                tested, others keep every tile) */
 };
 
 #define TTS_MAX_SCENES 64
@@ -314,8 +316,12 @@ int tts_debug_lists(const tts_batch* b, const void** keys, const void** vals,
                     const void** ranges, const void** surv, uint32_t* zmin_bits,
                     int32_t* depth_bits, tts_stream stream);
 
-/* Device pointer to the per-slot records (6 float4 each, see the design
- * notes) and to the per-slot survivor-relative tet index order. */
+/* Device pointer (*records) to the per-slot records of the last binning: 6
+ * float4 per slot (pixel bbox with the front-face count in its signs, the
+ * four face planes' P, A and B terms, the Eq. 1 field terms, mean depth and
+ * colour); slot = the view's record base + survivor index.  A slot whose tet
+ * is not visible in its view holds no defined record.  Does not launch or
+ * synchronise; the pointer stays valid while the workspace does. */
 int tts_debug_records(const tts_batch* b, const void** records, tts_stream stream);
 
 /* Sorts n (key, value) pairs by the low key_bits bits of the key, stably
@@ -323,7 +329,7 @@ int tts_debug_records(const tts_batch* b, const void** records, tts_stream strea
  * LSD radix sort with 8-bit digits (per pass: per-block digit counts, a scan
  * of the counts, a stable scatter), the device radix sort of Sec. 3.3's
  * (tile, depth) keys.  The binning of tts_bin_views does not call it: it
- * orders the same keys per tile on chip (see the design notes), with the
+ * orders the same keys per tile on chip (a merge sort per tile list), with the
  * same result.  keys_in/vals_in (device, n each) are read only;
  * keys_out/vals_out receive the sorted pairs and must not alias the inputs.
  * scratch: device, 256-byte aligned, at least tts_sort_pairs_scratch_size(n)

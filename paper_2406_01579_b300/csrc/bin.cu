@@ -399,6 +399,8 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
   if (k0 >= nsurv) return;
   __shared__ unsigned s_zmn, s_zmx;
   __shared__ int s_left;
+  // each warp's 32 records of the current view, stored out coalesced
+  __shared__ __align__(16) float4 s_rec[PRE_THREADS / 32][32 * REC_Q];
   // the scene's view constants in shared memory (up to PP_SMEM_VIEWS views)
   __shared__ ViewD s_vw[PP_SMEM_VIEWS];
   const int nv = S.view_cnt;
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
           ty1 = G.j1 >> tsh;
           ntx = tx1 - tx0 + 1;
           nt = ntx * (ty1 - ty0 + 1);
-          write_record(vw, s, in, G, colour, B->rec + slot * REC_Q);
+          write_record(vw, s, in, G, colour, &s_rec[threadIdx.x >> 5][(threadIdx.x & 31) * REC_Q]);
           // the hull test after the record (most of the geometry is dead by then)
           if constexpr (HULL) {
             mask = hull_tile_mask(pu, pv, G, tsh, tx0, ty0, ntx, ty1 - ty0 + 1);
@@ -464,6 +466,18 @@ __global__ void __launch_bounds__(PRE_THREADS, 5) k_preprocess(const Batch* __re
                                                tx1 | (int)((mask >> 16) << 16), ty0, ty1)
                                    : make_int4(1, 0, 0, 0);
         B->rec_z[slot] = G.zbits;
+      }
+      // the warp's records: its slots are consecutive (k = k0 + 32 w + lane), the
+      // lanes with k < nsurv a prefix; a record of an invisible slot is never read
+      {
+        __syncwarp();
+        const int lane = threadIdx.x & 31;
+        const int nvalid = __popc(__ballot_sync(0xffffffffu, k < nsurv));
+        const long long slot0 = vw.rec_base + (k - lane);
+        float4* __restrict__ dst = B->rec + slot0 * REC_Q;
+        const float4* srcw = s_rec[threadIdx.x >> 5];
+        for (int i = lane; i < nvalid * REC_Q; i += 32) dst[i] = srcw[i];
+        __syncwarp();
       }
       // key counts per kept tile, one atomic per (warp, tile) and round
       int* __restrict__ cnt = B->tile_cnt + vw.tile_base;
