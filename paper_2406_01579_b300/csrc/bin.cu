@@ -796,15 +796,16 @@ __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], uns
     unsigned long long vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
 #pragma unroll
     for (int q = 0; q < K; ++q) {
+      // branch free: one shared load per output, from the side that advanced
       const bool ta = (i < run) && (j >= run || !(vb < va));
       k[q] = ta ? va : vb;
-      if (ta) {
-        ++i;
-        va = (i < run) ? s[spad(a0 + i)] : ~0ull;
-      } else {
-        ++j;
-        vb = (j < run) ? s[spad(b0 + j)] : ~0ull;
-      }
+      i += ta;
+      j += !ta;
+      const int nx = ta ? i : j;
+      const int e = (ta ? a0 : b0) + nx;
+      const unsigned long long nv = (nx < run) ? s[spad(e)] : ~0ull;
+      va = ta ? nv : va;
+      vb = ta ? vb : nv;
     }
     if (in_warp) __syncwarp();
     else group_sync<NT>(bar);
