@@ -84,6 +84,9 @@ def parse():
     ap.add_argument("--blend-warps", type=int, default=0,
                     help="warps per block of the blend kernels (0: autotuned, or the library "
                          "default with --tile)")
+    ap.add_argument("--frag-cap", type=int, default=0,
+                    help="per-pixel fragment lists for the backward (0: library default, "
+                         "-1: none)")
     ap.add_argument("--hull", type=int, default=0, choices=[0, 1],
                     help="tile test against the projected tet (1) or bbox rects only (0)")
     ap.add_argument("--res", type=int, default=512)
@@ -107,8 +110,10 @@ def parse():
 def workload_name(a):
     return (f"spheres128: 128^3 grid x6 tets (12,582,912 tets, 2,146,689 vertices), "
             f"{a.views} views at {a.res}x{a.res}, s={a.s:g}, tile {a.tile}, "
-            f"backward segment {a.blend_segment or 256}, {a.blend_warps or 4} warps per blend block"
-            f"{', hull test' if a.hull else ', bbox rects'}")
+            f"backward segment {a.blend_segment or 256}, {a.blend_warps or 4} warps per blend block, "
+            + (f"per-pixel fragment lists of {a.frag_cap or 128}" if a.frag_cap >= 0
+               else "no per-pixel fragment lists")
+            + f"{', hull test' if a.hull else ', bbox rects'}")
 
 
 # ---------------------------------------------------------------------------
@@ -218,11 +223,13 @@ def run_ours(a, rank, world):
             a.blend_segment = best["blend_segment"]
         if a.blend_warps == 0:
             a.blend_warps = best["blend_warps"]
+        if a.frag_cap == 0:
+            a.frag_cap = best["frag_cap"]
         tune = {"picked": best,
                 "ms_per_step": {k: {str(c): round(t, 4) for c, t in v.items()}
                                 for k, v in times.items()}}
     params = Params(s=a.s, tile=a.tile, blend_segment=a.blend_segment, hull=bool(a.hull),
-                    blend_warps=a.blend_warps)
+                    blend_warps=a.blend_warps, frag_cap=a.frag_cap)
     r = Rasterizer([st], [(c, 0) for c in sc.cams], params, device=dev)
     r.forward()
     r.shrink_to_fit(1.15)
@@ -327,6 +334,13 @@ def run_ours(a, rank, world):
               "surv_vertices": int(torch.unique(st.T[surv_ids].reshape(-1)).numel()),
               "visible_slots": int(torch.unique(d["vals"]).numel())}
     del d
+    fl = r.debug_frag_lists()
+    if fl is not None:   # the backward's per-pixel fragment lists
+        nbl = fl[1].long()
+        counts.update(blended=int(nbl.sum().item()),
+                      listed_pixels=int(((nbl > 0) & (nbl <= fl[3])).sum().item()),
+                      overflow_pixels=int((nbl > fl[3]).sum().item()), frag_cap=fl[3])
+    del fl
     res = {
         "kernel_ms": kt, "counts": counts,
         "autotune_ms": tune,
@@ -608,6 +622,18 @@ def kernel_rooflines(kt, counts, peaks, hbm_gbs):
         "k_blend_bwd": ("alu", (frag * (BWD_FLOP_PER_FRAG - BWD_MUFU_PER_FRAG),
                                 frag * BWD_MUFU_PER_FRAG)),
     }
+    if "k_blend_bwd_px" in kt:
+        # per-pixel fragment lists: the pixel-list kernel does the backward of
+        # every listed pixel, the list walk only that of pixels past the cap
+        # (the work split by their blended fragments; all of it to the
+        # pixel-list kernel when none is past the cap)
+        share = 1.0
+        if counts.get("overflow_pixels", 0) > 0:
+            share = counts["listed_pixels"] / max(counts["listed_pixels"] + counts["overflow_pixels"], 1)
+        bf, bm = model.pop("k_blend_bwd")[1]
+        model["k_blend_bwd_px"] = ("alu", (bf * share, bm * share))
+        if share < 1.0:
+            model["k_blend_bwd"] = ("alu", (bf * (1 - share), bm * (1 - share)))
     out = []
     for name, ms in sorted(kt.items(), key=lambda x: -x[1]):
         rec = {"kernel": name, "ms": round(ms, 5)}

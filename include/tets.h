@@ -133,6 +133,14 @@ typedef struct {
   int32_t blend_warps;    /* warps per block of the persistent blend kernels: 0 (library
                              default, 4), 2, 4 or 8 (the resort-window kernels always use 4).
                              Changes the scheduling only, not the result. */
+  int32_t frag_cap;       /* per-pixel fragment lists for the backward: 0 (library default,
+                             128), 1..255, or -1 (none).  The forward records, per pixel, the
+                             record slots of up to frag_cap blended fragments (4 bytes each,
+                             frag_cap x pixels of workspace); the backward then walks each
+                             pixel's own fragments back to front, one lane per pixel, and
+                             re-walks the tile lists only for tiles holding a pixel with more
+                             blended fragments.  The same arithmetic per fragment either way.
+                             Unused with a resort window or TTS_FLAG_FORWARD_ONLY. */
 } tts_params;
 
 /* One scene: caller-owned device arrays (must outlive every call using them). */
@@ -300,6 +308,17 @@ int tts_debug_scan_wait(int64_t spin_limit, int32_t unset_block);
  * chord was non-empty, up to where the pixel stopped). */
 int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last,
                      const void** n_frag, tts_stream stream);
+
+/* Device pointers into the workspace to the per-pixel fragment lists of the
+ * last forward (tts_params.frag_cap): *frag (uint32, frag_cap per pixel,
+ * pixel-major: entry i of pixel p at p * frag_cap + i, the record slots of
+ * the pixel's blended fragments in blend order), *n_blend (int32 per pixel:
+ * its blended fragments, possibly more than the list holds) and *tile_over
+ * (int32 per global tile: 1 when a pixel of the tile has more than frag_cap).
+ * All three are null and *frag_cap is 0 when the batch keeps no lists.  Does
+ * not launch or synchronise. */
+int tts_debug_frag_lists(const tts_batch* b, const void** frag, const void** n_blend,
+                         const void** tile_over, int32_t* frag_cap, tts_stream stream);
 
 /* Synchronises the stream and copies the status word and counters. */
 int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream);

@@ -90,7 +90,7 @@ def lib():
         L.orc_fragment_grad.restype = ctypes.c_int
         L.orc_render.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P,
                                  P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int,
-                                 P, P, P, P, P, P, P, P, P, P, P, P, P]
+                                 P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.orc_render.restype = ctypes.c_int
         L.orc_render_dirderiv.argtypes = [i64, P, P, P, P, i64, P, P, P, P, P, P, P, P, P,
                                           P, P, P, P, P, P, P, P]
@@ -195,7 +195,7 @@ def bin_view(surv, T, V, cam, tile: int, hull: bool = False):
 
 def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=None,
            nthreads: int = 0, V64=None, f64=None, rgb64=None, normals: bool = False,
-           branch=None, abs_terms: bool = False):
+           branch=None, abs_terms: bool = False, blend_cap: int = 0):
     """Render one view; returns a dict with image (3,H,W), alpha, depth, amb,
     alt_*, nfrag, the binning lists and (if ``upstream`` = (dimg, dalpha,
     ddepth) is given) the FP64 gradients dV, df, drgb.  ``V64``/``f64``/``rgb64``
@@ -209,7 +209,10 @@ def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=
     change of the fragment's term under the other one-sided derivative, and
     dV_graze (df_graze, drgb_graze zero): per entry the sum over fragments of
     |the term through the opacity| / c^2, c the smaller |cos| between the
-    pixel ray and the chord's entry and exit face normals."""
+    pixel ray and the chord's entry and exit face normals.  ``blend_cap`` > 0:
+    also return nblend (H,W int32: the pixel's blended fragments, primary
+    branch) and blend_slots (H,W,blend_cap int32: the view slots of its first
+    blend_cap blended fragments in blend order, -1 past the end)."""
     V = _c(V, np.float32)
     T = _c(T, np.int32)
     f = _c(f, np.float32)
@@ -249,16 +252,22 @@ def render(V, T, f, rgb, cam, params: OrcParams, surv=None, bins=None, upstream=
     if br is not None:
         assert br.shape == (H, W)
     surv = _c(surv, np.int32)
+    nbl = bsl = None
+    if blend_cap > 0:
+        nbl = np.zeros((H, W), np.int32)
+        bsl = np.full((H, W, blend_cap), -1, np.int32)
     rc = lib().orc_render(N, _p(V), _p(f), _p(rgb), _p(T), len(surv), _p(surv),
                           _p(bins["rect"]), ctypes.byref(c), ctypes.byref(params),
                           _p(bins["key_val"]), _p(bins["ranges"]), _p(img), _p(alpha), _p(depth),
                           _p(amb), _p(aimg), _p(aalpha), _p(adepth), _p(nfrag), _p(gi), _p(ga),
                           _p(gd), _p(dV), _p(df), _p(drgb), nthreads, _p(V64), _p(f64),
                           _p(rgb64), _p(nrm), _p(anrm), _p(gn), _p(br), _p(aV), _p(af),
-                          _p(argb), _p(kV), _p(kf), _p(gzV))
+                          _p(argb), _p(kV), _p(kf), _p(gzV), _p(nbl), _p(bsl), int(blend_cap))
     assert rc == 0
     out = dict(image=img, alpha=alpha, depth=depth, amb=amb, alt_image=aimg, alt_alpha=aalpha,
                alt_depth=adepth, nfrag=nfrag, surv=surv, bins=bins, normal=nrm, alt_normal=anrm)
+    if blend_cap > 0:
+        out.update(nblend=nbl, blend_slots=bsl)
     if upstream is not None:
         out.update(dV=dV, df=df, drgb=drgb)
         if abs_terms:

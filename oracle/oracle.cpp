@@ -670,7 +670,8 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
                const double* V64, const double* f64, const double* rgb64,
                double* nrm, double* alt_nrm, const float* dnrm, const int8_t* branch,
                double* dV_abs, double* df_abs, double* drgb_abs, double* dV_kink,
-               double* df_kink, double* dV_graze) {
+               double* df_kink, double* dV_graze, int32_t* nblend, int32_t* blend_slots,
+               int blend_cap) {
   const OrcCam& c = *cam;
   const Fields fld(N, V, f, rgb, V64, f64, rgb64);
   const int W = c.width, H = c.height, B = p->tile;
@@ -717,8 +718,15 @@ int orc_render(int64_t N, const float* V, const float* f, const float* rgb, cons
           fg.c[q] = 0.25 * (((fld.rgb[3 * t[0] + q] + fld.rgb[3 * t[1] + q]) + fld.rgb[3 * t[2] + q]) + fld.rgb[3 * t[3] + q]);
         fr.push_back(fg);
       }
-      composite(fr, *p, -1, want_grad, &pr);
+      composite(fr, *p, -1, want_grad || nblend != nullptr, &pr);
       const int64_t pix = (int64_t)j * W + i;
+      if (nblend) {
+        // the pixel's blended fragments: how many, and the view slots of the
+        // first blend_cap of them in blend order
+        nblend[pix] = (int32_t)pr.blended.size();
+        for (int q = 0; q < blend_cap && q < (int)pr.blended.size(); ++q)
+          blend_slots[pix * blend_cap + q] = pr.blended[q].s;
+      }
       for (int q = 0; q < 3; ++q) img[q * HW + pix] = pr.C[q];
       if (nrm)
         for (int q = 0; q < 3; ++q) nrm[q * HW + pix] = pr.N[q];

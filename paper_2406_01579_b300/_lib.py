@@ -44,7 +44,7 @@ class tts_params(ctypes.Structure):
                 ("alpha_skip", ctypes.c_float), ("alpha_cap", ctypes.c_float),
                 ("t_eps", ctypes.c_float), ("tile", ctypes.c_int32), ("flags", ctypes.c_int32),
                 ("resort_window", ctypes.c_int32), ("blend_segment", ctypes.c_int32),
-                ("blend_warps", ctypes.c_int32)]
+                ("blend_warps", ctypes.c_int32), ("frag_cap", ctypes.c_int32)]
 
 
 class tts_scene(ctypes.Structure):
@@ -85,7 +85,8 @@ ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
                 "tts_survivor_bounds", "tts_fit_grid", "tts_render_fwd",
                 "tts_render_bwd", "tts_render_fwd_ex", "tts_render_bwd_ex", "tts_bin_views",
                 "tts_blend_fwd", "tts_blend_bwd", "tts_blend_fwd_ex", "tts_blend_bwd_ex",
-                "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_get_info",
+                "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_debug_frag_lists",
+                "tts_get_info",
                 "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
                 "tts_sort_pairs_scratch_size", "tts_sort_pairs",
                 "tts_tet_edges_workspace_size", "tts_tet_edges", "tts_regularizers_workspace_size",
@@ -133,6 +134,8 @@ def load():
     L.tts_scatter_bwd.argtypes = [B, P, P, P, P]
     L.tts_launch_count.argtypes = []
     L.tts_debug_pixels.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
+    L.tts_debug_frag_lists.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                       ctypes.POINTER(ctypes.c_int32), P]
     L.tts_get_info.argtypes = [B, ctypes.POINTER(tts_info), P]
     L.tts_debug_lists.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                   ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint32),

@@ -6,8 +6,9 @@ actual batch for each candidate and keeps the fastest:
   autotune_tile  the tile size (8, 16, 32);
   autotune       a coordinate search over the tile size (library defaults
                  otherwise), then the backward's list-segment length for the
-                 best tile, then the warps per block of the blend kernels for
-                 both (the knobs that change the scheduling, not the result).
+                 best tile, then the warps per block of the blend kernels,
+                 then the backward's per-pixel fragment list capacity (the
+                 knobs that change the scheduling, not the result).
 
 The hot path's per-tile depth sort is a comparison (merge) sort, so it has
 no digit-width knob.  Decisions are cached in a JSON file (when a path is
@@ -123,20 +124,24 @@ def _store_cache(path, cache):
 
 
 def autotune(scenes, views, params: Params, tiles=(8, 16, 32), segments=(128, 256, 512),
-             warps=(2, 4, 8), with_backward=True, reps: int = 5,
+             warps=(2, 4, 8), frag_caps=(128, 32, -1), with_backward=True, reps: int = 5,
              cache_path: str | None = DEFAULT_CACHE):
-    """Coordinate search of (tile, blend_segment, blend_warps): the tile with
-    the library defaults for the others, then the segment length at that
-    tile, then the warps per block at both.  Returns ({"tile", "blend_segment",
-    "blend_warps"}, {knob: {candidate: ms per step}}).  Uses and updates the
+    """Coordinate search of (tile, blend_segment, blend_warps, frag_cap): the
+    tile with the library defaults for the others, then the segment length at
+    that tile, then the warps per block, then the per-pixel fragment list
+    capacity of the backward (-1: none) at all three (forward-only searches
+    skip the last).  Returns ({"tile", "blend_segment", "blend_warps",
+    "frag_cap"}, {knob: {candidate: ms per step}}).  Uses and updates the
     cache."""
     probe = Rasterizer(scenes, views, dataclasses.replace(params, tile=16))
     probe.forward()
     n_surv = int(sum(probe.info().n_surv[i] for i in range(len(scenes))))
     del probe
+    if not with_backward:
+        frag_caps = ()
     key = json.dumps({"shape": shape_key(views, n_surv, params, with_backward),
-                      "tiles": list(tiles), "segments": list(segments), "warps": list(warps)},
-                     sort_keys=True)
+                      "tiles": list(tiles), "segments": list(segments), "warps": list(warps),
+                      "frag_caps": list(frag_caps)}, sort_keys=True)
     cache = _load_cache(cache_path)
     if key in cache:
         c = cache[key]
@@ -152,8 +157,9 @@ def autotune(scenes, views, params: Params, tiles=(8, 16, 32), segments=(128, 25
         del r
         return t
 
-    best = {"tile": int(params.tile), "blend_segment": 0, "blend_warps": 0}
-    ms = {"tile": {}, "blend_segment": {}, "blend_warps": {}}
+    best = {"tile": int(params.tile), "blend_segment": 0, "blend_warps": 0,
+            "frag_cap": int(params.frag_cap)}
+    ms = {"tile": {}, "blend_segment": {}, "blend_warps": {}, "frag_cap": {}}
     for t in tiles:
         ms["tile"][t] = time_cfg(tile=t, blend_segment=0, blend_warps=0)
     best["tile"] = min(ms["tile"], key=ms["tile"].get)
@@ -164,6 +170,11 @@ def autotune(scenes, views, params: Params, tiles=(8, 16, 32), segments=(128, 25
         ms["blend_warps"][w] = time_cfg(tile=best["tile"], blend_segment=best["blend_segment"],
                                         blend_warps=w)
     best["blend_warps"] = min(ms["blend_warps"], key=ms["blend_warps"].get)
+    for fc in frag_caps:
+        ms["frag_cap"][fc] = time_cfg(tile=best["tile"], blend_segment=best["blend_segment"],
+                                      blend_warps=best["blend_warps"], frag_cap=fc)
+    if ms["frag_cap"]:
+        best["frag_cap"] = min(ms["frag_cap"], key=ms["frag_cap"].get)
     cache[key] = {"best": best, "ms": {k: {str(a): b for a, b in v.items()} for k, v in ms.items()}}
     _store_cache(cache_path, cache)
     return best, ms

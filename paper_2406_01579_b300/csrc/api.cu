@@ -117,6 +117,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     return TTS_ERR_ARG;
   if (!(pr.blend_warps == 0 || pr.blend_warps == 2 || pr.blend_warps == 4 || pr.blend_warps == 8))
     return TTS_ERR_ARG;
+  if (pr.frag_cap < -1 || pr.frag_cap > 255) return TTS_ERR_ARG;
   if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS |
                    TTS_FLAG_HULL))
     return TTS_ERR_ARG;
@@ -266,6 +267,16 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   const bool normals = (pr.flags & TTS_FLAG_NORMALS) != 0;
   const size_t o_sn = take(normals ? sizeof(float4) * surv_total : 0);
   const size_t o_pNm = take((normals && !fwd_only) ? sizeof(float4) * pix : 0);
+  // per-pixel fragment lists (slot of each blended fragment, planar by index),
+  // their lengths and the tiles holding a pixel past the cap
+  const int fcap = (fwd_only || pr.resort_window > 0 || pr.frag_cap < 0 || pix > 0xffffffffLL)
+                       ? 0
+                       : (pr.frag_cap == 0 ? kFragCapDefault : pr.frag_cap);
+  B.frag_cap = fcap;
+  const size_t o_frag = take(fcap > 0 ? sizeof(unsigned) * (size_t)fcap * pix : 0);
+  const size_t o_pnb = take(fcap > 0 ? sizeof(int) * pix : 0);
+  const size_t o_tovf = take(fcap > 0 ? sizeof(int) * tiles : 0);
+  const size_t o_pxl = take(fcap > 0 ? sizeof(uint2) * pix : 0);
   P->bytes = align_up(off, 256);
   if (need_ws) {
     if (!b->workspace || (reinterpret_cast<uintptr_t>(b->workspace) % 256) != 0)
@@ -305,6 +316,10 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     B.pix_CD = reinterpret_cast<float4*>(base + o_pC);
     B.surv_n = normals ? reinterpret_cast<float4*>(base + o_sn) : nullptr;
     B.pix_N = (normals && !fwd_only) ? reinterpret_cast<float4*>(base + o_pNm) : nullptr;
+    B.frag = fcap > 0 ? reinterpret_cast<unsigned*>(base + o_frag) : nullptr;
+    B.pix_nb = fcap > 0 ? reinterpret_cast<int*>(base + o_pnb) : nullptr;
+    B.tile_ovf = fcap > 0 ? reinterpret_cast<int*>(base + o_tovf) : nullptr;
+    B.px_list = fcap > 0 ? reinterpret_cast<uint2*>(base + o_pxl) : nullptr;
   }
   HostPlan& H = P->hp;
   H.n_scenes = b->n_scenes;
@@ -322,6 +337,9 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.normal_blocks = (int)std::min<long long>((max_surv + 255) / 256, 8LL * sm_count());
   H.tet_bwd_blocks = 2 * sm_count();
   H.blend_warps = pr.blend_warps > 0 ? pr.blend_warps : 4;
+  H.frag_cap = fcap;
+  H.px_clear = (need_ws && fcap > 0) ? &B.ctr->px_n : nullptr;
+  H.px_blocks = fcap > 0 ? px_grid(pr.tile, normals, sm_count()) : 0;
   blend_grid(pr.tile, normals, pr.resort_window, H.blend_warps, sm_count(), &H.blend_fwd_blocks,
              &H.blend_bwd_blocks);
   H.total_pixels = pix;
@@ -568,6 +586,19 @@ int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last
   if (T_final) *T_final = P.hb.pix_T;
   if (last) *last = P.hb.pix_last;
   if (n_frag) *n_frag = P.hb.pix_nfrag;
+  return TTS_OK;
+}
+
+int tts_debug_frag_lists(const tts_batch* b, const void** frag, const void** n_blend,
+                         const void** tile_over, int32_t* frag_cap, tts_stream stream) {
+  (void)stream;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  if (frag) *frag = P.hb.frag;
+  if (n_blend) *n_blend = P.hb.pix_nb;
+  if (tile_over) *tile_over = P.hb.tile_ovf;
+  if (frag_cap) *frag_cap = P.hb.frag_cap;
   return TTS_OK;
 }
 

@@ -80,8 +80,10 @@ __global__ void k_fwd_reset(const Batch* __restrict__ B) {
   const int nlb = (B->total_tiles + TS_TILES - 1) / TS_TILES;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nlb; t += gridDim.x * blockDim.x)
     B->scan_lb[t] = 0ull;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B->total_tiles; t += gridDim.x * blockDim.x) {
     B->tile_cnt[t] = 0;
+    if (B->tile_ovf) B->tile_ovf[t] = 0;
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -206,11 +206,15 @@ __device__ __forceinline__ void store_normal(const Batch* __restrict__ B, const 
   if (B->pix_N) B->pix_N[vw.pix_base + p] = make_float4(N0, N1, N2, 0.f);
 }
 
-// Per-pixel compositing state of the forward.
+// Per-pixel compositing state of the forward.  fl: the pixel's fragment list
+// (record slots of its blended fragments, at most frag_cap of them; null when
+// the batch keeps no lists), nb: its blended fragments so far.
 struct FwdState {
   float T, C0, C1, C2, D, N0, N1, N2;
   int last, nfrag;
   bool done;
+  int nb;
+  unsigned* fl;
 };
 
 // Final per-pixel outputs of the forward.
@@ -230,6 +234,13 @@ __device__ __forceinline__ void store_pixel(const Batch* __restrict__ B, const V
   B->pix_last[vw.pix_base + p] = S.last;
   B->pix_nfrag[vw.pix_base + p] = S.nfrag;
   B->pix_CD[vw.pix_base + p] = make_float4(S.C0, S.C1, S.C2, S.D);
+  if (B->pix_nb) {
+    B->pix_nb[vw.pix_base + p] = S.nb;
+    if (S.nb > B->frag_cap) {   // the backward re-walks this tile's list
+      B->tile_ovf[wb.gt] = 1;
+      B->ctr->ovf_any = 1u;
+    }
+  }
   if constexpr (NRM) store_normal(B, vw, p, normal, S.N0, S.N1, S.N2);
 }
 
@@ -243,7 +254,8 @@ constexpr float FRAG_SKIP = -1.f;
 // its code v: counts the chord, blends alpha' or stops the pixel.
 template <bool NRM>
 __device__ __forceinline__ void composite(float v, int k, int base, bool pure, float eps,
-                                          float4 (*st)[32], const int* sidx, FwdState& S) {
+                                          float4 (*st)[32], const int* sidx,
+                                          const unsigned* sslot, int fcap, FwdState& S) {
   if (v == 0.f || S.done) return;
   ++S.nfrag;
   if (v == FRAG_SKIP) return;
@@ -267,6 +279,10 @@ __device__ __forceinline__ void composite(float v, int k, int base, bool pure, f
   }
   S.T = Tn;
   S.last = base + sidx[k] + 1;
+  if (S.fl) {
+    if (S.nb < fcap) S.fl[S.nb] = sslot[k];
+    ++S.nb;
+  }
 }
 
 // Eq. 1 with the cap and skip decisions, as a fragment code.
@@ -288,7 +304,8 @@ __device__ __forceinline__ float fragment_code(const float4& q4, const Chord& ch
 // those of its four lanes).  T, done agree over the four lanes.
 template <bool NRM>
 __device__ __forceinline__ void composite4(float v, int k, int base, bool pure, float eps,
-                                           float4 (*st)[32], const int* sidx, FwdState& S) {
+                                           float4 (*st)[32], const int* sidx,
+                                           const unsigned* sslot, int fcap, FwdState& S) {
   const int lane = threadIdx.x & 31, sub = lane & 3, g0 = lane & ~3;
   const bool bl = (v != 0.f) & (v != FRAG_SKIP);
   const float a = bl ? fmaxf(v, 0.f) : 0.f;
@@ -304,6 +321,16 @@ __device__ __forceinline__ void composite4(float v, int k, int base, bool pure, 
   const unsigned sbits = (__ballot_sync(FULL, stop) >> g0) & 0xfu;
   const int f = sbits ? __ffs(sbits) - 1 : 4;     // the first stopping lane (4: none)
   const float Tl = __shfl_sync(FULL, Tn, g0 + max(f - 1, 0));
+  // the pixel's blended fragments of this group, in list (lane) order
+  if (fcap > 0) {   // the same for the whole batch
+    const bool blend = bl && sub < f && !S.done;
+    const unsigned bm = (__ballot_sync(FULL, blend) >> g0) & 0xfu;
+    if (S.fl) {
+      const int at = S.nb + __popc(bm & ((1u << sub) - 1u));
+      if (blend && at < fcap) S.fl[at] = sslot[k];
+      S.nb += __popc(bm);
+    }
+  }
   if (S.done) return;
   S.nfrag += (v != 0.f) && sub <= f;
   if (bl && sub < f) {
@@ -371,7 +398,8 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
                                          const float4* __restrict__ rec,
                                          const float4* __restrict__ nrm, int lo, int hi, int2 ts,
                                          int tt, bool pure, float cap, float skip, float eps,
-                                         float4 (*st)[32], int* sidx, FwdState& S) {
+                                         float4 (*st)[32], int* sidx, unsigned* sslot, int fcap,
+                                         FwdState& S) {
   const int lane = threadIdx.x & 31;
   const int sub = lane & (LPP - 1);
   const unsigned ltm = (1u << lane) - 1u;
@@ -417,6 +445,7 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
         for (int q = 1; q < REC_Q; ++q) st[q][pos] = __ldg(r + q);
         if constexpr (NRM) st[REC_Q][pos] = __ldg(nrm + slot);
         sidx[pos] = lane;
+        sslot[pos] = slot;
       }
       __syncwarp();
       const int cnt = __popc(m);
@@ -431,8 +460,8 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           if (!__any_sync(FULL, (ha || hb) && !S.done)) continue;
           const float va = fragment_code(st[4][ka], cha, pure, cap, skip);
           const float vb = fragment_code(st[4][kb], chb, pure, cap, skip);
-          composite<NRM>(ha ? va : 0.f, ka, base, pure, eps, st, sidx, S);
-          composite<NRM>(hb ? vb : 0.f, kb, base, pure, eps, st, sidx, S);
+          composite<NRM>(ha ? va : 0.f, ka, base, pure, eps, st, sidx, sslot, fcap, S);
+          composite<NRM>(hb ? vb : 0.f, kb, base, pure, eps, st, sidx, sslot, fcap, S);
         } else {
           const int k = min(k0 + sub, cnt - 1);
           const Chord ch = chord_eval(st[0][k], st[1][k], st[2][k], st[3][k], wb.fpx, wb.fpy);
@@ -441,7 +470,7 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           // pixel's exchange); a miss codes 0
           const float code = fragment_code(st[4][k], ch, pure, cap, skip);
           const float mine = h ? code : 0.f;
-          composite4<NRM>(mine, k, base, pure, eps, st, sidx, S);
+          composite4<NRM>(mine, k, base, pure, eps, st, sidx, sslot, fcap, S);
         }
         // with four lanes per pixel a group is short: the walk checks for an
         // all-stopped block once per group of 32 entries only
@@ -453,6 +482,24 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
     q0 = q0_n;
     slot_n = slot_nn;
   }
+}
+
+// The backward's task list: every pixel of the warp block (lanes with `own`)
+// whose fragment list holds all of its 1..fcap blended fragments, one
+// atomic per warp.
+__device__ __forceinline__ void list_pixel(const Batch* __restrict__ B, const ViewD& vw,
+                                           const WarpBlock& wb, int nb, int fcap, bool own) {
+  const bool want = own && wb.inimg && nb > 0 && nb <= fcap;
+  const unsigned m = __ballot_sync(FULL, want);
+  if (m == 0u) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  unsigned base = 0u;
+  if (lane == leader) base = atomicAdd(&B->ctr->px_n, (unsigned)__popc(m));
+  base = __shfl_sync(FULL, base, leader);
+  if (want)
+    B->px_list[base + __popc(m & ((1u << lane) - 1u))] =
+        make_uint2((unsigned)(vw.pix_base + (long long)wb.py * vw.W + wb.px),
+                   (unsigned)nb | ((unsigned)(&vw - B->vw) << 8));
 }
 
 // ---------------------------------------------------------------------------
@@ -472,12 +519,14 @@ __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__
   constexpr int SB = (TILE / 8) * (TILE / 4);
   __shared__ float4 st[NW][REC_Q + NRM][32];
   __shared__ int sidx[NW][32];
+  __shared__ unsigned sslot[NW][32];
   const int wid = threadIdx.x >> 5;
   Counters* c = B->ctr;
   const unsigned* __restrict__ vals = B->vals;
   const float4* __restrict__ rec = B->rec;
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip, eps = B->t_eps;
+  const int fcap = B->frag_cap;
   const int total = c->n_units * SB;
   for (int item = next_item(&c->work_fwd); item < total; item = next_item(&c->work_fwd)) {
     WarpBlock wb;
@@ -490,10 +539,12 @@ __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__
     const ViewD& vw = *vwp;
     if (!__any_sync(FULL, wb.inimg)) continue;
     const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
-    FwdState S = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, !wb.inimg};
+    FwdState S = {1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0, 0, !wb.inimg, 0, nullptr};
+    if (B->frag && wb.inimg)
+      S.fl = B->frag + (vw.pix_base + (long long)wb.py * vw.W + wb.px) * (long long)fcap;
     if (four) {
       fwd_walk<NRM, 4>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
-                       st[wid], sidx[wid], S);
+                       st[wid], sidx[wid], sslot[wid], fcap, S);
       // the pixel's sums over its four lanes
       S.C0 = pix_sum<4>(S.C0);
       S.C1 = pix_sum<4>(S.C1);
@@ -510,10 +561,12 @@ __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__
       // the tile's largest blended index: the backward skips the segments past it
       const unsigned ml = __reduce_max_sync(FULL, (unsigned)S.last);
       if ((threadIdx.x & 31) == 0 && ml > 0u) atomicMax(B->tile_last + wb.gt, (int)ml);
+      if (fcap > 0) list_pixel(B, vw, wb, S.nb, fcap, (threadIdx.x & 3) == 0);
     } else {
       fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
-                       st[wid], sidx[wid], S);
+                       st[wid], sidx[wid], sslot[wid], fcap, S);
       if (wb.inimg) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
+      if (fcap > 0) list_pixel(B, vw, wb, S.nb, fcap, true);
     }
   }
   queue_done(&c->work_fwd, &c->done_fwd);
@@ -731,9 +784,17 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
   const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
   const float cap = B->alpha_cap, skip = B->alpha_skip;
   const int total = c->n_units_b * SB;
-  for (int item = next_item(&c->work_bwd); item < total; item = next_item(&c->work_bwd)) {
+  const int fcap = B->frag_cap;
+  // with per-pixel fragment lists and no pixel past the cap, nothing is left
+  // for the list walk (its queue is not even taken)
+  const bool walk = fcap == 0 || *reinterpret_cast<const volatile unsigned*>(&c->ovf_any) != 0u;
+  for (int item = walk ? next_item(&c->work_bwd) : total; item < total;
+       item = next_item(&c->work_bwd)) {
     WarpBlock wb;
     const ViewD& vw = decode_item<TILE>(B, B->worklist_b, item, wb);
+    // with per-pixel fragment lists, only tiles holding a pixel past the cap
+    // are walked here (their other pixels are left to k_blend_bwd_px)
+    if (fcap > 0 && B->tile_ovf[wb.gt] == 0) continue;
     // a segment past every entry the tile's pixels blended has no work
     const int2 ts = B->tseg[wb.gt];
     if (ts.y > 1 && wb.seg * B->seg_len >= B->tile_last[wb.gt]) continue;
@@ -747,6 +808,7 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
     if (wb.inimg) {
       Tfin = B->pix_T[vw.pix_base + p];
       last = B->pix_last[vw.pix_base + p];
+      if (fcap > 0 && B->pix_nb[vw.pix_base + p] <= fcap) last = 0;   // a listed pixel
       gC0 = dimage[3 * vw.pix_base + p];
       gC1 = dimage[3 * vw.pix_base + HW + p];
       gC2 = dimage[3 * vw.pix_base + 2 * HW + p];
@@ -906,6 +968,204 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
   }
   zero_tail(B, zg, &c->zero_q);
   queue_done(&c->work_bwd, &c->done_bwd, &c->zero_q);
+}
+
+// ---------------------------------------------------------------------------
+// K7 from the per-pixel fragment lists.  Warps take the listed pixels (the
+// forward's task list) in grid stride, one pixel per warp at a time and one
+// lane per fragment, in chunks of 32 fragments from the pixel's last chunk
+// to its first.  Each lane recomputes its fragment from its record bit for
+// bit as the list walk does; the transmittance in front of each fragment is
+// the product of (1 - alpha') of the fragments before it (a product scan over
+// the lanes, times the product of the earlier chunks) and the suffix of
+// T_j alpha'_j w_j behind it a sum scan (plus the later chunks' sums).  The
+// record-field gradients leave as in the list walk, one set of vector
+// atomics per fragment.  Pixels past the cap are left to k_blend_bwd.
+// ---------------------------------------------------------------------------
+constexpr int PXW = 4;          // warps per block
+constexpr int PX_CHUNKS = 8;    // 32-fragment chunks of a pixel (frag_cap <= 255)
+
+// Fragment i of a pixel: its record slot, chord, opacity and alpha'.
+struct PxFrag {
+  unsigned sl;
+  float4 q5;
+  Chord ch;
+  Opacity o;
+  float a;
+};
+
+__device__ __forceinline__ void px_frag(const float4* __restrict__ rec, const unsigned* fl, int i,
+                                        bool pure, float cap, float fpx, float fpy, PxFrag& F) {
+  F.sl = fl[i];
+  const float4* r = rec + (size_t)F.sl * REC_Q;
+  const float4 q0 = __ldg(r), q1 = __ldg(r + 1), q2 = __ldg(r + 2), q3 = __ldg(r + 3);
+  const float4 q4 = __ldg(r + 4);
+  F.q5 = __ldg(r + 5);
+  F.ch = chord_eval(q0, q1, q2, q3, fpx, fpy);
+  F.o = opacity_eval(q4, F.ch);
+  F.a = pure ? F.o.alpha : fminf(F.o.alpha, cap);
+}
+
+// Product of x over the lanes below (exclusive; 1 at lane 0) and over all lanes.
+__device__ __forceinline__ float prod_excl(float x, float* all) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float y = __shfl_up_sync(FULL, x, d);
+    if (lane >= d) x = __fmul_rn(y, x);
+  }
+  *all = __shfl_sync(FULL, x, 31);
+  const float e = __shfl_up_sync(FULL, x, 1);
+  return lane == 0 ? 1.f : e;
+}
+
+// Sum of x over the lanes above (exclusive; 0 at lane 31) and over all lanes.
+__device__ __forceinline__ float sum_above(float x, float* all) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float y = __shfl_down_sync(FULL, x, d);
+    if (lane + d < 32) x += y;
+  }
+  *all = __shfl_sync(FULL, x, 0);
+  const float e = __shfl_down_sync(FULL, x, 1);
+  return lane == 31 ? 0.f : e;
+}
+
+template <int TILE, bool NRM>
+__global__ void __launch_bounds__(PXW * 32) k_blend_bwd_px(const Batch* __restrict__ B,
+                                                           const float* __restrict__ dimage,
+                                                           const float* __restrict__ dalpha,
+                                                           const float* __restrict__ ddepth,
+                                                           const float* __restrict__ dnormal,
+                                                           GradOut zg) {
+  pdl_wait();
+  pdl_launch_dependents();
+  Counters* c = B->ctr;
+  const int lane = threadIdx.x & 31;
+  const unsigned n = c->px_n;
+  const int fcap = B->frag_cap;
+  const float4* __restrict__ rec = B->rec;
+  float4* __restrict__ rgrad = B->rec_grad;
+  unsigned char* __restrict__ touched = B->rec_touched;
+  const bool pure = (B->flags & TTS_FLAG_PURE) != 0;
+  const float cap = B->alpha_cap;
+  const unsigned stride = gridDim.x * PXW;
+  unsigned t = blockIdx.x * PXW + (threadIdx.x >> 5);
+  uint2 task = (t < n) ? B->px_list[t] : make_uint2(0u, 0u);
+  for (; t < n; t += stride) {
+    const long long pg = task.x;
+    const int nb = (int)(task.y & 0xffu);
+    const ViewD& vw = B->vw[task.y >> 8];
+    if (t + stride < n) task = B->px_list[t + stride];   // the next task's entry, early
+    const long long p = pg - vw.pix_base;
+    const int py = (int)(p / vw.W), px = (int)(p - (long long)py * vw.W);
+    const float fpx = (float)px + 0.5f, fpy = (float)py + 0.5f;
+    const float4* __restrict__ nrm = surv_normals<NRM>(B, vw);
+    const long long HW = (long long)vw.W * vw.H;
+    const float Tfin = B->pix_T[pg];
+    const float gC0 = dimage[3 * vw.pix_base + p];
+    const float gC1 = dimage[3 * vw.pix_base + HW + p];
+    const float gC2 = dimage[3 * vw.pix_base + 2 * HW + p];
+    const float gO = dalpha ? dalpha[pg] : 0.f;
+    const float gD = ddepth ? ddepth[pg] : 0.f;
+    float gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
+    if (NRM && dnormal) {
+      gN0 = dnormal[3 * vw.pix_base + p];
+      gN1 = dnormal[3 * vw.pix_base + HW + p];
+      gN2 = dnormal[3 * vw.pix_base + 2 * HW + p];
+    }
+    const float gOT = gO * Tfin;
+    const unsigned* __restrict__ fl = B->frag + pg * (long long)fcap;
+    const int nch = (nb + 31) >> 5;
+    // the transmittance in front of each chunk (more than one chunk: a first
+    // pass over the earlier chunks' alpha')
+    float Tch[PX_CHUNKS];
+    Tch[0] = 1.f;
+#pragma unroll
+    for (int k = 1; k < PX_CHUNKS; ++k) {
+      Tch[k] = Tch[k - 1];
+      if (k < nch) {
+        const int i = 32 * (k - 1) + lane;
+        float om = 1.f;
+        if (i < nb) {
+          PxFrag F;
+          px_frag(rec, fl, i, pure, cap, fpx, fpy, F);
+          om = __fsub_rn(1.f, F.a);
+        }
+        float all;
+        prod_excl(om, &all);
+        Tch[k] = __fmul_rn(Tch[k - 1], all);
+      }
+    }
+    float Sc = 0.f;   // suffix of the later chunks
+#pragma unroll 1
+    for (int k = nch - 1; k >= 0; --k) {
+      float T0 = Tch[0];
+#pragma unroll
+      for (int q = 1; q < PX_CHUNKS; ++q)
+        if (q == k) T0 = Tch[q];
+      const int i = 32 * k + lane;
+      const bool on = i < nb;
+      PxFrag F;
+      float om = 1.f, wv = 0.f;
+      float4 nv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (on) {
+        px_frag(rec, fl, i, pure, cap, fpx, fpy, F);
+        om = __fsub_rn(1.f, F.a);
+        wv = gC0 * F.q5.y + gC1 * F.q5.z + gC2 * F.q5.w + gD * F.q5.x;
+        if constexpr (NRM) {
+          nv = __ldg(nrm + F.sl);
+          wv += gN0 * nv.x + gN1 * nv.y + gN2 * nv.z;
+        }
+      }
+      float pall, sall;
+      const float Ti = __fmul_rn(T0, prod_excl(om, &pall));
+      const float cterm = on ? Ti * F.a * wv : 0.f;
+      const float S = Sc + sum_above(cterm, &sall);
+      Sc += sall;
+      if (on) {
+        const float iom = rcp_approx(om);
+        const float dLda = Ti * wv - (S - gOT) * iom;
+        const float wgt = Ti * F.a;
+        const Chord& ch = F.ch;
+        const Opacity& o = F.o;
+        float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
+        float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f;
+        const bool clamped = !pure && (o.alpha > cap);
+        if (!clamped) {
+          const float dx = dLda * o.e1 * o.B;
+          const float dy = -dLda * o.alpha * (1.f - o.B);
+          const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
+          const float dpin = -dx * o.sGz * iin * iin;
+          const float dpout = (dx - dy) * o.sGz * iout * iout;
+          const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
+            gP[q] = dp;
+            gA[q] = dp * ch.dx;
+            gB[q] = dp * ch.dy;
+          }
+          gF = dy;
+          gK0 = dsGz;
+          gKx = (dy + dsGz) * ch.dx;
+          gKy = (dy + dsGz) * ch.dy;
+        }
+        touched[F.sl] = 1;
+        float4* dst = rgrad + (size_t)F.sl * REC_Q;
+        atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
+        atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
+        atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
+        atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
+        atomicAdd(dst + 5, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2));
+        if constexpr (NRM) atomicAdd(dst, make_float4(wgt * gN0, wgt * gN1, wgt * gN2, 0.f));
+      }
+    }
+  }
+  // the vertex-gradient arrays of the scatter that follows, cleared by the
+  // warps once their pixels are done (the list walk takes what is left)
+  zero_tail(B, zg, &c->zero_q);
 }
 
 // Backward with the resort window: replays the forward (same walk, same
@@ -1301,6 +1561,24 @@ void blend_grid(int tile, bool normals, int window, int warps, int sms, int* fwd
   c[1] = *bwd_blocks;
 }
 
+// Persistent grid of the pixel-list backward: as many blocks as fit at once.
+int px_grid(int tile, bool normals, int sms) {
+  static int cache[3][2] = {};
+  const int ti = (tile == 8) ? 0 : (tile == 16) ? 1 : 2, ni = normals ? 1 : 0;
+  if (cache[ti][ni] > 0) return cache[ti][ni];
+  int g = 0;
+  switch (tile * 2 + ni) {
+    case 16: g = occ_blocks(k_blend_bwd_px<8, false>, PXW * 32, sms); break;
+    case 17: g = occ_blocks(k_blend_bwd_px<8, true>, PXW * 32, sms); break;
+    case 32: g = occ_blocks(k_blend_bwd_px<16, false>, PXW * 32, sms); break;
+    case 33: g = occ_blocks(k_blend_bwd_px<16, true>, PXW * 32, sms); break;
+    case 64: g = occ_blocks(k_blend_bwd_px<32, false>, PXW * 32, sms); break;
+    default: g = occ_blocks(k_blend_bwd_px<32, true>, PXW * 32, sms); break;
+  }
+  cache[ti][ni] = g;
+  return g;
+}
+
 template <int TILE, bool NRM, int NW>
 static void fwd_nw(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                    float* normal, cudaStream_t st) {
@@ -1312,6 +1590,9 @@ template <int TILE, bool NRM>
 static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                  float* normal, cudaStream_t st) {
   const int g = P.blend_fwd_blocks;
+  // the backward's task list and overflow flag start empty for each forward
+  if (P.px_clear && cudaMemsetAsync(P.px_clear, 0, 2 * sizeof(unsigned), st) != cudaSuccess)
+    note_launch_error(cudaErrorInvalidValue);
   if (P.window > 0) {
     launch_k(k_blend_fwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, image, alpha, depth, normal);
     return 1;
@@ -1332,19 +1613,26 @@ static void bwd_nw(const HostPlan& P, const Batch* dB, const float* dimage, cons
 }
 
 template <int TILE, bool NRM>
-static void bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
-                  const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
+static int bwd_t(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
+                 const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
   const int g = P.blend_bwd_blocks;
+  int n = 1;
+  if (P.frag_cap > 0 && P.window == 0) {
+    launch_k(k_blend_bwd_px<TILE, NRM>, dim3(P.px_blocks), dim3(PXW * 32), 0, st, dB, dimage,
+             dalpha, ddepth, dnormal, zg);
+    n = 2;
+  }
   if (P.window > 0) {
     launch_k(k_blend_bwd_win<TILE, NRM>, dim3(g), dim3(WPB * 32), 0, st, dB, dimage, dalpha, ddepth,
              dnormal, zg);
-    return;
+    return n;
   }
   switch (warps_index(P.blend_warps)) {
     case 0: bwd_nw<TILE, NRM, 2>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
     case 2: bwd_nw<TILE, NRM, 8>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
     default: bwd_nw<TILE, NRM, 4>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
   }
+  return n;
 }
 
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
@@ -1366,14 +1654,13 @@ int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, co
   if (zero) zg = *zero;
   else zg.dV[0] = nullptr;
   switch (P.tile * 2 + (P.normals ? 1 : 0)) {
-    case 16: bwd_t<8, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
-    case 17: bwd_t<8, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
-    case 32: bwd_t<16, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
-    case 33: bwd_t<16, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
-    case 64: bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
-    default: bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st); break;
+    case 16: return bwd_t<8, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
+    case 17: return bwd_t<8, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
+    case 32: return bwd_t<16, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
+    case 33: return bwd_t<16, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
+    case 64: return bwd_t<32, false>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
+    default: return bwd_t<32, true>(P, dB, dimage, dalpha, ddepth, dnormal, zg, st);
   }
-  return 1;
 }
 
 int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st) {

@@ -21,6 +21,9 @@ struct HostPlan {
   int tet_bwd_blocks;
   int blend_fwd_blocks, blend_bwd_blocks;
   int blend_warps;          // warps per block of the main blend kernels (2, 4 or 8)
+  int frag_cap;             // per-pixel fragment list capacity (0: no lists)
+  unsigned* px_clear;       // device address of Counters::px_n and ::ovf_any (cleared per forward)
+  int px_blocks;            // grid of the pixel-list backward (grid stride over the listed pixels)
   long long total_pixels;
 };
 
@@ -63,6 +66,7 @@ int launch_fit_grid(const float* V_in, long long N, const float lo[3], const flo
                     const float* aabb, float pad, float* V_out, cudaStream_t st);
 int launch_blend_fwd(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                      float* normal, cudaStream_t st);
+int px_grid(int tile, bool normals, int sms);
 int launch_blend_bwd(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                      const float* ddepth, const float* dnormal, const GradOut* zero,
                      cudaStream_t st);

@@ -3,6 +3,8 @@
 // evaluation shared by the forward and backward blend kernels.
 #pragma once
 
+#include <cstddef>
+
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -20,6 +22,7 @@ constexpr int SCAN_THREADS = 1024;
 constexpr int TS_THREADS = 256;     // tile scan: threads per block
 constexpr int TS_ITEMS = 8;         // tiles per thread
 constexpr int TS_TILES = TS_THREADS * TS_ITEMS;
+constexpr int kFragCapDefault = 128;  // per-pixel fragment list capacity (tts_params.frag_cap 0)
 constexpr int TSORT_CLASSES = 6;    // depth-sort list lengths (0,256] (256,512] (512,1K] (1K,2K] (2K,4K] (4K,...)
 
 // Counters at the start of the workspace (after the descriptor).
@@ -43,7 +46,11 @@ struct Counters {
   unsigned int scan_ticket; // tile-scan blocks started
   unsigned int zero_q;      // gradient-clearing chunks taken by the backward
   unsigned long long scan_unset; // a look-back word no kernel writes (the scan-wait test hook)
+  unsigned int px_n;        // pixels in Batch::px_list (cleared before each forward)
+  unsigned int ovf_any;     // 1: a pixel has more blended fragments than frag_cap (cleared with px_n)
 };
+static_assert(offsetof(Counters, ovf_any) == offsetof(Counters, px_n) + 4,
+              "px_n and ovf_any are cleared together");
 
 struct SceneD {
   const float* V;
@@ -119,6 +126,13 @@ struct Batch {
   float4* pix_CD;           // [total_pixels] final (C0, C1, C2, D)
   float4* surv_n;           // [sum surv_cap] world unit normal per survivor (normals only)
   float4* pix_N;            // [total_pixels] final normal (normals with a backward)
+  int frag_cap;             // per-pixel fragment list capacity (0: no lists)
+  unsigned* frag;           // [frag_cap * total_pixels] slot of the i-th blended fragment of
+                            // pixel p at frag[i * total_pixels + p]
+  int* pix_nb;              // [total_pixels] blended fragments of the pixel (may exceed the cap)
+  int* tile_ovf;            // [total_tiles] 1: a pixel of the tile has more than frag_cap
+  uint2* px_list;           // [total_pixels] pixels with 1..frag_cap blended fragments:
+                            // (pixel, blended count | view << 8)
   SceneD sc[TTS_MAX_SCENES];
   ViewD vw[TTS_MAX_VIEWS];
   int scene_views[TTS_MAX_VIEWS];

@@ -41,6 +41,7 @@ class Params:
     blend_segment: int = 0      # list entries per backward work unit (0: library default)
     hull: bool = False          # tile test against the projected tet (fewer keys, same image)
     blend_warps: int = 0        # warps per block of the blend kernels (0: library default, 4)
+    frag_cap: int = 0           # per-pixel fragment lists for the backward (0: default 128, -1: none)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -57,6 +58,7 @@ class Params:
         p.resort_window = int(self.resort_window)
         p.blend_segment = int(self.blend_segment)
         p.blend_warps = int(self.blend_warps)
+        p.frag_cap = int(self.frag_cap)
         return p
 
 
@@ -414,6 +416,28 @@ class Rasterizer:
         n = 4 * self.total_pixels
         return (self._ws_slice(t.value, n, torch.float32), self._ws_slice(last.value, n, torch.int32),
                 self._ws_slice(nf.value, n, torch.int32))
+
+    def debug_frag_lists(self):
+        """Per-pixel fragment lists of the last forward: (lists (pixels, cap)
+        int32 record slots in blend order, blended count per pixel (int32),
+        per-tile overflow flags (int32), cap); None when the batch keeps no
+        lists."""
+        P = ctypes.c_void_p
+        fr, nb, ov = P(), P(), P()
+        cap = ctypes.c_int32(0)
+        b = self.batch()
+        check(self.lib.tts_debug_frag_lists(ctypes.byref(b), ctypes.byref(fr), ctypes.byref(nb),
+                                            ctypes.byref(ov), ctypes.byref(cap), _stream_ptr()),
+              "tts_debug_frag_lists")
+        if cap.value == 0:
+            return None
+        n, c = self.total_pixels, cap.value
+        tiles = sum(((int(cam.width) + self.params.tile - 1) // self.params.tile) *
+                    ((int(cam.height) + self.params.tile - 1) // self.params.tile)
+                    for cam, _ in self.views)
+        lists = self._ws_slice(fr.value, 4 * n * c, torch.int32).view(n, c)
+        return (lists, self._ws_slice(nb.value, 4 * n, torch.int32),
+                self._ws_slice(ov.value, 4 * tiles, torch.int32), c)
 
     def view_outputs(self, img, alpha, depth, normal=None):
         """Split flat outputs into per-view (3,H,W), (H,W), (H,W) tensors

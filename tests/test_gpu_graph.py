@@ -35,8 +35,12 @@ def test_graph_replay_matches_eager():
     got = list(out) + list(grads[0])
     for a, b in zip(ref[:3], got[:3]):
         assert torch.equal(a, b)
-    for a, b in zip(ref[3:], got[3:]):   # atomics: summation order may differ
-        assert torch.allclose(a, b, rtol=1e-5, atol=1e-6 * float(a.abs().max()))
+    # float atomics: the summation order differs from run to run.  Two eager
+    # steps differ by up to ~7e-7 of the largest entry where terms cancel
+    # (with or without the per-pixel fragment lists), so the floor is 1e-5 of
+    # it; a wrong replay would be off by O(1).
+    for a, b in zip(ref[3:], got[3:]):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-5 * float(a.abs().max()))
     # inputs updated in place are picked up by the next replay
     st.f.add_(0.01)
     g.replay()

@@ -332,6 +332,71 @@ def test_spheres128_full_gradients(spheres128):
     assert sum(v["band"] for v in rep["views"]) <= BAND_MAX * 4 * 512 * 512
 
 
+@pytest.mark.parametrize("s,tile,cap", [(175.0, 8, 4), (620.0, 16, 16), (20.0, 8, 8)])
+def test_fragment_lists_match_oracle(sphere16, s, tile, cap):
+    """The forward's per-pixel fragment lists, bit for bit: off the decision
+    band every pixel's blended count and the record slots of its first
+    frag_cap blended fragments (in blend order) equal the oracle's, and the
+    overflow flags mark exactly the tiles holding a pixel past the cap."""
+    cam = sphere16.cams[0]
+    p = Params(s=s, tile=tile, frag_cap=cap)
+    r = gpu_run([sphere16], [(cam, 0)], p)["raster"]
+    lists, nb, ov, c = r.debug_frag_lists()
+    assert c == cap
+    H, W = cam.height, cam.width
+    lists = lists.cpu().numpy().reshape(H, W, cap)
+    nb = nb.cpu().numpy().reshape(H, W)
+    ov = ov.cpu().numpy()
+    orc = oracle.render(sphere16.V, sphere16.T, sphere16.f, sphere16.rgb, cam, oracle_params(p),
+                        blend_cap=cap)
+    off = orc["amb"] == 0
+    assert (~off).sum() <= BAND_MAX * H * W
+    assert np.array_equal(nb[off], orc["nblend"][off])
+    k = np.minimum(nb, cap)
+    for q in range(cap):
+        sel = off & (k > q)
+        assert np.array_equal(lists[..., q][sel], orc["blend_slots"][..., q][sel]), q
+    tx = (W + tile - 1) // tile
+    over = np.zeros_like(ov)
+    jj, ii = np.nonzero(nb > cap)
+    np.maximum.at(over, (jj // tile) * tx + ii // tile, 1)
+    assert np.array_equal(ov, over)
+    if s < 600:
+        assert over.any()   # some pixels past the cap: the list walk takes their tiles
+
+
+@pytest.mark.parametrize("frag_cap,normals", [(1, False), (6, False), (-1, False), (3, True)])
+def test_fragment_list_caps(sphere16, frag_cap, normals):
+    """The backward from the forward's per-pixel fragment lists and its
+    list-walk fallback: with a cap of 1 almost every covered pixel is past
+    the cap and its tile is re-walked, with 3 or 6 the two paths share most
+    tiles (each pixel taken by exactly one), with -1 no lists are kept.
+    Per-element gradients against the oracle, split lists included
+    (segments of 64 entries), with the normal channel in one case."""
+    p = Params(s=60.0 if normals else 175.0, tile=8, frag_cap=frag_cap, blend_segment=64,
+               normals=normals)
+    cam = sphere16.cams[0]
+    up = _with_normal_upstream(14, 15, cam) if normals else synth.upstream_grads(4, [cam])[0]
+    check_gradients([sphere16], [(cam, 0)], p, [up], name=f"frag_cap {frag_cap} normals {normals}")
+
+
+def test_fragment_lists_match_list_walk(sphere16):
+    """Gradients from the per-pixel fragment lists equal those of the list
+    walk alone (-1) up to the order of the float atomics, on the benchmark's
+    tile size with split lists; images are identical."""
+    cam = sphere16.cams[0]
+    up = synth.upstream_grads(5, [cam])[0]
+    out = {}
+    for fc in (0, -1):
+        p = Params(s=175.0, tile=8, frag_cap=fc, blend_segment=64)
+        out[fc] = gpu_run([sphere16], [(cam, 0)], p, upstream=[up])
+    for a, b in zip(out[0]["views"][0][:3], out[-1]["views"][0][:3]):
+        assert np.array_equal(np.asarray(a), np.asarray(b))
+    for a, b in zip(out[0]["grads"][0], out[-1]["grads"][0]):
+        a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+        assert np.abs(a - b).max() <= 2e-4 * max(np.abs(b).max(), 1e-30)
+
+
 @pytest.mark.parametrize("warps", [2, 8])
 def test_blend_warps_per_block(sphere16, warps):
     """The blend kernels at 2 and 8 warps per block (the autotuner's other

@@ -506,3 +506,60 @@ def test_colour_gradient_is_independent_of_colours(sphere16):
     rgb2 = np.random.default_rng(12).uniform(size=s.rgb.shape).astype(np.float32)
     r2 = oracle.render(s.V, s.T, s.f, rgb2, s.cams[0], p, upstream=up)
     np.testing.assert_allclose(r2["drgb"], r["drgb"], rtol=1e-12, atol=1e-14)
+
+
+def _check_blend_lists(s, p, r, cap):
+    """Blended lists of every pixel: at most the hits, distinct slots whose
+    bbox rect covers the pixel, in the order of the tile's sorted list, -1
+    past the end."""
+    bins = r["bins"]
+    nb, sl = r["nblend"], r["blend_slots"]
+    assert np.all(nb <= r["nfrag"])
+    tx = bins["tiles_x"]
+    pos_in_list = {}
+    H, W = nb.shape
+    for j in range(H):
+        for i in range(W):
+            n = int(nb[j, i])
+            row = sl[j, i]
+            k = min(n, cap)
+            assert np.all(row[k:] == -1)
+            if k == 0:
+                continue
+            t = (j // p.tile) * tx + i // p.tile
+            a, b = bins["ranges"][t]
+            if t not in pos_in_list:
+                pos_in_list[t] = {int(v): q for q, v in enumerate(bins["key_val"][a:b])}
+            pos = [pos_in_list[t][int(x)] for x in row[:k]]
+            assert pos == sorted(pos) and len(set(pos)) == k
+            for x in row[:k]:
+                x0, x1, y0, y1 = (int(v) for v in bins["rect"][x])   # pixel bbox of the slot
+                assert x0 <= i <= x1 and y0 <= j <= y1
+
+
+def test_blend_lists_soft_surface(sphere16):
+    """sphere16 at s = 175: blended counts below the hits where the pixel
+    stops, and the recorded slots obey the list order (checked on the full
+    128x128 view)."""
+    s, p, up, r0 = sphere16
+    r = oracle.render(s.V, s.T, s.f, s.rgb, s.cams[0], p, blend_cap=8)
+    assert np.array_equal(r["image"], r0["image"])    # recording changes nothing
+    nb = r["nblend"]
+    assert nb.max() > 8 and (nb > 0).mean() > 0.1
+    assert np.any(nb < r["nfrag"])                      # some pixels stop early
+    _check_blend_lists(s, p, r, 8)
+
+
+def test_blend_lists_pure_mode_blend_every_hit():
+    """PURE mode (no stop, no skip) on a linear field that decreases along
+    every camera ray (f = 0.6 c.x, c the unit vector to the camera), so every
+    chord has f_prev > f_next and a positive alpha: every hit is blended and
+    the blended count equals the hit count."""
+    a, e = math.radians(-20.0), math.radians(15.0)
+    c = np.array([math.cos(e) * math.cos(a), math.cos(e) * math.sin(a), math.sin(e)])
+    V, T, f, rgb = small_grid(3, lambda X: 0.6 * X @ c)
+    cam = synth.orbit_camera(-20.0, 15.0, 40, 40)
+    p = oracle.make_params(s=6.0, tile=8, pure=True)
+    r = oracle.render(V, T, f, rgb, cam, p, blend_cap=64)
+    assert np.array_equal(r["nblend"], r["nfrag"]) and r["nblend"].max() > 2
+    _check_blend_lists(None, p, r, 64)
