@@ -279,7 +279,7 @@ __device__ __forceinline__ void composite(float v, int k, int base, bool pure, f
   }
   S.T = Tn;
   S.last = base + sidx[k] + 1;
-  if (S.fl) {
+  if (fcap > 0) {   // (a done pixel, or one outside the image, never gets here)
     if (S.nb < fcap) S.fl[S.nb] = sslot[k];
     ++S.nb;
   }
@@ -322,14 +322,12 @@ __device__ __forceinline__ void composite4(float v, int k, int base, bool pure, 
   const int f = sbits ? __ffs(sbits) - 1 : 4;     // the first stopping lane (4: none)
   const float Tl = __shfl_sync(FULL, Tn, g0 + max(f - 1, 0));
   // the pixel's blended fragments of this group, in list (lane) order
-  if (fcap > 0) {   // the same for the whole batch
+  if (fcap > 0) {   // the same for the whole batch; a done pixel never blends
     const bool blend = bl && sub < f && !S.done;
     const unsigned bm = (__ballot_sync(FULL, blend) >> g0) & 0xfu;
-    if (S.fl) {
-      const int at = S.nb + __popc(bm & ((1u << sub) - 1u));
-      if (blend && at < fcap) S.fl[at] = sslot[k];
-      S.nb += __popc(bm);
-    }
+    const int at = S.nb + __popc(bm & ((1u << sub) - 1u));
+    if (blend && at < fcap) S.fl[at] = sslot[k];
+    S.nb += __popc(bm);
   }
   if (S.done) return;
   S.nfrag += (v != 0.f) && sub <= f;
