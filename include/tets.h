@@ -135,12 +135,15 @@ typedef struct {
                              Changes the scheduling only, not the result. */
   int32_t frag_cap;       /* per-pixel fragment lists for the backward: 0 (library default,
                              128), 1..255, or -1 (none).  The forward records, per pixel, the
-                             record slots of up to frag_cap blended fragments (4 bytes each,
-                             frag_cap x pixels of workspace); the backward then walks each
-                             pixel's own fragments back to front, one lane per pixel, and
-                             re-walks the tile lists only for tiles holding a pixel with more
-                             blended fragments.  The same arithmetic per fragment either way.
-                             Unused with a resort window or TTS_FLAG_FORWARD_ONLY. */
+                             record slots of up to frag_cap blended fragments (4 bytes each:
+                             frag_cap x 4 + 12 bytes of workspace per pixel) and a task list of
+                             those pixels; the backward then takes each listed pixel with one
+                             warp, one lane per fragment (transmittance and suffix by scans
+                             over the lanes), and re-walks the tile lists only for tiles
+                             holding a pixel with more blended fragments.  The same
+                             arithmetic per fragment either way, up to rounding order.
+                             Unused with a resort window, TTS_FLAG_FORWARD_ONLY or a batch of
+                             2^32 pixels or more. */
 } tts_params;
 
 /* One scene: caller-owned device arrays (must outlive every call using them). */
