@@ -882,9 +882,9 @@ def cpu_configs(a, sc3):
 def run_single_views(a, dev):
     """The two single-view configurations on the GPU (16^3 sphere at 128^2,
     64^3 torus at 512^2): one view per call, pre-filter + forward + backward,
-    the tile picked by the autotuner.  Each step is timed alone with CUDA
-    events, after a write of 256 MB (more than L2) that evicts the previous
-    step's data."""
+    the tile picked by the autotuner, eager and as a replayed CUDA graph of
+    the step.  Each step is timed alone with CUDA events, after a write of
+    256 MB (more than L2) that evicts the previous step's data."""
     import torch
 
     import synth
@@ -906,18 +906,24 @@ def run_single_views(a, dev):
         g = [(torch.empty_like(st.V), torch.empty_like(st.f), torch.empty_like(st.rgb))]
         for _ in range(3):
             r.step(o, up, g)
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(a.steps)]
-        for e0, e1 in ev:
-            flush.fill_(1.0)
-            e0.record()
-            r.step(o, up, g)
-            e1.record()
-        torch.cuda.synchronize(dev)
-        ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+        def timed(run):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(a.steps)]
+            for e0, e1 in ev:
+                flush.fill_(1.0)
+                e0.record()
+                run()
+                e1.record()
+            torch.cuda.synchronize(dev)
+            return sum(e0.elapsed_time(e1) for e0, e1 in ev) / len(ev)
+
+        ms = timed(lambda: r.step(o, up, g))
+        graph = r.capture_step(o, up, g)
+        ms_g = timed(graph.replay)
         out[name] = {"value": r.total_pixels / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
-                     "steps": len(ev), "tile": tile, "l2": "flushed before every step"}
-        del r, o, g
+                     "graph_mpix_s": r.total_pixels / (ms_g / 1e3) / 1e6, "graph_ms_per_step": ms_g,
+                     "steps": a.steps, "tile": tile, "l2": "flushed before every step"}
+        del r, o, g, graph
     return out
 
 
