@@ -55,6 +55,8 @@ SLOT_BYTES = 4 + 4 + 16 + 96      # per (view, survivor) workspace bytes, forwar
 GRAD_SLOT_BYTES = 96               # extra per slot with a backward
 KEY_BYTES = 24                     # keys and values, double buffered
 PIXEL_BYTES = 12 + 20              # per-pixel state + outputs
+LIST_PIXEL_BYTES = 4 + 8           # per pixel with a backward: blended count, task entry
+DEFAULT_FRAG_CAP = 128             # tts_params.frag_cap 0
 MAX_TIMEOUTS = 2                   # device-wait timeouts a request may meet before it fails
 
 
@@ -207,6 +209,10 @@ class Server:
         key_cap = _bucket(int(keys) + 65536)
         nbytes = slots * (SLOT_BYTES + (GRAD_SLOT_BYTES if want_grad else 0)) + \
             key_cap * KEY_BYTES + px * PIXEL_BYTES
+        if want_grad and self.params.frag_cap >= 0 and self.params.resort_window == 0:
+            # the backward's per-pixel fragment lists
+            cap = self.params.frag_cap or DEFAULT_FRAG_CAP
+            nbytes += px * (4 * cap + LIST_PIXEL_BYTES)
         return scenes, views, surv_cap, key_cap, nbytes
 
     def _rasterizer(self, slot: _Slot, scenes, views, p, surv_cap, key_cap):
