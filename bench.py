@@ -47,7 +47,7 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "b3aab3611050d266": {8: {"blend_fwd": 141391488, "blend_bwd_px": 152256128}},
+    "45254eb1cccf26b1": {8: {"blend_fwd": 141434624, "blend_bwd_px": 152218496}},
 }
 
 
@@ -55,11 +55,11 @@ KERNEL_TRAFFIC = {
 # capture each on the one-view case of this workload (tile 8,
 # profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
 KERNEL_NCU_ONE_VIEW = {
-    "b3aab3611050d266": {8: {
-        "blend_fwd": {"issued_warps_per_scheduler": 0.49, "achieved_occupancy": 0.217,
-                      "warp_instructions": 52644712, "ms": 0.1333},
-        "blend_bwd_px": {"issued_warps_per_scheduler": 0.26, "achieved_occupancy": 0.412,
-                         "warp_instructions": 15214518, "ms": 0.0550}}},
+    "45254eb1cccf26b1": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.219,
+                      "warp_instructions": 51431589, "ms": 0.1345},
+        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.419,
+                         "warp_instructions": 15214518, "ms": 0.0580}}},
 }
 
 
