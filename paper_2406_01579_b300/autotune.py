@@ -124,7 +124,7 @@ def _store_cache(path, cache):
 
 
 def autotune(scenes, views, params: Params, tiles=(8, 16, 32), segments=(128, 256, 512),
-             warps=(2, 4, 8), frag_caps=(128, 32, -1), with_backward=True, reps: int = 5,
+             warps=(2, 4, 8), frag_caps=(128, 255, -1), with_backward=True, reps: int = 5,
              cache_path: str | None = DEFAULT_CACHE):
     """Coordinate search of (tile, blend_segment, blend_warps, frag_cap): the
     tile with the library defaults for the others, then the segment length at
