@@ -47,7 +47,7 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "45254eb1cccf26b1": {8: {"blend_fwd": 141434624, "blend_bwd_px": 152218496}},
+    "a180c63228461951": {8: {"blend_fwd": 141269760, "blend_bwd_px": 152213632}},
 }
 
 
@@ -55,11 +55,11 @@ KERNEL_TRAFFIC = {
 # capture each on the one-view case of this workload (tile 8,
 # profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
 KERNEL_NCU_ONE_VIEW = {
-    "45254eb1cccf26b1": {8: {
-        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.219,
-                      "warp_instructions": 51431589, "ms": 0.1345},
-        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.419,
-                         "warp_instructions": 15214518, "ms": 0.0580}}},
+    "a180c63228461951": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.218,
+                      "warp_instructions": 51431589, "ms": 0.1311},
+        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.401,
+                         "warp_instructions": 15214518, "ms": 0.0567}}},
 }
 
 
@@ -765,6 +765,29 @@ def extras(a, st, sc, params, ups, dev, barrier):
     out["coarse_to_fine_ms"] = timed(
         lambda: fit_grid(st.V, [-1.0] * 3, [1.0] * 3, rb.survivor_bounds()[0], 0.05, out=V2), 5)
     del rb
+    # walk statistics of one untimed step (TTS_FLAG_COUNT), with bbox rects and
+    # with the hull test: keys, list groups scanned, candidates staged (forward
+    # and list-walk backward), blended fragments of the pixel-list backward
+    walks = {}
+    for hull in (False, True):
+        pw = dataclasses.replace(params, hull=hull, count_walk=True)
+        rw = Rasterizer([st], [(c, 0) for c in sc.cams], pw, device=dev)
+        rw.forward()
+        rw.shrink_to_fit(1.15)
+        ow = rw._outputs()
+        uw = tuple(torch.from_numpy(np.concatenate([u[i].ravel() for u in ups])).to(dev)
+                   for i in range(3))
+        gw = [(torch.empty_like(st.V), torch.empty_like(st.f), torch.empty_like(st.rgb))]
+        rw.debug_walk_counts(reset=True)
+        rw.step(ow, uw, gw)
+        w = rw.debug_walk_counts(reset=True)
+        w["keys"] = int(rw.info().n_keys)
+        fl = rw.debug_frag_lists()
+        if fl is not None:
+            w["blended"] = int(fl[1].long().sum().item())
+        walks["hull" if hull else "bbox"] = w
+        del rw, ow, gw
+    out["walk_counts"] = walks
     return out
 
 

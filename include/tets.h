@@ -91,13 +91,16 @@ enum {
   TTS_FLAG_ACCUM_GRAD = 2,  /* backward adds into dV/df/drgb instead of overwriting */
   TTS_FLAG_FORWARD_ONLY = 4, /* workspace without backward state; backward calls fail */
   TTS_FLAG_NORMALS = 8,      /* also render the normal map: use the _ex calls */
-  TTS_FLAG_HULL = 16         /* tile test against the projected tet (Sec. 3.3 culling): a tile
+  TTS_FLAG_HULL = 16,        /* tile test against the projected tet (Sec. 3.3 culling): a tile
                                 of a tet's bbox rect gets no key when, for some edge of the
                                 convex hull of the four projected vertices, the corner pixel
                                 centres of (tile x bbox) all lie strictly outside it (the exact
                                 FP32 edge function fma(bu - au, pv - av, -((bv - av) * (pu - au)))
                                 of hull edge (a, b) at corner p; rects of 2 to 2 x 2 tiles are
                                 tested, others keep every tile) */
+  TTS_FLAG_COUNT = 32        /* the blend kernels also count their walk (list groups scanned,
+                                candidates staged, blocks walked): see
+                                tts_debug_walk_counts; the result is unchanged */
 };
 
 #define TTS_MAX_SCENES 64
@@ -322,6 +325,18 @@ int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last
  * not launch or synchronise. */
 int tts_debug_frag_lists(const tts_batch* b, const void** frag, const void** n_blend,
                          const void** tile_over, int32_t* frag_cap, tts_stream stream);
+
+/* Walk statistics of the blend kernels since the last tts_workspace_init or
+ * reset, accumulated by calls made with TTS_FLAG_COUNT (zero otherwise):
+ * counts[0] the forward's list groups of 32 entries scanned, counts[1] list
+ * entries it staged as candidates (their bbox meets a live pixel of the
+ * warp's pixel block), counts[2] its pixel blocks walked; counts[3] and
+ * counts[4] the groups and candidates of the list-walk backward (the
+ * pixel-list backward's fragments are the blended counts of
+ * tts_debug_frag_lists).  reset != 0 zeroes them after the copy.
+ * Synchronises the stream. */
+int tts_debug_walk_counts(const tts_batch* b, uint64_t counts[5], int32_t reset,
+                          tts_stream stream);
 
 /* Synchronises the stream and copies the status word and counters. */
 int tts_get_info(const tts_batch* b, tts_info* info, tts_stream stream);

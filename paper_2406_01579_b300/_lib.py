@@ -27,6 +27,7 @@ TTS_FLAG_ACCUM_GRAD = 2
 TTS_FLAG_FORWARD_ONLY = 4
 TTS_FLAG_NORMALS = 8
 TTS_FLAG_HULL = 16
+TTS_FLAG_COUNT = 32
 
 TTS_MAX_SCENES = 64
 TTS_MAX_VIEWS = 128
@@ -86,6 +87,7 @@ ENTRY_POINTS = ("tts_workspace_size", "tts_workspace_init", "tts_prepare_scene",
                 "tts_render_bwd", "tts_render_fwd_ex", "tts_render_bwd_ex", "tts_bin_views",
                 "tts_blend_fwd", "tts_blend_bwd", "tts_blend_fwd_ex", "tts_blend_bwd_ex",
                 "tts_scatter_bwd", "tts_launch_count", "tts_debug_pixels", "tts_debug_frag_lists",
+                "tts_debug_walk_counts",
                 "tts_get_info",
                 "tts_debug_lists", "tts_debug_records", "tts_sort_pairs_noalloc",
                 "tts_sort_pairs_scratch_size", "tts_sort_pairs",
@@ -136,6 +138,7 @@ def load():
     L.tts_debug_pixels.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P]
     L.tts_debug_frag_lists.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                        ctypes.POINTER(ctypes.c_int32), P]
+    L.tts_debug_walk_counts.argtypes = [B, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int32, P]
     L.tts_get_info.argtypes = [B, ctypes.POINTER(tts_info), P]
     L.tts_debug_lists.argtypes = [B, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
                                   ctypes.POINTER(P), ctypes.POINTER(ctypes.c_uint32),

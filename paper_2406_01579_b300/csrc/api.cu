@@ -119,7 +119,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
     return TTS_ERR_ARG;
   if (pr.frag_cap < -1 || pr.frag_cap > 255) return TTS_ERR_ARG;
   if (pr.flags & ~(TTS_FLAG_PURE | TTS_FLAG_ACCUM_GRAD | TTS_FLAG_FORWARD_ONLY | TTS_FLAG_NORMALS |
-                   TTS_FLAG_HULL))
+                   TTS_FLAG_HULL | TTS_FLAG_COUNT))
     return TTS_ERR_ARG;
   std::memset(&P->hb, 0, sizeof(Batch));
   Batch& B = P->hb;
@@ -334,6 +334,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.window = pr.resort_window;
   H.normals = normals;
   H.hull = (pr.flags & TTS_FLAG_HULL) != 0;
+  H.count = (pr.flags & TTS_FLAG_COUNT) != 0;
   H.normal_blocks = (int)std::min<long long>((max_surv + 255) / 256, 8LL * sm_count());
   H.tet_bwd_blocks = 2 * sm_count();
   H.blend_warps = pr.blend_warps > 0 ? pr.blend_warps : 4;
@@ -587,6 +588,20 @@ int tts_debug_pixels(const tts_batch* b, const void** T_final, const void** last
   if (last) *last = P.hb.pix_last;
   if (n_frag) *n_frag = P.hb.pix_nfrag;
   return TTS_OK;
+}
+
+int tts_debug_walk_counts(const tts_batch* b, uint64_t counts[5], int32_t reset,
+                          tts_stream stream) {
+  if (!counts) return TTS_ERR_ARG;
+  Plan P;
+  int rc = make_plan(b, &P, true);
+  if (rc != TTS_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned long long* w = P.hb.ctr->walk;
+  if (cudaMemcpyAsync(counts, w, 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TTS_ERR_CUDA;
+  if (reset && cudaMemsetAsync(w, 0, 5 * sizeof(uint64_t), st) != cudaSuccess) return TTS_ERR_CUDA;
+  return cudaStreamSynchronize(st) == cudaSuccess ? TTS_OK : TTS_ERR_CUDA;
 }
 
 int tts_debug_frag_lists(const tts_batch* b, const void** frag, const void** n_blend,

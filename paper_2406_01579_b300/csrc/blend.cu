@@ -390,7 +390,7 @@ __device__ __forceinline__ int pix_max_i(int x) {
 // counts list entries from lo.  When the list is split into segments for
 // the backward (ts.y > 1), the state at the end of each segment is stored as
 // the walk passes it.
-template <bool NRM, int LPP>
+template <bool NRM, int LPP, bool CNT>
 __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock wb,
                                          const unsigned* __restrict__ vals,
                                          const float4* __restrict__ rec,
@@ -403,6 +403,9 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
   const unsigned ltm = (1u << lane) - 1u;
   const int L = B->seg_len;
   const bool split = ts.y > 1;
+  // TTS_FLAG_COUNT (diagnostics, an instantiation of its own): one atomic per group
+  constexpr bool count = CNT;
+  if (count && lane == 0) atomicAdd(B->ctr->walk + 2, 1ull);
   // one group of lookahead on (slot, bbox)
   int idx = lo + lane;
   unsigned slot = (idx < hi) ? vals[idx] : 0u;
@@ -434,6 +437,10 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
     const unsigned slot_nn = (idn + 32 < hi) ? vals[idn + 32] : 0u;
     const bool ov = (g + lane < hi) && !wb.misses(q0);
     const unsigned m = __ballot_sync(FULL, ov);
+    if (count && lane == 0) {
+      atomicAdd(B->ctr->walk + 0, 1ull);
+      atomicAdd(B->ctr->walk + 1, (unsigned long long)__popc(m));
+    }
     if (m != 0u) {
       if (ov) {
         const int pos = __popc(m & ltm);
@@ -506,7 +513,7 @@ __device__ __forceinline__ void list_pixel(const Batch* __restrict__ B, const Vi
 // front to back (fwd_walk).  Units of the backward's later list segments
 // (segment index > 0) have no forward work.
 // ---------------------------------------------------------------------------
-template <int TILE, bool NRM, int NW>
+template <int TILE, bool NRM, int NW, bool CNT = false>
 __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__ B,
                                                       float* __restrict__ image,
                                                       float* __restrict__ alpha,
@@ -541,8 +548,8 @@ __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__
     if (B->frag && wb.inimg)
       S.fl = B->frag + (vw.pix_base + (long long)wb.py * vw.W + wb.px) * (long long)fcap;
     if (four) {
-      fwd_walk<NRM, 4>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
-                       st[wid], sidx[wid], sslot[wid], fcap, S);
+      fwd_walk<NRM, 4, CNT>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip,
+                            eps, st[wid], sidx[wid], sslot[wid], fcap, S);
       // the pixel's sums over its four lanes
       S.C0 = pix_sum<4>(S.C0);
       S.C1 = pix_sum<4>(S.C1);
@@ -561,8 +568,8 @@ __global__ void __launch_bounds__(NW * 32) k_blend_fwd(const Batch* __restrict__
       if ((threadIdx.x & 31) == 0 && ml > 0u) atomicMax(B->tile_last + wb.gt, (int)ml);
       if (fcap > 0) list_pixel(B, vw, wb, S.nb, fcap, (threadIdx.x & 3) == 0);
     } else {
-      fwd_walk<NRM, 1>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip, eps,
-                       st[wid], sidx[wid], sslot[wid], fcap, S);
+      fwd_walk<NRM, 1, CNT>(B, wb, vals, rec, nrm, rg.x, rg.y, ts, TILE * TILE, pure, cap, skip,
+                            eps, st[wid], sidx[wid], sslot[wid], fcap, S);
       if (wb.inimg) store_pixel<NRM>(B, vw, wb, S, image, alpha, depth, normal);
       if (fcap > 0) list_pixel(B, vw, wb, S.nb, fcap, true);
     }
@@ -759,7 +766,7 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_fwd_win(const Batch* __restr
 // (per contributing lane, one vector atomic per field group) into the
 // per-slot record gradient buffer.
 // ---------------------------------------------------------------------------
-template <int TILE, bool NRM, int NW>
+template <int TILE, bool NRM, int NW, bool CNT = false>
 __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__ B,
                                                       const float* __restrict__ dimage,
                                                       const float* __restrict__ dalpha,
@@ -783,6 +790,7 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
   const float cap = B->alpha_cap, skip = B->alpha_skip;
   const int total = c->n_units_b * SB;
   const int fcap = B->frag_cap;
+  constexpr bool count = CNT;   // TTS_FLAG_COUNT: an instantiation of its own
   // with per-pixel fragment lists and no pixel past the cap, nothing is left
   // for the list walk (its queue is not even taken)
   const bool walk = fcap == 0 || *reinterpret_cast<const volatile unsigned*>(&c->ovf_any) != 0u;
@@ -869,6 +877,10 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
       const bool live = wb.cull_to(last > g0 - rg.x);
       const bool ov = live && (idx < ge) && !wb.misses(q0);
       const unsigned m = __ballot_sync(FULL, ov);
+      if (count && lane == 0) {
+        atomicAdd(c->walk + 3, 1ull);
+        atomicAdd(c->walk + 4, (unsigned long long)__popc(m));
+      }
       if (m != 0u) {
       if (ov) {
         const int pos = __popc(m & ltm);
@@ -1580,8 +1592,12 @@ int px_grid(int tile, bool normals, int sms) {
 template <int TILE, bool NRM, int NW>
 static void fwd_nw(const HostPlan& P, const Batch* dB, float* image, float* alpha, float* depth,
                    float* normal, cudaStream_t st) {
-  launch_k(k_blend_fwd<TILE, NRM, NW>, dim3(P.blend_fwd_blocks), dim3(NW * 32), 0, st, dB, image,
-           alpha, depth, normal);
+  if (P.count)
+    launch_k(k_blend_fwd<TILE, NRM, NW, true>, dim3(P.blend_fwd_blocks), dim3(NW * 32), 0, st, dB,
+             image, alpha, depth, normal);
+  else
+    launch_k(k_blend_fwd<TILE, NRM, NW>, dim3(P.blend_fwd_blocks), dim3(NW * 32), 0, st, dB, image,
+             alpha, depth, normal);
 }
 
 template <int TILE, bool NRM>
@@ -1606,8 +1622,12 @@ static int fwd_t(const HostPlan& P, const Batch* dB, float* image, float* alpha,
 template <int TILE, bool NRM, int NW>
 static void bwd_nw(const HostPlan& P, const Batch* dB, const float* dimage, const float* dalpha,
                    const float* ddepth, const float* dnormal, const GradOut& zg, cudaStream_t st) {
-  launch_k(k_blend_bwd<TILE, NRM, NW>, dim3(P.blend_bwd_blocks), dim3(NW * 32), 0, st, dB, dimage,
-           dalpha, ddepth, dnormal, zg);
+  if (P.count)
+    launch_k(k_blend_bwd<TILE, NRM, NW, true>, dim3(P.blend_bwd_blocks), dim3(NW * 32), 0, st, dB,
+             dimage, dalpha, ddepth, dnormal, zg);
+  else
+    launch_k(k_blend_bwd<TILE, NRM, NW>, dim3(P.blend_bwd_blocks), dim3(NW * 32), 0, st, dB,
+             dimage, dalpha, ddepth, dnormal, zg);
 }
 
 template <int TILE, bool NRM>

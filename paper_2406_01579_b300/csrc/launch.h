@@ -22,6 +22,7 @@ struct HostPlan {
   int blend_fwd_blocks, blend_bwd_blocks;
   int blend_warps;          // warps per block of the main blend kernels (2, 4 or 8)
   int frag_cap;             // per-pixel fragment list capacity (0: no lists)
+  bool count;               // TTS_FLAG_COUNT: the counting instantiation of the forward
   unsigned* px_clear;       // device address of Counters::px_n and ::ovf_any (cleared per forward)
   int px_blocks;            // grid of the pixel-list backward (grid stride over the listed pixels)
   long long total_pixels;

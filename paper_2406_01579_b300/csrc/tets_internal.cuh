@@ -48,6 +48,7 @@ struct Counters {
   unsigned long long scan_unset; // a look-back word no kernel writes (the scan-wait test hook)
   unsigned int px_n;        // pixels in Batch::px_list (cleared before each forward)
   unsigned int ovf_any;     // 1: a pixel has more blended fragments than frag_cap (cleared with px_n)
+  unsigned long long walk[5];   // TTS_FLAG_COUNT: walk statistics (tts_debug_walk_counts)
 };
 static_assert(offsetof(Counters, ovf_any) == offsetof(Counters, px_n) + 4,
               "px_n and ovf_any are cleared together");

@@ -42,6 +42,7 @@ class Params:
     hull: bool = False          # tile test against the projected tet (fewer keys, same image)
     blend_warps: int = 0        # warps per block of the blend kernels (0: library default, 4)
     frag_cap: int = 0           # per-pixel fragment lists for the backward (0: default 128, -1: none)
+    count_walk: bool = False    # the blend kernels count their walk (debug_walk_counts)
 
     def to_c(self) -> _lib.tts_params:
         p = _lib.tts_params()
@@ -54,7 +55,8 @@ class Params:
         p.flags = ((TTS_FLAG_PURE if self.pure else 0) | (TTS_FLAG_ACCUM_GRAD if self.accum_grad else 0)
                    | (TTS_FLAG_FORWARD_ONLY if self.forward_only else 0)
                    | (TTS_FLAG_NORMALS if self.normals else 0)
-                   | (_lib.TTS_FLAG_HULL if self.hull else 0))
+                   | (_lib.TTS_FLAG_HULL if self.hull else 0)
+                   | (_lib.TTS_FLAG_COUNT if self.count_walk else 0))
         p.resort_window = int(self.resort_window)
         p.blend_segment = int(self.blend_segment)
         p.blend_warps = int(self.blend_warps)
@@ -416,6 +418,16 @@ class Rasterizer:
         n = 4 * self.total_pixels
         return (self._ws_slice(t.value, n, torch.float32), self._ws_slice(last.value, n, torch.int32),
                 self._ws_slice(nf.value, n, torch.int32))
+
+    def debug_walk_counts(self, reset: bool = True) -> dict:
+        """Walk statistics of the blend kernels accumulated by the calls made
+        with ``params.count_walk`` (see tts_debug_walk_counts)."""
+        c = (ctypes.c_uint64 * 5)()
+        b = self.batch()
+        check(self.lib.tts_debug_walk_counts(ctypes.byref(b), c, 1 if reset else 0, _stream_ptr()),
+              "tts_debug_walk_counts")
+        return dict(zip(("fwd_groups", "fwd_candidates", "fwd_blocks", "bwd_groups",
+                         "bwd_candidates"), (int(x) for x in c)))
 
     def debug_frag_lists(self):
         """Per-pixel fragment lists of the last forward: (lists (pixels, cap)
