@@ -185,6 +185,31 @@ __device__ __forceinline__ const ViewD& decode_item(const Batch* __restrict__ B,
   return vw;
 }
 
+// Record-field gradients of one fragment, added into its slot's six float4
+// (face major): row q < 4 holds face q's plane terms (dP, dA, dB) and, for
+// q < 3, component q of the normal gradient in .w; row 4 the opacity terms
+// (dF, dK0, dKx, dKy); row 5 depth and colour.  Only the chord's entry and
+// exit faces (kin in 0..2, kout in 1..3, never equal) have nonzero plane
+// terms, so a fragment takes four vector atomics; with normals, the
+// components that neither face row carried go as scalar atomics.
+template <bool NRM>
+__device__ __forceinline__ void add_frag_grad(float4* __restrict__ dst, int kin, int kout,
+                                              float dpin, float dpout, float cdx, float cdy,
+                                              float4 r4, float4 r5, float gn0, float gn1,
+                                              float gn2) {
+  const float win = NRM ? (kin == 0 ? gn0 : (kin == 1 ? gn1 : gn2)) : 0.f;
+  const float wout = NRM ? (kout == 1 ? gn1 : (kout == 2 ? gn2 : 0.f)) : 0.f;
+  atomicAdd(dst + kin, make_float4(dpin, dpin * cdx, dpin * cdy, win));
+  atomicAdd(dst + kout, make_float4(dpout, dpout * cdx, dpout * cdy, wout));
+  atomicAdd(dst + 4, r4);
+  atomicAdd(dst + 5, r5);
+  if constexpr (NRM) {
+    if (kin != 0) atomicAdd(&dst[0].w, gn0);
+    if (kin != 1 && kout != 1) atomicAdd(&dst[1].w, gn1);
+    if (kin != 2 && kout != 2) atomicAdd(&dst[2].w, gn2);
+  }
+}
+
 // Per-slot normals of a view's tile lists: the survivor normals of its scene
 // (slot - rec_base is the survivor index).
 template <bool NRM>
@@ -475,6 +500,11 @@ __device__ __forceinline__ void fwd_walk(const Batch* __restrict__ B, WarpBlock 
           // pixel's exchange); a miss codes 0
           const float code = fragment_code(st[4][k], ch, pure, cap, skip);
           const float mine = h ? code : 0.f;
+          // no lane blends: only the chord counts change
+          if (!__any_sync(FULL, (mine != 0.f) & (mine != FRAG_SKIP))) {
+            if (!S.done) S.nfrag += (mine != 0.f);
+            continue;
+          }
           composite4<NRM>(mine, k, base, pure, eps, st, sidx, sslot, fcap, S);
         }
         // with four lanes per pixel a group is short: the walk checks for an
@@ -907,8 +937,9 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
           a = pure ? o.alpha : fminf(o.alpha, cap);
           contrib = pure ? (a > 0.f) : (a >= skip);
         }
-        float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
-        float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
+        float dpin = 0.f, dpout = 0.f;
+        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
         float gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
         if (contrib) {
           const float4 q5 = st[wid][5][k];
@@ -937,20 +968,10 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
             const float dx = dLda * o.e1 * o.B;
             const float dy = -dLda * o.alpha * (1.f - o.B);
             const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
-            const float dpin = -dx * o.sGz * iin * iin;
-            const float dpout = (dx - dy) * o.sGz * iout * iout;
+            dpin = -dx * o.sGz * iin * iin;
+            dpout = (dx - dy) * o.sGz * iout * iout;
             const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
-              gP[q] = dp;
-              gA[q] = dp * ch.dx;
-              gB[q] = dp * ch.dy;
-            }
-            gF = dy;
-            gK0 = dsGz;
-            gKx = (dy + dsGz) * ch.dx;
-            gKy = (dy + dsGz) * ch.dy;
+            r4 = make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy);
           }
         }
         // each contributing lane adds its record-field gradients with vector
@@ -958,13 +979,8 @@ __global__ void __launch_bounds__(NW * 32) k_blend_bwd(const Batch* __restrict__
         if (contrib) {
           const unsigned sl = sslot[wid][k];
           touched[sl] = 1;   // the same byte from every contributing lane
-          float4* dst = rgrad + (size_t)sl * REC_Q;
-          atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-          atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-          atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-          atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-          atomicAdd(dst + 5, make_float4(gz, gc0, gc1, gc2));
-          if constexpr (NRM) atomicAdd(dst, make_float4(gn0, gn1, gn2, 0.f));
+          add_frag_grad<NRM>(rgrad + (size_t)sl * REC_Q, ch.kin, ch.kout, dpin, dpout, ch.dx,
+                             ch.dy, r4, make_float4(gz, gc0, gc1, gc2), gn0, gn1, gn2);
         }
       }
       __syncwarp();
@@ -1140,36 +1156,22 @@ __global__ void __launch_bounds__(PXW * 32) k_blend_bwd_px(const Batch* __restri
         const float wgt = Ti * F.a;
         const Chord& ch = F.ch;
         const Opacity& o = F.o;
-        float gP[4] = {0.f, 0.f, 0.f, 0.f}, gA[4] = {0.f, 0.f, 0.f, 0.f}, gB[4] = {0.f, 0.f, 0.f, 0.f};
-        float gF = 0.f, gK0 = 0.f, gKx = 0.f, gKy = 0.f;
+        float dpin = 0.f, dpout = 0.f;
+        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
         const bool clamped = !pure && (o.alpha > cap);
         if (!clamped) {
           const float dx = dLda * o.e1 * o.B;
           const float dy = -dLda * o.alpha * (1.f - o.B);
           const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
-          const float dpin = -dx * o.sGz * iin * iin;
-          const float dpout = (dx - dy) * o.sGz * iout * iout;
+          dpin = -dx * o.sGz * iin * iin;
+          dpout = (dx - dy) * o.sGz * iout * iout;
           const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
-            gP[q] = dp;
-            gA[q] = dp * ch.dx;
-            gB[q] = dp * ch.dy;
-          }
-          gF = dy;
-          gK0 = dsGz;
-          gKx = (dy + dsGz) * ch.dx;
-          gKy = (dy + dsGz) * ch.dy;
+          r4 = make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy);
         }
         touched[F.sl] = 1;
-        float4* dst = rgrad + (size_t)F.sl * REC_Q;
-        atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-        atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-        atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-        atomicAdd(dst + 4, make_float4(gF, gK0, gKx, gKy));
-        atomicAdd(dst + 5, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2));
-        if constexpr (NRM) atomicAdd(dst, make_float4(wgt * gN0, wgt * gN1, wgt * gN2, 0.f));
+        add_frag_grad<NRM>(rgrad + (size_t)F.sl * REC_Q, ch.kin, ch.kout, dpin, dpout, ch.dx, ch.dy,
+                           r4, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2), wgt * gN0,
+                           wgt * gN1, wgt * gN2);
       }
     }
   }
@@ -1261,31 +1263,22 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
       const float dLda = T * wv - (suffix - gOT) * rcp_approx(__fsub_rn(1.f, a));
       Pw += twa;
       const float wgt = T * a;
-      float4* dst = rgrad + (size_t)slot * REC_Q;
       B->rec_touched[slot] = 1;
       const bool clamped = !pure && (o.alpha > cap);
+      float dpin = 0.f, dpout = 0.f;
+      float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (!clamped) {
         const float dx = dLda * o.e1 * o.B;
         const float dy = -dLda * o.alpha * (1.f - o.B);
         const float iin = o.rho_out * o.r, iout = o.rho_in * o.r;
-        const float dpin = -dx * o.sGz * iin * iin;
-        const float dpout = (dx - dy) * o.sGz * iout * iout;
+        dpin = -dx * o.sGz * iin * iin;
+        dpout = (dx - dy) * o.sGz * iout * iout;
         const float dsGz = dx * (ch.p_out - ch.p_in) * o.r - dy * ch.p_out * iout;
-        float gP[4], gA[4], gB[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float dp = (q == ch.kin) ? dpin : ((q == ch.kout) ? dpout : 0.f);
-          gP[q] = dp;
-          gA[q] = dp * ch.dx;
-          gB[q] = dp * ch.dy;
-        }
-        atomicAdd(dst + 1, make_float4(gP[0], gP[1], gP[2], gP[3]));
-        atomicAdd(dst + 2, make_float4(gA[0], gA[1], gA[2], gA[3]));
-        atomicAdd(dst + 3, make_float4(gB[0], gB[1], gB[2], gB[3]));
-        atomicAdd(dst + 4, make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy));
+        r4 = make_float4(dy, dsGz, (dy + dsGz) * ch.dx, (dy + dsGz) * ch.dy);
       }
-      atomicAdd(dst + 5, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2));
-      if constexpr (NRM) atomicAdd(dst, make_float4(wgt * gN0, wgt * gN1, wgt * gN2, 0.f));
+      add_frag_grad<NRM>(rgrad + (size_t)slot * REC_Q, ch.kin, ch.kout, dpin, dpout, ch.dx, ch.dy,
+                         r4, make_float4(wgt * gD, wgt * gC0, wgt * gC1, wgt * gC2), wgt * gN0,
+                         wgt * gN1, wgt * gN2);
       T = Tn;
     };
     for (int g = rg.x; g < rg.y; g += 32) {
@@ -1385,9 +1378,14 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
       // the touched ones are read (and cleared, with their flag)
       if (!B->rec_touched[slot]) continue;
       B->rec_touched[slot] = 0;
+      // face-major rows: (dP, dA, dB, normal component) of faces 0..3, then
+      // the opacity row and the depth / colour row
       float4* gq = B->rec_grad + slot * REC_Q;
-      const float4 g0 = nrm ? gq[0] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 g1 = gq[1], g2 = gq[2], g3 = gq[3], g4 = gq[4], g5 = gq[5];
+      const float4 r0 = gq[0], r1 = gq[1], r2 = gq[2], r3 = gq[3], g4 = gq[4], g5 = gq[5];
+      const float4 g0 = make_float4(r0.w, r1.w, r2.w, 0.f);
+      const float4 g1 = make_float4(r0.x, r1.x, r2.x, r3.x);
+      const float4 g2 = make_float4(r0.y, r1.y, r2.y, r3.y);
+      const float4 g3 = make_float4(r0.z, r1.z, r2.z, r3.z);
       // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
       const float4 q0 = __ldg(B->rec + slot * REC_Q);
       const float mag = fabsf(g0.x) + fabsf(g0.y) + fabsf(g0.z) + fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
@@ -1396,8 +1394,7 @@ __global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B,
                         fabsf(g4.w) + fabsf(g5.x) + fabsf(g5.y) + fabsf(g5.z) + fabsf(g5.w);
       if (mag == 0.f) continue;
       const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (nrm) gq[0] = z4;
-      gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
+      gq[0] = z4; gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
       dnw = dnw + f3(g0.x, g0.y, g0.z);
       Geo G;
       tet_geometry_at(vw, in, (int)(fabsf(q0.x) - 0.5f), (int)(fabsf(q0.y) - 0.5f), G);
