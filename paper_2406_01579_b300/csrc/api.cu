@@ -327,7 +327,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.max_pf_chunks = max_pf;
   H.max_pp_chunks = max_pp;
   H.max_pre_chunks = (int)((max_surv + PRE_CHUNK - 1) / PRE_CHUNK);
-  H.tsort_blocks = std::max(1, std::min(tiles, 3 * sm_count()));
+  H.tsort_blocks = std::max(1, std::min(tiles, TSORT_BLOCKS_PER_SM * sm_count()));
   H.wl_blocks = wl_blocks;
   H.total_tiles = tiles;
   H.tile = pr.tile;

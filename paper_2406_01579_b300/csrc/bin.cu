@@ -719,19 +719,21 @@ __global__ void __launch_bounds__(PP_THREADS) k_place(const Batch* __restrict__ 
 // them sequentially).  Padding keys are all ones (no real key: the depth
 // bits of a kept slot are those of a finite positive float).
 //
-// One persistent kernel of 512-thread blocks sorts every list, longest
-// first: the tile scan lists the tiles by length class, and the blocks take
-// (1) lists of more than 2,048 keys, one per block (more than 4,096: sorted
-// runs of 4,096 merged in global memory), then lists of (2) 1,025..2,048
-// keys, one per half block, (3) 513..1,024, one per quarter block, (4)
-// 257..512, one per eighth of a block, and (5) up to 256 keys, one per warp,
-// each from its own device queue.  A group sorts its list padded to 8 keys
-// per thread, so the finer classes bound the padding by the list length.
+// One persistent kernel of 256-thread blocks (four per SM) sorts every
+// list, longest first: the tile scan lists the tiles by length class, and
+// the blocks take (1) lists of more than 2,048 keys, one per block (more
+// than 4,096: sorted runs of 4,096 merged in global memory), then lists of
+// (2) 1,025..2,048 keys, one per half block, (3) 513..1,024, one per
+// quarter block, (4) 257..512, one per warp, and (5) up to 256 keys, one per
+// warp at 8 keys per lane, each from its own device queue.  A group sorts
+// its list padded to 16 keys per thread (8 in (5)), so the finer classes
+// bound the padding by the list length; 16 keys per thread take one merge
+// round fewer and half the merge-path searches per key of 8.
 // ---------------------------------------------------------------------------
-constexpr int TSORT_NT = 512;
+constexpr int TSORT_NT = 256;
 
 // Barrier of a group of NT threads: the warp, the whole block, or the named
-// barrier bar of a half block (1, 2), a quarter (3..6) or an eighth (7..14).
+// barrier bar of a half block (1, 2) or a quarter (3..6).
 // Named barriers take immediate ids.
 template <int NT>
 __device__ __forceinline__ void group_sync(int bar) {
@@ -742,9 +744,7 @@ __device__ __forceinline__ void group_sync(int bar) {
   } else {
     switch (bar) {
 #define TSORT_BAR(i) case i: asm volatile("bar.sync " #i ", %0;" ::"n"(NT) : "memory"); break;
-      TSORT_BAR(1) TSORT_BAR(2) TSORT_BAR(3) TSORT_BAR(4) TSORT_BAR(5) TSORT_BAR(6) TSORT_BAR(7)
-      TSORT_BAR(8) TSORT_BAR(9) TSORT_BAR(10) TSORT_BAR(11) TSORT_BAR(12) TSORT_BAR(13)
-      TSORT_BAR(14)
+      TSORT_BAR(1) TSORT_BAR(2) TSORT_BAR(3) TSORT_BAR(4) TSORT_BAR(5) TSORT_BAR(6)
 #undef TSORT_BAR
       default: break;
     }
@@ -764,17 +764,34 @@ __host__ __device__ constexpr int spad_size() { return N + N / 16; }
 template <int NT, int K>
 __device__ __forceinline__ void group_merge_sort(unsigned long long (&k)[K], unsigned long long* s,
                                                  int tid, int bar) {
-  static_assert(K == 8, "the register network sorts 8 keys");
-  // Batcher's odd-even merge network for 8 keys (19 compare-exchanges)
+  static_assert(K == 8 || K == 16, "the register networks sort 8 or 16 keys");
+  // Batcher's odd-even merge network for 8 keys (19 compare-exchanges); for
+  // 16, two of them and Batcher's merge of the two sorted halves (25 more)
   constexpr int NET[19][2] = {{0, 1}, {2, 3}, {4, 5}, {6, 7}, {0, 2}, {1, 3}, {4, 6},
                               {5, 7}, {1, 2}, {5, 6}, {0, 4}, {1, 5}, {2, 6}, {3, 7},
                               {2, 4}, {3, 5}, {1, 2}, {3, 4}, {5, 6}};
+  constexpr int MERGE16[25][2] = {{0, 8}, {4, 12}, {4, 8}, {2, 10}, {6, 14}, {6, 10}, {2, 4},
+                                  {6, 8}, {10, 12}, {1, 9}, {5, 13}, {5, 9}, {3, 11}, {7, 15},
+                                  {7, 11}, {3, 5}, {7, 9}, {11, 13}, {1, 2}, {3, 4}, {5, 6},
+                                  {7, 8}, {9, 10}, {11, 12}, {13, 14}};
 #pragma unroll
-  for (int c = 0; c < 19; ++c) {
-    const unsigned long long x = k[NET[c][0]], y = k[NET[c][1]];
-    const bool sw = y < x;
-    k[NET[c][0]] = sw ? y : x;
-    k[NET[c][1]] = sw ? x : y;
+  for (int h = 0; h < K; h += 8) {
+#pragma unroll
+    for (int c = 0; c < 19; ++c) {
+      const unsigned long long x = k[h + NET[c][0]], y = k[h + NET[c][1]];
+      const bool sw = y < x;
+      k[h + NET[c][0]] = sw ? y : x;
+      k[h + NET[c][1]] = sw ? x : y;
+    }
+  }
+  if constexpr (K == 16) {
+#pragma unroll
+    for (int c = 0; c < 25; ++c) {
+      const unsigned long long x = k[MERGE16[c][0]], y = k[MERGE16[c][1]];
+      const bool sw = y < x;
+      k[MERGE16[c][0]] = sw ? y : x;
+      k[MERGE16[c][1]] = sw ? x : y;
+    }
   }
   for (int run = K; run < NT * K; run <<= 1) {
     // merges of runs within one warp's 32 K keys need only the warp's barrier
@@ -838,9 +855,10 @@ __device__ __forceinline__ void group_sort_list(const unsigned long long* in, in
   group_sync<NT>(bar);
 }
 
-constexpr int TSORT_K = 8;
+constexpr int TSORT_K = 16;
 constexpr int TSORT_BLOCK_CAP = TSORT_NT * TSORT_K;        // 4,096
-constexpr int TSORT_WARP_CAP = 32 * TSORT_K;               // 256
+constexpr int TSORT_WARP_CAP = 32 * TSORT_K;               // 512
+constexpr int TSORT_SMALL_K = 8;                           // lists of up to 256 keys
 
 // Merge of the sorted runs a[0, la) and b[0, lb) into o[0, la + lb) by all
 // threads of the block (merge path in global memory).
@@ -892,7 +910,7 @@ __device__ void sort_long_list(const Batch* __restrict__ B, int2 r, unsigned lon
 
 // Lists of one class, one per group of NT threads (group g of the block,
 // named barrier bar), from device queue q; s: the group's shared memory.
-template <int NT>
+template <int NT, int K = TSORT_K>
 __device__ __forceinline__ void sort_group_lists(const Batch* __restrict__ B, int cls, int q,
                                                  int g, int bar, unsigned long long* s,
                                                  int* s_item) {
@@ -908,11 +926,11 @@ __device__ __forceinline__ void sort_group_lists(const Batch* __restrict__ B, in
     group_sync<NT>(bar);
     if (it >= n) break;
     const int2 r = B->ranges[list[it]];
-    group_sort_list<NT, TSORT_K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, s, tid, bar);
+    group_sort_list<NT, K>(in + r.x, r.y - r.x, B->vals + r.x, nullptr, s, tid, bar);
   }
 }
 
-__global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restrict__ B) {
+__global__ void __launch_bounds__(TSORT_NT, TSORT_BLOCKS_PER_SM) k_tile_sort(const Batch* __restrict__ B) {
   pdl_wait();
   pdl_launch_dependents();
   __shared__ unsigned long long s[spad_size<TSORT_BLOCK_CAP>()];
@@ -940,15 +958,16 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
                                          threadIdx.x, 0);
     }
   }
-  // (2) .. (4): halves, quarters, eighths, each inside the shared memory of
+  // (2) .. (4): halves, quarters, warps, each inside the shared memory of
   // the group it came from
-  const int h = threadIdx.x >> 8, qd = threadIdx.x >> 7, e = threadIdx.x >> 6;
-  sort_group_lists<256>(B, 3, 1, h, 1 + h, s + h * spad_size<2048>(), s_item);
-  sort_group_lists<128>(B, 2, 2, 2 + qd, 3 + qd, s + qd * spad_size<1024>(), s_item);
-  sort_group_lists<64>(B, 1, 3, 6 + e, 7 + e, s + e * spad_size<512>(), s_item);
-  // (5) lists of up to 256 keys, a warp each, inside the warp's eighth
+  const int h = threadIdx.x >> 7, qd = threadIdx.x >> 6;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned long long* sw = s + w * spad_size<TSORT_WARP_CAP>();
+  sort_group_lists<128>(B, 3, 1, h, 1 + h, s + h * spad_size<2048>(), s_item);
+  sort_group_lists<64>(B, 2, 2, 2 + qd, 3 + qd, s + qd * spad_size<1024>(), s_item);
+  sort_group_lists<32>(B, 1, 3, 6 + w, 0, sw, s_item);
+  // (5) lists of up to 256 keys, a warp each (8 keys per lane), inside the
+  // warp's share
   for (;;) {
     int it = 0;
     if (lane == 0) it = atomicAdd(&c->sort_q[4], 1);
@@ -960,7 +979,7 @@ __global__ void __launch_bounds__(TSORT_NT, 3) k_tile_sort(const Batch* __restri
       if (lane == 0) B->vals[r.x] = (unsigned)in[r.x];
       continue;
     }
-    group_sort_list<32, TSORT_K>(in + r.x, n, B->vals + r.x, nullptr, sw, lane, 0);
+    group_sort_list<32, TSORT_SMALL_K>(in + r.x, n, B->vals + r.x, nullptr, sw, lane, 0);
   }
 }
 

@@ -23,6 +23,7 @@ constexpr int TS_THREADS = 256;     // tile scan: threads per block
 constexpr int TS_ITEMS = 8;         // tiles per thread
 constexpr int TS_TILES = TS_THREADS * TS_ITEMS;
 constexpr int kFragCapDefault = 128;  // per-pixel fragment list capacity (tts_params.frag_cap 0)
+constexpr int TSORT_BLOCKS_PER_SM = 4;   // resident blocks of the persistent depth sort
 constexpr int TSORT_CLASSES = 6;    // depth-sort list lengths (0,256] (256,512] (512,1K] (1K,2K] (2K,4K] (4K,...)
 
 // Counters at the start of the workspace (after the descriptor).
