@@ -47,7 +47,7 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "a180c63228461951": {8: {"blend_fwd": 141269760, "blend_bwd_px": 152213632}},
+    "67a3dd1ce75aea6b": {8: {"blend_fwd": 141314176, "blend_bwd_px": 151594368}},
 }
 
 
@@ -55,11 +55,11 @@ KERNEL_TRAFFIC = {
 # capture each on the one-view case of this workload (tile 8,
 # profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
 KERNEL_NCU_ONE_VIEW = {
-    "a180c63228461951": {8: {
-        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.218,
-                      "warp_instructions": 51431589, "ms": 0.1311},
-        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.401,
-                         "warp_instructions": 15214518, "ms": 0.0567}}},
+    "67a3dd1ce75aea6b": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.221,
+                      "warp_instructions": 47448529, "ms": 0.1213},
+        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.407,
+                         "warp_instructions": 14462974, "ms": 0.0529}}},
 }
 
 
