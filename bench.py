@@ -466,6 +466,53 @@ def run_ours(a, rank, world):
                       "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                       "overlap": "copies of neighbouring steps overlap compute (two buffer sets)"}
         r.set_scenes([st])
+
+        # the same with the scene resident (a training loop keeps the grid's
+        # parameters and their gradients on the device for its optimizer):
+        # every step copies its upstream gradients in from pinned host memory
+        # (two buffer sets, step i+1's copy under step i's compute) and reads
+        # back one scalar of its result (the sum of dL/df)
+        h2d = torch.cuda.Stream(device=dev)
+        hup = (hgi, hga, hgd)
+        ubufs = [tuple(torch.empty(x.shape, dtype=x.dtype, device=dev) for x in hup)
+                 for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        hsum = torch.empty(1, dtype=torch.float32).pin_memory()
+        out_r = r._outputs()
+
+        def resident_step(i):
+            b = i & 1
+            if i >= 2:
+                h2d.wait_event(ev_used[b])       # step i-2 has consumed buffer set b
+            with torch.cuda.stream(h2d):
+                for d, h in zip(ubufs[b], hup):
+                    d.copy_(h, non_blocking=True)
+                ev_in[b].record(h2d)
+            stream.wait_event(ev_in[b])
+            r.step(out_r, ubufs[b], grads)
+            ev_used[b].record(stream)
+            hsum.copy_(grads[0][1].sum().reshape(1), non_blocking=True)
+
+        h2d.wait_stream(stream)
+        for i in range(3):
+            resident_step(i)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        h2d.wait_stream(stream)
+        for i in range(a.steps):
+            resident_step(i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        tr = e0.elapsed_time(e1) / 1e3
+        res["e2e_resident"] = {
+            "value": job_mpix_s(pixels_per_step, a.steps, tr, dist, dev), "unit": UNIT,
+            "h2d_bytes_per_step": sum(x.numel() * 4 for x in hup), "d2h_bytes_per_step": 4,
+            "what": "scene parameters and gradients resident on the device; per step the "
+                    "upstream gradients from pinned host memory in, one scalar of the result "
+                    "(sum of dL/df) out"}
     # the quick serve (a small mix with the benchmark scene) when the full
     # serving summary does not run
     if not a.no_serve and rank == 0 and (a.no_workloads or world > 1):
@@ -1199,6 +1246,8 @@ def main():
         out["extras"] = res["extras"]
     if "e2e" in res:
         out["e2e"] = res["e2e"]
+    if "e2e_resident" in res:
+        out["e2e_resident"] = res["e2e_resident"]
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, res["sc"])
         out["cpu_baseline"]["configs"] = cpu_configs(a, res["sc"])
