@@ -1339,150 +1339,242 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
 }
 
 // ---------------------------------------------------------------------------
-// K8: record -> vertex adjoint.  One thread per survivor of a scene; loops
-// over the scene's views, recomputes the view's tet geometry, applies the
-// adjoint of the record fields (App. A.3's affine SDF and the face planes),
-// clears the record gradient slot, and scatters into dV, df, drgb.
+// K8: record -> vertex adjoint.  Only the (survivor, view) slots the blend
+// backward touched carry a gradient (a sixth of them on a typical step), so
+// the slots are compacted first: each warp takes 32 survivors at a time,
+// reads their touched flags (eight views at a time) and appends the touched
+// (survivor, view) pairs to a queue of its own in shared memory; every 32
+// queued pairs are then processed one per lane.  A lane recomputes the
+// view's tet geometry, applies the adjoint of the record fields (App. A.3's
+// affine SDF and the face planes) and clears the slot's gradient and flag.
+// A survivor's pairs sit in consecutive lanes; they are summed over those
+// lanes and the first of them scatters the sum into dV, df, drgb.
 // The reference point x_r (ray through the bbox corner pixel at the centroid
 // depth) is held constant: the fragment opacity does not depend on it.
-// With the normal map channel, the per-view dL/dn (record gradient q0.xyz)
-// is summed over the views and pushed once through the world-space
-// n = g / |g| of the tet's affine SDF.
+// With the normal map channel, the per-view dL/dn (record gradient .w of the
+// face rows) is summed over the survivor's lanes and pushed once through the
+// world-space n = g / |g| of the tet's affine SDF.
 // ---------------------------------------------------------------------------
+constexpr int TB_WARPS = 8;
+constexpr int TB_QUEUE = 512;   // ring of (survivor, view) pairs per warp (> 31 + 32 * 8)
+
 template <bool NRM>
-__global__ void __launch_bounds__(256, 2) k_tet_bwd(const Batch* __restrict__ B, GradOut go) {
+__global__ void __launch_bounds__(TB_WARPS * 32, 2) k_tet_bwd(const Batch* __restrict__ B,
+                                                              GradOut go) {
   pdl_wait();
   pdl_launch_dependents();
+  __shared__ int2 s_q[TB_WARPS][TB_QUEUE];
   const int s = blockIdx.y;
   const SceneD& S = B->sc[s];
   const int nsurv = B->ctr->n_surv[s];
+  const int nv = S.view_cnt;
   const float sv = B->s;
   float* __restrict__ gV = go.dV[s];
   float* __restrict__ gf = go.df[s];
   float* __restrict__ gc = go.drgb[s];
   constexpr bool nrm = NRM;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nsurv; k += gridDim.x * blockDim.x) {
-    const int4 t = B->surv_T[S.surv_off + k];
-    TetIn in;
-    load_tet_ids<false>(S, t, in);   // in flight while the first view's gradient loads
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int2* __restrict__ q = s_q[wid];
+  unsigned head = 0u, tail = 0u;   // warp-uniform ring positions
+
+  // one (survivor, view) pair per lane (k < 0: none), then the per-survivor
+  // sums and their scatter
+  auto process = [&](int2 pr) {
+    const int k = pr.x;
     float3 dv[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
     float dfv[4] = {0.f, 0.f, 0.f, 0.f};
     float3 dcol = f3(0, 0, 0);
     float3 dnw = f3(0, 0, 0);
     bool any = false;
-    for (int vi = 0; vi < S.view_cnt; ++vi) {
-      const int v = B->scene_views[S.view_off + vi];
-      const ViewD& vw = B->vw[v];
+    int4 t = make_int4(0, 0, 0, 0);
+    TetIn in;
+    if (k >= 0) {
+      t = B->surv_T[S.surv_off + k];
+      load_tet_ids<false>(S, t, in);
+      const ViewD& vw = B->vw[B->scene_views[S.view_off + pr.y]];
       const long long slot = vw.rec_base + k;
-      // a slot the blend backward never added to has a zero gradient: only
-      // the touched ones are read (and cleared, with their flag)
-      if (!B->rec_touched[slot]) continue;
       B->rec_touched[slot] = 0;
-      // face-major rows: (dP, dA, dB, normal component) of faces 0..3, then
-      // the opacity row and the depth / colour row
-      float4* gq = B->rec_grad + slot * REC_Q;
-      const float4 r0 = gq[0], r1 = gq[1], r2 = gq[2], r3 = gq[3], g4 = gq[4], g5 = gq[5];
-      const float4 g0 = make_float4(r0.w, r1.w, r2.w, 0.f);
-      const float4 g1 = make_float4(r0.x, r1.x, r2.x, r3.x);
-      const float4 g2 = make_float4(r0.y, r1.y, r2.y, r3.y);
-      const float4 g3 = make_float4(r0.z, r1.z, r2.z, r3.z);
-      // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
-      const float4 q0 = __ldg(B->rec + slot * REC_Q);
-      const float mag = fabsf(g0.x) + fabsf(g0.y) + fabsf(g0.z) + fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
-                        fabsf(g2.y) + fabsf(g2.z) + fabsf(g2.w) + fabsf(g3.x) + fabsf(g3.y) +
-                        fabsf(g3.z) + fabsf(g3.w) + fabsf(g4.x) + fabsf(g4.y) + fabsf(g4.z) +
-                        fabsf(g4.w) + fabsf(g5.x) + fabsf(g5.y) + fabsf(g5.z) + fabsf(g5.w);
-      if (mag == 0.f) continue;
-      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      gq[0] = z4; gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
-      dnw = dnw + f3(g0.x, g0.y, g0.z);
-      Geo G;
-      tet_geometry_at(vw, in, (int)(fabsf(q0.x) - 0.5f), (int)(fabsf(q0.y) - 0.5f), G);
-      if (!G.visible) continue;
-      any = true;
-      const float gPs[4] = {g1.x, g1.y, g1.z, g1.w};
-      const float gAs[4] = {g2.x, g2.y, g2.z, g2.w};
-      const float gBs[4] = {g3.x, g3.y, g3.z, g3.w};
-      float3 dX[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
-      float dff[4] = {0.f, 0.f, 0.f, 0.f};
-      // All of the geometry lives in the pixel-scaled frame xi = (fx x, fy y, z)
-      // where the record is P = m.x_r - 1, A = z_r m_x, B = z_r m_y with
-      // m = n / e, F = s f(x_r), K0 = s z_r g.d_r, Kx = s z_r g_x, Ky = s z_r g_y.
-      const float3 xr = G.zr * G.dr;
-#pragma unroll
-      for (int fk = 0; fk < 4; ++fk) {
-        const int sl = G.slot_of[fk];
-        const float gP = (sl == 0) ? gPs[0] : (sl == 1) ? gPs[1] : (sl == 2) ? gPs[2] : gPs[3];
-        const float gA = (sl == 0) ? gAs[0] : (sl == 1) ? gAs[1] : (sl == 2) ? gAs[2] : gAs[3];
-        const float gB = (sl == 0) ? gBs[0] : (sl == 1) ? gBs[1] : (sl == 2) ? gBs[2] : gBs[3];
-        const int i = kFaceVerts[fk][0], j = kFaceVerts[fk][1], l = kFaceVerts[fk][2];
-        const float3 dm = f3(gP * xr.x + gA * G.zr, gP * xr.y + gB * G.zr, gP * xr.z);
-        const float e = G.e[fk];
-        const float3 n = G.n[fk];
-        const float ie = rcp_approx(e);
-        const float lam = dot3(n, dm) * (ie * ie);
-        const float3 Xi = G.xm + G.y[i];
-        const float3 dn = ie * dm - lam * Xi;
-        dX[i] = dX[i] - lam * n;
-        const float3 dnr = G.sgn[fk] * dn;
-        const float3 ea = G.y[j] - G.y[i], eb = G.y[l] - G.y[i];
-        const float3 da = cross3(eb, dnr), db = cross3(dnr, ea);
-        dX[j] = dX[j] + da;
-        dX[l] = dX[l] + db;
-        dX[i] = dX[i] - (da + db);
-      }
-      const float dfr = sv * g4.x;
-      float3 dg = f3(sv * G.zr * (g4.y * G.dr.x + g4.z), sv * G.zr * (g4.y * G.dr.y + g4.w),
-                     sv * G.zr * g4.y);
-      dg = dg + dfr * G.w;     // f_r = f_m + g.(x_r - x_m)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        dff[q] += 0.25f * dfr;
-        dX[q] = dX[q] - (0.25f * dfr) * G.g;
-      }
-      // g = Y^-1 df with Y rows y_j - y_0 (j = 1..3)
-      const float idet = rcp_approx(G.det);
-      const float dd1 = dot3(G.cof[0], dg) * idet, dd2 = dot3(G.cof[1], dg) * idet,
-                  dd3 = dot3(G.cof[2], dg) * idet;
-      dff[1] += dd1; dff[2] += dd2; dff[3] += dd3;
-      dff[0] -= dd1 + dd2 + dd3;
-      dX[1] = dX[1] - dd1 * G.g;
-      dX[2] = dX[2] - dd2 * G.g;
-      dX[3] = dX[3] - dd3 * G.g;
-      dX[0] = dX[0] + (dd1 + dd2 + dd3) * G.g;
-      // depth term: zbar = mean camera z (unscaled axis)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dX[q].z += 0.25f * g5.x;
-      // xi = S (R v + t), S = diag(fx, fy, 1)  ->  dv = R^T S dxi
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        dv[q] = dv[q] + rotT(vw.R, f3(vw.fx * dX[q].x, vw.fy * dX[q].y, dX[q].z));
-        dfv[q] += dff[q];
-      }
-      dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
-    }
-    if (NRM && (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f)) {
-      TetGrad TG;
-      tet_grad(in.v, in.f, TG);
-      float ih, sg;
-      const float3 n = tet_unit_normal(TG, &ih, &sg);
-      if (ih > 0.f) {
-        tet_grad_adjoint(TG, tet_normal_adjoint(n, ih, sg, dnw), 0.f, dv, dfv);
+      do {
+        // face-major rows: (dP, dA, dB, normal component) of faces 0..3, then
+        // the opacity row and the depth / colour row
+        float4* gq = B->rec_grad + slot * REC_Q;
+        const float4 r0 = gq[0], r1 = gq[1], r2 = gq[2], r3 = gq[3], g4 = gq[4], g5 = gq[5];
+        const float4 g0 = make_float4(r0.w, r1.w, r2.w, 0.f);
+        const float4 g1 = make_float4(r0.x, r1.x, r2.x, r3.x);
+        const float4 g2 = make_float4(r0.y, r1.y, r2.y, r3.y);
+        const float4 g3 = make_float4(r0.z, r1.z, r2.z, r3.z);
+        // the forward's pixel bbox corner, from the record: q0 = (+-(i0 + .5), +-(j0 + .5), ...)
+        const float4 q0 = __ldg(B->rec + slot * REC_Q);
+        const float mag = fabsf(g0.x) + fabsf(g0.y) + fabsf(g0.z) + fabsf(g1.x) + fabsf(g1.y) + fabsf(g1.z) + fabsf(g1.w) + fabsf(g2.x) +
+                          fabsf(g2.y) + fabsf(g2.z) + fabsf(g2.w) + fabsf(g3.x) + fabsf(g3.y) +
+                          fabsf(g3.z) + fabsf(g3.w) + fabsf(g4.x) + fabsf(g4.y) + fabsf(g4.z) +
+                          fabsf(g4.w) + fabsf(g5.x) + fabsf(g5.y) + fabsf(g5.z) + fabsf(g5.w);
+        if (mag == 0.f) break;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        gq[0] = z4; gq[1] = z4; gq[2] = z4; gq[3] = z4; gq[4] = z4; gq[5] = z4;
+        dnw = dnw + f3(g0.x, g0.y, g0.z);
+        Geo G;
+        tet_geometry_at(vw, in, (int)(fabsf(q0.x) - 0.5f), (int)(fabsf(q0.y) - 0.5f), G);
+        if (!G.visible) break;
         any = true;
+        const float gPs[4] = {g1.x, g1.y, g1.z, g1.w};
+        const float gAs[4] = {g2.x, g2.y, g2.z, g2.w};
+        const float gBs[4] = {g3.x, g3.y, g3.z, g3.w};
+        float3 dX[4] = {f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0), f3(0, 0, 0)};
+        float dff[4] = {0.f, 0.f, 0.f, 0.f};
+        // All of the geometry lives in the pixel-scaled frame xi = (fx x, fy y, z)
+        // where the record is P = m.x_r - 1, A = z_r m_x, B = z_r m_y with
+        // m = n / e, F = s f(x_r), K0 = s z_r g.d_r, Kx = s z_r g_x, Ky = s z_r g_y.
+        const float3 xr = G.zr * G.dr;
+  #pragma unroll
+        for (int fk = 0; fk < 4; ++fk) {
+          const int sl = G.slot_of[fk];
+          const float gP = (sl == 0) ? gPs[0] : (sl == 1) ? gPs[1] : (sl == 2) ? gPs[2] : gPs[3];
+          const float gA = (sl == 0) ? gAs[0] : (sl == 1) ? gAs[1] : (sl == 2) ? gAs[2] : gAs[3];
+          const float gB = (sl == 0) ? gBs[0] : (sl == 1) ? gBs[1] : (sl == 2) ? gBs[2] : gBs[3];
+          const int i = kFaceVerts[fk][0], j = kFaceVerts[fk][1], l = kFaceVerts[fk][2];
+          const float3 dm = f3(gP * xr.x + gA * G.zr, gP * xr.y + gB * G.zr, gP * xr.z);
+          const float e = G.e[fk];
+          const float3 n = G.n[fk];
+          const float ie = rcp_approx(e);
+          const float lam = dot3(n, dm) * (ie * ie);
+          const float3 Xi = G.xm + G.y[i];
+          const float3 dn = ie * dm - lam * Xi;
+          dX[i] = dX[i] - lam * n;
+          const float3 dnr = G.sgn[fk] * dn;
+          const float3 ea = G.y[j] - G.y[i], eb = G.y[l] - G.y[i];
+          const float3 da = cross3(eb, dnr), db = cross3(dnr, ea);
+          dX[j] = dX[j] + da;
+          dX[l] = dX[l] + db;
+          dX[i] = dX[i] - (da + db);
+        }
+        const float dfr = sv * g4.x;
+        float3 dg = f3(sv * G.zr * (g4.y * G.dr.x + g4.z), sv * G.zr * (g4.y * G.dr.y + g4.w),
+                       sv * G.zr * g4.y);
+        dg = dg + dfr * G.w;     // f_r = f_m + g.(x_r - x_m)
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          dff[q] += 0.25f * dfr;
+          dX[q] = dX[q] - (0.25f * dfr) * G.g;
+        }
+        // g = Y^-1 df with Y rows y_j - y_0 (j = 1..3)
+        const float idet = rcp_approx(G.det);
+        const float dd1 = dot3(G.cof[0], dg) * idet, dd2 = dot3(G.cof[1], dg) * idet,
+                    dd3 = dot3(G.cof[2], dg) * idet;
+        dff[1] += dd1; dff[2] += dd2; dff[3] += dd3;
+        dff[0] -= dd1 + dd2 + dd3;
+        dX[1] = dX[1] - dd1 * G.g;
+        dX[2] = dX[2] - dd2 * G.g;
+        dX[3] = dX[3] - dd3 * G.g;
+        dX[0] = dX[0] + (dd1 + dd2 + dd3) * G.g;
+        // depth term: zbar = mean camera z (unscaled axis)
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) dX[q].z += 0.25f * g5.x;
+        // xi = S (R v + t), S = diag(fx, fy, 1)  ->  dv = R^T S dxi
+  #pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          dv[q] = dv[q] + rotT(vw.R, f3(vw.fx * dX[q].x, vw.fy * dX[q].y, dX[q].z));
+          dfv[q] += dff[q];
+        }
+        dcol = dcol + f3(0.25f * g5.y, 0.25f * g5.z, 0.25f * g5.w);
+      } while (0);
+    }
+    // sums over each run of lanes holding the same survivor and view group
+    // (one survivor's pairs of one group of eight views: at most 8 lanes)
+    const int kp = __shfl_up_sync(0xffffffffu, k, 1);
+    const int gp = __shfl_up_sync(0xffffffffu, pr.y >> 3, 1);
+    const bool run_head = lane == 0 || kp != k || gp != (pr.y >> 3);
+    const unsigned heads = __ballot_sync(0xffffffffu, run_head);
+    const int run = __popc(heads & (0xffffffffu >> (31 - lane)));   // run index of the lane
+    float acc[22] = {dv[0].x, dv[0].y, dv[0].z, dv[1].x, dv[1].y, dv[1].z, dv[2].x, dv[2].y,
+                     dv[2].z, dv[3].x, dv[3].y, dv[3].z, dfv[0], dfv[1], dfv[2], dfv[3],
+                     dcol.x, dcol.y, dcol.z, dnw.x, dnw.y, dnw.z};
+    int anyi = any ? 1 : 0;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+      const int rd = __shfl_down_sync(0xffffffffu, run, d);
+      const bool take = lane + d < 32 && rd == run;
+#pragma unroll
+      for (int j = 0; j < (NRM ? 22 : 19); ++j) {
+        const float y = __shfl_down_sync(0xffffffffu, acc[j], d);
+        if (take) acc[j] += y;
+      }
+      const int ya = __shfl_down_sync(0xffffffffu, anyi, d);
+      if (take) anyi |= ya;
+    }
+    if (!run_head || k < 0) return;
+#pragma unroll
+    for (int q4 = 0; q4 < 4; ++q4) {
+      dv[q4] = f3(acc[3 * q4], acc[3 * q4 + 1], acc[3 * q4 + 2]);
+      dfv[q4] = acc[12 + q4];
+    }
+    dcol = f3(acc[16], acc[17], acc[18]);
+    any = anyi != 0;
+    if (NRM) {
+      dnw = f3(acc[19], acc[20], acc[21]);
+      if (dnw.x != 0.f || dnw.y != 0.f || dnw.z != 0.f) {
+        TetGrad TG;
+        tet_grad(in.v, in.f, TG);
+        float ih, sg;
+        const float3 n = tet_unit_normal(TG, &ih, &sg);
+        if (ih > 0.f) {
+          tet_grad_adjoint(TG, tet_normal_adjoint(n, ih, sg, dnw), 0.f, dv, dfv);
+          any = true;
+        }
       }
     }
-    if (!any) continue;
+    if (!any) return;
     const int id[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      atomicAdd(gV + 3ll * id[q], dv[q].x);
-      atomicAdd(gV + 3ll * id[q] + 1, dv[q].y);
-      atomicAdd(gV + 3ll * id[q] + 2, dv[q].z);
-      atomicAdd(gf + id[q], dfv[q]);
-      atomicAdd(gc + 3ll * id[q], dcol.x);
-      atomicAdd(gc + 3ll * id[q] + 1, dcol.y);
-      atomicAdd(gc + 3ll * id[q] + 2, dcol.z);
+    for (int q4 = 0; q4 < 4; ++q4) {
+      atomicAdd(gV + 3ll * id[q4], dv[q4].x);
+      atomicAdd(gV + 3ll * id[q4] + 1, dv[q4].y);
+      atomicAdd(gV + 3ll * id[q4] + 2, dv[q4].z);
+      atomicAdd(gf + id[q4], dfv[q4]);
+      atomicAdd(gc + 3ll * id[q4], dcol.x);
+      atomicAdd(gc + 3ll * id[q4] + 1, dcol.y);
+      atomicAdd(gc + 3ll * id[q4] + 2, dcol.z);
     }
+  };
+
+  const int gw = blockIdx.x * TB_WARPS + wid, nw = gridDim.x * TB_WARPS;
+  for (int base = gw * 32; base < nsurv; base += nw * 32) {
+    const int k = base + lane;
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+      // the touched flags of eight views, loaded together
+      unsigned m = 0u;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (k < nsurv && v0 + j < nv)
+          m |= (unsigned)(B->rec_touched[B->vw[B->scene_views[S.view_off + v0 + j]].rec_base + k] != 0)
+               << j;
+      const int c = __popc(m);
+      int incl = c;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const unsigned tot = (unsigned)__shfl_sync(0xffffffffu, incl, 31);
+      unsigned p = tail + (unsigned)(incl - c);
+      while (m) {
+        const int j = __ffs(m) - 1;
+        m &= m - 1u;
+        q[p++ & (TB_QUEUE - 1)] = make_int2(k, v0 + j);
+      }
+      tail += tot;
+      __syncwarp();
+      while (tail - head >= 32u) {
+        const int2 pr = q[(head + lane) & (TB_QUEUE - 1)];
+        __syncwarp();
+        head += 32u;
+        process(pr);
+      }
+    }
+  }
+  if (tail != head) {   // the last, partial batch
+    const int2 pr = (head + lane < tail) ? q[(head + lane) & (TB_QUEUE - 1)] : make_int2(-1, 0);
+    process(pr);
   }
 }
 
