@@ -1244,6 +1244,18 @@ def main():
         out["workloads"] = workloads
     if "extras" in res:
         out["extras"] = res["extras"]
+        w = res["extras"].get("walk_counts", {}).get("hull" if a.hull else "bbox")
+        if w:
+            # the forward's per-entry reject tests: overhead, not algorithmic
+            # work (the roofline counts fragments); counts of one untimed
+            # TTS_FLAG_COUNT step over the timed forward's mean duration
+            fwd_s = st["blend_fwd"] / 1e3
+            out["reject_tests"] = {
+                "entries_tested": 32 * w["fwd_groups"], "candidates_staged": w["fwd_candidates"],
+                "blended": w.get("blended"), "entries_tested_per_s": 32 * w["fwd_groups"] / fwd_s,
+                "candidates_per_s": w["fwd_candidates"] / fwd_s,
+                "note": "bbox tests of list entries (groups of 32) and candidates the forward "
+                        "staged; their chord tests at the block's pixels are overhead"}
     if "e2e" in res:
         out["e2e"] = res["e2e"]
     if "e2e_resident" in res:
