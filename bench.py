@@ -47,7 +47,7 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "67a3dd1ce75aea6b": {8: {"blend_fwd": 141314176, "blend_bwd_px": 151594368}},
+    "b5ec4a00f5d989a2": {8: {"blend_fwd": 141554304, "blend_bwd_px": 151717504}},
 }
 
 
@@ -55,11 +55,11 @@ KERNEL_TRAFFIC = {
 # capture each on the one-view case of this workload (tile 8,
 # profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
 KERNEL_NCU_ONE_VIEW = {
-    "67a3dd1ce75aea6b": {8: {
-        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.221,
-                      "warp_instructions": 47448529, "ms": 0.1213},
-        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.407,
-                         "warp_instructions": 14462974, "ms": 0.0529}}},
+    "b5ec4a00f5d989a2": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.49, "achieved_occupancy": 0.224,
+                      "warp_instructions": 47448529, "ms": 0.1207},
+        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.396,
+                         "warp_instructions": 14462974, "ms": 0.0546}}},
 }
 
 
@@ -869,6 +869,7 @@ def quick_serve(a, big_scene, dev, n_requests=300, rate=200.0):
             on_result=lambda r: None)   # warm-up
     srv.run(poisson_requests(np.random.default_rng(3), 100, 4 * rate, len(scenes), pinned=True),
             on_result=lambda r: None)
+    srv.reserve()
     reqs = poisson_requests(np.random.default_rng(2), n_requests, rate, len(scenes), pinned=True)
     _, stats = srv.run(reqs, on_result=lambda r: None)
     stats.update({"rate_req_s": rate, "scenes": len(scenes),
@@ -1135,6 +1136,7 @@ def run_serve(a, emit=True, requests=None):
             on_result=lambda r: None)
     srv.run(poisson_requests(np.random.default_rng(3), 300, 4000.0, len(scenes), pinned=True),
             on_result=lambda r: None)
+    srv.reserve()
     out = []
     nreq = requests or a.serve_requests
     for rate in [float(x) for x in a.serve_rates.split(",")]:

@@ -305,6 +305,23 @@ class Server:
                                     len(b.reqs)))
         return "ok"
 
+    def reserve(self):
+        """Grows every slot's workspace and device buffer to the largest any
+        slot holds (e.g. after a warm-up run), so that no batch of a later run
+        allocates device memory: a large allocation in the middle of a run
+        stalls every batch in flight."""
+        torch.cuda.synchronize(self.device)
+        ws = max((sl.ws.numel() for sl in self.slots if sl.ws is not None), default=0)
+        nf = max((sl.dev.numel() for sl in self.slots if sl.dev is not None), default=0)
+        for sl in self.slots:
+            if ws and (sl.ws is None or sl.ws.numel() < ws):
+                sl.ws = None
+                sl.rasters.clear()
+                sl.last_layout = None
+                sl.ws = torch.empty(ws, dtype=torch.uint8, device=self.device)
+            if nf and (sl.dev is None or sl.dev.numel() < nf):
+                sl.dev = torch.empty(nf, dtype=torch.float32, device=self.device)
+
     # -- the loop --------------------------------------------------------------
     def run(self, requests: Sequence[Request], realtime: bool = True,
             on_result: Callable[[Result], None] | None = None):

@@ -136,3 +136,24 @@ def test_layout_reuse_matches_fresh_rasterizer(server):
     f1, _ = fresh.run([Request(1, 0, q1.camera, False, 0.0)])
     assert (r1[1].image - f1[1].image).abs().max().item() <= 1e-6
     assert (r0[0].alpha - r1[1].alpha).abs().max().item() > 0.0   # different cameras
+
+
+def test_reserve_sizes_every_slot_and_keeps_results(server):
+    """After reserve() every slot holds the largest workspace and buffer any
+    slot had, and a request served afterwards equals one served by a fresh
+    server."""
+    rng = np.random.default_rng(41)
+    reqs = [Request(i, i % len(server.scenes), on_sphere(rng, 128, 128), i % 2 == 0, 0.0,
+                    upstream=_upstream(rng, 128) if i % 2 == 0 else None) for i in range(6)]
+    server.run(reqs)
+    server.reserve()
+    ws = {sl.ws.numel() for sl in server.slots if sl.ws is not None}
+    nf = {sl.dev.numel() for sl in server.slots if sl.dev is not None}
+    assert len(ws) == 1 and len(nf) == 1 and len(server.slots) == 3
+    assert all(sl.ws is not None and sl.dev is not None for sl in server.slots)
+    q = Request(99, 1, on_sphere(rng, 160, 160), False, 0.0)
+    r, _ = server.run([q])
+    fresh = Server(server.scenes, Params(s=120.0, tile=16), hbm_budget=4e9, max_views=8,
+                   streams=1, ref_res=256)
+    f, _ = fresh.run([Request(99, 1, q.camera, False, 0.0)])
+    assert (r[99].image - f[99].image).abs().max().item() <= 1e-6
