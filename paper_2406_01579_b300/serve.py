@@ -38,6 +38,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import math
 import threading
 import time
@@ -327,7 +328,19 @@ class Server:
             on_result: Callable[[Result], None] | None = None):
         """Serves ``requests`` (arrival times in seconds from the start) and
         returns ({rid: Result}, stats).  With ``on_result``, each result is
-        handed to it as it completes instead of being kept in the dict."""
+        handed to it as it completes instead of being kept in the dict.
+        Python's cyclic garbage collector is paused while the loop runs (its
+        full collections over the run's request and result objects stall the
+        loop for tens of milliseconds); it is restored afterwards."""
+        paused = gc.isenabled()
+        gc.disable()
+        try:
+            return self._run(requests, realtime, on_result)
+        finally:
+            if paused:
+                gc.enable()
+
+    def _run(self, requests, realtime, on_result):
         pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
         ready = collections.deque()
         inflight: list[_Inflight] = []
