@@ -1372,7 +1372,6 @@ __global__ void __launch_bounds__(TB_WARPS * 32, 2) k_tet_bwd(const Batch* __res
   float* __restrict__ gV = go.dV[s];
   float* __restrict__ gf = go.df[s];
   float* __restrict__ gc = go.drgb[s];
-  constexpr bool nrm = NRM;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int2* __restrict__ q = s_q[wid];
   unsigned head = 0u, tail = 0u;   // warp-uniform ring positions
