@@ -340,6 +340,11 @@ def run_ours(a, rank, world):
         counts.update(blended=int(nbl.sum().item()),
                       listed_pixels=int(((nbl > 0) & (nbl <= fl[3])).sum().item()),
                       overflow_pixels=int((nbl > fl[3]).sum().item()), frag_cap=fl[3])
+        # (view, survivor) slots with a blended fragment: those the record ->
+        # vertex adjoint reads (exact when no pixel is past the cap)
+        lists = fl[0]
+        used = torch.arange(lists.shape[1], device=lists.device)[None, :] < nbl[:, None]
+        counts["touched_slots"] = int(torch.unique(lists[used]).numel())
     del fl
     res = {
         "kernel_ms": kt, "counts": counts,
@@ -660,10 +665,13 @@ def kernel_rooflines(kt, counts, peaks, hbm_gbs):
         "k_tile_sort": ("hbm", 12 * keys),
         "k_worklist_count": ("hbm", 24 * tiles),
         "k_worklist_place": ("hbm", 24 * tiles),
-        # K8: touched flags of all slots; for each visible slot its record
-        # gradient (80 B used) and bbox corner (16 B); the survivors' vertices
-        # read and their gradients written (28 B each way)
-        "k_tet_bwd": ("hbm", slots + 96 * vis + 56 * U),
+        # K8: touched flags of all slots; for each touched slot (a blended
+        # fragment's; every visible slot when that count is missing) its
+        # record gradient read and cleared (96 B each way), bbox corner and
+        # vertex ids (16 B each) and flag cleared; the survivors' vertices read
+        # and their gradients written (28 B each way)
+        "k_tet_bwd": ("hbm", slots + (96 + 96 + 16 + 16 + 1) * counts.get("touched_slots", vis)
+                      + 56 * U),
         "k_blend_fwd": ("alu", (frag * (FWD_FLOP_PER_FRAG - FWD_MUFU_PER_FRAG),
                                 frag * FWD_MUFU_PER_FRAG)),
         "k_blend_bwd": ("alu", (frag * (BWD_FLOP_PER_FRAG - BWD_MUFU_PER_FRAG),
