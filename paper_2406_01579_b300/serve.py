@@ -42,6 +42,7 @@ import gc
 import math
 import threading
 import time
+import weakref
 from typing import Any, Callable, Sequence
 
 import numpy as np
@@ -91,6 +92,46 @@ def _bucket(x: int, step: float = 1.25) -> int:
     if x <= 1024:
         return 1024
     return int(math.ceil(1024 * step ** math.ceil(math.log(x / 1024.0, step))))
+
+
+class _PinnedPool:
+    """Pinned host buffers for results, by size class (a power of two of
+    floats), reused once the tensors handed out on them are freed.  A fresh
+    pinned allocation costs a few hundred microseconds, which bounded the
+    loop at high request rates."""
+
+    def __init__(self):
+        self.free = collections.defaultdict(list)
+        self.out = collections.Counter()    # buffers handed out and not yet back
+        self.peak = collections.Counter()   # the most of them at once
+
+    @staticmethod
+    def _new(cls: int):
+        return torch.empty(cls, dtype=torch.float32, pin_memory=True).untyped_storage()
+
+    def _back(self, cls: int, store):
+        self.out[cls] -= 1
+        self.free[cls].append(store)
+
+    def get(self, n: int) -> torch.Tensor:
+        cls = 1 << max(16, (n - 1).bit_length())
+        pool = self.free[cls]
+        store = pool.pop() if pool else self._new(cls)
+        t = torch.empty(0, dtype=torch.float32).set_(store, 0, (n,), (1,))
+        self.out[cls] += 1
+        self.peak[cls] = max(self.peak[cls], self.out[cls])
+        # the storage goes back to the pool when the tensor (and every view of
+        # it) is gone: a result is freed only after its copy has completed
+        weakref.finalize(t, self._back, cls, store)
+        return t
+
+    def top_up(self, factor: float, cap: int):
+        """Allocates ahead, per size class used so far, up to factor x the
+        most buffers of it ever out at once (at most cap)."""
+        for cls, pk in list(self.peak.items()):
+            want = min(cap, int(math.ceil(factor * pk)))
+            while len(self.free[cls]) + self.out[cls] < want:
+                self.free[cls].append(self._new(cls))
 
 
 class _Slot:
@@ -145,6 +186,7 @@ class Server:
         self.max_views = int(max_views)
         self.max_layouts = int(max_layouts)
         self.slots = [_Slot(self.device) for _ in range(streams)]
+        self._pinned = _PinnedPool()
         self.surv = []
         self.key_scale = []     # per scene: c in keys ~ surv (1 + c res / tile)^2
         self.key_margin = []    # per scene: safety factor, doubled after an overflow
@@ -272,7 +314,7 @@ class Server:
             outs = []
             for q, off in zip(reqs, r.pix_off):
                 H, W = int(q.camera.height), int(q.camera.width)
-                h = torch.empty(5 * H * W, dtype=torch.float32, pin_memory=True)
+                h = self._pinned.get(5 * H * W)
                 h[:3 * H * W].copy_(dev[3 * off:3 * off + 3 * H * W], non_blocking=True)
                 h[3 * H * W:4 * H * W].copy_(dev[3 * P + off:3 * P + off + H * W], non_blocking=True)
                 h[4 * H * W:].copy_(dev[4 * P + off:4 * P + off + H * W], non_blocking=True)
@@ -310,7 +352,10 @@ class Server:
         """Grows every slot's workspace and device buffer to the largest any
         slot holds (e.g. after a warm-up run), so that no batch of a later run
         allocates device memory: a large allocation in the middle of a run
-        stalls every batch in flight."""
+        stalls every batch in flight.  The pinned result buffers are topped up
+        to twice the most of each size that the runs so far held at once (at
+        most one per view the slots can run together)."""
+        self._pinned.top_up(2.0, len(self.slots) * self.max_views)
         torch.cuda.synchronize(self.device)
         ws = max((sl.ws.numel() for sl in self.slots if sl.ws is not None), default=0)
         nf = max((sl.dev.numel() for sl in self.slots if sl.dev is not None), default=0)

@@ -157,3 +157,40 @@ def test_reserve_sizes_every_slot_and_keeps_results(server):
                    streams=1, ref_res=256)
     f, _ = fresh.run([Request(99, 1, q.camera, False, 0.0)])
     assert (r[99].image - f[99].image).abs().max().item() <= 1e-6
+
+
+def test_pinned_result_pool_reuses_freed_buffers():
+    """Result buffers are pinned, of the requested size, and their storage is
+    reused once every tensor on it is gone (not before)."""
+    from paper_2406_01579_b300.serve import _PinnedPool
+    pool = _PinnedPool()
+    a = pool.get(1000)
+    assert a.is_pinned() and a.numel() == 1000 and a.dtype == torch.float32
+    view = a[10:20].view(2, 5)
+    pa = a.data_ptr()
+    del a
+    b = pool.get(900)                 # the first buffer is still held by its view
+    assert b.data_ptr() != pa
+    del view
+    c = pool.get(800)                 # now free: the same storage again
+    assert c.data_ptr() == pa and c.numel() == 800 and c.is_pinned()
+    d = torch.arange(800, dtype=torch.float32, device="cuda")
+    c.copy_(d, non_blocking=True)
+    torch.cuda.synchronize()
+    assert torch.equal(c, d.cpu())
+    big = pool.get(1 << 20)
+    assert big.numel() == 1 << 20 and big.data_ptr() not in (pa, b.data_ptr())
+
+
+def test_pinned_pool_top_up_allocates_ahead():
+    from paper_2406_01579_b300.serve import _PinnedPool
+    pool = _PinnedPool()
+    held = [pool.get(3000) for _ in range(3)]          # three out at once
+    del held
+    pool.top_up(2.0, 100)
+    cls = 1 << 16
+    assert pool.out[cls] == 0 and len(pool.free[cls]) == 6
+    pool.top_up(2.0, 4)                                 # the cap never shrinks the pool
+    assert len(pool.free[cls]) == 6
+    ptrs = {pool.get(100).data_ptr() for _ in range(1)}
+    assert ptrs and all(p != 0 for p in ptrs)
