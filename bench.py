@@ -47,7 +47,7 @@ BWD_MUFU_PER_FRAG = 5
 # sha256 prefix of the kernel source they were taken on and the tile size: a
 # changed kernel reports no traffic until it is captured again.
 KERNEL_TRAFFIC = {
-    "9b18eaacd77da1ca": {8: {"blend_fwd": 141388160, "blend_bwd_px": 151551616}},
+    "d610ca1a9a522701": {8: {"blend_fwd": 141488128, "blend_bwd_px": 151716736}},
 }
 
 
@@ -55,11 +55,11 @@ KERNEL_TRAFFIC = {
 # capture each on the one-view case of this workload (tile 8,
 # profiles/blend_spheres128_4x512.md), keyed like KERNEL_TRAFFIC.
 KERNEL_NCU_ONE_VIEW = {
-    "9b18eaacd77da1ca": {8: {
-        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.221,
-                      "warp_instructions": 47448529, "ms": 0.1220},
-        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.415,
-                         "warp_instructions": 14462974, "ms": 0.0528}}},
+    "d610ca1a9a522701": {8: {
+        "blend_fwd": {"issued_warps_per_scheduler": 0.48, "achieved_occupancy": 0.220,
+                      "warp_instructions": 47448529, "ms": 0.1231},
+        "blend_bwd_px": {"issued_warps_per_scheduler": 0.27, "achieved_occupancy": 0.422,
+                         "warp_instructions": 14462974, "ms": 0.0536}}},
 }
 
 

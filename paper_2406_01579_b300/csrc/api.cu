@@ -336,7 +336,7 @@ int make_plan(const tts_batch* b, Plan* P, bool need_ws) {
   H.hull = (pr.flags & TTS_FLAG_HULL) != 0;
   H.count = (pr.flags & TTS_FLAG_COUNT) != 0;
   H.normal_blocks = (int)std::min<long long>((max_surv + 255) / 256, 8LL * sm_count());
-  H.tet_bwd_blocks = 2 * sm_count();
+  H.tet_bwd_blocks = 4 * sm_count();
   H.blend_warps = pr.blend_warps > 0 ? pr.blend_warps : 4;
   H.frag_cap = fcap;
   H.px_clear = (need_ws && fcap > 0) ? &B.ctr->px_n : nullptr;

@@ -1355,11 +1355,11 @@ __global__ void __launch_bounds__(WPB * 32) k_blend_bwd_win(const Batch* __restr
 // face rows) is summed over the survivor's lanes and pushed once through the
 // world-space n = g / |g| of the tet's affine SDF.
 // ---------------------------------------------------------------------------
-constexpr int TB_WARPS = 8;
+constexpr int TB_WARPS = 4;
 constexpr int TB_QUEUE = 512;   // ring of (survivor, view) pairs per warp (> 31 + 32 * 8)
 
 template <bool NRM>
-__global__ void __launch_bounds__(TB_WARPS * 32, 2) k_tet_bwd(const Batch* __restrict__ B,
+__global__ void __launch_bounds__(TB_WARPS * 32, 4) k_tet_bwd(const Batch* __restrict__ B,
                                                               GradOut go) {
   pdl_wait();
   pdl_launch_dependents();
@@ -1776,8 +1776,8 @@ int launch_zero_grads(const HostPlan& P, const Batch* dB, const GradOut& go, cud
 
 int launch_tet_bwd(const HostPlan& P, const Batch* dB, const GradOut& go, cudaStream_t st) {
   dim3 g(P.tet_bwd_blocks, P.n_scenes);
-  if (P.normals) launch_k(k_tet_bwd<true>, dim3(g), dim3(256), 0, st, dB, go);
-  else launch_k(k_tet_bwd<false>, dim3(g), dim3(256), 0, st, dB, go);
+  if (P.normals) launch_k(k_tet_bwd<true>, dim3(g), dim3(TB_WARPS * 32), 0, st, dB, go);
+  else launch_k(k_tet_bwd<false>, dim3(g), dim3(TB_WARPS * 32), 0, st, dB, go);
   return 1;
 }
 
